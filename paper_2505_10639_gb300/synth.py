@@ -1,0 +1,80 @@
+"""Seeded synthetic inputs for the MOMFBD hot path.
+
+This module only draws random numbers and shapes them into the statistical
+structure of the paper's workloads (solar granulation-like objects,
+Kolmogorov wavefront coefficients, detector noise). It contains none of the
+method's arithmetic (no pupil, PSF, OTF, Wiener filter or loss), so both the
+CUDA path and the FP64 oracle may use it as their common source of inputs.
+
+All draws use numpy's Philox4x32-10 counter-based generator, keyed by an
+integer seed and a stream tag, so every array is reproducible on any host.
+
+Input recipe (the paper's data are not available, Sec. 6):
+* object: positive Gaussian random field with a k^-3 power spectrum, mean 1
+  and rms contrast 10 %: white complex noise times |k|^(-3/2) (k != 0), real
+  part of the inverse DFT, rescaled to the target mean and contrast, clamped
+  at 1e-3;
+* wavefront coefficients: independent N(0, var_m (D/r0)^(5/3)) per mode, with
+  the per-mode Kolmogorov variances var_m supplied by the caller;
+* noise: white Gaussian, sigma = 1e-3 times the object mean, image domain.
+"""
+
+import numpy as np
+
+_STREAMS = {"object": 1, "coeff": 2, "noise": 3, "misc": 4}
+
+
+def rng(seed, stream="misc", sub=0):
+    """Philox generator for (seed, stream, sub) -- independent streams."""
+    key = (int(seed) & 0xFFFFFFFFFFFFFFFF)
+    ctr = [_STREAMS.get(stream, 0), int(sub), 0, 0]
+    return np.random.Generator(np.random.Philox(key=key, counter=ctr))
+
+
+def object_field(seed, shape, mean=1.0, contrast=0.1, slope=-3.0, sub=0):
+    """Real field(s) of shape [..., ny, nx] with power spectrum |k|^slope."""
+    g = rng(seed, "object", sub)
+    ny, nx = shape[-2:]
+    white = g.standard_normal(shape) + 1j * g.standard_normal(shape)
+    ky = np.fft.fftfreq(ny)[:, None]
+    kx = np.fft.fftfreq(nx)[None, :]
+    k = np.hypot(ky, kx)
+    amp = np.zeros_like(k)
+    amp[k > 0] = k[k > 0] ** (slope / 2.0)
+    field = np.fft.ifft2(white * amp).real
+    field -= field.mean(axis=(-2, -1), keepdims=True)
+    field /= field.std(axis=(-2, -1), keepdims=True)
+    field = mean * (1.0 + contrast * field)
+    return np.maximum(field, 1e-3 * mean)
+
+
+def patches_from_field(field, n_pix, stride):
+    """Cut [..., H, W] into overlapping [..., n_py * n_px, n_pix, n_pix]."""
+    h, w = field.shape[-2:]
+    ny = (h - n_pix) // stride + 1
+    nx = (w - n_pix) // stride + 1
+    out = []
+    for iy in range(ny):
+        for ix in range(nx):
+            out.append(field[..., iy * stride: iy * stride + n_pix,
+                             ix * stride: ix * stride + n_pix])
+    return np.stack(out, axis=-3)
+
+
+def kolmogorov_coeffs(seed, variances, d_over_r0, shape, sub=0):
+    """Coefficients [..., M] ~ N(0, variances * (D/r0)^(5/3)), rad at lambda_0.
+
+    ``variances`` are per-mode variances in units of (D/r0)^(5/3)."""
+    var = np.asarray(variances, np.float64)
+    g = rng(seed, "coeff", sub)
+    z = g.standard_normal(tuple(shape) + (var.size,))
+    return z * np.sqrt(var * d_over_r0 ** (5.0 / 3.0))
+
+
+def noise(seed, shape, sigma, sub=0):
+    """White Gaussian image-domain noise with standard deviation sigma."""
+    return rng(seed, "noise", sub).standard_normal(shape) * sigma
+
+
+def uniform(seed, shape, lo=0.0, hi=1.0, sub=0):
+    return rng(seed, "misc", sub).uniform(lo, hi, shape)
