@@ -1,0 +1,464 @@
+#!/usr/bin/env python
+"""Benchmark of the MOMFBD loss+gradient hot path on GB300.
+
+Workload (one "step" = one loss+gradient evaluation of the whole field):
+a 1024 x 1024 px field of view cut into 64 x 64 px patches at 50 % overlap
+(31 x 31 = 961 patches), 2 objects (6563 A with a 36 px pupil, 8542 A with a
+28 px pupil, sharing the wavefront), 12 frames, 44 KL modes, FP32 path,
+through ``mfbd_loss_grad``. Inputs are seeded and synthetic: a k^-3
+granulation-like object, Kolmogorov (D/r0 = 5) wavefronts, image-domain noise
+sigma = 1e-3, data D = F(o (*) s + n). The spectra (390 MB) are larger than
+the 129 MB L2, so no flush is needed between steps.
+
+Metric: loss+grad evaluations per second, counted in (patch x object x frame)
+units at 64 px. ``--gpus N`` runs N replicas (one per rank, each its own
+field): there is no data-path collective; the value is the units all ranks
+processed divided by the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead
+(a bounded sample of the same workload).
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SEED = 20250517  # 20250515 + workload index 2
+WORKLOAD = dict(workload="fov1024_64px_961patches_2obj_12frames_44kl", fov=1024, n_pix=64, stride=32,
+                n_patches=961, diams=[36.0, 28.0], wavelengths=[6563.0, 8542.0], n_frames=12,
+                n_modes=44, basis="kl", d_over_r0=5.0, noise_sigma=1e-3)
+FP32_LANES_PER_SM = 128
+METRIC = "loss+grad evals/s (patch*obj*frame units at 64px)"
+UNIT = "units/s"
+
+
+def gamma_of(w):
+    return 1e-3 * w["n_pix"] ** 2 * w["noise_sigma"] ** 2
+
+
+def units_of(w):
+    return w["n_patches"] * len(w["diams"]) * w["n_frames"]
+
+
+# ------------------------------------------------------------ distributed
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def aggregate(local_ms, local_units, world, reduce_max=None, reduce_sum=None):
+    """Whole-job figures: time = max over ranks, units = sum over ranks."""
+    ms = reduce_max(local_ms) if (world > 1 and reduce_max) else local_ms
+    units = reduce_sum(local_units) if (world > 1 and reduce_sum) else local_units
+    return ms, units, (units / (ms * 1e-3) if ms > 0 else 0.0)
+
+
+def torch_reducers():
+    import torch
+    import torch.distributed as dist
+
+    dev = torch.device("cuda") if torch.cuda.is_available() and dist.get_backend() == "nccl" else torch.device("cpu")
+
+    def rmax(v):
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def rsum(v):
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    return rmax, rsum
+
+
+# ------------------------------------------------------------ inputs
+
+def per_patch_draws(w, seed, p, variances):
+    from paper_2505_10639_gb300 import synth
+    a_true = synth.kolmogorov_coeffs(seed, variances, w["d_over_r0"], (w["n_frames"],), sub=2 * p)
+    delta = synth.kolmogorov_coeffs(seed, variances, w["d_over_r0"], (w["n_frames"],), sub=2 * p + 1)
+    return a_true, a_true + 0.3 * delta
+
+
+def object_patches(w, seed):
+    from paper_2505_10639_gb300 import synth
+    field = synth.object_field(seed, (len(w["diams"]), w["fov"], w["fov"]))
+    pat = synth.patches_from_field(field, w["n_pix"], w["stride"])  # [K, P, N, N]
+    return np.ascontiguousarray(np.swapaxes(pat, 0, 1))[: w["n_patches"]]
+
+
+def make_gpu_inputs(plan, w, seed):
+    """Synthetic spectra built on the GPU with the library's own OTF."""
+    import torch
+    from paper_2505_10639_gb300 import synth
+    from paper_2505_10639_gb300.mfbd import describe_object
+    _, _, var, _ = describe_object(0, w["n_pix"], w["diams"], w["wavelengths"], w["n_frames"],
+                                   w["n_modes"], basis=w["basis"])
+    P, K, J, N = w["n_patches"], len(w["diams"]), w["n_frames"], w["n_pix"]
+    a_true = np.zeros((P, J, w["n_modes"]), np.float32)
+    a_eval = np.zeros_like(a_true)
+    for p in range(P):
+        a_true[p], a_eval[p] = per_patch_draws(w, seed, p, var)
+    dev = plan.device
+    h = plan.otf(torch.from_numpy(a_true).to(dev))
+    obj = torch.from_numpy(object_patches(w, seed)).to(dev)
+    spec = torch.fft.rfft2(obj.to(torch.float64)).to(torch.complex64)[:, :, None] * h
+    del h
+    for p in range(P):
+        n = torch.from_numpy(synth.noise(seed, (K, J, N, N), w["noise_sigma"], sub=p)).to(dev)
+        spec[p] += torch.fft.rfft2(n).to(torch.complex64)
+    torch.cuda.synchronize()
+    return torch.from_numpy(a_eval).to(dev), spec.contiguous()
+
+
+# ------------------------------------------------------------ clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and not r[5 + i].startswith("Not")})
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows))
+        return out
+
+
+# ------------------------------------------------------------ roofline
+
+def fused_flops_per_unit(n_pix, npup):
+    """Algorithmic FP32 flops of the fused kernel per (patch, object, frame):
+    four 2-D transforms at 5 N^2 log2(N^2) (complex) or half that (real):
+    pupil->field (complex), PSF->OTF (real), adjoint OTF->PSF (real),
+    adjoint field->pupil (complex); plus the pointwise work: PSF 3 N^2,
+    frame reduction / loss / adjoint seed 32 per half-spectrum frequency,
+    g_q scaling N^2, G_p = g_q p 2 N^2, dL/dphi 4 per pupil pixel."""
+    n2 = n_pix * n_pix
+    c2 = 5.0 * n2 * math.log2(n2)
+    fft = 2 * c2 + 2 * (c2 / 2)
+    half = n_pix * (n_pix // 2 + 1)
+    pointwise = 3 * n2 + 32 * half + n2 + 2 * n2 + 4 * npup
+    return fft + pointwise
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def fp32_peak_tflops(n_sm, sm_mhz):
+    return n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------ CPU oracle leg
+
+def _oracle_worker(args):
+    """Generate this worker's patches (untimed), wait at the barrier, then
+    time the oracle's loss+object+gradient on them."""
+    (w, seed, patch_ids, barrier, queue) = args
+    from oracle import mfbd as omfbd
+    from oracle import optics
+    from paper_2505_10639_gb300 import synth
+    masks = [optics.pupil_mask(w["n_pix"], d) for d in w["diams"]]
+    bases, var = [], None
+    for d in w["diams"]:
+        b, v, _ = optics.kl_basis(w["n_pix"], d, w["n_modes"])
+        bases.append(b)
+        var = v
+    scales = [w["wavelengths"][0] / x for x in w["wavelengths"]]
+    setup = omfbd.Setup(masks, bases, scales, np.ones((len(w["diams"]), w["n_frames"])), gamma_of(w))
+    objs = object_patches(w, seed)
+    data = []
+    K, J, N = len(w["diams"]), w["n_frames"], w["n_pix"]
+    for p in patch_ids:
+        a_true, a_eval = per_patch_draws(w, seed, p, var)
+        noise = synth.noise(seed, (K, J, N, N), w["noise_sigma"], sub=p)
+        d = omfbd.synth_spectra(setup, a_true, objs[p], noise)
+        data.append((a_eval.astype(np.float32).astype(np.float64), d.astype(np.complex64).astype(np.complex128)))
+    barrier.wait()
+    t0 = time.time()
+    for a, d in data:
+        omfbd.loss_object_grad_patch(setup, a, d)
+    t1 = time.time()
+    queue.put((t0, t1, len(patch_ids)))
+
+
+def run_oracle_sample(w, seed, n_patches, cores):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    ids = list(range(n_patches))
+    chunks = [ids[i::cores] for i in range(cores)]
+    chunks = [c for c in chunks if c]
+    barrier = ctx.Barrier(len(chunks))
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=((w, seed, c, barrier, queue),)) for c in chunks]
+    for p in procs:
+        p.start()
+    res = [queue.get() for _ in procs]
+    for p in procs:
+        p.join()
+    t0 = min(r[0] for r in res)
+    t1 = max(r[1] for r in res)
+    n = sum(r[2] for r in res)
+    units = n * len(w["diams"]) * w["n_frames"]
+    return units / (t1 - t0), t1 - t0, n, len(chunks)
+
+
+def cpu_sample_size(cores):
+    # ~0.05 s of CPU per patch: about 15 s of CPU work in total
+    return max(16, min(961, 300))
+
+
+# ------------------------------------------------------------ GPU leg
+
+def run_gpu(args, rank, local_rank, world):
+    import torch
+    import torch.distributed as dist
+    from paper_2505_10639_gb300.mfbd import Plan
+
+    torch.cuda.set_device(local_rank)
+    w = WORKLOAD
+    seed = SEED + rank
+    plan = Plan(w["n_pix"], w["n_patches"], w["diams"], w["wavelengths"], w["n_frames"], w["n_modes"],
+                basis=w["basis"], gamma=gamma_of(w))
+    info = plan.info()
+    coeffs, spectra = make_gpu_inputs(plan, w, seed)
+    loss = torch.empty(w["n_patches"], dtype=torch.float64, device=plan.device)
+    grad = torch.empty(plan.coeff_shape(), dtype=torch.float32, device=plan.device)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.loss_grad(coeffs, spectra, loss=loss, grad=grad)
+    torch.cuda.synchronize()
+    if not np.isfinite(loss.cpu().numpy()).all():
+        raise RuntimeError("non-finite loss")
+
+    clocks = ClockSampler(local_rank)
+    plan.set_profiling(True, max_launches=8 * (args.steps + 2) * (2 * plan.n_objects + 1))
+    plan.read_profile(reset=True)
+    if world > 1:
+        dist.barrier()
+    clocks.start()
+    time.sleep(0.2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.loss_grad(coeffs, spectra, loss=loss, grad=grad)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    local_ms = e0.elapsed_time(e1) / args.steps
+    prof = plan.read_profile(reset=True)
+    plan.set_profiling(False)
+
+    rmax, rsum = (torch_reducers() if world > 1 else (None, None))
+    ms, units, value = aggregate(local_ms, units_of(w), world, rmax, rsum)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, w)
+    return finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk)
+
+
+def run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, w):
+    """Same metric through the public API with host buffers: every step
+    copies its inputs from pinned host memory and reads back loss and grad."""
+    import torch
+    import torch.distributed as dist
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    a_host = coeffs.cpu().pin_memory()
+    d_host = spectra.cpu().pin_memory()
+    l_host = torch.empty_like(loss, device="cpu").pin_memory()
+    g_host = torch.empty_like(grad, device="cpu").pin_memory()
+    a_dev = torch.empty_like(coeffs)
+    d_dev = torch.empty_like(spectra)
+
+    def e2e_step():
+        a_dev.copy_(a_host, non_blocking=True)
+        d_dev.copy_(d_host, non_blocking=True)
+        plan.loss_grad(a_dev, d_dev, loss=loss, grad=grad)
+        l_host.copy_(loss, non_blocking=True)
+        g_host.copy_(grad, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_local = e0.elapsed_time(e1) / args.steps
+    e2e_ms, _, e2e_value = aggregate(e2e_local, units_of(w), world, rmax, rsum)
+    h2d = coeffs.numel() * 4 + spectra.numel() * 8
+    d2h = loss.numel() * 8 + grad.numel() * 4
+    return {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
+    import torch
+    local_rank = dist_env()[1]
+    # roofline of the dominant (fused) kernel
+    npup = info["pupil_pixels"]
+    flops_launch = sum(fused_flops_per_unit(w["n_pix"], npup[k]) * w["n_patches"] * w["n_frames"]
+                       for k in range(len(npup)))
+    fused_ms, fused_n = prof["fused"]
+    fused_avg = fused_ms / max(1, fused_n)
+    achieved = flops_launch / (fused_avg * 1e-3) / 1e12
+    peaks = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak = fp32_peak_tflops(n_sm, sm_max)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["workload"], "patch_px": w["n_pix"], "patches": w["n_patches"],
+                   "objects": len(w["diams"]), "frames": w["n_frames"], "modes": w["n_modes"],
+                   "basis": w["basis"], "pupil_px": w["diams"], "precision": "fp32",
+                   "units_per_step": units_of(w),
+                   "l2": "inputs larger than L2 (%.0f MB spectra)" % (units_of(w) * 64 * 33 * 8 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": e2e,
+        "roofline": {"bound": "alu", "kernel": "mfbd_fused_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_basis": "FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock)"
+                                   % (n_sm, FP32_LANES_PER_SM, sm_max),
+                     "flops_per_launch": flops_launch, "kernel_ms": fused_avg},
+        "kernels_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in prof.items()},
+        "gpu_launches": int(sum(v[1] for v in prof.values())),
+        "clocks": clk,
+        "plan": info,
+    }
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-patches", type=int, default=0)
+    ap.add_argument("--patches", type=int, default=0,
+                    help="use only the first N patches of the field (smaller profiling cases)")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.patches:
+        WORKLOAD["n_patches"] = args.patches
+        WORKLOAD["workload"] += "_first%d" % args.patches
+    args.warmup = max(3, args.warmup)
+    rank, local_rank, world = dist_env()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        cores = os.cpu_count() or 1
+        n = args.cpu_patches or cpu_sample_size(cores)
+        total_t, total_u, rates = 0.0, 0, []
+        for _ in range(args.warmup):
+            pass  # the oracle has no warm state; warm-up steps are not needed
+        for _ in range(args.steps):
+            rate, t, npat, used = run_oracle_sample(WORKLOAD, SEED, n, cores)
+            rates.append(rate)
+            total_t += t
+            total_u += npat * len(WORKLOAD["diams"]) * WORKLOAD["n_frames"]
+        value = total_u / total_t
+        sample = "%d of %d patches (all %d objects x %d frames) per step" % (
+            n, WORKLOAD["n_patches"], len(WORKLOAD["diams"]), WORKLOAD["n_frames"])
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD["workload"], "patch_px": 64, "precision": "fp64 oracle"},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    line = run_gpu(args, rank, local_rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            cores = os.cpu_count() or 1
+            n = args.cpu_patches or cpu_sample_size(cores)
+            rate, t, npat, used = run_oracle_sample(WORKLOAD, SEED, n, cores)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+                                    "sample": "%d of %d patches (2 objects x 12 frames each), %.1f s wall"
+                                              % (npat, WORKLOAD["n_patches"], t)}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,171 @@
+/*
+ * mfbd.h -- C ABI of the GB300 (sm_103a) MOMFBD hot path.
+ *
+ * Method: Asensio Ramos et al., "torchmfbd: a flexible multi-object
+ * multi-frame blind deconvolution code" (arXiv:2505.10639).
+ *   Sec. 3.1, Eq. 22  wavefront  phi_kj = c_k sum_m a_jm B_km, c_k = lambda_0/lambda_k
+ *   Sec. 3.1, Eq. 20  pupil      P_kj   = A_k exp(i phi_kj)
+ *   Sec. 3.1, Eq. 21  PSF        s_kj   = |F P_kj|^2 / sum |F P_kj|^2   (forward FFT)
+ *                     OTF        H_kj   = F s_kj
+ *   Sec. 2.2.1, Eq. 11  Wiener object  O_k = sum_j w D conj(H) / (sum_j w |H|^2 + gamma)
+ *   Sec. 2.2.1, Eq. 12  loss  L_p = sum_k sum_u [ sum_j w |D|^2
+ *                                    - |sum_j w D conj(H)|^2 / (sum_j w |H|^2 + gamma) ]
+ *   and dL/da by the adjoint of Eqs. 20-22 and 12.
+ * Index names: p patch, k object, j frame (diversity channels folded in,
+ * Sec. 2.1), m mode, u frequency.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named "dev" are device memory owned by the caller; they must stay
+ *   valid until the stream reaches the call. Pointers named "host" are read
+ *   during the call only.
+ * - Every compute call is asynchronous on the given stream (a cudaStream_t
+ *   passed as void*; NULL means the legacy default stream) and never
+ *   synchronises, allocates or frees after mfbd_plan_create.
+ * - Every function returns an mfbd_status. Errors are returned, never thrown.
+ *   A failed launch or CUDA error returns MFBD_ERR_CUDA and marks the plan
+ *   failed: later compute calls on it return MFBD_ERR_STATE.
+ * - There is no CPU fallback: without a usable CUDA device the compute calls
+ *   return MFBD_ERR_UNSUPPORTED (or MFBD_ERR_CUDA) and compute nothing.
+ * - Grids: the patch size N (n_pix) is 64 in this version. Images are
+ *   [row y][column x], row-major. Spectra are unnormalised forward DFTs
+ *   X[ky][kx] = sum_{y,x} x[y][x] exp(-2 pi i (ky y + kx x) / N), stored as
+ *   interleaved complex64 (float re, float im). A "half spectrum" is the
+ *   columns kx = 0..N/2 of every row: [N][N/2+1] (the layout of a real-to-
+ *   complex 2-D FFT); a "full spectrum" is [N][N].
+ * - Pupil sampling: centre at ((N-1)/2, (N-1)/2); pixel (y, x) is inside iff
+ *   (x-c)^2 + (y-c)^2 <= (D_p/2)^2 (minus a central obscuration), computed in
+ *   double from the float diameter.
+ */
+#ifndef MFBD_H
+#define MFBD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MFBD_ABI_VERSION 1
+
+typedef enum {
+    MFBD_OK = 0,
+    MFBD_ERR_INVALID_ARG = 1, /* bad descriptor, NULL pointer, size mismatch */
+    MFBD_ERR_UNSUPPORTED = 2, /* valid request this build cannot run (N, no GPU) */
+    MFBD_ERR_OOM = 3,         /* device or host allocation failed in create */
+    MFBD_ERR_CUDA = 4,        /* a CUDA call or kernel launch failed */
+    MFBD_ERR_STATE = 5,       /* wrong call order or a failed plan */
+    MFBD_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up */
+} mfbd_status;
+
+typedef enum {
+    MFBD_BASIS_ZERNIKE = 0, /* Noll modes 2..M+1 (Noll 1976 normalisation) */
+    MFBD_BASIS_KL = 1,      /* Karhunen-Loeve modes of Kolmogorov turbulence */
+    MFBD_BASIS_USER = 2     /* caller-supplied basis, see user_basis */
+} mfbd_basis;
+
+typedef enum {
+    MFBD_PREC_FP32 = 0,      /* phase projection, FFTs, adjoint in FP32 */
+    MFBD_PREC_BF16_PHASE = 1 /* phase projection on BF16 tensor cores */
+} mfbd_precision;
+
+/* flags */
+#define MFBD_FLAG_FULL_SPECTRUM 0x1u /* spectra/object are [N][N], else [N][N/2+1] */
+
+typedef struct {
+    int n_pix;      /* N, patch size in pixels (64) */
+    int n_patches;  /* P >= 0 (0: every compute call is a no-op) */
+    int n_objects;  /* K, 1..8 */
+    int n_frames;   /* J, 1..1024 (frames x diversity channels) */
+    int n_modes;    /* M, 1..256 */
+    const float* pupil_diam_px; /* host [K], D_p in pixels, 0 < D_p <= N */
+    const double* wavelength;   /* host [K], any unit; c_k = wavelength[0]/wavelength[k] */
+    float central_obscuration;  /* fraction of the diameter, 0 <= e < 1 */
+    int basis;                  /* mfbd_basis */
+    const float* user_basis;    /* host [K][M][N][N] when basis == MFBD_BASIS_USER, else NULL */
+    double gamma;               /* Wiener constant S_n/S_0 (Eq. 11), > 0 */
+    const float* frame_weight;  /* host [K][J] weights w_kj >= 0 (Eq. 2), or NULL for 1 */
+    int precision;              /* mfbd_precision */
+    unsigned flags;             /* MFBD_FLAG_* */
+} mfbd_plan_desc;
+
+typedef struct mfbd_plan* mfbd_plan_t;
+
+typedef struct {
+    int n_pix, n_patches, n_objects, n_frames, n_modes;
+    int pupil_pixels[8];   /* n_pup,k: pixels inside pupil k */
+    int pupil_box[8];      /* W_k: side of the pupil's bounding box */
+    size_t workspace_bytes; /* device memory owned by the plan */
+    int slots_per_cta;      /* frames a CTA of the fused kernel works on at once */
+    int ctas;               /* CTAs of the fused kernel */
+} mfbd_plan_info;
+
+/* Create a plan: validates the descriptor, samples pupils, builds the modal
+ * bases (double precision, on the host) and the exact OTF supports, uploads
+ * them and allocates every workspace. Runs the uploads on `stream` and
+ * synchronises it once. *out receives the plan (NULL on failure). */
+int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* desc, void* stream);
+
+/* Release a plan and its device memory (synchronises the device). NULL is OK. */
+int mfbd_plan_destroy(mfbd_plan_t plan);
+
+int mfbd_plan_get_info(mfbd_plan_t plan, mfbd_plan_info* info);
+
+/* Forward pass (Eqs. 20-22, 11, 12).
+ *   coeffs  dev [P][J][M] float: a_pjm, radians at wavelength[0].
+ *   spectra dev [P][K][J][N][N/2+1] complex64 (or [N][N] with
+ *           MFBD_FLAG_FULL_SPECTRUM): D_pkj, the FFTs of the observed frames.
+ *   loss    dev [P] double: L_p = sum over objects and all N^2 frequencies.
+ *   object  dev [P][K][N][N/2+1] (or [N][N]) complex64: O_pk (Eq. 11), or NULL.
+ * Also keeps what mfbd_backward needs (the adjoint seeds dL/dconj(H) and the
+ * wavefronts) in the plan. */
+int mfbd_forward(mfbd_plan_t plan, const float* coeffs, const void* spectra,
+                 double* loss, void* object, void* stream);
+
+/* Backward pass: grad dev [P][J][M] float = dL_p/da_pjm for the coefficients
+ * and spectra of the last mfbd_forward on this plan (MFBD_ERR_STATE if there
+ * was none). */
+int mfbd_backward(mfbd_plan_t plan, float* grad, void* stream);
+
+/* Forward and backward in one pass (one fused launch plus the two modal
+ * projections): loss, object (or NULL) and grad as above. */
+int mfbd_loss_grad(mfbd_plan_t plan, const float* coeffs, const void* spectra,
+                   double* loss, void* object, float* grad, void* stream);
+
+/* Forward model only: otf dev [P][K][J][N][N/2+1] complex64 = H_pkj
+ * (Sec. 3.1, Eqs. 20-22, then H = F s), e.g. to synthesise data. */
+int mfbd_otf(mfbd_plan_t plan, const float* coeffs, void* otf, void* stream);
+
+/* Host-only plan-time data (no GPU needed), for inspection and tests:
+ *   mask     host [N][N] uint8, pupil k (1 inside), or NULL
+ *   basis    host [M][N][N] float, modes of object k (0 outside pupil), or NULL
+ *   variance host [M] double, Kolmogorov variance of each mode in units of
+ *            (D/r0)^(5/3) rad^2 (Zernike: Noll covariance diagonal; KL:
+ *            eigenvalues; USER: zeros), or NULL
+ *   support  host [N][N/2+1] uint8, exact OTF support of pupil k, or NULL */
+int mfbd_describe_object(const mfbd_plan_desc* desc, int object, unsigned char* mask,
+                         float* basis, double* variance, unsigned char* support);
+
+/* Kernel timing. When enabled, every compute call records a CUDA event pair
+ * on its stream around each kernel it launches, from a pool of max_launches
+ * pairs created here (enable = 0 destroys the pool). Calls made while the
+ * pool is full are not timed. */
+int mfbd_plan_set_profiling(mfbd_plan_t plan, int enable, int max_launches);
+
+/* Waits for the recorded events, then returns the summed device time in ms
+ * and the launch count of each kernel kind: [0] modal phase projection,
+ * [1] fused OTF/loss/adjoint kernel, [2] modal adjoint projection. With
+ * reset != 0 the pool is emptied for reuse. Arrays may be NULL. */
+int mfbd_plan_read_profile(mfbd_plan_t plan, double* ms, long long* launches, int reset);
+
+/* Static description of a status code (never NULL). */
+const char* mfbd_status_string(int status);
+
+/* Detail of the last error raised on the calling host thread (never NULL). */
+const char* mfbd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFBD_H */

@@ -1,0 +1,31 @@
+/*
+ * mfbd_testing.h -- host-side self-test hooks of the MOMFBD library.
+ *
+ * These entry points run the library's register-FFT building blocks on the
+ * HOST CPU (they are compiled __host__ __device__), so their arithmetic can
+ * be checked without a GPU. They are not part of the compute path and the
+ * paper has no counterpart; they exist for testing only.
+ */
+#ifndef MFBD_TESTING_H
+#define MFBD_TESTING_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* kind selects the transform, all of length 64, unnormalised:
+ *   0  complex forward  in: 64 complex (128 floats)  out: 64 complex
+ *   1  complex adjoint  in: 64 complex               out: 64 complex
+ *   2  real-to-complex  in: 64 floats                out: 33 complex (66 floats)
+ *   3  complex-to-real  in: 33 complex (Hermitian)   out: 64 floats
+ *   4  complex forward, length 32
+ * Forward: X[k] = sum x[n] exp(-2 pi i n k / N); adjoint uses exp(+...).
+ * Returns 0 (MFBD_OK) or 1 (MFBD_ERR_INVALID_ARG) for an unknown kind or
+ * NULL pointers. */
+int mfbd_test_fft_host(int kind, const float* in, float* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFBD_TESTING_H */

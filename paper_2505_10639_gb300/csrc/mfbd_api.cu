@@ -1,0 +1,529 @@
+// C ABI of the MOMFBD hot path: plans, validation, workspaces, launches.
+// The arithmetic lives in mfbd_kernels.cu (device) and optics_host.cpp
+// (plan-time host math); this file only validates, allocates and schedules.
+#include "../../include/mfbd.h"
+#include "mfbd_internal.h"
+#include "optics_host.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <string>
+#include <vector>
+
+using namespace mfbd_dev;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+int fail(int status, const std::string& why) {
+    g_last_error = why;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return MFBD_ERR_CUDA;
+}
+
+struct ObjectData {
+    int W = 0, x0 = 0, npup = 0;
+    float scale = 1.f, inv_z = 0.f;
+    long long phi_off = 0;
+    float* d_basis = nullptr;   // [M][W*W]
+    uint64_t* d_mask = nullptr; // [W]
+    uint64_t* d_supp = nullptr; // [N]
+};
+
+}  // namespace
+
+struct mfbd_plan {
+    int N = 0, P = 0, K = 0, J = 0, M = 0;
+    unsigned flags = 0;
+    double gamma = 0;
+    int device = 0;
+    ObjectData obj[kMaxObjects];
+    float* d_weights = nullptr;
+    float* d_phi = nullptr;
+    float* d_gphi = nullptr;
+    float2* d_gscr = nullptr;
+    long long phi_floats = 0;
+    size_t workspace = 0;
+    FusedGeometry geo{};
+    int ctas = 0;
+    bool failed = false;
+    bool have_forward = false;
+    std::vector<void*> allocations;
+    // kernel timing (mfbd_plan_set_profiling)
+    std::vector<cudaEvent_t> ev;    // 2 per pair
+    std::vector<int> ev_kind;       // kind of each used pair
+    int ev_used = 0;
+};
+
+namespace {
+
+int validate(const mfbd_plan_desc* d) {
+    if (!d) return fail(MFBD_ERR_INVALID_ARG, "descriptor is NULL");
+    if (d->n_pix <= 0) return fail(MFBD_ERR_INVALID_ARG, "n_pix must be positive");
+    if (d->n_patches < 0) return fail(MFBD_ERR_INVALID_ARG, "n_patches must be >= 0");
+    if (d->n_objects < 1 || d->n_objects > kMaxObjects)
+        return fail(MFBD_ERR_INVALID_ARG, "n_objects must be in 1..8");
+    if (d->n_frames < 1 || d->n_frames > 1024) return fail(MFBD_ERR_INVALID_ARG, "n_frames must be in 1..1024");
+    if (d->n_modes < 1 || d->n_modes > 256) return fail(MFBD_ERR_INVALID_ARG, "n_modes must be in 1..256");
+    if (!d->pupil_diam_px) return fail(MFBD_ERR_INVALID_ARG, "pupil_diam_px is NULL");
+    if (!d->wavelength) return fail(MFBD_ERR_INVALID_ARG, "wavelength is NULL");
+    for (int k = 0; k < d->n_objects; ++k) {
+        float dp = d->pupil_diam_px[k];
+        if (!(dp > 0.f) || !(dp <= (float)d->n_pix))
+            return fail(MFBD_ERR_INVALID_ARG, "pupil diameter must be in (0, n_pix]");
+        if (!(d->wavelength[k] > 0.0) || !std::isfinite(d->wavelength[k]))
+            return fail(MFBD_ERR_INVALID_ARG, "wavelength must be positive and finite");
+    }
+    if (!(d->central_obscuration >= 0.f) || !(d->central_obscuration < 1.f))
+        return fail(MFBD_ERR_INVALID_ARG, "central_obscuration must be in [0, 1)");
+    if (d->basis != MFBD_BASIS_ZERNIKE && d->basis != MFBD_BASIS_KL && d->basis != MFBD_BASIS_USER)
+        return fail(MFBD_ERR_INVALID_ARG, "unknown basis");
+    if (d->basis == MFBD_BASIS_USER && !d->user_basis)
+        return fail(MFBD_ERR_INVALID_ARG, "user_basis is NULL for MFBD_BASIS_USER");
+    if (!(d->gamma > 0.0) || !std::isfinite(d->gamma)) return fail(MFBD_ERR_INVALID_ARG, "gamma must be > 0");
+    if (d->frame_weight)
+        for (int i = 0; i < d->n_objects * d->n_frames; ++i)
+            if (!(d->frame_weight[i] >= 0.f) || !std::isfinite(d->frame_weight[i]))
+                return fail(MFBD_ERR_INVALID_ARG, "frame weights must be finite and >= 0");
+    if (d->precision != MFBD_PREC_FP32 && d->precision != MFBD_PREC_BF16_PHASE)
+        return fail(MFBD_ERR_INVALID_ARG, "unknown precision");
+    if (d->flags & ~MFBD_FLAG_FULL_SPECTRUM) return fail(MFBD_ERR_INVALID_ARG, "unknown flags");
+    if (d->n_pix != kN) return fail(MFBD_ERR_UNSUPPORTED, "this build supports n_pix == 64");
+    if (d->precision != MFBD_PREC_FP32) return fail(MFBD_ERR_UNSUPPORTED, "BF16 phase path not built");
+    return MFBD_OK;
+}
+
+// full-grid double basis [M][N][N] of object k
+std::vector<double> object_basis(const mfbd_plan_desc* d, int k, std::vector<double>* variance) {
+    const int n = d->n_pix, m = d->n_modes;
+    if (d->basis == MFBD_BASIS_USER) {
+        std::vector<double> b((size_t)m * n * n);
+        const float* src = d->user_basis + (size_t)k * m * n * n;
+        for (size_t i = 0; i < b.size(); ++i) b[i] = src[i];
+        if (variance) variance->assign(m, 0.0);
+        return b;
+    }
+    mfbd_host::ModalBasis mb = d->basis == MFBD_BASIS_ZERNIKE
+                                   ? mfbd_host::zernike_basis(n, d->pupil_diam_px[k], d->central_obscuration, m)
+                                   : mfbd_host::kl_basis(n, d->pupil_diam_px[k], d->central_obscuration, m);
+    if (variance) *variance = mb.variance;
+    return mb.modes;
+}
+
+template <class T>
+int dev_alloc(mfbd_plan* p, T** ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) return MFBD_OK;
+    void* raw = nullptr;
+    cudaError_t e = cudaMalloc(&raw, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MFBD_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    p->allocations.push_back(raw);
+    p->workspace += count * sizeof(T);
+    *ptr = static_cast<T*>(raw);
+    return MFBD_OK;
+}
+
+void release(mfbd_plan* p) {
+    for (void* a : p->allocations) cudaFree(a);
+    p->allocations.clear();
+}
+
+FusedParams fused_params(const mfbd_plan* p, const void* spectra, double* loss, void* object, float2* gscr) {
+    FusedParams f{};
+    f.P = p->P;
+    f.K = p->K;
+    f.J = p->J;
+    f.M = p->M;
+    f.gamma = p->gamma;
+    f.weights = p->d_weights;
+    f.phi = p->d_phi;
+    f.gphi = p->d_gphi;
+    f.gscr = gscr;
+    f.spectra = static_cast<const float2*>(spectra);
+    f.spec_ld = (p->flags & MFBD_FLAG_FULL_SPECTRUM) ? p->N : p->N / 2 + 1;
+    f.loss = loss;
+    f.object = static_cast<float2*>(object);
+    for (int k = 0; k < p->K; ++k) {
+        f.obj[k].W = p->obj[k].W;
+        f.obj[k].x0 = p->obj[k].x0;
+        f.obj[k].inv_z = p->obj[k].inv_z;
+        f.obj[k].phi_off = p->obj[k].phi_off;
+        f.obj[k].mask = p->obj[k].d_mask;
+        f.obj[k].supp = p->obj[k].d_supp;
+    }
+    return f;
+}
+
+int check_plan(mfbd_plan_t p) {
+    if (!p) return fail(MFBD_ERR_INVALID_ARG, "plan is NULL");
+    if (p->failed) return fail(MFBD_ERR_STATE, "plan failed earlier");
+    return MFBD_OK;
+}
+
+int set_device(mfbd_plan_t p) {
+    cudaError_t e = cudaSetDevice(p->device);
+    if (e != cudaSuccess) {
+        p->failed = true;
+        return cuda_fail(e, "cudaSetDevice");
+    }
+    return MFBD_OK;
+}
+
+// event pair around one launch when profiling: returns the pair index or -1
+int prof_begin(mfbd_plan_t p, int kind, cudaStream_t s) {
+    if (p->ev.empty() || p->ev_used * 2 >= (int)p->ev.size()) return -1;
+    const int i = p->ev_used++;
+    p->ev_kind[i] = kind;
+    cudaEventRecord(p->ev[2 * i], s);
+    return i;
+}
+
+void prof_end(mfbd_plan_t p, int i, cudaStream_t s) {
+    if (i >= 0) cudaEventRecord(p->ev[2 * i + 1], s);
+}
+
+int run_phase(mfbd_plan_t p, const float* coeffs, cudaStream_t s) {
+    for (int k = 0; k < p->K; ++k) {
+        const ObjectData& o = p->obj[k];
+        const int pi = prof_begin(p, 0, s);
+        cudaError_t e = launch_phase_gemm(coeffs, p->P * p->J, p->M, o.d_basis, o.W * o.W, o.scale,
+                                          p->d_phi + o.phi_off, s);
+        prof_end(p, pi, s);
+        if (e != cudaSuccess) {
+            p->failed = true;
+            return cuda_fail(e, "phase projection");
+        }
+    }
+    return MFBD_OK;
+}
+
+int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s) {
+    for (int k = 0; k < p->K; ++k) {
+        const ObjectData& o = p->obj[k];
+        const int pi = prof_begin(p, 2, s);
+        cudaError_t e = launch_grad_gemm(p->d_gphi + o.phi_off, p->P * p->J, o.W * o.W, o.d_basis, p->M,
+                                         o.scale, k > 0, grad, s);
+        prof_end(p, pi, s);
+        if (e != cudaSuccess) {
+            p->failed = true;
+            return cuda_fail(e, "modal adjoint");
+        }
+    }
+    return MFBD_OK;
+}
+
+int run_fused(mfbd_plan_t p, int mode, const void* spectra, double* loss, void* object, float2* gscr,
+              cudaStream_t s) {
+    FusedParams f = fused_params(p, spectra, loss, object, gscr);
+    const int pi = prof_begin(p, 1, s);
+    cudaError_t e = launch_fused(f, mode, p->geo, p->ctas, s);
+    prof_end(p, pi, s);
+    if (e != cudaSuccess) {
+        p->failed = true;
+        return cuda_fail(e, "fused kernel");
+    }
+    return MFBD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mfbd_status_string(int status) {
+    switch (status) {
+        case MFBD_OK: return "MFBD_OK";
+        case MFBD_ERR_INVALID_ARG: return "MFBD_ERR_INVALID_ARG: invalid argument";
+        case MFBD_ERR_UNSUPPORTED: return "MFBD_ERR_UNSUPPORTED: not supported by this build or device";
+        case MFBD_ERR_OOM: return "MFBD_ERR_OOM: allocation failed";
+        case MFBD_ERR_CUDA: return "MFBD_ERR_CUDA: CUDA error";
+        case MFBD_ERR_STATE: return "MFBD_ERR_STATE: wrong call order or failed plan";
+        case MFBD_ERR_TIMEOUT: return "MFBD_ERR_TIMEOUT: device wait gave up";
+        default: return "unknown mfbd status";
+    }
+}
+
+const char* mfbd_last_error(void) { return g_last_error.c_str(); }
+
+int mfbd_describe_object(const mfbd_plan_desc* desc, int object, unsigned char* mask, float* basis,
+                         double* variance, unsigned char* support) {
+    int st = validate(desc);
+    if (st == MFBD_ERR_UNSUPPORTED && desc && desc->n_pix > 0 && desc->n_pix <= 256 && desc->n_pix % 2 == 0)
+        st = MFBD_OK;  // host data is defined for any even N
+    if (st != MFBD_OK) return st;
+    if (object < 0 || object >= desc->n_objects) return fail(MFBD_ERR_INVALID_ARG, "object index out of range");
+    try {
+        const int n = desc->n_pix;
+        std::vector<uint8_t> m = mfbd_host::pupil_mask(n, desc->pupil_diam_px[object], desc->central_obscuration);
+        if (mask) std::memcpy(mask, m.data(), m.size());
+        if (basis || variance) {
+            std::vector<double> var;
+            std::vector<double> b = object_basis(desc, object, &var);
+            if (basis)
+                for (size_t i = 0; i < b.size(); ++i) basis[i] = (float)b[i];
+            if (variance)
+                for (int i = 0; i < desc->n_modes; ++i) variance[i] = var[i];
+        }
+        if (support) {
+            std::vector<uint8_t> s = mfbd_host::otf_support_half(m, n);
+            std::memcpy(support, s.data(), s.size());
+        }
+    } catch (const std::exception& e) {
+        return fail(MFBD_ERR_INVALID_ARG, e.what());
+    }
+    return MFBD_OK;
+}
+
+int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
+    if (!out) return fail(MFBD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int st = validate(d);
+    if (st != MFBD_OK) return st;
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(MFBD_ERR_UNSUPPORTED, "no CUDA device (there is no CPU fallback)");
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    if (prop.major * 10 + prop.minor != 103)
+        return fail(MFBD_ERR_UNSUPPORTED, "this build targets sm_103a (GB300)");
+
+    mfbd_plan* p = new (std::nothrow) mfbd_plan();
+    if (!p) return fail(MFBD_ERR_OOM, "host allocation failed");
+    p->N = d->n_pix;
+    p->P = d->n_patches;
+    p->K = d->n_objects;
+    p->J = d->n_frames;
+    p->M = d->n_modes;
+    p->flags = d->flags;
+    p->gamma = d->gamma;
+    p->device = dev;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n = p->N;
+
+    try {
+        std::vector<float> w((size_t)p->K * p->J, 1.0f);
+        if (d->frame_weight) std::memcpy(w.data(), d->frame_weight, w.size() * sizeof(float));
+        if ((st = dev_alloc(p, &p->d_weights, w.size()))) throw st;
+        if ((e = cudaMemcpyAsync(p->d_weights, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, s)))
+            throw cuda_fail(e, "upload weights");
+
+        std::vector<std::vector<float>> hb(p->K);
+        std::vector<std::vector<uint64_t>> hm(p->K), hs(p->K);
+        long long phi_floats = 0;
+        int max_box = 1;
+        for (int k = 0; k < p->K; ++k) {
+            ObjectData& o = p->obj[k];
+            std::vector<uint8_t> mask = mfbd_host::pupil_mask(n, d->pupil_diam_px[k], d->central_obscuration);
+            int lo = n, hi = -1, npup = 0;
+            for (int y = 0; y < n; ++y)
+                for (int x = 0; x < n; ++x)
+                    if (mask[(size_t)y * n + x]) {
+                        ++npup;
+                        lo = std::min(lo, std::min(x, y));
+                        hi = std::max(hi, std::max(x, y));
+                    }
+            if (npup == 0) throw fail(MFBD_ERR_INVALID_ARG, "pupil has no pixel");
+            o.npup = npup;
+            o.x0 = lo;
+            o.W = hi - lo + 1;
+            max_box = std::max(max_box, o.W);
+            o.scale = (float)(d->wavelength[0] / d->wavelength[k]);
+            o.inv_z = (float)(1.0 / ((double)n * n * npup));
+            o.phi_off = phi_floats;
+            phi_floats += (long long)p->P * p->J * o.W * o.W;
+            std::vector<double> full = object_basis(d, k, nullptr);
+            hb[k].assign((size_t)p->M * o.W * o.W, 0.f);
+            for (int m = 0; m < p->M; ++m)
+                for (int yy = 0; yy < o.W; ++yy)
+                    for (int xx = 0; xx < o.W; ++xx) {
+                        size_t src = (size_t)m * n * n + (size_t)(o.x0 + yy) * n + (o.x0 + xx);
+                        if (mask[(size_t)(o.x0 + yy) * n + (o.x0 + xx)])
+                            hb[k][(size_t)m * o.W * o.W + (size_t)yy * o.W + xx] = (float)full[src];
+                    }
+            hm[k].assign(o.W, 0);
+            for (int yy = 0; yy < o.W; ++yy)
+                for (int xx = 0; xx < o.W; ++xx)
+                    if (mask[(size_t)(o.x0 + yy) * n + (o.x0 + xx)]) hm[k][yy] |= 1ull << xx;
+            std::vector<uint8_t> sup = mfbd_host::otf_support_half(mask, n);
+            hs[k].assign(n, 0);
+            for (int ky = 0; ky < n; ++ky)
+                for (int kx = 0; kx <= n / 2; ++kx)
+                    if (sup[(size_t)ky * (n / 2 + 1) + kx]) hs[k][ky] |= 1ull << kx;
+            if ((st = dev_alloc(p, &o.d_basis, hb[k].size()))) throw st;
+            if ((st = dev_alloc(p, &o.d_mask, hm[k].size()))) throw st;
+            if ((st = dev_alloc(p, &o.d_supp, hs[k].size()))) throw st;
+            if ((e = cudaMemcpyAsync(o.d_basis, hb[k].data(), hb[k].size() * sizeof(float), cudaMemcpyHostToDevice, s)) ||
+                (e = cudaMemcpyAsync(o.d_mask, hm[k].data(), hm[k].size() * 8, cudaMemcpyHostToDevice, s)) ||
+                (e = cudaMemcpyAsync(o.d_supp, hs[k].data(), hs[k].size() * 8, cudaMemcpyHostToDevice, s)))
+                throw cuda_fail(e, "upload plan data");
+        }
+        p->phi_floats = phi_floats;
+        if ((st = dev_alloc(p, &p->d_phi, (size_t)phi_floats))) throw st;
+        if ((st = dev_alloc(p, &p->d_gphi, (size_t)phi_floats))) throw st;
+        if ((st = dev_alloc(p, &p->d_gscr, (size_t)p->P * p->K * p->J * kHalf))) throw st;
+
+        p->geo = fused_geometry(max_box);
+        int per_sm = max_ctas_per_sm(p->geo);
+        if (per_sm < 1) throw fail(MFBD_ERR_UNSUPPORTED, "fused kernel does not fit on this device");
+        p->ctas = std::min(std::max(p->P, 1), prop.multiProcessorCount * per_sm);
+        if ((e = cudaStreamSynchronize(s))) throw cuda_fail(e, "plan upload");
+    } catch (int status) {
+        release(p);
+        delete p;
+        return status;
+    } catch (const std::exception& ex) {
+        release(p);
+        delete p;
+        return fail(MFBD_ERR_INVALID_ARG, ex.what());
+    }
+    *out = p;
+    return MFBD_OK;
+}
+
+int mfbd_plan_set_profiling(mfbd_plan_t p, int enable, int max_launches) {
+    if (!p) return fail(MFBD_ERR_INVALID_ARG, "plan is NULL");
+    cudaSetDevice(p->device);
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    p->ev.clear();
+    p->ev_kind.clear();
+    p->ev_used = 0;
+    if (!enable) return MFBD_OK;
+    if (max_launches < 1 || max_launches > 1 << 16) return fail(MFBD_ERR_INVALID_ARG, "max_launches out of range");
+    p->ev.resize((size_t)2 * max_launches);
+    p->ev_kind.assign(max_launches, 0);
+    for (size_t i = 0; i < p->ev.size(); ++i) {
+        cudaError_t e = cudaEventCreate(&p->ev[i]);
+        if (e != cudaSuccess) {
+            for (size_t j = 0; j < i; ++j) cudaEventDestroy(p->ev[j]);
+            p->ev.clear();
+            p->ev_kind.clear();
+            return cuda_fail(e, "cudaEventCreate");
+        }
+    }
+    return MFBD_OK;
+}
+
+int mfbd_plan_read_profile(mfbd_plan_t p, double* ms, long long* launches, int reset) {
+    if (!p) return fail(MFBD_ERR_INVALID_ARG, "plan is NULL");
+    double acc[3] = {0, 0, 0};
+    long long cnt[3] = {0, 0, 0};
+    for (int i = 0; i < p->ev_used; ++i) {
+        cudaError_t e = cudaEventSynchronize(p->ev[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        float t = 0.f;
+        if ((e = cudaEventElapsedTime(&t, p->ev[2 * i], p->ev[2 * i + 1])) != cudaSuccess)
+            return cuda_fail(e, "cudaEventElapsedTime");
+        acc[p->ev_kind[i]] += t;
+        cnt[p->ev_kind[i]] += 1;
+    }
+    for (int k = 0; k < 3; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (launches) launches[k] = cnt[k];
+    }
+    if (reset) p->ev_used = 0;
+    return MFBD_OK;
+}
+
+int mfbd_plan_destroy(mfbd_plan_t p) {
+    if (!p) return MFBD_OK;
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    release(p);
+    delete p;
+    return MFBD_OK;
+}
+
+int mfbd_plan_get_info(mfbd_plan_t p, mfbd_plan_info* info) {
+    if (!p || !info) return fail(MFBD_ERR_INVALID_ARG, "NULL argument");
+    std::memset(info, 0, sizeof *info);
+    info->n_pix = p->N;
+    info->n_patches = p->P;
+    info->n_objects = p->K;
+    info->n_frames = p->J;
+    info->n_modes = p->M;
+    for (int k = 0; k < p->K; ++k) {
+        info->pupil_pixels[k] = p->obj[k].npup;
+        info->pupil_box[k] = p->obj[k].W;
+    }
+    info->workspace_bytes = p->workspace;
+    info->slots_per_cta = p->geo.slots;
+    info->ctas = p->ctas;
+    return MFBD_OK;
+}
+
+int mfbd_forward(mfbd_plan_t p, const float* coeffs, const void* spectra, double* loss, void* object,
+                 void* stream) {
+    int st = check_plan(p);
+    if (st) return st;
+    if (p->P == 0) {
+        p->have_forward = true;
+        return MFBD_OK;
+    }
+    if (!coeffs || !spectra || !loss) return fail(MFBD_ERR_INVALID_ARG, "coeffs, spectra and loss are required");
+    if ((st = set_device(p))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((st = run_phase(p, coeffs, s))) return st;
+    if ((st = run_fused(p, MODE_FWD, spectra, loss, object, p->d_gscr, s))) return st;
+    p->have_forward = true;
+    return MFBD_OK;
+}
+
+int mfbd_backward(mfbd_plan_t p, float* grad, void* stream) {
+    int st = check_plan(p);
+    if (st) return st;
+    if (!p->have_forward) return fail(MFBD_ERR_STATE, "mfbd_backward needs a preceding mfbd_forward");
+    if (p->P == 0) return MFBD_OK;
+    if (!grad) return fail(MFBD_ERR_INVALID_ARG, "grad is NULL");
+    if ((st = set_device(p))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((st = run_fused(p, MODE_BWD, nullptr, nullptr, nullptr, p->d_gscr, s))) return st;
+    return run_grad(p, grad, s);
+}
+
+int mfbd_loss_grad(mfbd_plan_t p, const float* coeffs, const void* spectra, double* loss, void* object,
+                   float* grad, void* stream) {
+    int st = check_plan(p);
+    if (st) return st;
+    if (p->P == 0) return MFBD_OK;
+    if (!coeffs || !spectra || !loss || !grad)
+        return fail(MFBD_ERR_INVALID_ARG, "coeffs, spectra, loss and grad are required");
+    if ((st = set_device(p))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((st = run_phase(p, coeffs, s))) return st;
+    if ((st = run_fused(p, MODE_FUSED, spectra, loss, object, p->d_gscr, s))) return st;
+    if ((st = run_grad(p, grad, s))) return st;
+    p->have_forward = true;
+    return MFBD_OK;
+}
+
+int mfbd_otf(mfbd_plan_t p, const float* coeffs, void* otf, void* stream) {
+    int st = check_plan(p);
+    if (st) return st;
+    if (p->P == 0) return MFBD_OK;
+    if (!coeffs || !otf) return fail(MFBD_ERR_INVALID_ARG, "coeffs and otf are required");
+    if ((st = set_device(p))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    p->have_forward = false;  // the phases now belong to these coefficients
+    if ((st = run_phase(p, coeffs, s))) return st;
+    return run_fused(p, MODE_OTF, nullptr, nullptr, nullptr, static_cast<float2*>(otf), s);
+}
+
+}  // extern "C"

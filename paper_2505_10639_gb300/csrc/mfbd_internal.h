@@ -1,0 +1,62 @@
+// Internal launch interface between the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace mfbd_dev {
+
+constexpr int kMaxObjects = 8;
+constexpr int kN = 64;                  // patch size supported by the fused kernel
+constexpr int kNH = kN / 2 + 1;         // 33 half-spectrum columns
+constexpr int kHalf = kN * kNH;         // 2112 half-spectrum frequencies
+
+// Fused-kernel modes.
+enum Mode : int { MODE_FWD = 0, MODE_BWD = 1, MODE_FUSED = 2, MODE_OTF = 3 };
+
+struct ObjParams {
+    int W;                   // side of the pupil's bounding box
+    int x0;                  // first row/column of the box
+    float inv_z;             // 1 / (N^2 n_pup): PSF normalisation (Parseval)
+    long long phi_off;       // float offset of this object's phase block
+    const uint64_t* mask;    // [W] rows, bit t = pupil pixel at box column t
+    const uint64_t* supp;    // [N] rows, bit kx = OTF support (kx <= N/2)
+};
+
+struct FusedParams {
+    int P, K, J, M;
+    double gamma;
+    const float* weights;     // [K][J]
+    const float* phi;         // phases, per object [P*J][W*W] at phi_off
+    float* gphi;              // dL/dphi, same layout
+    float2* gscr;             // [P][K][J][N][N/2+1]: OTF, then dL/dconj(H)
+    const float2* spectra;    // D
+    int spec_ld;              // row stride of D and O in complex elements (33 or 64)
+    double* loss;             // [P]
+    float2* object;           // [P][K][N][spec_ld] or null
+    ObjParams obj[kMaxObjects];
+};
+
+// Fused kernel geometry for the largest box of a plan.
+struct FusedGeometry {
+    int slots;          // frames per CTA in flight (64 threads each)
+    size_t smem_bytes;  // dynamic shared memory per CTA
+    int xs;             // row stride of the X exchange buffer (complex)
+};
+
+FusedGeometry fused_geometry(int max_box);
+
+cudaError_t launch_fused(const FusedParams& prm, int mode, const FusedGeometry& g, int ctas,
+                         cudaStream_t s);
+
+// phase[u][i] = scale * sum_m a[u][m] basis[m][i]  (u < U, i < npix)
+cudaError_t launch_phase_gemm(const float* a, int U, int M, const float* basis, int npix,
+                              float scale, float* phase, cudaStream_t s);
+
+// grad[u][m] (+)= scale * sum_i gphi[u][i] basis[m][i]
+cudaError_t launch_grad_gemm(const float* gphi, int U, int npix, const float* basis, int M,
+                             float scale, int accumulate, float* grad, cudaStream_t s);
+
+int max_ctas_per_sm(const FusedGeometry& g);
+
+}  // namespace mfbd_dev

@@ -1,0 +1,213 @@
+"""Python binding of the MOMFBD C ABI (argument marshalling only).
+
+Every call forwards torch tensors' device pointers and the current CUDA
+stream to ``libmfbd.so``; all arithmetic runs in the library's kernels.
+Names follow the C ABI: ``Plan.forward`` -> ``mfbd_forward`` and so on.
+"""
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+_BASIS = {"zernike": _lib.MFBD_BASIS_ZERNIKE, "kl": _lib.MFBD_BASIS_KL, "user": _lib.MFBD_BASIS_USER}
+_PREC = {"fp32": _lib.MFBD_PREC_FP32, "bf16_phase": _lib.MFBD_PREC_BF16_PHASE}
+
+
+def _fptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype)) if a is not None else None
+
+
+class _Desc:
+    """A PlanDesc plus the host arrays it points into (kept alive)."""
+
+    def __init__(self, n_pix, n_patches, diams, wavelengths, n_frames, n_modes, basis, gamma,
+                 weights, obscuration, user_basis, precision, full_spectrum):
+        k = len(diams)
+        self.diams = np.ascontiguousarray(diams, dtype=np.float32)
+        self.wl = np.ascontiguousarray(wavelengths, dtype=np.float64)
+        self.weights = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32).reshape(k, n_frames)
+        self.user = None if user_basis is None else np.ascontiguousarray(user_basis, dtype=np.float32)
+        self.desc = _lib.PlanDesc(
+            n_pix=n_pix, n_patches=n_patches, n_objects=k, n_frames=n_frames, n_modes=n_modes,
+            pupil_diam_px=_fptr(self.diams, ctypes.c_float), wavelength=_fptr(self.wl, ctypes.c_double),
+            central_obscuration=obscuration, basis=_BASIS[basis],
+            user_basis=_fptr(self.user, ctypes.c_float), gamma=gamma,
+            frame_weight=_fptr(self.weights, ctypes.c_float), precision=_PREC[precision],
+            flags=_lib.MFBD_FLAG_FULL_SPECTRUM if full_spectrum else 0)
+
+
+def describe_object(obj, n_pix, diams, wavelengths, n_frames, n_modes, basis="kl", gamma=1e-3,
+                    obscuration=0.0, user_basis=None):
+    """Host-only plan-time data of object ``obj`` (mfbd_describe_object):
+    (mask [N,N] uint8, basis [M,N,N] float32, variance [M], support [N,N/2+1])."""
+    lib = _lib.load()
+    d = _Desc(n_pix, 1, diams, wavelengths, n_frames, n_modes, basis, gamma, None, obscuration,
+              user_basis, "fp32", False)
+    mask = np.zeros((n_pix, n_pix), np.uint8)
+    bas = np.zeros((n_modes, n_pix, n_pix), np.float32)
+    var = np.zeros(n_modes, np.float64)
+    sup = np.zeros((n_pix, n_pix // 2 + 1), np.uint8)
+    _lib.check(lib.mfbd_describe_object(ctypes.byref(d.desc), obj, mask.ctypes.data, bas.ctypes.data,
+                                        var.ctypes.data, sup.ctypes.data), "mfbd_describe_object")
+    return mask, bas, var, sup
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """An mfbd plan: fixed sizes, pupils, bases and workspaces on one GPU.
+
+    coeffs  [P, J, M] float32 (radians at wavelengths[0])
+    spectra [P, K, J, N, N//2+1] complex64 (or [.., N, N] with full_spectrum)
+    """
+
+    def __init__(self, n_pix, n_patches, diams, wavelengths, n_frames, n_modes, basis="kl",
+                 gamma=1e-3, weights=None, obscuration=0.0, user_basis=None, precision="fp32",
+                 full_spectrum=False, stream=None):
+        self._lib = _lib.load()
+        self._d = _Desc(n_pix, n_patches, diams, wavelengths, n_frames, n_modes, basis, gamma, weights,
+                        obscuration, user_basis, precision, full_spectrum)
+        self.n_pix, self.n_patches, self.n_objects = n_pix, n_patches, len(diams)
+        self.n_frames, self.n_modes = n_frames, n_modes
+        self.full_spectrum = full_spectrum
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        handle = ctypes.c_void_p()
+        _lib.check(self._lib.mfbd_plan_create(ctypes.byref(handle), ctypes.byref(self._d.desc),
+                                              _stream(stream)), "mfbd_plan_create")
+        self._h = handle
+
+    # ------------------------------------------------------------ shapes
+    @property
+    def spec_cols(self):
+        return self.n_pix if self.full_spectrum else self.n_pix // 2 + 1
+
+    def coeff_shape(self):
+        return (self.n_patches, self.n_frames, self.n_modes)
+
+    def spectra_shape(self):
+        return (self.n_patches, self.n_objects, self.n_frames, self.n_pix, self.spec_cols)
+
+    def object_shape(self):
+        return (self.n_patches, self.n_objects, self.n_pix, self.spec_cols)
+
+    def otf_shape(self):
+        return (self.n_patches, self.n_objects, self.n_frames, self.n_pix, self.n_pix // 2 + 1)
+
+    def info(self):
+        inf = _lib.PlanInfo()
+        _lib.check(self._lib.mfbd_plan_get_info(self._h, ctypes.byref(inf)), "mfbd_plan_get_info")
+        k = self.n_objects
+        return dict(pupil_pixels=list(inf.pupil_pixels[:k]), pupil_box=list(inf.pupil_box[:k]),
+                    workspace_bytes=inf.workspace_bytes, slots_per_cta=inf.slots_per_cta, ctas=inf.ctas)
+
+    # ------------------------------------------------------------ calls
+    def forward(self, coeffs, spectra, loss=None, obj=None, want_object=True, stream=None):
+        """mfbd_forward -> (loss [P] float64, object or None)."""
+        if loss is None:
+            loss = torch.empty(self.n_patches, dtype=torch.float64, device=self.device)
+        if obj is None and want_object:
+            obj = torch.empty(self.object_shape(), dtype=torch.complex64, device=self.device)
+        _lib.check(self._lib.mfbd_forward(
+            self._h, _dev(coeffs, torch.float32, self.coeff_shape(), "coeffs"),
+            _dev(spectra, torch.complex64, self.spectra_shape(), "spectra"),
+            _dev(loss, torch.float64, (self.n_patches,), "loss"),
+            _dev(obj, torch.complex64, self.object_shape(), "object") if obj is not None else None,
+            _stream(stream)), "mfbd_forward")
+        return loss, obj
+
+    def backward(self, grad=None, stream=None):
+        """mfbd_backward -> dL/da [P, J, M] float32."""
+        if grad is None:
+            grad = torch.empty(self.coeff_shape(), dtype=torch.float32, device=self.device)
+        _lib.check(self._lib.mfbd_backward(self._h, _dev(grad, torch.float32, self.coeff_shape(), "grad"),
+                                           _stream(stream)), "mfbd_backward")
+        return grad
+
+    def loss_grad(self, coeffs, spectra, loss=None, grad=None, obj=None, want_object=False, stream=None):
+        """mfbd_loss_grad -> (loss, grad, object or None)."""
+        if loss is None:
+            loss = torch.empty(self.n_patches, dtype=torch.float64, device=self.device)
+        if grad is None:
+            grad = torch.empty(self.coeff_shape(), dtype=torch.float32, device=self.device)
+        if obj is None and want_object:
+            obj = torch.empty(self.object_shape(), dtype=torch.complex64, device=self.device)
+        _lib.check(self._lib.mfbd_loss_grad(
+            self._h, _dev(coeffs, torch.float32, self.coeff_shape(), "coeffs"),
+            _dev(spectra, torch.complex64, self.spectra_shape(), "spectra"),
+            _dev(loss, torch.float64, (self.n_patches,), "loss"),
+            _dev(obj, torch.complex64, self.object_shape(), "object") if obj is not None else None,
+            _dev(grad, torch.float32, self.coeff_shape(), "grad"), _stream(stream)), "mfbd_loss_grad")
+        return loss, grad, obj
+
+    def otf(self, coeffs, out=None, stream=None):
+        """mfbd_otf -> H [P, K, J, N, N//2+1] complex64."""
+        if out is None:
+            out = torch.empty(self.otf_shape(), dtype=torch.complex64, device=self.device)
+        _lib.check(self._lib.mfbd_otf(self._h, _dev(coeffs, torch.float32, self.coeff_shape(), "coeffs"),
+                                      _dev(out, torch.complex64, self.otf_shape(), "otf"), _stream(stream)),
+                   "mfbd_otf")
+        return out
+
+    def set_profiling(self, enable=True, max_launches=4096):
+        """mfbd_plan_set_profiling: time every kernel with CUDA events."""
+        _lib.check(self._lib.mfbd_plan_set_profiling(self._h, int(enable), int(max_launches)),
+                   "mfbd_plan_set_profiling")
+
+    def read_profile(self, reset=True):
+        """mfbd_plan_read_profile -> {kind: (ms, launches)} for the kinds
+        'phase', 'fused', 'grad'."""
+        ms = np.zeros(3, np.float64)
+        n = np.zeros(3, np.int64)
+        _lib.check(self._lib.mfbd_plan_read_profile(self._h, ms.ctypes.data, n.ctypes.data, int(reset)),
+                   "mfbd_plan_read_profile")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(("phase", "fused", "grad"))}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mfbd_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MOMFBDLoss(torch.autograd.Function):
+    """loss[P] = MOMFBD loss of every patch as a differentiable function of
+    the modal coefficients (spectra are data: no gradient)."""
+
+    @staticmethod
+    def forward(ctx, coeffs, spectra, plan):
+        loss, _ = plan.forward(coeffs.detach().contiguous(), spectra.contiguous(), want_object=False)
+        ctx.plan = plan
+        return loss
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        g = ctx.plan.backward()
+        return g * grad_loss.to(g.dtype)[:, None, None], None, None
+
+
+def momfbd_loss(coeffs, spectra, plan):
+    return MOMFBDLoss.apply(coeffs, spectra, plan)

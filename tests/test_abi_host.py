@@ -1,0 +1,163 @@
+"""Host-side tests of the C ABI (no GPU): the library builds, loads and
+exports every declared symbol; descriptors are validated; compute calls
+refuse to run without a GPU (no CPU fallback); plan-time pupil, support and
+modal bases built by the library's C++ agree with the independent oracle;
+the library's register FFTs (run on the host) agree with the oracle's FFT.
+"""
+
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import dft, optics
+from paper_2505_10639_gb300 import _lib, mfbd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _lib.load()
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(mfbd_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert "mfbd_plan_create" in names and "mfbd_loss_grad" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings(lib):
+    for code in range(7):
+        assert lib.mfbd_status_string(code).decode().startswith("MFBD_")
+    assert b"unknown" in lib.mfbd_status_string(99)
+
+
+def _desc(**kw):
+    args = dict(n_pix=64, n_patches=1, diams=[32.0], wavelengths=[8542.0], n_frames=8, n_modes=20,
+                basis="zernike", gamma=1e-3, weights=None, obscuration=0.0, user_basis=None,
+                precision="fp32", full_spectrum=False)
+    args.update(kw)
+    return mfbd._Desc(**args)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n_objects_override=0), dict(n_frames=0), dict(n_modes=0), dict(n_modes=300),
+    dict(diams=[0.0]), dict(diams=[65.0]), dict(wavelengths=[-1.0]), dict(gamma=0.0),
+    dict(gamma=float("nan")), dict(obscuration=1.0), dict(n_patches=-1),
+    dict(weights=[[1.0] * 7 + [-1.0]]), dict(basis="user"),
+])
+def test_invalid_descriptors_are_rejected(lib, bad):
+    bad = dict(bad)
+    k0 = bad.pop("n_objects_override", None)
+    d = _desc(**bad)
+    if k0 is not None:
+        d.desc.n_objects = k0
+    out = ctypes.c_void_p()
+    st = lib.mfbd_plan_create(ctypes.byref(out), ctypes.byref(d.desc), None)
+    assert st == _lib.MFBD_ERR_INVALID_ARG, lib.mfbd_last_error()
+    assert out.value is None
+    st = lib.mfbd_describe_object(ctypes.byref(d.desc), 0, None, None, None, None)
+    assert st == _lib.MFBD_ERR_INVALID_ARG
+
+
+def test_unsupported_size_and_null_arguments(lib):
+    d = _desc(n_pix=128, diams=[40.0])
+    out = ctypes.c_void_p()
+    assert lib.mfbd_plan_create(ctypes.byref(out), ctypes.byref(d.desc), None) == _lib.MFBD_ERR_UNSUPPORTED
+    assert lib.mfbd_plan_create(None, ctypes.byref(d.desc), None) == _lib.MFBD_ERR_INVALID_ARG
+    assert lib.mfbd_forward(None, None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
+    assert lib.mfbd_backward(None, None, None) == _lib.MFBD_ERR_INVALID_ARG
+    assert lib.mfbd_plan_destroy(None) == _lib.MFBD_OK
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU behaviour")
+def test_no_cpu_fallback_without_gpu(lib):
+    d = _desc()
+    out = ctypes.c_void_p()
+    st = lib.mfbd_plan_create(ctypes.byref(out), ctypes.byref(d.desc), None)
+    assert st == _lib.MFBD_ERR_UNSUPPORTED
+    assert b"no CUDA device" in lib.mfbd_last_error()
+    assert out.value is None
+
+
+@pytest.mark.parametrize("diam,obs", [(32.0, 0.0), (28.0, 0.0), (36.0, 0.0), (21.4, 0.0), (33.0, 0.25)])
+def test_pupil_and_support_match_oracle_exactly(diam, obs):
+    mask, _, _, sup = mfbd.describe_object(0, 64, [diam], [5000.0], 4, 5, basis="zernike", obscuration=obs)
+    om = optics.pupil_mask(64, diam, obs)
+    assert np.array_equal(mask.astype(bool), om)
+    osup = optics.otf_support(om)[:, :33]
+    assert np.array_equal(sup.astype(bool), osup)
+
+
+def test_zernike_basis_matches_oracle():
+    _, bas, var, _ = mfbd.describe_object(0, 64, [28.0], [6563.0], 4, 20, basis="zernike")
+    ob = optics.zernike_basis(64, 28.0, range(2, 22))
+    assert np.abs(bas - ob).max() <= 4e-7 * np.abs(ob).max()
+    assert np.allclose(var, optics.mode_variances("zernike", 20), rtol=1e-12)
+
+
+@pytest.mark.parametrize("diam,m", [(28.0, 44), (36.0, 44), (32.0, 20)])
+def test_kl_basis_matches_oracle(diam, m):
+    _, bas, var, _ = mfbd.describe_object(0, 64, [diam], [6563.0], 4, m, basis="kl")
+    ob, ovar, _ = optics.kl_basis(64, diam, m)
+    assert np.allclose(var, ovar, rtol=1e-10)
+    assert np.abs(bas - ob).max() <= 1e-6 * np.abs(ob).max()
+
+
+def test_user_basis_is_passed_through():
+    g = np.random.default_rng(0)
+    ub = g.standard_normal((1, 3, 64, 64)).astype(np.float32)
+    _, bas, var, _ = mfbd.describe_object(0, 64, [30.0], [5000.0], 2, 3, basis="user", user_basis=ub)
+    assert np.array_equal(bas, ub[0])
+    assert np.all(var == 0)
+
+
+# ------------------------------------------ register FFTs run on the host
+
+def _host_fft(lib, kind, x, nout):
+    xin = np.ascontiguousarray(x, np.float32)
+    out = np.zeros(nout, np.float32)
+    assert lib.mfbd_test_fft_host(kind, xin.ctypes.data, out.ctypes.data) == 0
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_register_ffts_match_oracle(lib, seed):
+    g = np.random.default_rng(seed)
+    z = (g.standard_normal(64) + 1j * g.standard_normal(64)).astype(np.complex64)
+    zin = np.stack([z.real, z.imag], -1).ravel()
+    for kind, sign in ((0, -1), (1, +1)):
+        o = _host_fft(lib, kind, zin, 128)
+        ref = dft.fft_radix2(z.astype(np.complex128), sign=sign)
+        got = o[0::2] + 1j * o[1::2]
+        assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
+    o = _host_fft(lib, 4, zin[:64], 64)
+    ref = dft.fft_radix2(z[:32].astype(np.complex128))
+    assert np.abs(o[0::2] + 1j * o[1::2] - ref).max() <= 2e-6 * np.abs(ref).max()
+    r = g.standard_normal(64).astype(np.float32)
+    o = _host_fft(lib, 2, r, 66)
+    ref = dft.fft_radix2(r.astype(np.complex128))[:33]
+    assert np.abs(o[0::2] + 1j * o[1::2] - ref).max() <= 2e-6 * np.abs(ref).max()
+    # complex-to-real adjoint of a Hermitian half spectrum
+    img = g.standard_normal(64)
+    half = dft.fft_radix2(img.astype(np.complex128))[:33]
+    hin = np.stack([half.real, half.imag], -1).ravel()
+    o = _host_fft(lib, 3, hin, 64)
+    full = np.concatenate([half, np.conj(half[1:32][::-1])])
+    ref = dft.fft_radix2(full, sign=+1).real
+    assert np.abs(o - ref).max() <= 2e-6 * np.abs(ref).max()

@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (FP32 path): loss relative 1e-5 per patch; dL/da norm-wise 1e-4
+per patch; Wiener object norm-wise 1e-4 over the OTF support; OTF absolute
+2e-6 (H(0) = 1). The oracle sees exactly the rounded inputs the GPU gets
+(float32 coefficients, complex64 spectra).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import mfbd as omfbd
+from oracle import optics
+from tests import cases
+
+pytestmark = pytest.mark.gpu
+
+LOSS_RTOL = 1e-5
+GRAD_RTOL = 1e-4
+OBJ_RTOL = 1e-4
+
+
+def _plan_for(case, n_patches=None, full_spectrum=False, weights=None, **kw):
+    from paper_2505_10639_gb300.mfbd import Plan
+    s = case["setup"]
+    return Plan(case["n_pix"], n_patches if n_patches is not None else case["d"].shape[0],
+                list(case["diams"]), list(case["wavelengths"]), case["n_frames"], case["n_modes"],
+                basis=case["basis"], gamma=s.gamma,
+                weights=s.weights if weights is None else weights,
+                obscuration=case["obscuration"], full_spectrum=full_spectrum, **kw)
+
+
+def _inputs(case, full_spectrum=False):
+    a32 = case["a_eval"].astype(np.float32)
+    dfull = case["d"]
+    n = case["n_pix"]
+    if full_spectrum:
+        d32 = dfull.astype(np.complex64)
+        d_or = d32.astype(np.complex128)
+    else:
+        d32 = omfbd.half_spectrum(dfull).astype(np.complex64)
+        d_or = omfbd.full_from_half(d32.astype(np.complex128), n)
+    return a32, d32, d_or
+
+
+def _oracle(case, a32, d_or):
+    return omfbd.loss_object_grad(case["setup"], a32.astype(np.float64), d_or)
+
+
+def _check(case, loss, grad, obj, ref, full_spectrum=False, patches=None):
+    lo, oo, go = ref
+    patches = range(len(lo)) if patches is None else patches
+    n = case["n_pix"]
+    for i, p in enumerate(patches):
+        assert abs(loss[p] - lo[i]) <= LOSS_RTOL * abs(lo[i]), (p, loss[p], lo[i])
+        err = np.linalg.norm(grad[p] - go[i]) / np.linalg.norm(go[i])
+        assert err <= GRAD_RTOL, (p, err)
+        if obj is not None:
+            for k, mask in enumerate(case["setup"].masks):
+                supp = optics.otf_support(mask)
+                ofull = obj[p, k] if full_spectrum else omfbd.full_from_half(obj[p, k], n)
+                e = np.linalg.norm((ofull - oo[i][k])[supp]) / np.linalg.norm(oo[i][k][supp])
+                assert e <= OBJ_RTOL, (p, k, e)
+
+
+def _run_fused(plan, a32, d32, want_object=True):
+    a = torch.from_numpy(a32).cuda()
+    d = torch.from_numpy(d32).cuda()
+    loss, grad, obj = plan.loss_grad(a, d, want_object=want_object)
+    torch.cuda.synchronize()
+    return (loss.cpu().numpy(), grad.cpu().numpy(),
+            obj.cpu().numpy().astype(np.complex128) if obj is not None else None)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return cases.config1()
+
+
+@pytest.fixture(scope="module")
+def c2_slice():
+    # config-2 shapes: 2 objects (6563 A: 36 px pupil, 8542 A: 28 px), 12
+    # frames, 44 KL modes; three patches
+    return cases.make_case(diams=(36.0, 28.0), wavelengths=(6563.0, 8542.0), n_frames=12, n_modes=44,
+                           basis="kl", n_patches=3, seed=20250517)
+
+
+def test_config1_fused_loss_object_grad(c1):
+    a32, d32, d_or = _inputs(c1)
+    ref = _oracle(c1, a32, d_or)
+    plan = _plan_for(c1)
+    loss, grad, obj = _run_fused(plan, a32, d32)
+    _check(c1, loss, grad, obj, ref)
+
+
+def test_config1_otf(c1):
+    a32, _, _ = _inputs(c1)
+    plan = _plan_for(c1)
+    h = plan.otf(torch.from_numpy(a32).cuda()).cpu().numpy()
+    inter = omfbd.otf_patch(c1["setup"], a32[0].astype(np.float64))
+    href = omfbd.half_spectrum(inter[0]["H"])
+    assert np.abs(h[0, 0] - href).max() <= 2e-6
+
+
+def test_config2_slice_fused(c2_slice):
+    a32, d32, d_or = _inputs(c2_slice)
+    ref = _oracle(c2_slice, a32, d_or)
+    plan = _plan_for(c2_slice)
+    loss, grad, obj = _run_fused(plan, a32, d32)
+    _check(c2_slice, loss, grad, obj, ref)
+
+
+def test_split_forward_backward_equals_fused(c2_slice):
+    a32, d32, _ = _inputs(c2_slice)
+    plan = _plan_for(c2_slice)
+    lf, gf, of = _run_fused(plan, a32, d32)
+    a = torch.from_numpy(a32).cuda()
+    d = torch.from_numpy(d32).cuda()
+    loss, obj = plan.forward(a, d)
+    grad = plan.backward()
+    torch.cuda.synchronize()
+    assert np.array_equal(loss.cpu().numpy(), lf)
+    assert np.array_equal(grad.cpu().numpy(), gf)
+    assert np.array_equal(obj.cpu().numpy().astype(np.complex128), of)
+
+
+def test_full_spectrum_layout(c1):
+    a32, d32, d_or = _inputs(c1, full_spectrum=True)
+    ref = _oracle(c1, a32, d_or)
+    plan = _plan_for(c1, full_spectrum=True)
+    loss, grad, obj = _run_fused(plan, a32, d32)
+    _check(c1, loss, grad, obj, ref, full_spectrum=True)
+
+
+@pytest.mark.parametrize("variant", ["one_frame", "weights", "ragged_pupil", "obscured", "one_mode"])
+def test_edge_cases(variant):
+    kw = dict(n_frames=4, seed=31)
+    if variant == "one_frame":
+        kw.update(n_frames=1)
+    elif variant == "weights":
+        kw.update(weights=[[1.0, 0.0, 2.5, 0.3]])
+    elif variant == "ragged_pupil":
+        kw.update(diams=(21.4,), n_modes=9)
+    elif variant == "obscured":
+        kw.update(diams=(40.0,), obscuration=0.3)
+    elif variant == "one_mode":
+        kw.update(n_modes=1)
+    case = cases.make_case(**kw)
+    a32, d32, d_or = _inputs(case)
+    ref = _oracle(case, a32, d_or)
+    plan = _plan_for(case)
+    loss, grad, obj = _run_fused(plan, a32, d32)
+    _check(case, loss, grad, obj, ref)
+
+
+def test_zero_patches_is_a_noop():
+    from paper_2505_10639_gb300.mfbd import Plan
+    plan = Plan(64, 0, [32.0], [5000.0], 4, 5, basis="zernike", gamma=1e-3)
+    a = torch.zeros((0, 4, 5), device="cuda")
+    d = torch.zeros((0, 1, 4, 64, 33), dtype=torch.complex64, device="cuda")
+    loss, grad, _ = plan.loss_grad(a, d)
+    assert loss.numel() == 0 and grad.numel() == 0
+
+
+def test_more_patches_than_ctas_and_determinism(c2_slice):
+    """A ragged persistent schedule (P not a multiple of the CTA count,
+    several patches per CTA): every copy of a patch gives the same bits."""
+    a32, d32, d_or = _inputs(c2_slice)
+    ref = _oracle(c2_slice, a32, d_or)
+    reps = 107  # 321 patches
+    plan = _plan_for(c2_slice, n_patches=3 * reps)
+    assert plan.info()["ctas"] < 3 * reps
+    aa = np.tile(a32, (reps, 1, 1))
+    dd = np.tile(d32, (reps, 1, 1, 1, 1))
+    loss, grad, obj = _run_fused(plan, aa, dd)
+    loss2, grad2, _ = _run_fused(plan, aa, dd, want_object=False)
+    assert np.array_equal(loss, loss2) and np.array_equal(grad, grad2)
+    for r in range(reps):
+        assert np.array_equal(loss[3 * r:3 * r + 3], loss[:3])
+        assert np.array_equal(grad[3 * r:3 * r + 3], grad[:3])
+    _check(c2_slice, loss[:3], grad[:3], obj[:3], ref)
+
+
+def test_autograd_function(c1):
+    from paper_2505_10639_gb300.mfbd import momfbd_loss
+    a32, d32, _ = _inputs(c1)
+    plan = _plan_for(c1)
+    a = torch.from_numpy(a32).cuda().requires_grad_(True)
+    d = torch.from_numpy(d32).cuda()
+    loss = momfbd_loss(a, d, plan)
+    (3.0 * loss.sum()).backward()
+    _, g, _ = _run_fused(plan, a32, d32, want_object=False)
+    assert np.allclose(a.grad.cpu().numpy(), 3.0 * g, rtol=1e-6, atol=0)
+
+
+def test_gradient_central_differences_on_gpu(c1):
+    """dL/da of the CUDA path against central differences of its own loss
+    (FP32 internals: a 1e-2 rad step, 1e-2 relative agreement)."""
+    a32, d32, _ = _inputs(c1)
+    plan = _plan_for(c1)
+    _, g, _ = _run_fused(plan, a32, d32, want_object=False)
+    d = torch.from_numpy(d32).cuda()
+    idx = np.argsort(-np.abs(g[0]).ravel())[:6]
+    h = 1e-2
+    for flat in idx:
+        j, m = np.unravel_index(flat, g[0].shape)
+        vals = []
+        for sgn in (+1, -1):
+            a = a32.copy()
+            a[0, j, m] += sgn * h
+            loss, _ = plan.forward(torch.from_numpy(a).cuda(), d, want_object=False)
+            vals.append(loss.cpu().numpy()[0])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - g[0, j, m]) <= 1e-2 * abs(g[0, j, m]), (j, m, fd, g[0, j, m])
