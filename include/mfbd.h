@@ -158,6 +158,41 @@ int mfbd_plan_set_profiling(mfbd_plan_t plan, int enable, int max_launches);
  * reset != 0 the pool is emptied for reuse. Arrays may be NULL. */
 int mfbd_plan_read_profile(mfbd_plan_t plan, double* ms, long long* launches, int reset);
 
+/* Allocation-free variant of the fused kernel, for callers that cannot
+ * allocate device memory (a plugin whose host framework owns all device
+ * memory, code where the CUDA allocator is off limits, a fixed memory
+ * budget): such callers cannot create a plan, because mfbd_plan_create
+ * allocates workspaces. The paper has no counterpart; this is library
+ * plumbing. No plan is needed and nothing is allocated: the caller passes
+ * the inputs and outputs, and the kernel's working memory is one 16 MiB
+ * array compiled into the library, held by every GPU that loads it until
+ * the process exits.
+ *   desc        host: n_pix (64), n_patches, n_objects, n_frames, pupil
+ *               diameters, obscuration, gamma, frame weights and flags are
+ *               used; n_modes, basis, user_basis, wavelength and precision
+ *               are ignored (the wavefront is given as a phase).
+ *   phase       dev [K][P][J][N][N] float: phi_kpj on the full grid, radians
+ *               (read on pupil pixels only)
+ *   spectra     dev as in mfbd_forward
+ *   loss        dev [P] double, as in mfbd_forward
+ *   object      dev as in mfbd_forward, or NULL
+ *   grad_phase  dev [K][P][J][N][N] float: dL/dphi (0 outside the pupil)
+ * Limits: n_frames <= 989 per call (MFBD_ERR_INVALID_ARG beyond that, as
+ * the per-CTA block of J x N x (N/2+1) complex64 must fit); large n_frames
+ * also lowers the number of CTAs that fit in the array.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any
+ * stream capture. Each call uploads its small constants with one
+ * cudaMemcpyAsync from pageable host memory (which may wait for the
+ * stream's earlier work) and clears grad_phase with cudaMemsetAsync.
+ * Calls are serialised on the host, but every call shares the one array
+ * and it keeps the last call's contents: calls whose work overlaps on the
+ * GPU (other streams, other host threads) race and give wrong results.
+ * Nothing in the array needs to start at zero: each element a call reads
+ * is written earlier in the same call. */
+int mfbd_phase_loss_grad_noalloc(const mfbd_plan_desc* desc, const float* phase, const void* spectra,
+                                 double* loss, void* object, float* grad_phase, void* stream);
+
 /* Static description of a status code (never NULL). */
 const char* mfbd_status_string(int status);
 

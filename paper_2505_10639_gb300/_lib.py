@@ -72,6 +72,7 @@ _SIGNATURES = {
     "mfbd_test_fft_host": (ctypes.c_int, [ctypes.c_int, _VP, _VP]),
     "mfbd_plan_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "mfbd_plan_read_profile": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
+    "mfbd_phase_loss_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(PlanDesc), _VP, _VP, _VP, _VP, _VP, _VP]),
 }
 
 _lib = None

@@ -18,15 +18,17 @@ using namespace mfbd_dev;
 
 namespace {
 
-thread_local std::string g_last_error = "no error";
+thread_local char g_last_error[512] = "no error";
 
-int fail(int status, const std::string& why) {
-    g_last_error = why;
+int fail(int status, const char* why) {
+    std::snprintf(g_last_error, sizeof g_last_error, "%s", why);
     return status;
 }
 
+int fail(int status, const std::string& why) { return fail(status, why.c_str()); }
+
 int cuda_fail(cudaError_t e, const char* where) {
-    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    std::snprintf(g_last_error, sizeof g_last_error, "%s: %s", where, cudaGetErrorString(e));
     return MFBD_ERR_CUDA;
 }
 
@@ -155,11 +157,15 @@ FusedParams fused_params(const mfbd_plan* p, const void* spectra, double* loss, 
     f.spec_ld = (p->flags & MFBD_FLAG_FULL_SPECTRUM) ? p->N : p->N / 2 + 1;
     f.loss = loss;
     f.object = static_cast<float2*>(object);
+    f.scratch_ring = 0;
     for (int k = 0; k < p->K; ++k) {
         f.obj[k].W = p->obj[k].W;
         f.obj[k].x0 = p->obj[k].x0;
         f.obj[k].inv_z = p->obj[k].inv_z;
         f.obj[k].phi_off = p->obj[k].phi_off;
+        f.obj[k].phi_unit = (long long)p->obj[k].W * p->obj[k].W;
+        f.obj[k].phi_org = 0;
+        f.obj[k].phi_ld = p->obj[k].W;
         f.obj[k].mask = p->obj[k].d_mask;
         f.obj[k].supp = p->obj[k].d_supp;
     }
@@ -239,6 +245,11 @@ int run_fused(mfbd_plan_t p, int mode, const void* spectra, double* loss, void* 
 
 }  // namespace
 
+namespace mfbd_dev {
+int set_error(int status, const char* why) { return fail(status, why); }
+int set_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+}  // namespace mfbd_dev
+
 extern "C" {
 
 const char* mfbd_status_string(int status) {
@@ -254,7 +265,7 @@ const char* mfbd_status_string(int status) {
     }
 }
 
-const char* mfbd_last_error(void) { return g_last_error.c_str(); }
+const char* mfbd_last_error(void) { return g_last_error; }
 
 int mfbd_describe_object(const mfbd_plan_desc* desc, int object, unsigned char* mask, float* basis,
                          double* variance, unsigned char* support) {

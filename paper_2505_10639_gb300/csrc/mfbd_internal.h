@@ -19,6 +19,9 @@ struct ObjParams {
     int x0;                  // first row/column of the box
     float inv_z;             // 1 / (N^2 n_pup): PSF normalisation (Parseval)
     long long phi_off;       // float offset of this object's phase block
+    long long phi_unit;      // floats per (patch, frame) phase image: W*W (box) or N*N (full grid)
+    int phi_org;             // offset of the box's first pixel in that image: 0 or x0*N + x0
+    int phi_ld;              // row stride of that image: W or N
     const uint64_t* mask;    // [W] rows, bit t = pupil pixel at box column t
     const uint64_t* supp;    // [N] rows, bit kx = OTF support (kx <= N/2)
 };
@@ -34,6 +37,7 @@ struct FusedParams {
     int spec_ld;              // row stride of D and O in complex elements (33 or 64)
     double* loss;             // [P]
     float2* object;           // [P][K][N][spec_ld] or null
+    int scratch_ring;         // 0: gscr is [P][K][J][half]; 1: [gridDim][J][half], reused per object
     ObjParams obj[kMaxObjects];
 };
 
@@ -58,5 +62,9 @@ cudaError_t launch_grad_gemm(const float* gphi, int U, int npix, const float* ba
                              float scale, int accumulate, float* grad, cudaStream_t s);
 
 int max_ctas_per_sm(const FusedGeometry& g);
+
+// Record an error for mfbd_last_error() (fixed-size buffer, no allocation).
+int set_error(int status, const char* why);
+int set_cuda_error(cudaError_t e, const char* where);
 
 }  // namespace mfbd_dev

@@ -56,7 +56,7 @@ __device__ __forceinline__ void pupil_columns(const ObjParams& ob, const float* 
     const int W = ob.W, x0 = ob.x0;
     for (int yy = 0; yy < W; ++yy) {
         float2 v = make_float2(0.f, 0.f);
-        if ((smask[yy] >> t) & 1ull) v = pupil_value(phi[yy * W + t]);
+        if ((smask[yy] >> t) & 1ull) v = pupil_value(phi[yy * ob.phi_ld + t]);
         X[(x0 + yy) * xs + t] = v;
     }
     float2 col[kN];
@@ -80,7 +80,7 @@ __device__ __forceinline__ void field_row(const ObjParams& ob, const float2* X, 
 __device__ void forward_unit(const FusedParams& prm, const ObjParams& ob, long long unit, float2* hout,
                              const uint64_t* smask, const uint64_t* ssupp, float2* X, float2* Y, int xs,
                              int t, int slot) {
-    const float* phi = prm.phi + ob.phi_off + unit * (long long)(ob.W * ob.W);
+    const float* phi = prm.phi + ob.phi_off + unit * ob.phi_unit + ob.phi_org;
     if (t < ob.W) pupil_columns(ob, phi, smask, X, xs, t);
     slot_sync(slot);
     {
@@ -134,8 +134,8 @@ __device__ void forward_unit(const FusedParams& prm, const ObjParams& ob, long l
 __device__ void backward_unit(const FusedParams& prm, const ObjParams& ob, long long unit, const float2* gin,
                               const uint64_t* smask, float2* X, float2* Y, int xs, int t, int slot) {
     const int W = ob.W, x0 = ob.x0;
-    const float* phi = prm.phi + ob.phi_off + unit * (long long)(W * W);
-    float* gphi = prm.gphi + ob.phi_off + unit * (long long)(W * W);
+    const float* phi = prm.phi + ob.phi_off + unit * ob.phi_unit + ob.phi_org;
+    float* gphi = prm.gphi + ob.phi_off + unit * ob.phi_unit + ob.phi_org;
     // B1: inverse column transforms of G (columns 0 and 32 packed)
     if (t < 32) {
         float2 col[kN];
@@ -204,11 +204,11 @@ __device__ void backward_unit(const FusedParams& prm, const ObjParams& ob, long 
         for (int yy = 0; yy < W; ++yy) {
             float gv = 0.f;
             if ((smask[yy] >> t) & 1ull) {
-                const float2 pv = pupil_value(phi[yy * W + t]);
+                const float2 pv = pupil_value(phi[yy * ob.phi_ld + t]);
                 const float2 gp = X[(x0 + yy) * xs + t];
                 gv = 2.0f * (pv.x * gp.y - pv.y * gp.x);
             }
-            gphi[yy * W + t] = gv;
+            gphi[yy * ob.phi_ld + t] = gv;
         }
     }
 }
@@ -221,12 +221,11 @@ __device__ void backward_unit(const FusedParams& prm, const ObjParams& ob, long 
 // r_j in FP64. With several frames this triggers at DC and little else.
 constexpr float kCancel = 1e-3f;
 
-__device__ double reduce_object(const FusedParams& prm, int p, int k, const uint64_t* ssupp) {
+__device__ double reduce_object(const FusedParams& prm, int p, int k, const uint64_t* ssupp, float2* hbase) {
     const int J = prm.J;
     const size_t unit0 = ((size_t)p * prm.K + k) * J;
     const size_t dstride = (size_t)kN * prm.spec_ld;
     const float2* dbase = prm.spectra + unit0 * dstride;
-    float2* hbase = prm.gscr + unit0 * (size_t)kHalf;
     const float* w = prm.weights + (size_t)k * J;
     double acc = 0.0;
     for (int f = threadIdx.x; f < kHalf; f += blockDim.x) {
@@ -341,22 +340,23 @@ __global__ void __launch_bounds__(kThreadsMax, 1)
             }
             __syncthreads();
             const size_t unit0 = ((size_t)p * prm.K + k) * J;
+            float2* hscr = prm.scratch_ring ? prm.gscr + (size_t)blockIdx.x * J * kHalf : prm.gscr + unit0 * kHalf;
             if (mode != MODE_BWD) {
                 for (int j0 = 0; j0 < J; j0 += slots) {
                     const int j = j0 + slot;
                     if (j < J)
-                        forward_unit(prm, ob, (long long)p * J + j, prm.gscr + (unit0 + j) * kHalf, smask, ssupp,
+                        forward_unit(prm, ob, (long long)p * J + j, hscr + (size_t)j * kHalf, smask, ssupp,
                                      X, Y, xs, t, slot);
                 }
                 __syncthreads();
-                if (mode != MODE_OTF) lacc += reduce_object(prm, p, k, ssupp);
+                if (mode != MODE_OTF) lacc += reduce_object(prm, p, k, ssupp, hscr);
                 __syncthreads();
             }
             if (mode == MODE_BWD || mode == MODE_FUSED) {
                 for (int j0 = 0; j0 < J; j0 += slots) {
                     const int j = j0 + slot;
                     if (j < J)
-                        backward_unit(prm, ob, (long long)p * J + j, prm.gscr + (unit0 + j) * kHalf, smask, X, Y,
+                        backward_unit(prm, ob, (long long)p * J + j, hscr + (size_t)j * kHalf, smask, X, Y,
                                       xs, t, slot);
                 }
             }

@@ -193,6 +193,35 @@ class Plan:
             pass
 
 
+def phase_loss_grad_noalloc(phase, spectra, n_patches, diams, n_frames, gamma, weights=None,
+                            obscuration=0.0, full_spectrum=False, loss=None, grad_phase=None, obj=None,
+                            want_object=False, stream=None):
+    """mfbd_phase_loss_grad_noalloc: loss [P], dL/dphi [K, P, J, 64, 64] (and
+    optionally the object) from full-grid phases [K, P, J, 64, 64], without a
+    plan and without any device allocation by the library (the output
+    tensors are the caller's)."""
+    lib = _lib.load()
+    k = len(diams)
+    d = _Desc(64, n_patches, diams, [1.0] * k, n_frames, 1, "zernike", gamma, weights, obscuration, None,
+              "fp32", full_spectrum)
+    dev = phase.device
+    if loss is None:
+        loss = torch.empty(n_patches, dtype=torch.float64, device=dev)
+    if grad_phase is None:
+        grad_phase = torch.empty_like(phase)
+    cols = 64 if full_spectrum else 33
+    if obj is None and want_object:
+        obj = torch.empty((n_patches, k, 64, cols), dtype=torch.complex64, device=dev)
+    shape = (k, n_patches, n_frames, 64, 64)
+    _lib.check(lib.mfbd_phase_loss_grad_noalloc(
+        ctypes.byref(d.desc), _dev(phase, torch.float32, shape, "phase"),
+        _dev(spectra, torch.complex64, (n_patches, k, n_frames, 64, cols), "spectra"),
+        _dev(loss, torch.float64, (n_patches,), "loss"),
+        _dev(obj, torch.complex64, (n_patches, k, 64, cols), "object") if obj is not None else None,
+        _dev(grad_phase, torch.float32, shape, "grad_phase"), _stream(stream)), "mfbd_phase_loss_grad_noalloc")
+    return loss, grad_phase, obj
+
+
 class MOMFBDLoss(torch.autograd.Function):
     """loss[P] = MOMFBD loss of every patch as a differentiable function of
     the modal coefficients (spectra are data: no gradient)."""

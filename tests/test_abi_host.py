@@ -161,3 +161,20 @@ def test_register_ffts_match_oracle(lib, seed):
     full = np.concatenate([half, np.conj(half[1:32][::-1])])
     ref = dft.fft_radix2(full, sign=+1).real
     assert np.abs(o - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
+def test_noalloc_entry_point_checks_arguments_on_host(lib):
+    """Argument checks of mfbd_phase_loss_grad_noalloc run before any CUDA
+    call: bad descriptors and frame counts beyond its fixed workspace are
+    rejected with MFBD_ERR_INVALID_ARG."""
+    f = lib.mfbd_phase_loss_grad_noalloc
+    assert f(None, None, None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
+    d = _desc(n_frames=990)
+    assert f(ctypes.byref(d.desc), None, None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
+    assert b"static workspace" in lib.mfbd_last_error()
+    d = _desc(gamma=-1.0)
+    assert f(ctypes.byref(d.desc), None, None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
+    d = _desc(n_patches=0)
+    assert f(ctypes.byref(d.desc), None, None, None, None, None, None) == _lib.MFBD_OK
+    d = _desc()
+    assert f(ctypes.byref(d.desc), None, None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
