@@ -177,9 +177,10 @@ int mfbd_plan_read_profile(mfbd_plan_t plan, double* ms, long long* launches, in
  *   loss        dev [P] double, as in mfbd_forward
  *   object      dev as in mfbd_forward, or NULL
  *   grad_phase  dev [K][P][J][N][N] float: dL/dphi (0 outside the pupil)
- * Limits: n_frames <= 989 per call (MFBD_ERR_INVALID_ARG beyond that, as
- * the per-CTA block of J x N x (N/2+1) complex64 must fit); large n_frames
- * also lowers the number of CTAs that fit in the array.
+ * Limits: n_frames <= 336 per call (MFBD_ERR_INVALID_ARG beyond that: one
+ * CTA's block of J x (N x (N/2+1) + N x N) complex64 must fit); the number
+ * of CTAs is what fits in the array (28 at 12 frames), so this path runs on
+ * part of the GPU.
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it; make that first call before any
  * stream capture. Each call uploads its small constants with one

@@ -52,7 +52,10 @@ struct mfbd_plan {
     float* d_weights = nullptr;
     float* d_phi = nullptr;
     float* d_gphi = nullptr;
-    float2* d_gscr = nullptr;
+    float2* d_gscr = nullptr;   // per unit [P][K][J][N][N/2+1] (split forward/backward)
+    float2* d_pscr = nullptr;   // per unit [P][K][J][N*N] field
+    float2* d_gring = nullptr;  // per CTA [ctas][J][N][N/2+1] (fused call)
+    float2* d_pring = nullptr;  // per CTA [ctas][J][N*N]
     long long phi_floats = 0;
     size_t workspace = 0;
     FusedGeometry geo{};
@@ -142,7 +145,8 @@ void release(mfbd_plan* p) {
     p->allocations.clear();
 }
 
-FusedParams fused_params(const mfbd_plan* p, const void* spectra, double* loss, void* object, float2* gscr) {
+FusedParams fused_params(const mfbd_plan* p, const void* spectra, double* loss, void* object, float2* gscr,
+                         float2* pscr, int ring) {
     FusedParams f{};
     f.P = p->P;
     f.K = p->K;
@@ -153,11 +157,12 @@ FusedParams fused_params(const mfbd_plan* p, const void* spectra, double* loss, 
     f.phi = p->d_phi;
     f.gphi = p->d_gphi;
     f.gscr = gscr;
+    f.pscr = pscr;
     f.spectra = static_cast<const float2*>(spectra);
     f.spec_ld = (p->flags & MFBD_FLAG_FULL_SPECTRUM) ? p->N : p->N / 2 + 1;
     f.loss = loss;
     f.object = static_cast<float2*>(object);
-    f.scratch_ring = 0;
+    f.scratch_ring = ring;
     for (int k = 0; k < p->K; ++k) {
         f.obj[k].W = p->obj[k].W;
         f.obj[k].x0 = p->obj[k].x0;
@@ -232,7 +237,9 @@ int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s) {
 
 int run_fused(mfbd_plan_t p, int mode, const void* spectra, double* loss, void* object, float2* gscr,
               cudaStream_t s) {
-    FusedParams f = fused_params(p, spectra, loss, object, gscr);
+    FusedParams f = mode == MODE_FUSED ? fused_params(p, spectra, loss, object, p->d_gring, p->d_pring, 1)
+                    : mode == MODE_OTF ? fused_params(p, spectra, loss, object, gscr, nullptr, 0)
+                                       : fused_params(p, spectra, loss, object, p->d_gscr, p->d_pscr, 0);
     const int pi = prof_begin(p, 1, s);
     cudaError_t e = launch_fused(f, mode, p->geo, p->ctas, s);
     prof_end(p, pi, s);
@@ -389,11 +396,14 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
         if ((st = dev_alloc(p, &p->d_phi, (size_t)phi_floats))) throw st;
         if ((st = dev_alloc(p, &p->d_gphi, (size_t)phi_floats))) throw st;
         if ((st = dev_alloc(p, &p->d_gscr, (size_t)p->P * p->K * p->J * kHalf))) throw st;
+        if ((st = dev_alloc(p, &p->d_pscr, (size_t)p->P * p->K * p->J * n * n))) throw st;
 
         p->geo = fused_geometry(max_box);
         int per_sm = max_ctas_per_sm(p->geo);
         if (per_sm < 1) throw fail(MFBD_ERR_UNSUPPORTED, "fused kernel does not fit on this device");
         p->ctas = std::min(std::max(p->P, 1), prop.multiProcessorCount * per_sm);
+        if ((st = dev_alloc(p, &p->d_gring, (size_t)p->ctas * p->J * kHalf))) throw st;
+        if ((st = dev_alloc(p, &p->d_pring, (size_t)p->ctas * p->J * n * n))) throw st;
         if ((e = cudaStreamSynchronize(s))) throw cuda_fail(e, "plan upload");
     } catch (int status) {
         release(p);

@@ -33,19 +33,20 @@ struct FusedParams {
     const float* phi;         // phases, per object [P*J][W*W] at phi_off
     float* gphi;              // dL/dphi, same layout
     float2* gscr;             // [P][K][J][N][N/2+1]: OTF, then dL/dconj(H)
+    float2* pscr;             // [P][K][J][N x N]: field p = F P, stored [x][y] (null: OTF mode)
     const float2* spectra;    // D
     int spec_ld;              // row stride of D and O in complex elements (33 or 64)
     double* loss;             // [P]
     float2* object;           // [P][K][N][spec_ld] or null
-    int scratch_ring;         // 0: gscr is [P][K][J][half]; 1: [gridDim][J][half], reused per object
+    int scratch_ring;         // 0: gscr/pscr per unit [P][K][J]; 1: per CTA [gridDim][J], reused per object
     ObjParams obj[kMaxObjects];
 };
 
-// Fused kernel geometry for the largest box of a plan.
+// Fused kernel geometry for the largest pupil box of a plan.
 struct FusedGeometry {
-    int slots;          // frames per CTA in flight (64 threads each)
+    int slots;          // warps per CTA; each warp works on one frame at a time
     size_t smem_bytes;  // dynamic shared memory per CTA
-    int xs;             // row stride of the X exchange buffer (complex)
+    int xs;             // row stride (complex elements) of a warp's exchange buffer
 };
 
 FusedGeometry fused_geometry(int max_box);

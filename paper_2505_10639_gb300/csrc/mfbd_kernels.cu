@@ -1,29 +1,37 @@
-// sm_103a kernels of the MOMFBD hot path (N = 64 patches).
+// sm_103a fused kernel of the MOMFBD hot path (N = 64 patches).
 //
-// Fused kernel (one persistent CTA per patch at a time, S frame slots of 64
-// threads each; one thread owns one 64-point line in registers):
-//   forward per frame (Sec. 3.1, Eqs. 20-22):
-//     F1  pupil columns:  P = A exp(i phi) on the pupil's bounding box,
-//                         column FFTs (only the W box columns are nonzero)
-//     F2  rows:           row FFTs -> field p; s = |p|^2 / (N^2 n_pup)
-//                         (Parseval: sum |p|^2 = N^2 n_pup for a phase-only
-//                         pupil); real-to-complex row FFTs of s
-//     F3  columns:        column FFTs -> H = F s on the half spectrum;
-//                         H(0) := 1, H := 0 outside the exact OTF support
-//   reduction per object (Sec. 2.2.1, Eqs. 11-12), per frequency u:
-//     N = sum_j w D conj(H) (FP32), Q = sum_j w |H|^2 + gamma (FP64),
-//     O = N / Q, t(u) = sum_j w |D - O H|^2 + gamma |O|^2 (equal to the
-//     summand of Eq. 12 at O = N/Q, without its cancellation), loss summed
-//     over u in FP64; adjoint seed G_j = dL/dconj(H_j) = -w conj(O)(D - O H)
-//     with G(0) := 0 and G := 0 outside the support (exact: H(0) == 1 and
-//     H == 0 there for every wavefront)
-//   backward per frame:
-//     B1/B2  C2R of G:    g_s = 2 Re F^H G,  g_q = g_s / (N^2 n_pup)
-//     F1r/F2r             recompute p, G_p = g_q p, row F^H
-//     B3                  column F^H on the box columns -> G_P,
-//                         dL/dphi = 2 Im(conj(P) G_P) on pupil pixels
-// The modal projections phi = c B a and dL/da = sum_k c_k B_k^T dL/dphi are
-// separate GEMM kernels.
+// Persistent CTAs of 6 warps work on one patch at a time; inside a CTA each
+// warp carries one frame (unit) through a sequence of passes over its own
+// 64 x es complex exchange buffer in shared memory, synchronising with
+// __syncwarp only. In every pass a lane owns one whole 64-point line in
+// registers and transforms it with the single register FFT instance of the
+// kernel (adjoint transforms use F^H x = conj(F conj x)).
+//
+// The pupil's W x W bounding box is placed at the origin of the grid: the
+// PSF |F P|^2 does not depend on where the pupil sits, so every quantity
+// that leaves the kernel is unchanged, and the nonzero rows and columns of
+// the pupil transforms are [0, W).
+//
+// Forward passes (Sec. 3.1, Eqs. 20-22):
+//   PUPIL  W columns: P = A exp(i phi) -> column FFT
+//   FIELD  rows: p = F P (stored for the adjoint), s = |p|^2 / (N^2 n_pup)
+//          (Parseval: sum |p|^2 = N^2 n_pup for a phase-only pupil); a third
+//          round transforms two real rows of s packed as one complex line
+//   OTF    columns: H = F s on the half spectrum (columns 0 and N/2 packed),
+//          H(0) := 1, H := 0 outside the exact OTF support
+// Frame reduction per object (Sec. 2.2.1, Eqs. 11-12), all warps:
+//   N = sum_j w D conj(H), Q = sum_j w |H|^2 + gamma, O = N / Q,
+//   t(u) = sum_j w |D - O H|^2 + gamma |O|^2 (the summand of Eq. 12 at
+//   O = N/Q without its cancellation), loss summed over u in FP64,
+//   G_j = dL/dconj(H_j) = -w conj(O)(D - O H) with G(0) := 0 and G := 0
+//   outside the support; frequencies whose residual cancels are redone
+//   in FP64.
+// Adjoint passes:
+//   SEED   columns: F^H along ky of G (columns 0 and N/2 packed)
+//   C2R    rows: g = F^H G (two Hermitian rows packed as one line),
+//          g_q = 2 g / (N^2 n_pup); then per row G_p = g_q p -> row F^H,
+//          keeping the W box columns
+//   ADJ    W columns: column F^H -> G_P, dL/dphi = 2 Im(conj(P) G_P)
 #include "mfbd_internal.h"
 #include "fft_reg.cuh"
 
@@ -37,187 +45,294 @@ using fftreg::csub;
 
 namespace {
 
-constexpr int kMaxSlots = 6;
-constexpr int kThreadsMax = 64 * kMaxSlots;
+constexpr int kWarps = 6;
+constexpr int kThreads = 32 * kWarps;
 
-__device__ __forceinline__ void slot_sync(int slot) {
-    asm volatile("bar.sync %0, 64;" ::"r"(slot + 1) : "memory");
-}
+enum Pass : int { P_PUPIL = 0, P_FIELD = 1, P_OTF = 2, P_SEED = 3, P_C2R = 4, P_ADJ = 5, P_END = 6 };
 
-__device__ __forceinline__ float2 pupil_value(float ph) {
+// exp(i phi): reduction to [-pi, pi] by a two-constant Cody-Waite step
+// (2 pi = 6.2831854820251465 - 1.7484556e-7), then the SFU sine/cosine.
+__device__ __forceinline__ float2 expi(float ph) {
+    const float n = rintf(ph * 0.159154943091895336f);
+    float r = fmaf(n, -6.28318548202514648f, ph);
+    r = fmaf(n, 1.74845553e-7f, r);
     float s, c;
-    sincosf(ph, &s, &c);
+    __sincosf(r, &s, &c);
     return make_float2(c, s);
 }
 
-// F1 / F1r: column t of the pupil's box -> column FFT -> X[:, t]
-__device__ __forceinline__ void pupil_columns(const ObjParams& ob, const float* phi, const uint64_t* smask,
-                                              float2* X, int xs, int t) {
-    const int W = ob.W, x0 = ob.x0;
-    for (int yy = 0; yy < W; ++yy) {
-        float2 v = make_float2(0.f, 0.f);
-        if ((smask[yy] >> t) & 1ull) v = pupil_value(phi[yy * ob.phi_ld + t]);
-        X[(x0 + yy) * xs + t] = v;
-    }
-    float2 col[kN];
-#pragma unroll
-    for (int y = 0; y < kN; ++y)
-        col[y] = ((unsigned)(y - x0) < (unsigned)W) ? X[y * xs + t] : make_float2(0.f, 0.f);
-    fftreg::fft<kN, -1>(col);
-#pragma unroll
-    for (int y = 0; y < kN; ++y) X[y * xs + t] = col[y];
-}
+struct Unit {
+    const float* phi;  // first box pixel of this unit's phase image
+    float* gphi;       // same for dL/dphi
+    float2* h;         // [N][N/2+1]: H (forward) then G (adjoint)
+    float2* pf;        // field p, [x][y]; null: not stored
+    int W, ld;
+    float inv_z;
+};
 
-// row t of the field p = F P (box columns of X are the only nonzero inputs)
-__device__ __forceinline__ void field_row(const ObjParams& ob, const float2* X, int xs, int t, float2 (&row)[kN]) {
-    const int W = ob.W, x0 = ob.x0;
-#pragma unroll
-    for (int x = 0; x < kN; ++x)
-        row[x] = ((unsigned)(x - x0) < (unsigned)W) ? X[t * xs + (x - x0)] : make_float2(0.f, 0.f);
-    fftreg::fft<kN, -1>(row);
-}
-
-__device__ void forward_unit(const FusedParams& prm, const ObjParams& ob, long long unit, float2* hout,
-                             const uint64_t* smask, const uint64_t* ssupp, float2* X, float2* Y, int xs,
-                             int t, int slot) {
-    const float* phi = prm.phi + ob.phi_off + unit * ob.phi_unit + ob.phi_org;
-    if (t < ob.W) pupil_columns(ob, phi, smask, X, xs, t);
-    slot_sync(slot);
-    {
-        float2 row[kN];
-        field_row(ob, X, xs, t, row);
-        float s[kN];
-#pragma unroll
-        for (int x = 0; x < kN; ++x) s[x] = (row[x].x * row[x].x + row[x].y * row[x].y) * ob.inv_z;
-        float2 sh[kNH];
-        fftreg::rfft<kN>(s, sh);
-#pragma unroll
-        for (int kx = 0; kx < kNH; ++kx) Y[t * kNH + kx] = sh[kx];
-    }
-    slot_sync(slot);
-    if (t < 32) {
-        float2 col[kN];
-        if (t == 0) {
-#pragma unroll
-            for (int ky = 0; ky < kN; ++ky) col[ky] = make_float2(Y[ky * kNH].x, Y[ky * kNH + 32].x);
-        } else {
-#pragma unroll
-            for (int ky = 0; ky < kN; ++ky) col[ky] = Y[ky * kNH + t];
-        }
-        fftreg::fft<kN, -1>(col);
-        if (t == 0) {
-            // split the transform of (real col 0) + i (real col 32)
-#pragma unroll
-            for (int ky = 0; ky < kN; ++ky) {
-                const float2 a = col[ky];
-                const float2 b = cconj(col[(kN - ky) % kN]);
-                float2 h0 = cscale(cadd(a, b), 0.5f);
-                const float2 d = cscale(csub(a, b), 0.5f);
-                float2 h32 = make_float2(d.y, -d.x);
-                if (!((ssupp[ky] >> 0) & 1ull)) h0 = make_float2(0.f, 0.f);
-                if (!((ssupp[ky] >> 32) & 1ull)) h32 = make_float2(0.f, 0.f);
-                if (ky == 0) h0 = make_float2(1.f, 0.f);
-                hout[ky * kNH] = h0;
-                hout[ky * kNH + 32] = h32;
-            }
-        } else {
-#pragma unroll
-            for (int ky = 0; ky < kN; ++ky) {
-                float2 h = col[ky];
-                if (!((ssupp[ky] >> t) & 1ull)) h = make_float2(0.f, 0.f);
-                hout[ky * kNH + t] = h;
-            }
-        }
+__device__ __forceinline__ int pass_rounds(int pass, int W) {
+    switch (pass) {
+        case P_PUPIL:
+        case P_ADJ: return (W + 31) >> 5;
+        case P_FIELD:
+        case P_C2R: return 3;
+        default: return 1;
     }
 }
 
-__device__ void backward_unit(const FusedParams& prm, const ObjParams& ob, long long unit, const float2* gin,
-                              const uint64_t* smask, float2* X, float2* Y, int xs, int t, int slot) {
-    const int W = ob.W, x0 = ob.x0;
-    const float* phi = prm.phi + ob.phi_off + unit * ob.phi_unit + ob.phi_org;
-    float* gphi = prm.gphi + ob.phi_off + unit * ob.phi_unit + ob.phi_org;
-    // B1: inverse column transforms of G (columns 0 and 32 packed)
-    if (t < 32) {
-        float2 col[kN];
-        if (t == 0) {
+__device__ __forceinline__ bool bit(uint64_t w, int b) { return (w >> b) & 1ull; }
+
+// Compiler-only fence: keeps the loads of a long gather from being hoisted
+// all at once (which would need registers for every loaded value).
+#define MFBD_CHUNK_FENCE(i) \
+    if (((i) & 7) == 7) asm volatile("" ::: "memory")
+
+// Runs passes [first, last) of one unit on the calling warp.
+__device__ __forceinline__ void run_passes(int first, int last, const volatile Unit* su, float2* __restrict__ E,
+                                           int es, const uint64_t* __restrict__ smask,
+                                           const uint64_t* __restrict__ ssupp) {
+    const int lane = threadIdx.x & 31;
+#define U_W (su->W)
+#define U_LD (su->ld)
+#define U_INVZ (su->inv_z)
+#define U_PHI ((const float*)su->phi)
+#define U_GPHI ((float*)su->gphi)
+#define U_H ((float2*)su->h)
+#define U_PF ((float2*)su->pf)
+    const int W = U_W;
+#pragma unroll 1
+    for (int pass = first; pass < last; ++pass) {
+        const int nr = pass_rounds(pass, W);
+#pragma unroll 1
+        for (int r = 0; r < nr; ++r) {
+            float2 v[kN];
+            const bool adj = pass >= P_SEED;
+            // ------------------------------------------------------ load
+            switch (pass) {
+                case P_PUPIL: {
+                    const int c = lane + 32 * r;
+                    if (c < W) {
+                        for (int yy = 0; yy < W; ++yy) {
+                            float2 pv = make_float2(0.f, 0.f);
+                            if (bit(smask[yy], c)) pv = expi(U_PHI[yy * U_LD + c]);
+                            E[yy * es + c] = pv;
+                        }
+                    }
 #pragma unroll
-            for (int ky = 0; ky < kN; ++ky) {
-                const float2 a = gin[ky * kNH], b = gin[ky * kNH + 32];
-                col[ky] = make_float2(a.x - b.y, a.y + b.x);
+                    for (int y = 0; y < kN; ++y)
+                        v[y] = (c < W && y < W) ? E[y * es + c] : make_float2(0.f, 0.f);
+                    break;
+                }
+                case P_FIELD: {
+                    if (r < 2) {
+                        const int y = lane + 32 * r;
+#pragma unroll
+                        for (int x = 0; x < kN; ++x) v[x] = (x < W) ? E[y * es + x] : make_float2(0.f, 0.f);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < kN / 2; ++i) {
+                            const float2 a = E[lane * es + i], b = E[(lane + 32) * es + i];
+                            v[2 * i] = make_float2(a.x, b.x);
+                            v[2 * i + 1] = make_float2(a.y, b.y);
+                        }
+                    }
+                    break;
+                }
+                case P_OTF: {  // lane 0: the packed real columns kx = 0, N/2
+#pragma unroll
+                    for (int ky = 0; ky < kN; ++ky) v[ky] = E[ky * es + lane];
+                    break;
+                }
+                case P_SEED: {  // lane 0: columns 0 and N/2 packed as a + i b
+#pragma unroll
+                    for (int ky = 0; ky < kN; ++ky) {
+                        const float2 a = U_H[ky * kNH + lane];
+                        const float2 b = lane == 0 ? U_H[ky * kNH + 32] : make_float2(0.f, 0.f);
+                        v[ky] = make_float2(a.x - b.y, -(a.y + b.x));  // conj(a + i b)
+                        MFBD_CHUNK_FENCE(ky);
+                    }
+                    break;
+                }
+                case P_C2R: {
+                    if (r == 0) {
+                        // rows lane and lane+32: Hermitian extension T[k] = conj T[N-k]
+#pragma unroll
+                        for (int k = 0; k < kN; ++k) {
+                            float2 a, b;
+                            if (k == 0) {
+                                a = make_float2(E[lane * es].x, 0.f);
+                                b = make_float2(E[(lane + 32) * es].x, 0.f);
+                            } else if (k == kN / 2) {
+                                a = make_float2(E[lane * es].y, 0.f);
+                                b = make_float2(E[(lane + 32) * es].y, 0.f);
+                            } else if (k < kN / 2) {
+                                a = E[lane * es + k];
+                                b = E[(lane + 32) * es + k];
+                            } else {
+                                a = cconj(E[lane * es + (kN - k)]);
+                                b = cconj(E[(lane + 32) * es + (kN - k)]);
+                            }
+                            v[k] = make_float2(a.x - b.y, -(a.y + b.x));  // conj(a + i b)
+                            MFBD_CHUNK_FENCE(k);
+                        }
+                    } else {
+                        const int y = lane + 32 * (r - 1);
+#pragma unroll
+                        for (int i = 0; i < kN / 2; ++i) {
+                            const float2 g = E[y * es + i];  // g_q at x = 2i, 2i+1
+                            const float2 p0 = U_PF[(2 * i) * kN + y], p1 = U_PF[(2 * i + 1) * kN + y];
+                            v[2 * i] = make_float2(g.x * p0.x, -g.x * p0.y);
+                            v[2 * i + 1] = make_float2(g.y * p1.x, -g.y * p1.y);
+                            MFBD_CHUNK_FENCE(i);
+                        }
+                    }
+                    break;
+                }
+                default: {  // P_ADJ
+                    const int c = lane + 32 * r;
+                    const int cc = c < W ? c : 0;  // inactive lanes transform a dummy column
+#pragma unroll
+                    for (int y = 0; y < kN; ++y) v[y] = cconj(E[y * es + cc]);
+                    break;
+                }
             }
-        } else {
+            // --------------------------------------------------- transform
+            fftreg::fft<kN, -1>(v);
+            if (adj) {
 #pragma unroll
-            for (int ky = 0; ky < kN; ++ky) col[ky] = gin[ky * kNH + t];
-        }
-        fftreg::fft<kN, +1>(col);
-        if (t == 0) {
-#pragma unroll
-            for (int y = 0; y < kN; ++y) {
-                Y[y * kNH] = make_float2(col[y].x, 0.f);
-                Y[y * kNH + 32] = make_float2(col[y].y, 0.f);
+                for (int i = 0; i < kN; ++i) v[i].y = -v[i].y;
             }
-        } else {
+            // ----------------------------------------------------- store
+            switch (pass) {
+                case P_PUPIL: {
+                    const int c = lane + 32 * r;
+                    if (c < W) {
 #pragma unroll
-            for (int y = 0; y < kN; ++y) Y[y * kNH + t] = col[y];
-        }
-    }
-    slot_sync(slot);
-    // B2: complex-to-real row transforms -> g_q = 2 Re F^H G / (N^2 n_pup),
-    // written over the thread's own row of Y as float pairs
-    {
-        float2 xh[kNH];
+                        for (int ky = 0; ky < kN; ++ky) E[ky * es + c] = v[ky];
+                    }
+                    break;
+                }
+                case P_FIELD: {
+                    if (r < 2) {
+                        const int y = lane + 32 * r;
+                        if (U_PF) {
 #pragma unroll
-        for (int kx = 0; kx < kNH; ++kx) xh[kx] = Y[t * kNH + kx];
-        float g[kN];
-        fftreg::irfft<kN>(xh, g);
-        const float sc = 2.0f * ob.inv_z;
+                            for (int x = 0; x < kN; ++x) U_PF[x * kN + y] = v[x];
+                        }
 #pragma unroll
-        for (int i = 0; i < kN / 2; ++i) Y[t * kNH + i] = make_float2(g[2 * i] * sc, g[2 * i + 1] * sc);
-    }
-    // F1r: recompute the pupil column transforms
-    if (t < W) pupil_columns(ob, phi, smask, X, xs, t);
-    slot_sync(slot);
-    // F2r: field row, G_p = g_q p, inverse row transform, keep box columns
-    {
-        float2 row[kN];
-        field_row(ob, X, xs, t, row);
+                        for (int i = 0; i < kN / 2; ++i)
+                            E[y * es + i] = make_float2(
+                                (v[2 * i].x * v[2 * i].x + v[2 * i].y * v[2 * i].y) * U_INVZ,
+                                (v[2 * i + 1].x * v[2 * i + 1].x + v[2 * i + 1].y * v[2 * i + 1].y) * U_INVZ);
+                    } else {
+                        // split the transform of s_lane + i s_(lane+32); the real
+                        // columns kx = 0 and N/2 share slot 0 as (S[0], S[N/2])
 #pragma unroll
-        for (int i = 0; i < kN / 2; ++i) {
-            const float2 q = Y[t * kNH + i];
-            row[2 * i] = cscale(row[2 * i], q.x);
-            row[2 * i + 1] = cscale(row[2 * i + 1], q.y);
-        }
-        fftreg::fft<kN, +1>(row);
+                        for (int k = 0; k <= kN / 2; ++k) {
+                            const float2 z = v[k];
+                            const float2 zc = cconj(v[(kN - k) % kN]);
+                            const float2 a = cscale(cadd(z, zc), 0.5f);
+                            const float2 d = cscale(csub(z, zc), 0.5f);
+                            const float2 b = make_float2(d.y, -d.x);
+                            if (k == 0) {
+                                E[lane * es] = make_float2(a.x, 0.f);
+                                E[(lane + 32) * es] = make_float2(b.x, 0.f);
+                            } else if (k == kN / 2) {
+                                E[lane * es].y = a.x;
+                                E[(lane + 32) * es].y = b.x;
+                            } else {
+                                E[lane * es + k] = a;
+                                E[(lane + 32) * es + k] = b;
+                            }
+                        }
+                    }
+                    break;
+                }
+                case P_OTF: {
 #pragma unroll
-        for (int x = 0; x < kN; ++x)
-            if ((unsigned)(x - x0) < (unsigned)W) X[t * xs + (x - x0)] = row[x];
-    }
-    slot_sync(slot);
-    // B3: inverse column transforms on box columns -> dL/dphi on the pupil
-    if (t < W) {
-        float2 col[kN];
+                    for (int ky = 0; ky < kN; ++ky)
+                        U_H[ky * kNH + lane] = (lane == 0 || bit(ssupp[ky], lane)) ? v[ky] : make_float2(0.f, 0.f);
+                    __syncwarp();
+                    // lane 0 stored Z = F(s_col0 + i s_colN/2); split it into both columns
+                    float2 zz[2], zm[2];
 #pragma unroll
-        for (int ky = 0; ky < kN; ++ky) col[ky] = X[ky * xs + t];
-        fftreg::fft<kN, +1>(col);
+                    for (int i = 0; i < 2; ++i) {
+                        const int ky = lane + 32 * i;
+                        zz[i] = U_H[ky * kNH];
+                        zm[i] = cconj(U_H[((kN - ky) & (kN - 1)) * kNH]);
+                    }
+                    __syncwarp();
 #pragma unroll
-        for (int y = 0; y < kN; ++y) X[y * xs + t] = col[y];
-        for (int yy = 0; yy < W; ++yy) {
-            float gv = 0.f;
-            if ((smask[yy] >> t) & 1ull) {
-                const float2 pv = pupil_value(phi[yy * ob.phi_ld + t]);
-                const float2 gp = X[(x0 + yy) * xs + t];
-                gv = 2.0f * (pv.x * gp.y - pv.y * gp.x);
+                    for (int i = 0; i < 2; ++i) {
+                        const int ky = lane + 32 * i;
+                        float2 h0 = cscale(cadd(zz[i], zm[i]), 0.5f);
+                        const float2 d = cscale(csub(zz[i], zm[i]), 0.5f);
+                        float2 h32 = make_float2(d.y, -d.x);
+                        if (!bit(ssupp[ky], 0)) h0 = make_float2(0.f, 0.f);
+                        if (!bit(ssupp[ky], 32)) h32 = make_float2(0.f, 0.f);
+                        if (ky == 0) h0 = make_float2(1.f, 0.f);
+                        U_H[ky * kNH] = h0;
+                        U_H[ky * kNH + 32] = h32;
+                    }
+                    break;
+                }
+                case P_SEED: {  // lane 0 keeps (T_0, T_N/2), both real, packed
+#pragma unroll
+                    for (int y = 0; y < kN; ++y) E[y * es + lane] = v[y];
+                    break;
+                }
+                case P_C2R: {
+                    if (r == 0) {
+                        const float sc = 2.0f * U_INVZ;
+#pragma unroll
+                        for (int i = 0; i < kN / 2; ++i) {
+                            E[lane * es + i] = make_float2(v[2 * i].x * sc, v[2 * i + 1].x * sc);
+                            E[(lane + 32) * es + i] = make_float2(v[2 * i].y * sc, v[2 * i + 1].y * sc);
+                        }
+                    } else {
+                        const int y = lane + 32 * (r - 1);
+#pragma unroll
+                        for (int x = 0; x < kN; ++x)
+                            if (x < W) E[y * es + x] = v[x];
+                    }
+                    break;
+                }
+                default: {  // P_ADJ
+                    const int c = lane + 32 * r;
+                    if (c < W) {
+#pragma unroll
+                        for (int y = 0; y < kN; ++y)
+                            if (y < W) E[y * es + c] = v[y];
+                        for (int yy = 0; yy < W; ++yy) {
+                            float gv = 0.f;
+                            if (bit(smask[yy], c)) {
+                                const float2 pv = expi(U_PHI[yy * U_LD + c]);
+                                const float2 gp = E[yy * es + c];
+                                gv = 2.0f * (pv.x * gp.y - pv.y * gp.x);
+                            }
+                            U_GPHI[yy * U_LD + c] = gv;
+                        }
+                    }
+                    break;
+                }
             }
-            gphi[yy * ob.phi_ld + t] = gv;
         }
+        __syncwarp();
     }
+#undef U_W
+#undef U_LD
+#undef U_INVZ
+#undef U_PHI
+#undef U_GPHI
+#undef U_H
+#undef U_PF
 }
 
 // Per-object frame reduction: O, loss terms, adjoint seeds G_j (over H_j).
 // The residual r_j = D_j - O H_j is formed in FP32. Where the fit leaves
 // little residual energy (sum_j w|r_j|^2 < kCancel sum_j w|D_j|^2, estimated
 // from E - |N|^2/Q), r_j cancels badly in FP32 (for J = 1, r = D gamma / Q
-// everywhere the OTF is large), so that frequency is redone with N, O and
+// everywhere the OTF is large), so that frequency is redone with N, Q, O and
 // r_j in FP64. With several frames this triggers at DC and little else.
 constexpr float kCancel = 1e-3f;
 
@@ -227,6 +342,7 @@ __device__ double reduce_object(const FusedParams& prm, int p, int k, const uint
     const size_t dstride = (size_t)kN * prm.spec_ld;
     const float2* dbase = prm.spectra + unit0 * dstride;
     const float* w = prm.weights + (size_t)k * J;
+    const float gam = (float)prm.gamma;
     double acc = 0.0;
     for (int f = threadIdx.x; f < kHalf; f += blockDim.x) {
         const int ky = f / kNH, kx = f - ky * kNH;
@@ -234,8 +350,7 @@ __device__ double reduce_object(const FusedParams& prm, int p, int k, const uint
         const float2* dp = dbase + doff;
         float2* hp = hbase + f;
         float2 num = make_float2(0.f, 0.f);
-        float e = 0.f;
-        double q = 0.0;
+        float e = 0.f, q = 0.f;
 #pragma unroll 4
         for (int j = 0; j < J; ++j) {
             const float2 d = dp[(size_t)j * dstride];
@@ -244,12 +359,12 @@ __device__ double reduce_object(const FusedParams& prm, int p, int k, const uint
             num.x += wj * (d.x * h.x + d.y * h.y);
             num.y += wj * (d.y * h.x - d.x * h.y);
             e += wj * (d.x * d.x + d.y * d.y);
-            q += (double)wj * ((double)h.x * h.x + (double)h.y * h.y);
+            q += wj * (h.x * h.x + h.y * h.y);
         }
-        q += prm.gamma;
-        const float invq = (float)(1.0 / q);
+        q += gam;
+        const float invq = 1.0f / q;
         float2 o = cscale(num, invq);
-        const bool seed = (f != 0) && ((ssupp[ky] >> kx) & 1ull);
+        const bool seed = (f != 0) && bit(ssupp[ky], kx);
         const float t_est = e - (num.x * num.x + num.y * num.y) * invq;
         float t;
         if (!(t_est < kCancel * e)) {
@@ -263,17 +378,18 @@ __device__ double reduce_object(const FusedParams& prm, int p, int k, const uint
                 tsum += wj * (r.x * r.x + r.y * r.y);
                 hp[(size_t)j * kHalf] = seed ? cscale(cmul(cconj(o), r), -wj) : make_float2(0.f, 0.f);
             }
-            t = tsum + (float)prm.gamma * (o.x * o.x + o.y * o.y);
+            t = tsum + gam * (o.x * o.x + o.y * o.y);
         } else {
-            double nx = 0.0, ny = 0.0;
+            double nx = 0.0, ny = 0.0, qd = prm.gamma;
             for (int j = 0; j < J; ++j) {
                 const float2 d = dp[(size_t)j * dstride];
                 const float2 h = hp[(size_t)j * kHalf];
                 const double wj = w[j];
                 nx += wj * ((double)d.x * h.x + (double)d.y * h.y);
                 ny += wj * ((double)d.y * h.x - (double)d.x * h.y);
+                qd += wj * ((double)h.x * h.x + (double)h.y * h.y);
             }
-            const double ox = nx / q, oy = ny / q;
+            const double ox = nx / qd, oy = ny / qd;
             double tsum = 0.0;
             for (int j = 0; j < J; ++j) {
                 const float2 d = dp[(size_t)j * dstride];
@@ -282,7 +398,6 @@ __device__ double reduce_object(const FusedParams& prm, int p, int k, const uint
                 const double rx = (double)d.x - (ox * h.x - oy * h.y);
                 const double ry = (double)d.y - (ox * h.y + oy * h.x);
                 tsum += wj * (rx * rx + ry * ry);
-                // G = -w conj(O) r
                 hp[(size_t)j * kHalf] =
                     seed ? make_float2((float)(-wj * (ox * rx + oy * ry)), (float)(-wj * (ox * ry - oy * rx)))
                          : make_float2(0.f, 0.f);
@@ -290,8 +405,7 @@ __device__ double reduce_object(const FusedParams& prm, int p, int k, const uint
             t = (float)(tsum + prm.gamma * (ox * ox + oy * oy));
             o = make_float2((float)ox, (float)oy);
         }
-        const double wt = (kx == 0 || kx == kN / 2) ? 1.0 : 2.0;
-        acc += wt * (double)t;
+        acc += ((kx == 0 || kx == kN / 2) ? 1.0 : 2.0) * (double)t;
         if (prm.object) {
             float2* ob = prm.object + ((size_t)p * prm.K + k) * dstride;
             ob[doff] = o;
@@ -315,19 +429,25 @@ __device__ double block_sum(double v, double* sred) {
     return tot;
 }
 
-__global__ void __launch_bounds__(kThreadsMax, 1)
-    mfbd_fused_kernel(const FusedParams prm, int mode, int xs) {
+__device__ __forceinline__ void prefetch_l2(const void* ptr, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(ptr)), "r"(bytes)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 2) mfbd_fused_kernel(const FusedParams prm, int mode, int es) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t smask[kN];
     __shared__ uint64_t ssupp[kN];
     __shared__ double sred[32];
+    __shared__ Unit sunit[kWarps];
     const int tid = threadIdx.x;
-    const int slot = tid >> 6, t = tid & 63;
-    const int slots = blockDim.x >> 6;
-    const size_t slot_bytes = (size_t)kN * xs * sizeof(float2) + (size_t)kN * kNH * sizeof(float2);
-    float2* X = reinterpret_cast<float2*>(smem + slot * slot_bytes);
-    float2* Y = X + kN * xs;
+    const int warp = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    float2* E = reinterpret_cast<float2*>(smem) + (size_t)warp * kN * es;
     const int J = prm.J;
+    const bool fwd = mode != MODE_BWD;
+    const bool red = mode == MODE_FWD || mode == MODE_FUSED;
+    const bool bwd = mode == MODE_BWD || mode == MODE_FUSED;
 
     for (int p = blockIdx.x; p < prm.P; p += gridDim.x) {
         double lacc = 0.0;
@@ -338,125 +458,49 @@ __global__ void __launch_bounds__(kThreadsMax, 1)
                 smask[tid] = tid < ob.W ? ob.mask[tid] : 0ull;
                 ssupp[tid] = ob.supp[tid];
             }
-            __syncthreads();
             const size_t unit0 = ((size_t)p * prm.K + k) * J;
-            float2* hscr = prm.scratch_ring ? prm.gscr + (size_t)blockIdx.x * J * kHalf : prm.gscr + unit0 * kHalf;
-            if (mode != MODE_BWD) {
-                for (int j0 = 0; j0 < J; j0 += slots) {
-                    const int j = j0 + slot;
-                    if (j < J)
-                        forward_unit(prm, ob, (long long)p * J + j, hscr + (size_t)j * kHalf, smask, ssupp,
-                                     X, Y, xs, t, slot);
-                }
-                __syncthreads();
-                if (mode != MODE_OTF) lacc += reduce_object(prm, p, k, ssupp, hscr);
-                __syncthreads();
+            if (red && tid == 0) {
+                const size_t bytes = (size_t)kN * prm.spec_ld * sizeof(float2);
+                const float2* d0 = prm.spectra + unit0 * (size_t)kN * prm.spec_ld;
+                if ((reinterpret_cast<uintptr_t>(d0) & 15) == 0)
+                    for (int j = 0; j < J; ++j) prefetch_l2(d0 + (size_t)j * kN * prm.spec_ld, (unsigned)bytes);
             }
-            if (mode == MODE_BWD || mode == MODE_FUSED) {
-                for (int j0 = 0; j0 < J; j0 += slots) {
-                    const int j = j0 + slot;
-                    if (j < J)
-                        backward_unit(prm, ob, (long long)p * J + j, hscr + (size_t)j * kHalf, smask, X, Y,
-                                      xs, t, slot);
+            __syncthreads();
+            const size_t slot0 = prm.scratch_ring ? (size_t)blockIdx.x * J : unit0;
+            float2* hscr = prm.gscr + slot0 * kHalf;
+            float2* pscr = prm.pscr ? prm.pscr + slot0 * (size_t)(kN * kN) : nullptr;
+            volatile Unit* su = &sunit[warp];
+            // stage 0: forward of every frame; 1: frame reduction; 2: adjoint
+            const int stage_end = bwd ? 2 : (red ? 1 : 0);
+#pragma unroll 1
+            for (int stage = fwd ? 0 : 2; stage <= stage_end; ++stage) {
+                if (stage == 1) {
+                    if (red) lacc += reduce_object(prm, p, k, ssupp, hscr);
+                    __syncthreads();
+                    continue;
                 }
+                const bool back = stage == 2;
+                for (int j = warp; j < J; j += nwarps) {
+                    const long long unit = (long long)p * J + j;
+                    __syncwarp();
+                    if ((tid & 31) == 0) {
+                        su->W = ob.W;
+                        su->ld = ob.phi_ld;
+                        su->inv_z = ob.inv_z;
+                        su->phi = prm.phi + ob.phi_off + unit * ob.phi_unit + ob.phi_org;
+                        su->gphi = back ? prm.gphi + ob.phi_off + unit * ob.phi_unit + ob.phi_org : nullptr;
+                        su->h = hscr + (size_t)j * kHalf;
+                        su->pf = pscr ? pscr + (size_t)j * kN * kN : nullptr;
+                    }
+                    __syncwarp();
+                    run_passes(back ? P_SEED : P_PUPIL, back ? P_END : P_OTF + 1, su, E, es, smask, ssupp);
+                }
+                __syncthreads();
             }
         }
-        if (mode == MODE_FWD || mode == MODE_FUSED) {
+        if (red) {
             const double tot = block_sum(lacc, sred);
             if (tid == 0) prm.loss[p] = tot;
-        }
-    }
-}
-
-// ---------------------------------------------------------------- GEMMs
-
-// phase[u][i] = scale * sum_m a[u][m] basis[m][i]; 64x64 tiles, 4x4 per thread
-__global__ void __launch_bounds__(256) phase_gemm_kernel(const float* __restrict__ a, int U, int M,
-                                                         const float* __restrict__ basis, int npix, float scale,
-                                                         float* __restrict__ out) {
-    __shared__ float As[16][68];
-    __shared__ float Bs[16][68];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int u0 = blockIdx.y * 64, i0 = blockIdx.x * 64;
-    float acc[4][4] = {};
-    for (int m0 = 0; m0 < M; m0 += 16) {
-        for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
-            const int uu = idx >> 4, mm = idx & 15;
-            const int u = u0 + uu, m = m0 + mm;
-            As[mm][uu] = (u < U && m < M) ? a[(size_t)u * M + m] : 0.f;
-            const int ii = idx & 63, mb = idx >> 6;
-            const int i = i0 + ii, mbm = m0 + mb;
-            Bs[mb][ii] = (i < npix && mbm < M) ? basis[(size_t)mbm * npix + i] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int mm = 0; mm < 16; ++mm) {
-            float ar[4], br[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) ar[r] = As[mm][ty * 4 + r];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) br[c] = Bs[mm][tx * 4 + c];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(ar[r], br[c], acc[r][c]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int u = u0 + ty * 4 + r;
-        if (u >= U) continue;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int i = i0 + tx * 4 + c;
-            if (i < npix) out[(size_t)u * npix + i] = scale * acc[r][c];
-        }
-    }
-}
-
-// grad[u][m] (+)= scale * sum_i gphi[u][i] basis[m][i]
-__global__ void __launch_bounds__(256) grad_gemm_kernel(const float* __restrict__ gphi, int U, int npix,
-                                                        const float* __restrict__ basis, int M, float scale,
-                                                        int accumulate, float* __restrict__ grad) {
-    __shared__ float As[16][68];
-    __shared__ float Bs[16][68];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int u0 = blockIdx.y * 64, m0 = blockIdx.x * 64;
-    float acc[4][4] = {};
-    for (int i0 = 0; i0 < npix; i0 += 16) {
-        for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
-            const int rr = idx >> 4, ii = idx & 15;
-            const int u = u0 + rr, m = m0 + rr, i = i0 + ii;
-            As[ii][rr] = (u < U && i < npix) ? gphi[(size_t)u * npix + i] : 0.f;
-            Bs[ii][rr] = (m < M && i < npix) ? basis[(size_t)m * npix + i] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ii = 0; ii < 16; ++ii) {
-            float ar[4], br[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) ar[r] = As[ii][ty * 4 + r];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) br[c] = Bs[ii][tx * 4 + c];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(ar[r], br[c], acc[r][c]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int u = u0 + ty * 4 + r;
-        if (u >= U) continue;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int m = m0 + tx * 4 + c;
-            if (m >= M) continue;
-            float v = scale * acc[r][c];
-            if (accumulate) v += grad[(size_t)u * M + m];
-            grad[(size_t)u * M + m] = v;
         }
     }
 }
@@ -465,13 +509,10 @@ __global__ void __launch_bounds__(256) grad_gemm_kernel(const float* __restrict_
 
 FusedGeometry fused_geometry(int max_box) {
     FusedGeometry g;
-    g.xs = max_box | 1;
-    const size_t slot_bytes = (size_t)kN * g.xs * sizeof(float2) + (size_t)kN * kNH * sizeof(float2);
-    int slots = (int)((216u * 1024u) / slot_bytes);
-    if (slots > kMaxSlots) slots = kMaxSlots;
-    if (slots < 1) slots = 1;
-    g.slots = slots;
-    g.smem_bytes = slot_bytes * slots;
+    const int es = max_box > kNH ? max_box : kNH;
+    g.xs = es | 1;
+    g.slots = kWarps;
+    g.smem_bytes = (size_t)kWarps * kN * g.xs * sizeof(float2);
     return g;
 }
 
@@ -480,7 +521,7 @@ int max_ctas_per_sm(const FusedGeometry& g) {
     if (cudaFuncSetAttribute(mfbd_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)g.smem_bytes) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mfbd_fused_kernel, g.slots * 64, g.smem_bytes) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mfbd_fused_kernel, g.slots * 32, g.smem_bytes) !=
         cudaSuccess)
         return 0;
     return n;
@@ -491,23 +532,7 @@ cudaError_t launch_fused(const FusedParams& prm, int mode, const FusedGeometry& 
     cudaError_t e = cudaFuncSetAttribute(mfbd_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)g.smem_bytes);
     if (e != cudaSuccess) return e;
-    mfbd_fused_kernel<<<ctas, g.slots * 64, g.smem_bytes, s>>>(prm, mode, g.xs);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_phase_gemm(const float* a, int U, int M, const float* basis, int npix, float scale,
-                              float* phase, cudaStream_t s) {
-    if (U == 0) return cudaSuccess;
-    dim3 grid((npix + 63) / 64, (U + 63) / 64);
-    phase_gemm_kernel<<<grid, 256, 0, s>>>(a, U, M, basis, npix, scale, phase);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_grad_gemm(const float* gphi, int U, int npix, const float* basis, int M, float scale,
-                             int accumulate, float* grad, cudaStream_t s) {
-    if (U == 0) return cudaSuccess;
-    dim3 grid((M + 63) / 64, (U + 63) / 64);
-    grad_gemm_kernel<<<grid, 256, 0, s>>>(gphi, U, npix, basis, M, scale, accumulate, grad);
+    mfbd_fused_kernel<<<ctas, g.slots * 32, g.smem_bytes, s>>>(prm, mode, g.xs);
     return cudaGetLastError();
 }
 

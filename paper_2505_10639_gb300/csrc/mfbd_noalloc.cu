@@ -21,8 +21,9 @@
 using namespace mfbd_dev;
 
 // 16 MiB per device: 64 KiB of per-call constants (pupil and OTF-support
-// bit rows, frame weights) followed by the adjoint-seed ring of the fused
-// kernel (one [J][N][N/2+1] complex64 block per CTA).
+// bit rows, frame weights) followed by the fused kernel's per-CTA blocks
+// (for each CTA: [J][N][N/2+1] complex64 adjoint seeds and [J][N][N]
+// complex64 fields).
 static __device__ __align__(256) unsigned char g_static_workspace[(size_t)16 << 20];
 
 namespace {
@@ -115,10 +116,10 @@ extern "C" int mfbd_phase_loss_grad_noalloc(const mfbd_plan_desc* desc, const fl
     int st = check_desc(desc);
     if (st != MFBD_OK) return st;
     const int P = desc->n_patches, K = desc->n_objects, J = desc->n_frames;
-    const size_t ring_per_cta = (size_t)J * kHalf * sizeof(float2);
+    const size_t ring_per_cta = (size_t)J * (kHalf + kN * kN) * sizeof(float2);
     if (ring_per_cta > kStaticBytes - kConstBytes)
         return set_error(MFBD_ERR_INVALID_ARG,
-                                       "n_frames exceeds the static workspace (at most 989 frames per call)");
+                         "n_frames exceeds the static workspace (at most 336 frames per call)");
     if (P == 0) return MFBD_OK;
     if (!phase || !spectra || !loss || !grad_phase)
         return set_error(MFBD_ERR_INVALID_ARG, "phase, spectra, loss and grad_phase are required");
@@ -191,7 +192,7 @@ extern "C" int mfbd_phase_loss_grad_noalloc(const mfbd_plan_desc* desc, const fl
     f.weights = reinterpret_cast<const float*>(base + kBitsBytes);
     f.phi = phase;
     f.gphi = grad_phase;
-    f.gscr = reinterpret_cast<float2*>(base + kConstBytes);
+    const size_t ring_ctas = (kStaticBytes - kConstBytes) / ring_per_cta;
     f.spectra = static_cast<const float2*>(spectra);
     f.spec_ld = (desc->flags & MFBD_FLAG_FULL_SPECTRUM) ? kN : kN / 2 + 1;
     f.loss = loss;
@@ -201,10 +202,11 @@ extern "C" int mfbd_phase_loss_grad_noalloc(const mfbd_plan_desc* desc, const fl
     const FusedGeometry g = fused_geometry(max_box);
     const int per_sm = max_ctas_per_sm(g);
     if (per_sm < 1) return set_error(MFBD_ERR_UNSUPPORTED, "fused kernel does not fit on this device");
-    const size_t ring_ctas = (kStaticBytes - kConstBytes) / ring_per_cta;
     size_t ctas = (size_t)sms * per_sm;
     if (ctas > ring_ctas) ctas = ring_ctas;
     if (ctas > (size_t)P) ctas = (size_t)P;
+    f.gscr = reinterpret_cast<float2*>(base + kConstBytes);
+    f.pscr = f.gscr + ctas * J * kHalf;
     if ((e = launch_fused(f, MODE_FUSED, g, (int)ctas, s)) != cudaSuccess)
         return set_cuda_error(e, "fused kernel");
     return MFBD_OK;

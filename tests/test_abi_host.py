@@ -169,7 +169,7 @@ def test_noalloc_entry_point_checks_arguments_on_host(lib):
     rejected with MFBD_ERR_INVALID_ARG."""
     f = lib.mfbd_phase_loss_grad_noalloc
     assert f(None, None, None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
-    d = _desc(n_frames=990)
+    d = _desc(n_frames=337)
     assert f(ctypes.byref(d.desc), None, None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
     assert b"static workspace" in lib.mfbd_last_error()
     d = _desc(gamma=-1.0)
