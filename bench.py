@@ -180,19 +180,25 @@ class ClockSampler:
 
 # ------------------------------------------------------------ roofline
 
-def fused_flops_per_unit(n_pix, npup):
-    """Algorithmic FP32 flops of the fused kernel per (patch, object, frame):
-    four 2-D transforms at 5 N^2 log2(N^2) (complex) or half that (real):
-    pupil->field (complex), PSF->OTF (real), adjoint OTF->PSF (real),
-    adjoint field->pupil (complex); plus the pointwise work: PSF 3 N^2,
-    frame reduction / loss / adjoint seed 32 per half-spectrum frequency,
-    g_q scaling N^2, G_p = g_q p 2 N^2, dL/dphi 4 per pupil pixel."""
+def pass_flops_per_unit(n_pix, npup):
+    """Algorithmic FP32 flops per (patch, object, frame) of the two pass
+    kernels, with 2-D transforms counted at 5 N^2 log2(N^2) (complex) or half
+    that (real):
+      forward: pupil -> field (complex) + PSF -> OTF (real) + PSF 3 N^2;
+      adjoint: OTF seed -> PSF (real) + field -> pupil (complex)
+               + g_q scaling N^2 + G_p = g_q p 2 N^2 + dL/dphi 4 n_pup."""
     n2 = n_pix * n_pix
     c2 = 5.0 * n2 * math.log2(n2)
-    fft = 2 * c2 + 2 * (c2 / 2)
-    half = n_pix * (n_pix // 2 + 1)
-    pointwise = 3 * n2 + 32 * half + n2 + 2 * n2 + 4 * npup
-    return fft + pointwise
+    fwd = c2 + c2 / 2 + 3 * n2
+    adj = c2 / 2 + c2 + 3 * n2 + 4 * npup
+    return fwd, adj
+
+
+def reduction_bytes_per_unit(n_pix, n_frames, spec_cols):
+    """Algorithmic bytes per unit of the frame reduction: D read, H read,
+    G written (complex64 half spectra), object written once per J frames."""
+    half = n_pix * (n_pix // 2 + 1) * 8
+    return n_pix * spec_cols * 8 + 2 * half + half / n_frames
 
 
 def measured_peaks():
@@ -289,7 +295,7 @@ def run_gpu(args, rank, local_rank, world):
         raise RuntimeError("non-finite loss")
 
     clocks = ClockSampler(local_rank)
-    plan.set_profiling(True, max_launches=8 * (args.steps + 2) * (2 * plan.n_objects + 1))
+    plan.set_profiling(True, max_launches=8 * (args.steps + 2) * (2 * plan.n_objects + 3))
     plan.read_profile(reset=True)
     if world > 1:
         dist.barrier()
@@ -361,17 +367,41 @@ def run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, 
 def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
     import torch
     local_rank = dist_env()[1]
-    # roofline of the dominant (fused) kernel
+    # roofline: every kernel against its bound; the dominant one is reported
     npup = info["pupil_pixels"]
-    flops_launch = sum(fused_flops_per_unit(w["n_pix"], npup[k]) * w["n_patches"] * w["n_frames"]
-                       for k in range(len(npup)))
-    fused_ms, fused_n = prof["fused"]
-    fused_avg = fused_ms / max(1, fused_n)
-    achieved = flops_launch / (fused_avg * 1e-3) / 1e12
+    per_obj = [pass_flops_per_unit(w["n_pix"], npup[k]) for k in range(len(npup))]
+    units_obj = w["n_patches"] * w["n_frames"]
+    fwd_flops = sum(f for f, _ in per_obj) * units_obj
+    adj_flops = sum(a for _, a in per_obj) * units_obj
+    red_bytes = reduction_bytes_per_unit(w["n_pix"], w["n_frames"], w["n_pix"] // 2 + 1) * units_of(w)
     peaks = measured_peaks()
     n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    peak = fp32_peak_tflops(n_sm, sm_max)
+    alu_peak = fp32_peak_tflops(n_sm, sm_max)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+
+    def per_launch(kind):
+        ms_, n_ = prof[kind]
+        return ms_ / max(1, n_)
+
+    kernels = {}
+    for name, kind, work in (("forward_passes", "forward", fwd_flops), ("adjoint_passes", "adjoint", adj_flops)):
+        t = per_launch(kind)
+        a = work / (t * 1e-3) / 1e12 if t > 0 else 0.0
+        kernels[name] = {"bound": "alu", "ms": t, "achieved": a, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": a / alu_peak, "work_per_launch": work}
+    t = per_launch("reduction")
+    a = red_bytes / (t * 1e-3) / 1e9 if t > 0 else 0.0
+    kernels["reduction"] = {"bound": "hbm", "ms": t, "achieved": a, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": a / hbm_peak, "work_per_launch": red_bytes}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    dk = kernels[dom]
+    roofline = {"bound": dk["bound"], "kernel": dom, "achieved": dk["achieved"], "peak": dk["peak"],
+                "unit": dk["unit"], "frac": dk["frac"], "traffic": None,
+                "peak_basis": ("FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock)"
+                               % (n_sm, FP32_LANES_PER_SM, sm_max)) if dk["bound"] == "alu"
+                else "HBM copy bandwidth of MEASURED_PEAKS.json",
+                "work_per_launch": dk["work_per_launch"], "kernel_ms": dk["ms"]}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -384,11 +414,8 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
                    "l2": "inputs larger than L2 (%.0f MB spectra)" % (units_of(w) * 64 * 33 * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": e2e,
-        "roofline": {"bound": "alu", "kernel": "mfbd_fused_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "peak_basis": "FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock)"
-                                   % (n_sm, FP32_LANES_PER_SM, sm_max),
-                     "flops_per_launch": flops_launch, "kernel_ms": fused_avg},
+        "roofline": roofline,
+        "kernels": kernels,
         "kernels_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in prof.items()},
         "gpu_launches": int(sum(v[1] for v in prof.values())),
         "clocks": clk,

@@ -153,9 +153,11 @@ int mfbd_describe_object(const mfbd_plan_desc* desc, int object, unsigned char* 
 int mfbd_plan_set_profiling(mfbd_plan_t plan, int enable, int max_launches);
 
 /* Waits for the recorded events, then returns the summed device time in ms
- * and the launch count of each kernel kind: [0] modal phase projection,
- * [1] fused OTF/loss/adjoint kernel, [2] modal adjoint projection. With
- * reset != 0 the pool is emptied for reuse. Arrays may be NULL. */
+ * and the launch count of each kernel kind, arrays of 5: [0] modal phase
+ * projection, [1] forward passes (pupil -> OTF), [2] frame reduction (loss,
+ * object, adjoint seeds), [3] adjoint passes (-> dL/dphi), [4] modal adjoint
+ * projection. With reset != 0 the pool is emptied for reuse. Arrays may be
+ * NULL. */
 int mfbd_plan_read_profile(mfbd_plan_t plan, double* ms, long long* launches, int reset);
 
 /* Allocation-free variant of the fused kernel, for callers that cannot
@@ -177,10 +179,11 @@ int mfbd_plan_read_profile(mfbd_plan_t plan, double* ms, long long* launches, in
  *   loss        dev [P] double, as in mfbd_forward
  *   object      dev as in mfbd_forward, or NULL
  *   grad_phase  dev [K][P][J][N][N] float: dL/dphi (0 outside the pupil)
- * Limits: n_frames <= 336 per call (MFBD_ERR_INVALID_ARG beyond that: one
- * CTA's block of J x (N x (N/2+1) + N x N) complex64 must fit); the number
- * of CTAs is what fits in the array (28 at 12 frames), so this path runs on
- * part of the GPU.
+ * Limits: n_objects x n_frames <= 336 per call (MFBD_ERR_INVALID_ARG beyond
+ * that: the scratch of one patch, K x J x (N x (N/2+1) + N x N) complex64,
+ * must fit); the patches are processed in batches that fit the array (14
+ * patches per batch at 2 objects x 12 frames), so this path is slower than
+ * the plan path for large fields.
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it; make that first call before any
  * stream capture. Each call uploads its small constants with one

@@ -19,6 +19,8 @@ extern "C" {
  *   2  real-to-complex  in: 64 floats                out: 33 complex (66 floats)
  *   3  complex-to-real  in: 33 complex (Hermitian)   out: 64 floats
  *   4  complex forward, length 32
+ *   5  complex forward, length 64, radix-4 network
+ *   6  complex adjoint, length 64, radix-4 network
  * Forward: X[k] = sum x[n] exp(-2 pi i n k / N); adjoint uses exp(+...).
  * Returns 0 (MFBD_OK) or 1 (MFBD_ERR_INVALID_ARG) for an unknown kind or
  * NULL pointers. */

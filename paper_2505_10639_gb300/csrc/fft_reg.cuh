@@ -141,6 +141,56 @@ MFBD_HD void fft(float2 (&a)[N]) {
     static_for<0, N>([&](auto i) { a[decltype(i)::value] = b[decltype(i)::value]; });
 }
 
+template <int N>
+constexpr int ilog4() {
+    int l = 0;
+    while ((1 << (2 * l)) < N) ++l;
+    return l;
+}
+
+// base-4 digit reversal of i for N = 4^k
+template <int N>
+constexpr int digitrev4(int i) {
+    int r = 0;
+    for (int d = 0; d < ilog4<N>(); ++d) {
+        r = (r << 2) | (i & 3);
+        i >>= 2;
+    }
+    return r;
+}
+
+// In-place radix-4 decimation-in-time FFT for N = 4^k (natural order in and
+// out). Each butterfly twiddles inputs 1..3 by W_{4L}^{qk} and applies the
+// 4-point DFT with t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3, t3 = a1 - a3:
+// X0 = t0 + t2, X2 = t0 - t2, X1 = t1 + DIR i t3, X3 = t1 - DIR i t3.
+template <int N, int DIR>
+MFBD_HD void fft4(float2 (&a)[N]) {
+    static_assert((1 << (2 * ilog4<N>())) == N, "fft4 needs N = 4^k");
+    float2 b[N];
+    static_for<0, N>([&](auto i) { b[decltype(i)::value] = a[digitrev4<N>(decltype(i)::value)]; });
+    static_for<0, ilog4<N>()>([&](auto s) {
+        constexpr int L = 1 << (2 * decltype(s)::value);
+        static_for<0, N / 4>([&](auto t) {
+            constexpr int T = decltype(t)::value;
+            constexpr int k = T % L;
+            constexpr int i0 = (T / L) * 4 * L + k;
+            const float2 a0 = b[i0];
+            const float2 a1 = twmul<4 * L, k, DIR>(b[i0 + L]);
+            const float2 a2 = twmul<4 * L, 2 * k, DIR>(b[i0 + 2 * L]);
+            const float2 a3 = twmul<4 * L, 3 * k, DIR>(b[i0 + 3 * L]);
+            const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+            const float2 t2 = cadd(a1, a3), t3 = csub(a1, a3);
+            // DIR i t3
+            const float2 it3 = DIR < 0 ? make_float2(t3.y, -t3.x) : make_float2(-t3.y, t3.x);
+            b[i0] = cadd(t0, t2);
+            b[i0 + 2 * L] = csub(t0, t2);
+            b[i0 + L] = cadd(t1, it3);
+            b[i0 + 3 * L] = csub(t1, it3);
+        });
+    });
+    static_for<0, N>([&](auto i) { a[decltype(i)::value] = b[decltype(i)::value]; });
+}
+
 // Real-to-complex forward FFT of N real samples -> X[0..N/2] (X[0], X[N/2]
 // real), by one N/2-point complex FFT of z[n] = r[2n] + i r[2n+1]:
 //   E[k] = (Z[k] + conj Z[H-k]) / 2,  O[k] = (Z[k] - conj Z[H-k]) / (2i),

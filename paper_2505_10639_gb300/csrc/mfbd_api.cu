@@ -52,14 +52,13 @@ struct mfbd_plan {
     float* d_weights = nullptr;
     float* d_phi = nullptr;
     float* d_gphi = nullptr;
-    float2* d_gscr = nullptr;   // per unit [P][K][J][N][N/2+1] (split forward/backward)
-    float2* d_pscr = nullptr;   // per unit [P][K][J][N*N] field
-    float2* d_gring = nullptr;  // per CTA [ctas][J][N][N/2+1] (fused call)
-    float2* d_pring = nullptr;  // per CTA [ctas][J][N*N]
+    float2* d_gscr = nullptr;   // per unit [P][K][J][N][N/2+1]: OTF, then adjoint seed
+    float2* d_pscr = nullptr;   // per unit [P][K][J][N*N]: field
     long long phi_floats = 0;
     size_t workspace = 0;
     FusedGeometry geo{};
-    int ctas = 0;
+    int ctas = 0;   // CTAs of a pass kernel
+    int sms = 0;
     bool failed = false;
     bool have_forward = false;
     std::vector<void*> allocations;
@@ -146,7 +145,7 @@ void release(mfbd_plan* p) {
 }
 
 FusedParams fused_params(const mfbd_plan* p, const void* spectra, double* loss, void* object, float2* gscr,
-                         float2* pscr, int ring) {
+                         float2* pscr) {
     FusedParams f{};
     f.P = p->P;
     f.K = p->K;
@@ -162,7 +161,6 @@ FusedParams fused_params(const mfbd_plan* p, const void* spectra, double* loss, 
     f.spec_ld = (p->flags & MFBD_FLAG_FULL_SPECTRUM) ? p->N : p->N / 2 + 1;
     f.loss = loss;
     f.object = static_cast<float2*>(object);
-    f.scratch_ring = ring;
     for (int k = 0; k < p->K; ++k) {
         f.obj[k].W = p->obj[k].W;
         f.obj[k].x0 = p->obj[k].x0;
@@ -223,7 +221,7 @@ int run_phase(mfbd_plan_t p, const float* coeffs, cudaStream_t s) {
 int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s) {
     for (int k = 0; k < p->K; ++k) {
         const ObjectData& o = p->obj[k];
-        const int pi = prof_begin(p, 2, s);
+        const int pi = prof_begin(p, 4, s);
         cudaError_t e = launch_grad_gemm(p->d_gphi + o.phi_off, p->P * p->J, o.W * o.W, o.d_basis, p->M,
                                          o.scale, k > 0, grad, s);
         prof_end(p, pi, s);
@@ -237,15 +235,27 @@ int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s) {
 
 int run_fused(mfbd_plan_t p, int mode, const void* spectra, double* loss, void* object, float2* gscr,
               cudaStream_t s) {
-    FusedParams f = mode == MODE_FUSED ? fused_params(p, spectra, loss, object, p->d_gring, p->d_pring, 1)
-                    : mode == MODE_OTF ? fused_params(p, spectra, loss, object, gscr, nullptr, 0)
-                                       : fused_params(p, spectra, loss, object, p->d_gscr, p->d_pscr, 0);
-    const int pi = prof_begin(p, 1, s);
-    cudaError_t e = launch_fused(f, mode, p->geo, p->ctas, s);
-    prof_end(p, pi, s);
+    FusedParams f = mode == MODE_OTF ? fused_params(p, spectra, loss, object, gscr, nullptr)
+                                     : fused_params(p, spectra, loss, object, p->d_gscr, p->d_pscr);
+    cudaError_t e = cudaSuccess;
+    if (mode != MODE_BWD) {
+        const int pi = prof_begin(p, 1, s);
+        e = launch_forward_passes(f, p->geo, p->sms, s);
+        prof_end(p, pi, s);
+        if (e == cudaSuccess && mode != MODE_OTF) {
+            const int pr = prof_begin(p, 2, s);
+            e = launch_reduction(f, p->sms, s);
+            prof_end(p, pr, s);
+        }
+    }
+    if (e == cudaSuccess && (mode == MODE_BWD || mode == MODE_FUSED)) {
+        const int pb = prof_begin(p, 3, s);
+        e = launch_adjoint_passes(f, p->geo, p->sms, s);
+        prof_end(p, pb, s);
+    }
     if (e != cudaSuccess) {
         p->failed = true;
-        return cuda_fail(e, "fused kernel");
+        return cuda_fail(e, "pass or reduction kernel");
     }
     return MFBD_OK;
 }
@@ -401,9 +411,8 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
         p->geo = fused_geometry(max_box);
         int per_sm = max_ctas_per_sm(p->geo);
         if (per_sm < 1) throw fail(MFBD_ERR_UNSUPPORTED, "fused kernel does not fit on this device");
-        p->ctas = std::min(std::max(p->P, 1), prop.multiProcessorCount * per_sm);
-        if ((st = dev_alloc(p, &p->d_gring, (size_t)p->ctas * p->J * kHalf))) throw st;
-        if ((st = dev_alloc(p, &p->d_pring, (size_t)p->ctas * p->J * n * n))) throw st;
+        p->sms = prop.multiProcessorCount;
+        p->ctas = prop.multiProcessorCount * per_sm;
         if ((e = cudaStreamSynchronize(s))) throw cuda_fail(e, "plan upload");
     } catch (int status) {
         release(p);
@@ -443,8 +452,8 @@ int mfbd_plan_set_profiling(mfbd_plan_t p, int enable, int max_launches) {
 
 int mfbd_plan_read_profile(mfbd_plan_t p, double* ms, long long* launches, int reset) {
     if (!p) return fail(MFBD_ERR_INVALID_ARG, "plan is NULL");
-    double acc[3] = {0, 0, 0};
-    long long cnt[3] = {0, 0, 0};
+    double acc[5] = {0, 0, 0, 0, 0};
+    long long cnt[5] = {0, 0, 0, 0, 0};
     for (int i = 0; i < p->ev_used; ++i) {
         cudaError_t e = cudaEventSynchronize(p->ev[2 * i + 1]);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
@@ -454,7 +463,7 @@ int mfbd_plan_read_profile(mfbd_plan_t p, double* ms, long long* launches, int r
         acc[p->ev_kind[i]] += t;
         cnt[p->ev_kind[i]] += 1;
     }
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 5; ++k) {
         if (ms) ms[k] = acc[k];
         if (launches) launches[k] = cnt[k];
     }

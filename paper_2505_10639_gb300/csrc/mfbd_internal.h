@@ -33,26 +33,32 @@ struct FusedParams {
     const float* phi;         // phases, per object [P*J][W*W] at phi_off
     float* gphi;              // dL/dphi, same layout
     float2* gscr;             // [P][K][J][N][N/2+1]: OTF, then dL/dconj(H)
-    float2* pscr;             // [P][K][J][N x N]: field p = F P, stored [x][y] (null: OTF mode)
+    float2* pscr;             // [P][K][J][N x N]: field p = F P, stored [x][y] (null: not kept)
     const float2* spectra;    // D
     int spec_ld;              // row stride of D and O in complex elements (33 or 64)
     double* loss;             // [P]
     float2* object;           // [P][K][N][spec_ld] or null
-    int scratch_ring;         // 0: gscr/pscr per unit [P][K][J]; 1: per CTA [gridDim][J], reused per object
     ObjParams obj[kMaxObjects];
 };
 
 // Fused kernel geometry for the largest pupil box of a plan.
 struct FusedGeometry {
-    int slots;          // warps per CTA; each warp works on one frame at a time
+    int slots;          // warps per CTA of the pass kernels; each works on one frame at a time
     size_t smem_bytes;  // dynamic shared memory per CTA
     int xs;             // row stride (complex elements) of a warp's exchange buffer
 };
 
 FusedGeometry fused_geometry(int max_box);
 
-cudaError_t launch_fused(const FusedParams& prm, int mode, const FusedGeometry& g, int ctas,
-                         cudaStream_t s);
+// The three kernels of an evaluation (`sms` is the device's SM count):
+// forward passes (OTF, field), frame reduction (loss, object, adjoint
+// seeds), adjoint passes (dL/dphi).
+cudaError_t launch_forward_passes(const FusedParams& prm, const FusedGeometry& g, int sms, cudaStream_t s);
+cudaError_t launch_reduction(const FusedParams& prm, int sms, cudaStream_t s);
+cudaError_t launch_adjoint_passes(const FusedParams& prm, const FusedGeometry& g, int sms, cudaStream_t s);
+// The kernels of `mode` in order (FWD: forward + reduction; BWD: adjoint;
+// FUSED: all three; OTF: forward only).
+cudaError_t launch_fused(const FusedParams& prm, int mode, const FusedGeometry& g, int sms, cudaStream_t s);
 
 // phase[u][i] = scale * sum_m a[u][m] basis[m][i]  (u < U, i < npix)
 cudaError_t launch_phase_gemm(const float* a, int U, int M, const float* basis, int npix,

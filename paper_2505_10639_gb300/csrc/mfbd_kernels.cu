@@ -1,11 +1,12 @@
 // sm_103a fused kernel of the MOMFBD hot path (N = 64 patches).
 //
-// Persistent CTAs of 6 warps work on one patch at a time; inside a CTA each
-// warp carries one frame (unit) through a sequence of passes over its own
-// 64 x es complex exchange buffer in shared memory, synchronising with
-// __syncwarp only. In every pass a lane owns one whole 64-point line in
+// Three launches per evaluation: a forward pass kernel and an adjoint pass
+// kernel in which every warp carries one frame (unit) at a time through a
+// sequence of passes over its own 64 x es complex exchange buffer in shared
+// memory, synchronising with __syncwarp only, and between them a
+// frequency-parallel frame-reduction kernel. In every pass a lane owns one whole 64-point line in
 // registers and transforms it with the single register FFT instance of the
-// kernel (adjoint transforms use F^H x = conj(F conj x)).
+// kernel, a radix-4 network (adjoint transforms use F^H x = conj(F conj x)).
 //
 // The pupil's W x W bounding box is placed at the origin of the grid: the
 // PSF |F P|^2 does not depend on where the pupil sits, so every quantity
@@ -61,6 +62,19 @@ __device__ __forceinline__ float2 expi(float ph) {
     return make_float2(c, s);
 }
 
+// L2 prefetch of [ptr, ptr + bytes) (bulk prefetch needs 16-byte alignment
+// and a multiple of 16 bytes; the range is widened to that).
+__device__ __forceinline__ void prefetch_l2(const void* ptr, size_t bytes) {
+    uintptr_t a = reinterpret_cast<uintptr_t>(ptr);
+    uintptr_t b = (a + bytes + 15) & ~uintptr_t(15);
+    a &= ~uintptr_t(15);
+    if (b > a)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(
+                         reinterpret_cast<const void*>(a))),
+                     "r"((unsigned)(b - a))
+                     : "memory");
+}
+
 struct Unit {
     const float* phi;  // first box pixel of this unit's phase image
     float* gphi;       // same for dL/dphi
@@ -82,15 +96,11 @@ __device__ __forceinline__ int pass_rounds(int pass, int W) {
 
 __device__ __forceinline__ bool bit(uint64_t w, int b) { return (w >> b) & 1ull; }
 
-// Compiler-only fence: keeps the loads of a long gather from being hoisted
-// all at once (which would need registers for every loaded value).
-#define MFBD_CHUNK_FENCE(i) \
-    if (((i) & 7) == 7) asm volatile("" ::: "memory")
 
-// Runs passes [first, last) of one unit on the calling warp.
-__device__ __forceinline__ void run_passes(int first, int last, const volatile Unit* su, float2* __restrict__ E,
-                                           int es, const uint64_t* __restrict__ smask,
-                                           const uint64_t* __restrict__ ssupp) {
+// Runs passes [FIRST, LAST) of one unit on the calling warp.
+template <int FIRST, int LAST>
+__device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __restrict__ E, int es,
+                                           const uint64_t* __restrict__ smask, const uint64_t* __restrict__ ssupp) {
     const int lane = threadIdx.x & 31;
 #define U_W (su->W)
 #define U_LD (su->ld)
@@ -101,7 +111,7 @@ __device__ __forceinline__ void run_passes(int first, int last, const volatile U
 #define U_PF ((float2*)su->pf)
     const int W = U_W;
 #pragma unroll 1
-    for (int pass = first; pass < last; ++pass) {
+    for (int pass = FIRST; pass < LAST; ++pass) {
         const int nr = pass_rounds(pass, W);
 #pragma unroll 1
         for (int r = 0; r < nr; ++r) {
@@ -109,21 +119,28 @@ __device__ __forceinline__ void run_passes(int first, int last, const volatile U
             const bool adj = pass >= P_SEED;
             // ------------------------------------------------------ load
             switch (pass) {
-                case P_PUPIL: {
+                case P_PUPIL: if constexpr (FIRST <= P_PUPIL && P_PUPIL < LAST) {
                     const int c = lane + 32 * r;
                     if (c < W) {
-                        for (int yy = 0; yy < W; ++yy) {
-                            float2 pv = make_float2(0.f, 0.f);
-                            if (bit(smask[yy], c)) pv = expi(U_PHI[yy * U_LD + c]);
-                            E[yy * es + c] = pv;
-                        }
+                        // all phase loads of the column are issued before use
+                        const float* ph = U_PHI + c;
+                        const int ld = U_LD;
+                        float phv[kN];
+#pragma unroll
+                        for (int yy = 0; yy < kN; ++yy) phv[yy] = (yy < W) ? ph[yy * ld] : 0.f;
+#pragma unroll
+                        for (int yy = 0; yy < kN; ++yy)
+                            if (yy < W) E[yy * es + c].x = phv[yy];
+#pragma unroll 4
+                        for (int yy = 0; yy < W; ++yy)
+                            E[yy * es + c] = bit(smask[yy], c) ? expi(E[yy * es + c].x) : make_float2(0.f, 0.f);
                     }
 #pragma unroll
                     for (int y = 0; y < kN; ++y)
                         v[y] = (c < W && y < W) ? E[y * es + c] : make_float2(0.f, 0.f);
                     break;
                 }
-                case P_FIELD: {
+                case P_FIELD: if constexpr (FIRST <= P_FIELD && P_FIELD < LAST) {
                     if (r < 2) {
                         const int y = lane + 32 * r;
 #pragma unroll
@@ -138,22 +155,21 @@ __device__ __forceinline__ void run_passes(int first, int last, const volatile U
                     }
                     break;
                 }
-                case P_OTF: {  // lane 0: the packed real columns kx = 0, N/2
+                case P_OTF: if constexpr (FIRST <= P_OTF && P_OTF < LAST) {  // lane 0: the packed real columns kx = 0, N/2
 #pragma unroll
                     for (int ky = 0; ky < kN; ++ky) v[ky] = E[ky * es + lane];
                     break;
                 }
-                case P_SEED: {  // lane 0: columns 0 and N/2 packed as a + i b
+                case P_SEED: if constexpr (FIRST <= P_SEED && P_SEED < LAST) {  // lane 0: columns 0 and N/2 packed as a + i b
 #pragma unroll
                     for (int ky = 0; ky < kN; ++ky) {
                         const float2 a = U_H[ky * kNH + lane];
                         const float2 b = lane == 0 ? U_H[ky * kNH + 32] : make_float2(0.f, 0.f);
                         v[ky] = make_float2(a.x - b.y, -(a.y + b.x));  // conj(a + i b)
-                        MFBD_CHUNK_FENCE(ky);
                     }
                     break;
                 }
-                case P_C2R: {
+                case P_C2R: if constexpr (FIRST <= P_C2R && P_C2R < LAST) {
                     if (r == 0) {
                         // rows lane and lane+32: Hermitian extension T[k] = conj T[N-k]
 #pragma unroll
@@ -173,7 +189,6 @@ __device__ __forceinline__ void run_passes(int first, int last, const volatile U
                                 b = cconj(E[(lane + 32) * es + (kN - k)]);
                             }
                             v[k] = make_float2(a.x - b.y, -(a.y + b.x));  // conj(a + i b)
-                            MFBD_CHUNK_FENCE(k);
                         }
                     } else {
                         const int y = lane + 32 * (r - 1);
@@ -183,12 +198,11 @@ __device__ __forceinline__ void run_passes(int first, int last, const volatile U
                             const float2 p0 = U_PF[(2 * i) * kN + y], p1 = U_PF[(2 * i + 1) * kN + y];
                             v[2 * i] = make_float2(g.x * p0.x, -g.x * p0.y);
                             v[2 * i + 1] = make_float2(g.y * p1.x, -g.y * p1.y);
-                            MFBD_CHUNK_FENCE(i);
                         }
                     }
                     break;
                 }
-                default: {  // P_ADJ
+                default: if constexpr (FIRST <= P_ADJ && P_ADJ < LAST) {  // P_ADJ
                     const int c = lane + 32 * r;
                     const int cc = c < W ? c : 0;  // inactive lanes transform a dummy column
 #pragma unroll
@@ -197,14 +211,14 @@ __device__ __forceinline__ void run_passes(int first, int last, const volatile U
                 }
             }
             // --------------------------------------------------- transform
-            fftreg::fft<kN, -1>(v);
+            fftreg::fft4<kN, -1>(v);
             if (adj) {
 #pragma unroll
                 for (int i = 0; i < kN; ++i) v[i].y = -v[i].y;
             }
             // ----------------------------------------------------- store
             switch (pass) {
-                case P_PUPIL: {
+                case P_PUPIL: if constexpr (FIRST <= P_PUPIL && P_PUPIL < LAST) {
                     const int c = lane + 32 * r;
                     if (c < W) {
 #pragma unroll
@@ -212,7 +226,7 @@ __device__ __forceinline__ void run_passes(int first, int last, const volatile U
                     }
                     break;
                 }
-                case P_FIELD: {
+                case P_FIELD: if constexpr (FIRST <= P_FIELD && P_FIELD < LAST) {
                     if (r < 2) {
                         const int y = lane + 32 * r;
                         if (U_PF) {
@@ -248,25 +262,23 @@ __device__ __forceinline__ void run_passes(int first, int last, const volatile U
                     }
                     break;
                 }
-                case P_OTF: {
+                case P_OTF: if constexpr (FIRST <= P_OTF && P_OTF < LAST) {
+                    // every lane writes its OTF column (lane 0 the packed
+                    // Z = F(s_col0 + i s_colN/2), overwritten below) and keeps
+                    // a copy in shared memory for the split of column 0
 #pragma unroll
-                    for (int ky = 0; ky < kN; ++ky)
+                    for (int ky = 0; ky < kN; ++ky) {
                         U_H[ky * kNH + lane] = (lane == 0 || bit(ssupp[ky], lane)) ? v[ky] : make_float2(0.f, 0.f);
-                    __syncwarp();
-                    // lane 0 stored Z = F(s_col0 + i s_colN/2); split it into both columns
-                    float2 zz[2], zm[2];
-#pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const int ky = lane + 32 * i;
-                        zz[i] = U_H[ky * kNH];
-                        zm[i] = cconj(U_H[((kN - ky) & (kN - 1)) * kNH]);
+                        E[ky * es + lane] = v[ky];
                     }
                     __syncwarp();
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
                         const int ky = lane + 32 * i;
-                        float2 h0 = cscale(cadd(zz[i], zm[i]), 0.5f);
-                        const float2 d = cscale(csub(zz[i], zm[i]), 0.5f);
+                        const float2 z = E[ky * es];
+                        const float2 zc = cconj(E[((kN - ky) & (kN - 1)) * es]);
+                        float2 h0 = cscale(cadd(z, zc), 0.5f);
+                        const float2 d = cscale(csub(z, zc), 0.5f);
                         float2 h32 = make_float2(d.y, -d.x);
                         if (!bit(ssupp[ky], 0)) h0 = make_float2(0.f, 0.f);
                         if (!bit(ssupp[ky], 32)) h32 = make_float2(0.f, 0.f);
@@ -276,12 +288,12 @@ __device__ __forceinline__ void run_passes(int first, int last, const volatile U
                     }
                     break;
                 }
-                case P_SEED: {  // lane 0 keeps (T_0, T_N/2), both real, packed
+                case P_SEED: if constexpr (FIRST <= P_SEED && P_SEED < LAST) {  // lane 0 keeps (T_0, T_N/2), both real, packed
 #pragma unroll
                     for (int y = 0; y < kN; ++y) E[y * es + lane] = v[y];
                     break;
                 }
-                case P_C2R: {
+                case P_C2R: if constexpr (FIRST <= P_C2R && P_C2R < LAST) {
                     if (r == 0) {
                         const float sc = 2.0f * U_INVZ;
 #pragma unroll
@@ -297,20 +309,29 @@ __device__ __forceinline__ void run_passes(int first, int last, const volatile U
                     }
                     break;
                 }
-                default: {  // P_ADJ
+                default: if constexpr (FIRST <= P_ADJ && P_ADJ < LAST) {  // P_ADJ
                     const int c = lane + 32 * r;
                     if (c < W) {
 #pragma unroll
                         for (int y = 0; y < kN; ++y)
                             if (y < W) E[y * es + c] = v[y];
-                        for (int yy = 0; yy < W; ++yy) {
-                            float gv = 0.f;
-                            if (bit(smask[yy], c)) {
-                                const float2 pv = expi(U_PHI[yy * U_LD + c]);
-                                const float2 gp = E[yy * es + c];
-                                gv = 2.0f * (pv.x * gp.y - pv.y * gp.x);
+                        const float* ph = U_PHI + c;
+                        float* gph = U_GPHI + c;
+                        const int ld = U_LD;
+                        float phv[kN];
+#pragma unroll
+                        for (int yy = 0; yy < kN; ++yy) phv[yy] = (yy < W) ? ph[yy * ld] : 0.f;
+#pragma unroll
+                        for (int yy = 0; yy < kN; ++yy) {
+                            if (yy < W) {
+                                float gv = 0.f;
+                                if (bit(smask[yy], c)) {
+                                    const float2 pv = expi(phv[yy]);
+                                    const float2 gp = E[yy * es + c];
+                                    gv = 2.0f * (pv.x * gp.y - pv.y * gp.x);
+                                }
+                                gph[yy * ld] = gv;
                             }
-                            U_GPHI[yy * U_LD + c] = gv;
                         }
                     }
                     break;
@@ -336,7 +357,7 @@ __device__ __forceinline__ void run_passes(int first, int last, const volatile U
 // r_j in FP64. With several frames this triggers at DC and little else.
 constexpr float kCancel = 1e-3f;
 
-__device__ double reduce_object(const FusedParams& prm, int p, int k, const uint64_t* ssupp, float2* hbase) {
+__device__ double reduce_object_any(const FusedParams& prm, int p, int k, const uint64_t* ssupp, float2* hbase) {
     const int J = prm.J;
     const size_t unit0 = ((size_t)p * prm.K + k) * J;
     const size_t dstride = (size_t)kN * prm.spec_ld;
@@ -351,7 +372,7 @@ __device__ double reduce_object(const FusedParams& prm, int p, int k, const uint
         float2* hp = hbase + f;
         float2 num = make_float2(0.f, 0.f);
         float e = 0.f, q = 0.f;
-#pragma unroll 4
+#pragma unroll 6
         for (int j = 0; j < J; ++j) {
             const float2 d = dp[(size_t)j * dstride];
             const float2 h = hp[(size_t)j * kHalf];
@@ -369,7 +390,7 @@ __device__ double reduce_object(const FusedParams& prm, int p, int k, const uint
         float t;
         if (!(t_est < kCancel * e)) {
             float tsum = 0.f;
-#pragma unroll 4
+#pragma unroll 6
             for (int j = 0; j < J; ++j) {
                 const float2 d = dp[(size_t)j * dstride];
                 const float2 h = hp[(size_t)j * kHalf];
@@ -416,6 +437,95 @@ __device__ double reduce_object(const FusedParams& prm, int p, int k, const uint
     return acc;
 }
 
+// J <= JM: the J spectra and OTFs of a frequency are loaded once, all at
+// once, into registers; both frame loops then run from registers.
+template <int JM>
+__device__ double reduce_object_reg(const FusedParams& prm, int p, int k, const uint64_t* ssupp, float2* hbase) {
+    const int J = prm.J;
+    const size_t unit0 = ((size_t)p * prm.K + k) * J;
+    const size_t dstride = (size_t)kN * prm.spec_ld;
+    const float2* dbase = prm.spectra + unit0 * dstride;
+    const float gam = (float)prm.gamma;
+    float wv[JM];
+#pragma unroll
+    for (int j = 0; j < JM; ++j) wv[j] = (j < J) ? prm.weights[(size_t)k * J + j] : 0.f;
+    double acc = 0.0;
+    for (int f = threadIdx.x; f < kHalf; f += blockDim.x) {
+        const int ky = f / kNH, kx = f - ky * kNH;
+        const size_t doff = (size_t)ky * prm.spec_ld + kx;
+        const float2* dp = dbase + doff;
+        float2* hp = hbase + f;
+        float2 d[JM], h[JM];
+#pragma unroll
+        for (int j = 0; j < JM; ++j) {
+            d[j] = (j < J) ? dp[(size_t)j * dstride] : make_float2(0.f, 0.f);
+            h[j] = (j < J) ? hp[(size_t)j * kHalf] : make_float2(0.f, 0.f);
+        }
+        float2 num = make_float2(0.f, 0.f);
+        float e = 0.f, q = 0.f;
+#pragma unroll
+        for (int j = 0; j < JM; ++j) {
+            num.x += wv[j] * (d[j].x * h[j].x + d[j].y * h[j].y);
+            num.y += wv[j] * (d[j].y * h[j].x - d[j].x * h[j].y);
+            e += wv[j] * (d[j].x * d[j].x + d[j].y * d[j].y);
+            q += wv[j] * (h[j].x * h[j].x + h[j].y * h[j].y);
+        }
+        q += gam;
+        const float invq = 1.0f / q;
+        float2 o = cscale(num, invq);
+        const bool seed = (f != 0) && bit(ssupp[ky], kx);
+        const float t_est = e - (num.x * num.x + num.y * num.y) * invq;
+        float t;
+        if (!(t_est < kCancel * e)) {
+            float tsum = 0.f;
+#pragma unroll
+            for (int j = 0; j < JM; ++j) {
+                const float2 r = csub(d[j], cmul(o, h[j]));
+                tsum += wv[j] * (r.x * r.x + r.y * r.y);
+                if (j < J) hp[(size_t)j * kHalf] = seed ? cscale(cmul(cconj(o), r), -wv[j]) : make_float2(0.f, 0.f);
+            }
+            t = tsum + gam * (o.x * o.x + o.y * o.y);
+        } else {
+            double nx = 0.0, ny = 0.0, qd = prm.gamma;
+#pragma unroll
+            for (int j = 0; j < JM; ++j) {
+                const double wj = wv[j];
+                nx += wj * ((double)d[j].x * h[j].x + (double)d[j].y * h[j].y);
+                ny += wj * ((double)d[j].y * h[j].x - (double)d[j].x * h[j].y);
+                qd += wj * ((double)h[j].x * h[j].x + (double)h[j].y * h[j].y);
+            }
+            const double ox = nx / qd, oy = ny / qd;
+            double tsum = 0.0;
+#pragma unroll
+            for (int j = 0; j < JM; ++j) {
+                const double wj = wv[j];
+                const double rx = (double)d[j].x - (ox * h[j].x - oy * h[j].y);
+                const double ry = (double)d[j].y - (ox * h[j].y + oy * h[j].x);
+                tsum += wj * (rx * rx + ry * ry);
+                if (j < J)
+                    hp[(size_t)j * kHalf] =
+                        seed ? make_float2((float)(-wj * (ox * rx + oy * ry)), (float)(-wj * (ox * ry - oy * rx)))
+                             : make_float2(0.f, 0.f);
+            }
+            t = (float)(tsum + prm.gamma * (ox * ox + oy * oy));
+            o = make_float2((float)ox, (float)oy);
+        }
+        acc += ((kx == 0 || kx == kN / 2) ? 1.0 : 2.0) * (double)t;
+        if (prm.object) {
+            float2* ob = prm.object + ((size_t)p * prm.K + k) * dstride;
+            ob[doff] = o;
+            if (prm.spec_ld == kN && kx > 0 && kx < kN / 2)
+                ob[(size_t)((kN - ky) % kN) * kN + (kN - kx)] = cconj(o);
+        }
+    }
+    return acc;
+}
+
+__device__ double reduce_object(const FusedParams& prm, int p, int k, const uint64_t* ssupp, float2* hbase) {
+    if (prm.J <= 16) return reduce_object_reg<16>(prm, p, k, ssupp, hbase);
+    return reduce_object_any(prm, p, k, ssupp, hbase);
+}
+
 __device__ double block_sum(double v, double* sred) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -429,79 +539,63 @@ __device__ double block_sum(double v, double* sred) {
     return tot;
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* ptr, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(ptr)), "r"(bytes)
-                 : "memory");
-}
 
-__global__ void __launch_bounds__(kThreads, 2) mfbd_fused_kernel(const FusedParams prm, int mode, int es) {
+// One warp per unit (patch, object, frame), persistent over the units;
+// FIRST..LAST selects the forward (PUPIL, FIELD, OTF) or adjoint (SEED,
+// C2R, ADJ) passes. No CTA-level synchronisation: warps progress
+// independently, so different warps overlap different passes.
+template <int FIRST, int LAST>
+__global__ void __launch_bounds__(kThreads, 2) mfbd_pass_kernel(const FusedParams prm, int es) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ uint64_t smask[kN];
-    __shared__ uint64_t ssupp[kN];
-    __shared__ double sred[32];
     __shared__ Unit sunit[kWarps];
-    const int tid = threadIdx.x;
-    const int warp = tid >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     float2* E = reinterpret_cast<float2*>(smem) + (size_t)warp * kN * es;
-    const int J = prm.J;
-    const bool fwd = mode != MODE_BWD;
-    const bool red = mode == MODE_FWD || mode == MODE_FUSED;
-    const bool bwd = mode == MODE_BWD || mode == MODE_FUSED;
+    volatile Unit* su = &sunit[warp];
+    const int J = prm.J, K = prm.K;
+    const long long units = (long long)prm.P * K * J;
+    const long long stride = (long long)gridDim.x * nwarps;
+    for (long long u = (long long)blockIdx.x * nwarps + warp; u < units; u += stride) {
+        const int j = (int)(u % J);
+        const long long pk = u / J;
+        const int k = (int)(pk % K);
+        const long long p = pk / K;
+        const ObjParams& ob = prm.obj[k];
+        const long long pj = p * J + j;  // index of the unit's phase image
+        __syncwarp();
+        if (lane == 0) {
+            su->W = ob.W;
+            su->ld = ob.phi_ld;
+            su->inv_z = ob.inv_z;
+            su->phi = prm.phi + ob.phi_off + pj * ob.phi_unit + ob.phi_org;
+            su->gphi = FIRST >= P_SEED ? prm.gphi + ob.phi_off + pj * ob.phi_unit + ob.phi_org : nullptr;
+            su->h = prm.gscr + (size_t)u * kHalf;
+            su->pf = prm.pscr ? prm.pscr + (size_t)u * kN * kN : nullptr;
+            if (FIRST == P_PUPIL && u + stride < units) {  // next unit's phase into L2
+                const long long un = u + stride;
+                const int jn = (int)(un % J), kn = (int)((un / J) % K);
+                const long long pn = un / J / K;
+                const ObjParams& on = prm.obj[kn];
+                prefetch_l2(prm.phi + on.phi_off + (pn * J + jn) * on.phi_unit + on.phi_org,
+                            ((size_t)(on.W - 1) * on.phi_ld + on.W) * 4);
+            }
+        }
+        __syncwarp();
+        run_passes<FIRST, LAST>(su, E, es, ob.mask, ob.supp);
+    }
+}
 
+// Frame reduction, one CTA per patch: every frequency of every object.
+__global__ void __launch_bounds__(256, 2) mfbd_reduce_kernel(const FusedParams prm) {
+    __shared__ double sred[32];
     for (int p = blockIdx.x; p < prm.P; p += gridDim.x) {
         double lacc = 0.0;
         for (int k = 0; k < prm.K; ++k) {
-            const ObjParams& ob = prm.obj[k];
-            __syncthreads();
-            if (tid < kN) {
-                smask[tid] = tid < ob.W ? ob.mask[tid] : 0ull;
-                ssupp[tid] = ob.supp[tid];
-            }
-            const size_t unit0 = ((size_t)p * prm.K + k) * J;
-            if (red && tid == 0) {
-                const size_t bytes = (size_t)kN * prm.spec_ld * sizeof(float2);
-                const float2* d0 = prm.spectra + unit0 * (size_t)kN * prm.spec_ld;
-                if ((reinterpret_cast<uintptr_t>(d0) & 15) == 0)
-                    for (int j = 0; j < J; ++j) prefetch_l2(d0 + (size_t)j * kN * prm.spec_ld, (unsigned)bytes);
-            }
-            __syncthreads();
-            const size_t slot0 = prm.scratch_ring ? (size_t)blockIdx.x * J : unit0;
-            float2* hscr = prm.gscr + slot0 * kHalf;
-            float2* pscr = prm.pscr ? prm.pscr + slot0 * (size_t)(kN * kN) : nullptr;
-            volatile Unit* su = &sunit[warp];
-            // stage 0: forward of every frame; 1: frame reduction; 2: adjoint
-            const int stage_end = bwd ? 2 : (red ? 1 : 0);
-#pragma unroll 1
-            for (int stage = fwd ? 0 : 2; stage <= stage_end; ++stage) {
-                if (stage == 1) {
-                    if (red) lacc += reduce_object(prm, p, k, ssupp, hscr);
-                    __syncthreads();
-                    continue;
-                }
-                const bool back = stage == 2;
-                for (int j = warp; j < J; j += nwarps) {
-                    const long long unit = (long long)p * J + j;
-                    __syncwarp();
-                    if ((tid & 31) == 0) {
-                        su->W = ob.W;
-                        su->ld = ob.phi_ld;
-                        su->inv_z = ob.inv_z;
-                        su->phi = prm.phi + ob.phi_off + unit * ob.phi_unit + ob.phi_org;
-                        su->gphi = back ? prm.gphi + ob.phi_off + unit * ob.phi_unit + ob.phi_org : nullptr;
-                        su->h = hscr + (size_t)j * kHalf;
-                        su->pf = pscr ? pscr + (size_t)j * kN * kN : nullptr;
-                    }
-                    __syncwarp();
-                    run_passes(back ? P_SEED : P_PUPIL, back ? P_END : P_OTF + 1, su, E, es, smask, ssupp);
-                }
-                __syncthreads();
-            }
+            float2* hbase = prm.gscr + ((size_t)p * prm.K + k) * prm.J * kHalf;
+            lacc += reduce_object(prm, p, k, prm.obj[k].supp, hbase);
         }
-        if (red) {
-            const double tot = block_sum(lacc, sred);
-            if (tid == 0) prm.loss[p] = tot;
-        }
+        const double tot = block_sum(lacc, sred);
+        if (threadIdx.x == 0) prm.loss[p] = tot;
     }
 }
 
@@ -511,29 +605,79 @@ FusedGeometry fused_geometry(int max_box) {
     FusedGeometry g;
     const int es = max_box > kNH ? max_box : kNH;
     g.xs = es | 1;
-    g.slots = kWarps;
-    g.smem_bytes = (size_t)kWarps * kN * g.xs * sizeof(float2);
+    // up to kWarps warps, two CTAs per SM when their buffers fit in 227 KB
+    const size_t per_warp = (size_t)kN * g.xs * sizeof(float2);
+    int warps = (int)(((size_t)113 * 1024) / per_warp);
+    if (warps < 1) warps = 1;
+    g.slots = warps < kWarps ? warps : kWarps;
+    g.smem_bytes = (size_t)g.slots * per_warp;
     return g;
 }
 
+namespace {
+
+}  // namespace
+
+template <int FIRST, int LAST>
+cudaError_t launch_pass(const FusedParams& prm, const FusedGeometry& g, int sms, cudaStream_t s) {
+    auto* kern = mfbd_pass_kernel<FIRST, LAST>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem_bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, g.slots * 32, g.smem_bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long units = (long long)prm.P * prm.K * prm.J;
+    long long ctas = (long long)sms * per_sm;
+    const long long need = (units + g.slots - 1) / g.slots;
+    if (ctas > need) ctas = need;
+    kern<<<(int)ctas, g.slots * 32, g.smem_bytes, s>>>(prm, g.xs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduction(const FusedParams& prm, int sms, cudaStream_t s) {
+    if (prm.P == 0) return cudaSuccess;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mfbd_reduce_kernel, 256, 0);
+    if (e != cudaSuccess) return e;
+    long long ctas = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (ctas > prm.P) ctas = prm.P;
+    mfbd_reduce_kernel<<<(int)ctas, 256, 0, s>>>(prm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_passes(const FusedParams& prm, const FusedGeometry& g, int sms, cudaStream_t s) {
+    if (prm.P == 0) return cudaSuccess;
+    return launch_pass<P_PUPIL, P_OTF + 1>(prm, g, sms, s);
+}
+
+cudaError_t launch_adjoint_passes(const FusedParams& prm, const FusedGeometry& g, int sms, cudaStream_t s) {
+    if (prm.P == 0) return cudaSuccess;
+    return launch_pass<P_SEED, P_END>(prm, g, sms, s);
+}
+
 int max_ctas_per_sm(const FusedGeometry& g) {
+    auto* kern = mfbd_pass_kernel<P_PUPIL, P_OTF + 1>;
     int n = 0;
-    if (cudaFuncSetAttribute(mfbd_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)g.smem_bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem_bytes) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mfbd_fused_kernel, g.slots * 32, g.smem_bytes) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, g.slots * 32, g.smem_bytes) != cudaSuccess)
         return 0;
     return n;
 }
 
-cudaError_t launch_fused(const FusedParams& prm, int mode, const FusedGeometry& g, int ctas, cudaStream_t s) {
+// mode FWD: forward passes + reduction; BWD: adjoint passes; FUSED: all
+// three launches; OTF: forward passes only. `sms` is the SM count.
+cudaError_t launch_fused(const FusedParams& prm, int mode, const FusedGeometry& g, int sms, cudaStream_t s) {
     if (prm.P == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(mfbd_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)g.smem_bytes);
-    if (e != cudaSuccess) return e;
-    mfbd_fused_kernel<<<ctas, g.slots * 32, g.smem_bytes, s>>>(prm, mode, g.xs);
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    if (mode != MODE_BWD) {
+        e = launch_forward_passes(prm, g, sms, s);
+        if (e != cudaSuccess || mode == MODE_OTF) return e;
+        e = launch_reduction(prm, sms, s);
+        if (e != cudaSuccess || mode == MODE_FWD) return e;
+    }
+    return launch_adjoint_passes(prm, g, sms, s);
 }
 
 }  // namespace mfbd_dev

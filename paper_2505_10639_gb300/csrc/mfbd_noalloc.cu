@@ -21,9 +21,9 @@
 using namespace mfbd_dev;
 
 // 16 MiB per device: 64 KiB of per-call constants (pupil and OTF-support
-// bit rows, frame weights) followed by the fused kernel's per-CTA blocks
-// (for each CTA: [J][N][N/2+1] complex64 adjoint seeds and [J][N][N]
-// complex64 fields).
+// bit rows, frame weights) followed by the per-unit scratch of one batch of
+// patches: [Pb][K][J][N][N/2+1] complex64 OTFs / adjoint seeds, then
+// [Pb][K][J][N][N] complex64 fields.
 static __device__ __align__(256) unsigned char g_static_workspace[(size_t)16 << 20];
 
 namespace {
@@ -116,10 +116,10 @@ extern "C" int mfbd_phase_loss_grad_noalloc(const mfbd_plan_desc* desc, const fl
     int st = check_desc(desc);
     if (st != MFBD_OK) return st;
     const int P = desc->n_patches, K = desc->n_objects, J = desc->n_frames;
-    const size_t ring_per_cta = (size_t)J * (kHalf + kN * kN) * sizeof(float2);
-    if (ring_per_cta > kStaticBytes - kConstBytes)
+    const size_t per_patch = (size_t)K * J * (kHalf + kN * kN) * sizeof(float2);
+    if (per_patch > kStaticBytes - kConstBytes)
         return set_error(MFBD_ERR_INVALID_ARG,
-                         "n_frames exceeds the static workspace (at most 336 frames per call)");
+                         "n_objects x n_frames exceeds the static workspace (at most 336 per call)");
     if (P == 0) return MFBD_OK;
     if (!phase || !spectra || !loss || !grad_phase)
         return set_error(MFBD_ERR_INVALID_ARG, "phase, spectra, loss and grad_phase are required");
@@ -184,30 +184,29 @@ extern "C" int mfbd_phase_loss_grad_noalloc(const mfbd_plan_desc* desc, const fl
     if ((e = cudaMemsetAsync(grad_phase, 0, (size_t)K * P * J * kN * kN * sizeof(float), s)) != cudaSuccess)
         return set_cuda_error(e, "cudaMemsetAsync");
 
-    f.P = P;
     f.K = K;
     f.J = J;
     f.M = 0;
     f.gamma = desc->gamma;
     f.weights = reinterpret_cast<const float*>(base + kBitsBytes);
-    f.phi = phase;
-    f.gphi = grad_phase;
-    const size_t ring_ctas = (kStaticBytes - kConstBytes) / ring_per_cta;
-    f.spectra = static_cast<const float2*>(spectra);
     f.spec_ld = (desc->flags & MFBD_FLAG_FULL_SPECTRUM) ? kN : kN / 2 + 1;
-    f.loss = loss;
-    f.object = static_cast<float2*>(object);
-    f.scratch_ring = 1;
-
     const FusedGeometry g = fused_geometry(max_box);
-    const int per_sm = max_ctas_per_sm(g);
-    if (per_sm < 1) return set_error(MFBD_ERR_UNSUPPORTED, "fused kernel does not fit on this device");
-    size_t ctas = (size_t)sms * per_sm;
-    if (ctas > ring_ctas) ctas = ring_ctas;
-    if (ctas > (size_t)P) ctas = (size_t)P;
-    f.gscr = reinterpret_cast<float2*>(base + kConstBytes);
-    f.pscr = f.gscr + ctas * J * kHalf;
-    if ((e = launch_fused(f, MODE_FUSED, g, (int)ctas, s)) != cudaSuccess)
-        return set_cuda_error(e, "fused kernel");
+    if (max_ctas_per_sm(g) < 1) return set_error(MFBD_ERR_UNSUPPORTED, "pass kernel does not fit on this device");
+    // the patches go through in batches whose scratch fits the array
+    const int batch = (int)((kStaticBytes - kConstBytes) / per_patch);
+    float2* gscr = reinterpret_cast<float2*>(base + kConstBytes);
+    for (int p0 = 0; p0 < P; p0 += batch) {
+        const int pb = P - p0 < batch ? P - p0 : batch;
+        const size_t img = (size_t)p0 * J * kN * kN;
+        f.P = pb;
+        f.phi = phase + img;
+        f.gphi = grad_phase + img;
+        f.gscr = gscr;
+        f.pscr = gscr + (size_t)pb * K * J * kHalf;
+        f.spectra = static_cast<const float2*>(spectra) + (size_t)p0 * K * J * kN * f.spec_ld;
+        f.loss = loss + p0;
+        f.object = object ? static_cast<float2*>(object) + (size_t)p0 * K * kN * f.spec_ld : nullptr;
+        if ((e = launch_fused(f, MODE_FUSED, g, sms, s)) != cudaSuccess) return set_cuda_error(e, "kernels");
+    }
     return MFBD_OK;
 }

@@ -37,6 +37,15 @@ extern "C" int mfbd_test_fft_host(int kind, const float* in, float* out) {
             for (int i = 0; i < 32; ++i) { out[2 * i] = a[i].x; out[2 * i + 1] = a[i].y; }
             return 0;
         }
+        case 5:
+        case 6: {
+            float2 a[64];
+            for (int i = 0; i < 64; ++i) a[i] = make_float2(in[2 * i], in[2 * i + 1]);
+            if (kind == 5) fftreg::fft4<64, -1>(a);
+            else fftreg::fft4<64, +1>(a);
+            for (int i = 0; i < 64; ++i) { out[2 * i] = a[i].x; out[2 * i + 1] = a[i].y; }
+            return 0;
+        }
         default:
             return 1;
     }

@@ -14,6 +14,7 @@ from . import _lib
 
 _BASIS = {"zernike": _lib.MFBD_BASIS_ZERNIKE, "kl": _lib.MFBD_BASIS_KL, "user": _lib.MFBD_BASIS_USER}
 _PREC = {"fp32": _lib.MFBD_PREC_FP32, "bf16_phase": _lib.MFBD_PREC_BF16_PHASE}
+KERNEL_KINDS = ("phase", "forward", "reduction", "adjoint", "grad")
 
 
 def _fptr(a, ctype):
@@ -173,13 +174,12 @@ class Plan:
                    "mfbd_plan_set_profiling")
 
     def read_profile(self, reset=True):
-        """mfbd_plan_read_profile -> {kind: (ms, launches)} for the kinds
-        'phase', 'fused', 'grad'."""
-        ms = np.zeros(3, np.float64)
-        n = np.zeros(3, np.int64)
+        """mfbd_plan_read_profile -> {kind: (ms, launches)} for KERNEL_KINDS."""
+        ms = np.zeros(5, np.float64)
+        n = np.zeros(5, np.int64)
         _lib.check(self._lib.mfbd_plan_read_profile(self._h, ms.ctypes.data, n.ctypes.data, int(reset)),
                    "mfbd_plan_read_profile")
-        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(("phase", "fused", "grad"))}
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
 
     def close(self):
         if getattr(self, "_h", None):

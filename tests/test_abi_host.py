@@ -141,7 +141,7 @@ def test_register_ffts_match_oracle(lib, seed):
     g = np.random.default_rng(seed)
     z = (g.standard_normal(64) + 1j * g.standard_normal(64)).astype(np.complex64)
     zin = np.stack([z.real, z.imag], -1).ravel()
-    for kind, sign in ((0, -1), (1, +1)):
+    for kind, sign in ((0, -1), (1, +1), (5, -1), (6, +1)):
         o = _host_fft(lib, kind, zin, 128)
         ref = dft.fft_radix2(z.astype(np.complex128), sign=sign)
         got = o[0::2] + 1j * o[1::2]
@@ -169,7 +169,7 @@ def test_noalloc_entry_point_checks_arguments_on_host(lib):
     rejected with MFBD_ERR_INVALID_ARG."""
     f = lib.mfbd_phase_loss_grad_noalloc
     assert f(None, None, None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
-    d = _desc(n_frames=337)
+    d = _desc(n_frames=337)  # 1 object x 337 frames
     assert f(ctypes.byref(d.desc), None, None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
     assert b"static workspace" in lib.mfbd_last_error()
     d = _desc(gamma=-1.0)

@@ -134,11 +134,14 @@ def test_full_spectrum_layout(c1):
     _check(c1, loss, grad, obj, ref, full_spectrum=True)
 
 
-@pytest.mark.parametrize("variant", ["one_frame", "weights", "ragged_pupil", "obscured", "one_mode"])
+@pytest.mark.parametrize("variant", ["one_frame", "weights", "ragged_pupil", "obscured", "one_mode",
+                                     "many_frames"])
 def test_edge_cases(variant):
     kw = dict(n_frames=4, seed=31)
     if variant == "one_frame":
         kw.update(n_frames=1)
+    elif variant == "many_frames":  # more frames than the register-resident reduction holds
+        kw.update(n_frames=20, n_modes=10)
     elif variant == "weights":
         kw.update(weights=[[1.0, 0.0, 2.5, 0.3]])
     elif variant == "ragged_pupil":
