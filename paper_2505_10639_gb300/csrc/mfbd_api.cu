@@ -36,6 +36,7 @@ struct ObjectData {
     int W = 0, x0 = 0, npup = 0;
     float scale = 1.f, inv_z = 0.f;
     long long phi_off = 0;
+    long long part_off = 0;     // offset of this object's modal-adjoint partial sums
     float* d_basis = nullptr;   // [M][W*W]
     uint64_t* d_mask = nullptr; // [W]
     uint64_t* d_supp = nullptr; // [N]
@@ -52,6 +53,7 @@ struct mfbd_plan {
     float* d_weights = nullptr;
     float* d_phi = nullptr;
     float* d_gphi = nullptr;
+    float* d_gpart = nullptr;   // modal-adjoint partial sums [K][splits][P*J][M]
     float2* d_gscr = nullptr;   // per unit [P][K][J][N][N/2+1]: OTF, then adjoint seed
     float2* d_pscr = nullptr;   // per unit [P][K][J][N*N]: field
     long long phi_floats = 0;
@@ -219,16 +221,24 @@ int run_phase(mfbd_plan_t p, const float* coeffs, cudaStream_t s) {
 }
 
 int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s) {
-    for (int k = 0; k < p->K; ++k) {
+    const int U = p->P * p->J;
+    GradParts gp{};
+    gp.K = p->K;
+    const int pi = prof_begin(p, 4, s);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < p->K && e == cudaSuccess; ++k) {
         const ObjectData& o = p->obj[k];
-        const int pi = prof_begin(p, 4, s);
-        cudaError_t e = launch_grad_gemm(p->d_gphi + o.phi_off, p->P * p->J, o.W * o.W, o.d_basis, p->M,
-                                         o.scale, k > 0, grad, s);
-        prof_end(p, pi, s);
-        if (e != cudaSuccess) {
-            p->failed = true;
-            return cuda_fail(e, "modal adjoint");
-        }
+        int chunk = 0;
+        gp.splits[k] = grad_splits(o.W * o.W, &chunk);
+        gp.scale[k] = o.scale;
+        gp.part[k] = p->d_gpart + o.part_off;
+        e = launch_grad_gemm(p->d_gphi + o.phi_off, U, o.W * o.W, o.d_basis, p->M, p->d_gpart + o.part_off, s);
+    }
+    if (e == cudaSuccess) e = launch_grad_combine(gp, U, p->M, grad, s);
+    prof_end(p, pi, s);
+    if (e != cudaSuccess) {
+        p->failed = true;
+        return cuda_fail(e, "modal adjoint");
     }
     return MFBD_OK;
 }
@@ -403,6 +413,13 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
                 throw cuda_fail(e, "upload plan data");
         }
         p->phi_floats = phi_floats;
+        long long part_floats = 0;
+        for (int k = 0; k < p->K; ++k) {
+            int chunk = 0;
+            p->obj[k].part_off = part_floats;
+            part_floats += (long long)grad_splits(p->obj[k].W * p->obj[k].W, &chunk) * p->P * p->J * p->M;
+        }
+        if ((st = dev_alloc(p, &p->d_gpart, (size_t)part_floats))) throw st;
         if ((st = dev_alloc(p, &p->d_phi, (size_t)phi_floats))) throw st;
         if ((st = dev_alloc(p, &p->d_gphi, (size_t)phi_floats))) throw st;
         if ((st = dev_alloc(p, &p->d_gscr, (size_t)p->P * p->K * p->J * kHalf))) throw st;

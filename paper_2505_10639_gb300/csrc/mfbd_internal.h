@@ -64,9 +64,21 @@ cudaError_t launch_fused(const FusedParams& prm, int mode, const FusedGeometry& 
 cudaError_t launch_phase_gemm(const float* a, int U, int M, const float* basis, int npix,
                               float scale, float* phase, cudaStream_t s);
 
-// grad[u][m] (+)= scale * sum_i gphi[u][i] basis[m][i]
-cudaError_t launch_grad_gemm(const float* gphi, int U, int npix, const float* basis, int M,
-                             float scale, int accumulate, float* grad, cudaStream_t s);
+// Modal adjoint, split over pixels: part[z][u][m] = sum over chunk z of
+// gphi[u][i] basis[m][i]; grad_splits gives the number of chunks (and the
+// chunk length) for npix pixels.
+int grad_splits(int npix, int* chunk);
+cudaError_t launch_grad_gemm(const float* gphi, int U, int npix, const float* basis, int M, float* part,
+                             cudaStream_t s);
+
+// grad[u][m] = sum_k scale_k sum_z part_k[z][u][m] (fixed summation order)
+struct GradParts {
+    int K;
+    int splits[kMaxObjects];
+    float scale[kMaxObjects];
+    const float* part[kMaxObjects];
+};
+cudaError_t launch_grad_combine(const GradParts& gp, int U, int M, float* grad, cudaStream_t s);
 
 int max_ctas_per_sm(const FusedGeometry& g);
 

@@ -349,84 +349,145 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
 #undef U_PF
 }
 
-// Per-object frame reduction: O, loss terms, adjoint seeds G_j (over H_j).
-// The residual r_j = D_j - O H_j is formed in FP32. Where the fit leaves
-// little residual energy (sum_j w|r_j|^2 < kCancel sum_j w|D_j|^2, estimated
-// from E - |N|^2/Q), r_j cancels badly in FP32 (for J = 1, r = D gamma / Q
-// everywhere the OTF is large), so that frequency is redone with N, Q, O and
-// r_j in FP64. With several frames this triggers at DC and little else.
+// Frame reduction of one (patch, object) by one warp: per frequency u,
+// N = sum_j w D conj(H), Q = sum_j w |H|^2 + gamma, O = N / Q, the loss term
+// t(u) = sum_j w |D - O H|^2 + gamma |O|^2 and the adjoint seeds
+// G_j = -w conj(O)(D - O H) (written over H_j). The residual is formed in
+// FP32. Where the fit leaves little residual energy (sum_j w|r_j|^2 <
+// kCancel sum_j w|D_j|^2, estimated from E - |N|^2/Q) it cancels badly in
+// FP32 (for J = 1, r = D gamma / Q everywhere the OTF is large), so such a
+// frequency is redone with N, Q, O and r_j in FP64 -- except DC, whose seed
+// is zero and whose loss term is exact enough in FP32. Each lane sums its
+// loss terms with Kahan compensation; the warp combines them in FP64.
 constexpr float kCancel = 1e-3f;
 
-__device__ double reduce_object_any(const FusedParams& prm, int p, int k, const uint64_t* ssupp, float2* hbase) {
+struct KahanSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+__device__ __forceinline__ void fp64_frequency(int J, const float2* dp, size_t dstride, float2* hp, const float* w,
+                                               double gamma, bool seed, float& t, float2& o) {
+    double nx = 0.0, ny = 0.0, qd = gamma;
+    for (int j = 0; j < J; ++j) {
+        const float2 d = dp[(size_t)j * dstride];
+        const float2 h = hp[(size_t)j * kHalf];
+        const double wj = w[j];
+        nx += wj * ((double)d.x * h.x + (double)d.y * h.y);
+        ny += wj * ((double)d.y * h.x - (double)d.x * h.y);
+        qd += wj * ((double)h.x * h.x + (double)h.y * h.y);
+    }
+    const double ox = nx / qd, oy = ny / qd;
+    double tsum = 0.0;
+    for (int j = 0; j < J; ++j) {
+        const float2 d = dp[(size_t)j * dstride];
+        const float2 h = hp[(size_t)j * kHalf];
+        const double wj = w[j];
+        const double rx = (double)d.x - (ox * h.x - oy * h.y);
+        const double ry = (double)d.y - (ox * h.y + oy * h.x);
+        tsum += wj * (rx * rx + ry * ry);
+        hp[(size_t)j * kHalf] = seed ? make_float2((float)(-wj * (ox * rx + oy * ry)), (float)(-wj * (ox * ry - oy * rx)))
+                                     : make_float2(0.f, 0.f);
+    }
+    t = (float)(tsum + gamma * (ox * ox + oy * oy));
+    o = make_float2((float)ox, (float)oy);
+}
+
+// JM > 0: J <= JM, the J spectra and OTFs of a frequency are loaded once, all
+// at once, into registers. JM == 0: any J, streamed from memory twice.
+template <int JM>
+__device__ double reduce_object_warp(const FusedParams& prm, int p, int k) {
+    const int lane = threadIdx.x & 31;
     const int J = prm.J;
     const size_t unit0 = ((size_t)p * prm.K + k) * J;
     const size_t dstride = (size_t)kN * prm.spec_ld;
     const float2* dbase = prm.spectra + unit0 * dstride;
+    float2* hbase = prm.gscr + unit0 * kHalf;
     const float* w = prm.weights + (size_t)k * J;
+    const uint64_t* supp = prm.obj[k].supp;
     const float gam = (float)prm.gamma;
-    double acc = 0.0;
-    for (int f = threadIdx.x; f < kHalf; f += blockDim.x) {
+    float wv[JM > 0 ? JM : 1];
+    if constexpr (JM > 0) {
+#pragma unroll
+        for (int j = 0; j < JM; ++j) wv[j] = (j < J) ? w[j] : 0.f;
+    }
+    KahanSum acc;
+    for (int f = lane; f < kHalf; f += 32) {
         const int ky = f / kNH, kx = f - ky * kNH;
         const size_t doff = (size_t)ky * prm.spec_ld + kx;
         const float2* dp = dbase + doff;
         float2* hp = hbase + f;
-        float2 num = make_float2(0.f, 0.f);
-        float e = 0.f, q = 0.f;
-#pragma unroll 6
-        for (int j = 0; j < J; ++j) {
-            const float2 d = dp[(size_t)j * dstride];
-            const float2 h = hp[(size_t)j * kHalf];
-            const float wj = w[j];
-            num.x += wj * (d.x * h.x + d.y * h.y);
-            num.y += wj * (d.y * h.x - d.x * h.y);
-            e += wj * (d.x * d.x + d.y * d.y);
-            q += wj * (h.x * h.x + h.y * h.y);
-        }
-        q += gam;
-        const float invq = 1.0f / q;
-        float2 o = cscale(num, invq);
-        const bool seed = (f != 0) && bit(ssupp[ky], kx);
-        const float t_est = e - (num.x * num.x + num.y * num.y) * invq;
-        float t;
-        if (!(t_est < kCancel * e)) {
-            float tsum = 0.f;
-#pragma unroll 6
+        const bool seed = (f != 0) && bit(supp[ky], kx);
+        float2 num = make_float2(0.f, 0.f), o;
+        float e = 0.f, q = 0.f, t;
+        if constexpr (JM > 0) {
+            float2 d[JM], h[JM];
+#pragma unroll
+            for (int j = 0; j < JM; ++j) {
+                d[j] = (j < J) ? dp[(size_t)j * dstride] : make_float2(0.f, 0.f);
+                h[j] = (j < J) ? hp[(size_t)j * kHalf] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < JM; ++j) {
+                num.x += wv[j] * (d[j].x * h[j].x + d[j].y * h[j].y);
+                num.y += wv[j] * (d[j].y * h[j].x - d[j].x * h[j].y);
+                e += wv[j] * (d[j].x * d[j].x + d[j].y * d[j].y);
+                q += wv[j] * (h[j].x * h[j].x + h[j].y * h[j].y);
+            }
+            q += gam;
+            const float invq = 1.0f / q;
+            o = cscale(num, invq);
+            const float t_est = e - (num.x * num.x + num.y * num.y) * invq;
+            if (f != 0 && t_est < kCancel * e) {
+                fp64_frequency(J, dp, dstride, hp, w, prm.gamma, seed, t, o);
+            } else {
+                float tsum = 0.f;
+#pragma unroll
+                for (int j = 0; j < JM; ++j) {
+                    const float2 r = csub(d[j], cmul(o, h[j]));
+                    tsum += wv[j] * (r.x * r.x + r.y * r.y);
+                    if (j < J)
+                        hp[(size_t)j * kHalf] = seed ? cscale(cmul(cconj(o), r), -wv[j]) : make_float2(0.f, 0.f);
+                }
+                t = tsum + gam * (o.x * o.x + o.y * o.y);
+            }
+        } else {
+#pragma unroll 4
             for (int j = 0; j < J; ++j) {
                 const float2 d = dp[(size_t)j * dstride];
                 const float2 h = hp[(size_t)j * kHalf];
                 const float wj = w[j];
-                const float2 r = csub(d, cmul(o, h));
-                tsum += wj * (r.x * r.x + r.y * r.y);
-                hp[(size_t)j * kHalf] = seed ? cscale(cmul(cconj(o), r), -wj) : make_float2(0.f, 0.f);
+                num.x += wj * (d.x * h.x + d.y * h.y);
+                num.y += wj * (d.y * h.x - d.x * h.y);
+                e += wj * (d.x * d.x + d.y * d.y);
+                q += wj * (h.x * h.x + h.y * h.y);
             }
-            t = tsum + gam * (o.x * o.x + o.y * o.y);
-        } else {
-            double nx = 0.0, ny = 0.0, qd = prm.gamma;
-            for (int j = 0; j < J; ++j) {
-                const float2 d = dp[(size_t)j * dstride];
-                const float2 h = hp[(size_t)j * kHalf];
-                const double wj = w[j];
-                nx += wj * ((double)d.x * h.x + (double)d.y * h.y);
-                ny += wj * ((double)d.y * h.x - (double)d.x * h.y);
-                qd += wj * ((double)h.x * h.x + (double)h.y * h.y);
+            q += gam;
+            const float invq = 1.0f / q;
+            o = cscale(num, invq);
+            const float t_est = e - (num.x * num.x + num.y * num.y) * invq;
+            if (f != 0 && t_est < kCancel * e) {
+                fp64_frequency(J, dp, dstride, hp, w, prm.gamma, seed, t, o);
+            } else {
+                float tsum = 0.f;
+#pragma unroll 4
+                for (int j = 0; j < J; ++j) {
+                    const float2 d = dp[(size_t)j * dstride];
+                    const float2 h = hp[(size_t)j * kHalf];
+                    const float wj = w[j];
+                    const float2 r = csub(d, cmul(o, h));
+                    tsum += wj * (r.x * r.x + r.y * r.y);
+                    hp[(size_t)j * kHalf] = seed ? cscale(cmul(cconj(o), r), -wj) : make_float2(0.f, 0.f);
+                }
+                t = tsum + gam * (o.x * o.x + o.y * o.y);
             }
-            const double ox = nx / qd, oy = ny / qd;
-            double tsum = 0.0;
-            for (int j = 0; j < J; ++j) {
-                const float2 d = dp[(size_t)j * dstride];
-                const float2 h = hp[(size_t)j * kHalf];
-                const double wj = w[j];
-                const double rx = (double)d.x - (ox * h.x - oy * h.y);
-                const double ry = (double)d.y - (ox * h.y + oy * h.x);
-                tsum += wj * (rx * rx + ry * ry);
-                hp[(size_t)j * kHalf] =
-                    seed ? make_float2((float)(-wj * (ox * rx + oy * ry)), (float)(-wj * (ox * ry - oy * rx)))
-                         : make_float2(0.f, 0.f);
-            }
-            t = (float)(tsum + prm.gamma * (ox * ox + oy * oy));
-            o = make_float2((float)ox, (float)oy);
         }
-        acc += ((kx == 0 || kx == kN / 2) ? 1.0 : 2.0) * (double)t;
+        acc.add((kx == 0 || kx == kN / 2) ? t : 2.0f * t);
         if (prm.object) {
             float2* ob = prm.object + ((size_t)p * prm.K + k) * dstride;
             ob[doff] = o;
@@ -434,111 +495,11 @@ __device__ double reduce_object_any(const FusedParams& prm, int p, int k, const 
                 ob[(size_t)((kN - ky) % kN) * kN + (kN - kx)] = cconj(o);
         }
     }
-    return acc;
+    double v = (double)acc.s - (double)acc.c;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;  // valid in lane 0
 }
-
-// J <= JM: the J spectra and OTFs of a frequency are loaded once, all at
-// once, into registers; both frame loops then run from registers.
-template <int JM>
-__device__ double reduce_object_reg(const FusedParams& prm, int p, int k, const uint64_t* ssupp, float2* hbase) {
-    const int J = prm.J;
-    const size_t unit0 = ((size_t)p * prm.K + k) * J;
-    const size_t dstride = (size_t)kN * prm.spec_ld;
-    const float2* dbase = prm.spectra + unit0 * dstride;
-    const float gam = (float)prm.gamma;
-    float wv[JM];
-#pragma unroll
-    for (int j = 0; j < JM; ++j) wv[j] = (j < J) ? prm.weights[(size_t)k * J + j] : 0.f;
-    double acc = 0.0;
-    for (int f = threadIdx.x; f < kHalf; f += blockDim.x) {
-        const int ky = f / kNH, kx = f - ky * kNH;
-        const size_t doff = (size_t)ky * prm.spec_ld + kx;
-        const float2* dp = dbase + doff;
-        float2* hp = hbase + f;
-        float2 d[JM], h[JM];
-#pragma unroll
-        for (int j = 0; j < JM; ++j) {
-            d[j] = (j < J) ? dp[(size_t)j * dstride] : make_float2(0.f, 0.f);
-            h[j] = (j < J) ? hp[(size_t)j * kHalf] : make_float2(0.f, 0.f);
-        }
-        float2 num = make_float2(0.f, 0.f);
-        float e = 0.f, q = 0.f;
-#pragma unroll
-        for (int j = 0; j < JM; ++j) {
-            num.x += wv[j] * (d[j].x * h[j].x + d[j].y * h[j].y);
-            num.y += wv[j] * (d[j].y * h[j].x - d[j].x * h[j].y);
-            e += wv[j] * (d[j].x * d[j].x + d[j].y * d[j].y);
-            q += wv[j] * (h[j].x * h[j].x + h[j].y * h[j].y);
-        }
-        q += gam;
-        const float invq = 1.0f / q;
-        float2 o = cscale(num, invq);
-        const bool seed = (f != 0) && bit(ssupp[ky], kx);
-        const float t_est = e - (num.x * num.x + num.y * num.y) * invq;
-        float t;
-        if (!(t_est < kCancel * e)) {
-            float tsum = 0.f;
-#pragma unroll
-            for (int j = 0; j < JM; ++j) {
-                const float2 r = csub(d[j], cmul(o, h[j]));
-                tsum += wv[j] * (r.x * r.x + r.y * r.y);
-                if (j < J) hp[(size_t)j * kHalf] = seed ? cscale(cmul(cconj(o), r), -wv[j]) : make_float2(0.f, 0.f);
-            }
-            t = tsum + gam * (o.x * o.x + o.y * o.y);
-        } else {
-            double nx = 0.0, ny = 0.0, qd = prm.gamma;
-#pragma unroll
-            for (int j = 0; j < JM; ++j) {
-                const double wj = wv[j];
-                nx += wj * ((double)d[j].x * h[j].x + (double)d[j].y * h[j].y);
-                ny += wj * ((double)d[j].y * h[j].x - (double)d[j].x * h[j].y);
-                qd += wj * ((double)h[j].x * h[j].x + (double)h[j].y * h[j].y);
-            }
-            const double ox = nx / qd, oy = ny / qd;
-            double tsum = 0.0;
-#pragma unroll
-            for (int j = 0; j < JM; ++j) {
-                const double wj = wv[j];
-                const double rx = (double)d[j].x - (ox * h[j].x - oy * h[j].y);
-                const double ry = (double)d[j].y - (ox * h[j].y + oy * h[j].x);
-                tsum += wj * (rx * rx + ry * ry);
-                if (j < J)
-                    hp[(size_t)j * kHalf] =
-                        seed ? make_float2((float)(-wj * (ox * rx + oy * ry)), (float)(-wj * (ox * ry - oy * rx)))
-                             : make_float2(0.f, 0.f);
-            }
-            t = (float)(tsum + prm.gamma * (ox * ox + oy * oy));
-            o = make_float2((float)ox, (float)oy);
-        }
-        acc += ((kx == 0 || kx == kN / 2) ? 1.0 : 2.0) * (double)t;
-        if (prm.object) {
-            float2* ob = prm.object + ((size_t)p * prm.K + k) * dstride;
-            ob[doff] = o;
-            if (prm.spec_ld == kN && kx > 0 && kx < kN / 2)
-                ob[(size_t)((kN - ky) % kN) * kN + (kN - kx)] = cconj(o);
-        }
-    }
-    return acc;
-}
-
-__device__ double reduce_object(const FusedParams& prm, int p, int k, const uint64_t* ssupp, float2* hbase) {
-    if (prm.J <= 16) return reduce_object_reg<16>(prm, p, k, ssupp, hbase);
-    return reduce_object_any(prm, p, k, ssupp, hbase);
-}
-
-__device__ double block_sum(double v, double* sred) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) sred[warp] = v;
-    __syncthreads();
-    double tot = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += sred[i];
-    return tot;
-}
-
 
 // One warp per unit (patch, object, frame), persistent over the units;
 // FIRST..LAST selects the forward (PUPIL, FIELD, OTF) or adjoint (SEED,
@@ -585,17 +546,22 @@ __global__ void __launch_bounds__(kThreads, 2) mfbd_pass_kernel(const FusedParam
     }
 }
 
-// Frame reduction, one CTA per patch: every frequency of every object.
-__global__ void __launch_bounds__(256, 2) mfbd_reduce_kernel(const FusedParams prm) {
-    __shared__ double sred[32];
+// Frame reduction: one CTA per patch, warp k reduces object k; the patch
+// loss sums the objects in order (deterministic).
+template <int JM>
+__global__ void __launch_bounds__(32 * kMaxObjects) mfbd_reduce_kernel(const FusedParams prm) {
+    __shared__ double sobj[kMaxObjects];
+    const int k = threadIdx.x >> 5;
     for (int p = blockIdx.x; p < prm.P; p += gridDim.x) {
-        double lacc = 0.0;
-        for (int k = 0; k < prm.K; ++k) {
-            float2* hbase = prm.gscr + ((size_t)p * prm.K + k) * prm.J * kHalf;
-            lacc += reduce_object(prm, p, k, prm.obj[k].supp, hbase);
+        const double v = reduce_object_warp<JM>(prm, p, k);
+        if ((threadIdx.x & 31) == 0) sobj[k] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int i = 0; i < prm.K; ++i) tot += sobj[i];
+            prm.loss[p] = tot;
         }
-        const double tot = block_sum(lacc, sred);
-        if (threadIdx.x == 0) prm.loss[p] = tot;
+        __syncthreads();
     }
 }
 
@@ -635,15 +601,21 @@ cudaError_t launch_pass(const FusedParams& prm, const FusedGeometry& g, int sms,
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduction(const FusedParams& prm, int sms, cudaStream_t s) {
-    if (prm.P == 0) return cudaSuccess;
+template <int JM>
+cudaError_t launch_reduction_jm(const FusedParams& prm, int sms, cudaStream_t s) {
+    const int threads = 32 * prm.K;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mfbd_reduce_kernel, 256, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mfbd_reduce_kernel<JM>, threads, 0);
     if (e != cudaSuccess) return e;
     long long ctas = (long long)sms * (per_sm > 0 ? per_sm : 1);
     if (ctas > prm.P) ctas = prm.P;
-    mfbd_reduce_kernel<<<(int)ctas, 256, 0, s>>>(prm);
+    mfbd_reduce_kernel<JM><<<(int)ctas, threads, 0, s>>>(prm);
     return cudaGetLastError();
+}
+
+cudaError_t launch_reduction(const FusedParams& prm, int sms, cudaStream_t s) {
+    if (prm.P == 0) return cudaSuccess;
+    return prm.J <= 16 ? launch_reduction_jm<16>(prm, sms, s) : launch_reduction_jm<0>(prm, sms, s);
 }
 
 cudaError_t launch_forward_passes(const FusedParams& prm, const FusedGeometry& g, int sms, cudaStream_t s) {
