@@ -56,6 +56,8 @@ struct mfbd_plan {
     float* d_gpart = nullptr;   // modal-adjoint partial sums [K][splits][P*J][M]
     float2* d_gscr = nullptr;   // per unit [P][K][J][N][N/2+1]: OTF, then adjoint seed
     float2* d_pscr = nullptr;   // per unit [P][K][J][N*N]: field
+    float2* d_uscr = nullptr;   // per unit [P][K][J][ustride]: pupil phasors on the box
+    int ustride = 0;
     long long phi_floats = 0;
     size_t workspace = 0;
     FusedGeometry geo{};
@@ -147,7 +149,7 @@ void release(mfbd_plan* p) {
 }
 
 FusedParams fused_params(const mfbd_plan* p, const void* spectra, double* loss, void* object, float2* gscr,
-                         float2* pscr) {
+                         float2* pscr, float2* uscr) {
     FusedParams f{};
     f.P = p->P;
     f.K = p->K;
@@ -159,6 +161,8 @@ FusedParams fused_params(const mfbd_plan* p, const void* spectra, double* loss, 
     f.gphi = p->d_gphi;
     f.gscr = gscr;
     f.pscr = pscr;
+    f.uscr = uscr;
+    f.ustride = uscr ? p->ustride : 0;
     f.spectra = static_cast<const float2*>(spectra);
     f.spec_ld = (p->flags & MFBD_FLAG_FULL_SPECTRUM) ? p->N : p->N / 2 + 1;
     f.loss = loss;
@@ -245,8 +249,8 @@ int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s) {
 
 int run_fused(mfbd_plan_t p, int mode, const void* spectra, double* loss, void* object, float2* gscr,
               cudaStream_t s) {
-    FusedParams f = mode == MODE_OTF ? fused_params(p, spectra, loss, object, gscr, nullptr)
-                                     : fused_params(p, spectra, loss, object, p->d_gscr, p->d_pscr);
+    FusedParams f = mode == MODE_OTF ? fused_params(p, spectra, loss, object, gscr, nullptr, nullptr)
+                                     : fused_params(p, spectra, loss, object, p->d_gscr, p->d_pscr, p->d_uscr);
     cudaError_t e = cudaSuccess;
     if (mode != MODE_BWD) {
         const int pi = prof_begin(p, 1, s);
@@ -424,6 +428,8 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
         if ((st = dev_alloc(p, &p->d_gphi, (size_t)phi_floats))) throw st;
         if ((st = dev_alloc(p, &p->d_gscr, (size_t)p->P * p->K * p->J * kHalf))) throw st;
         if ((st = dev_alloc(p, &p->d_pscr, (size_t)p->P * p->K * p->J * n * n))) throw st;
+        p->ustride = (max_box * max_box + 31) & ~31;  // 256-byte aligned units
+        if ((st = dev_alloc(p, &p->d_uscr, (size_t)p->P * p->K * p->J * p->ustride))) throw st;
 
         p->geo = fused_geometry(max_box);
         int per_sm = max_ctas_per_sm(p->geo);

@@ -34,6 +34,8 @@ struct FusedParams {
     float* gphi;              // dL/dphi, same layout
     float2* gscr;             // [P][K][J][N][N/2+1]: OTF, then dL/dconj(H)
     float2* pscr;             // [P][K][J][N x N]: field p = F P, stored [x][y] (null: not kept)
+    float2* uscr;             // [P][K][J][ustride]: pupil phasors exp(i phi) on the box (null: not kept)
+    int ustride;              // complex elements per unit in uscr (>= W_k^2 for every object)
     const float2* spectra;    // D
     int spec_ld;              // row stride of D and O in complex elements (33 or 64)
     double* loss;             // [P]

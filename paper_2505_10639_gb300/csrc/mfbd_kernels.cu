@@ -62,6 +62,20 @@ __device__ __forceinline__ float2 expi(float ph) {
     return make_float2(c, s);
 }
 
+// Asynchronous global -> shared copies of 4 or 8 bytes (both addresses
+// aligned to the size); complete for the issuing thread after cp_async_wait.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(__cvta_generic_to_global(gmem))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(__cvta_generic_to_global(gmem))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // L2 prefetch of [ptr, ptr + bytes) (bulk prefetch needs 16-byte alignment
 // and a multiple of 16 bytes; the range is widened to that).
 __device__ __forceinline__ void prefetch_l2(const void* ptr, size_t bytes) {
@@ -75,11 +89,15 @@ __device__ __forceinline__ void prefetch_l2(const void* ptr, size_t bytes) {
                      : "memory");
 }
 
+// Per-unit pointers of the warp's current unit, kept in shared memory (one
+// per warp) so they do not occupy registers across the transforms; every
+// pass reads the ones it needs once.
 struct Unit {
-    const float* phi;  // first box pixel of this unit's phase image
+    const float* phi;  // first box pixel of the unit's phase image (row stride ld)
     float* gphi;       // same for dL/dphi
-    float2* h;         // [N][N/2+1]: H (forward) then G (adjoint)
-    float2* pf;        // field p, [x][y]; null: not stored
+    float2* pp;        // pupil phasors exp(i phi) on the box, [W][W]
+    float2* h;         // [N][N/2+1]: H (forward), then the adjoint seed G
+    float2* pf;        // field p = F P, [x][y]; null: not kept
     int W, ld;
     float inv_z;
 };
@@ -96,148 +114,173 @@ __device__ __forceinline__ int pass_rounds(int pass, int W) {
 
 __device__ __forceinline__ bool bit(uint64_t w, int b) { return (w >> b) & 1ull; }
 
+// ------------------------------------------------------------ load stages
+
+template <int ES>
+__device__ __forceinline__ void load_pupil(const volatile Unit* su, float2* E, const uint64_t* smask, int W, int c,
+                                           float2 (&v)[kN]) {
+    if (c < W) {
+        const float* ph = (const float*)su->phi + c;
+        float2* pp = (float2*)su->pp + c;
+        const int ld = su->ld;
+        float phv[kN];  // every phase load of the column is issued before use
+#pragma unroll
+        for (int yy = 0; yy < kN; ++yy) phv[yy] = (yy < W) ? ph[yy * ld] : 0.f;
+#pragma unroll
+        for (int yy = 0; yy < kN; ++yy)
+            if (yy < W) E[yy * ES + c].x = phv[yy];
+#pragma unroll 4
+        for (int yy = 0; yy < W; ++yy) {
+            const float2 pv = bit(smask[yy], c) ? expi(E[yy * ES + c].x) : make_float2(0.f, 0.f);
+            E[yy * ES + c] = pv;
+            if (pp) pp[yy * W] = pv;
+        }
+    }
+#pragma unroll
+    for (int y = 0; y < kN; ++y) v[y] = (c < W && y < W) ? E[y * ES + c] : make_float2(0.f, 0.f);
+}
+
+// ----------------------------------------------------------- the machine
 
 // Runs passes [FIRST, LAST) of one unit on the calling warp.
-template <int FIRST, int LAST>
-__device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __restrict__ E, int es,
+template <int FIRST, int LAST, int ES>
+__device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __restrict__ E,
                                            const uint64_t* __restrict__ smask, const uint64_t* __restrict__ ssupp) {
     const int lane = threadIdx.x & 31;
-#define U_W (su->W)
-#define U_LD (su->ld)
-#define U_INVZ (su->inv_z)
-#define U_PHI ((const float*)su->phi)
-#define U_GPHI ((float*)su->gphi)
-#define U_H ((float2*)su->h)
-#define U_PF ((float2*)su->pf)
-    const int W = U_W;
+    const int W = su->W;
 #pragma unroll 1
     for (int pass = FIRST; pass < LAST; ++pass) {
         const int nr = pass_rounds(pass, W);
 #pragma unroll 1
         for (int r = 0; r < nr; ++r) {
             float2 v[kN];
-            const bool adj = pass >= P_SEED;
             // ------------------------------------------------------ load
-            switch (pass) {
-                case P_PUPIL: if constexpr (FIRST <= P_PUPIL && P_PUPIL < LAST) {
-                    const int c = lane + 32 * r;
-                    if (c < W) {
-                        // all phase loads of the column are issued before use
-                        const float* ph = U_PHI + c;
-                        const int ld = U_LD;
-                        float phv[kN];
-#pragma unroll
-                        for (int yy = 0; yy < kN; ++yy) phv[yy] = (yy < W) ? ph[yy * ld] : 0.f;
-#pragma unroll
-                        for (int yy = 0; yy < kN; ++yy)
-                            if (yy < W) E[yy * es + c].x = phv[yy];
-#pragma unroll 4
-                        for (int yy = 0; yy < W; ++yy)
-                            E[yy * es + c] = bit(smask[yy], c) ? expi(E[yy * es + c].x) : make_float2(0.f, 0.f);
-                    }
-#pragma unroll
-                    for (int y = 0; y < kN; ++y)
-                        v[y] = (c < W && y < W) ? E[y * es + c] : make_float2(0.f, 0.f);
-                    break;
-                }
-                case P_FIELD: if constexpr (FIRST <= P_FIELD && P_FIELD < LAST) {
-                    if (r < 2) {
+            if constexpr (FIRST <= P_PUPIL && P_PUPIL < LAST) {
+                if (pass == P_PUPIL) load_pupil<ES>(su, E, smask, W, lane + 32 * r, v);
+            }
+            if constexpr (FIRST <= P_FIELD && P_FIELD < LAST) {
+                if (pass == P_FIELD) {
+                    if (r < 2) {  // row y of the pupil's column transform (box columns [0, W))
                         const int y = lane + 32 * r;
 #pragma unroll
-                        for (int x = 0; x < kN; ++x) v[x] = (x < W) ? E[y * es + x] : make_float2(0.f, 0.f);
-                    } else {
+                        for (int x = 0; x < kN; ++x) v[x] = (x < W) ? E[y * ES + x] : make_float2(0.f, 0.f);
+                    } else {  // two real PSF rows as one complex line
 #pragma unroll
                         for (int i = 0; i < kN / 2; ++i) {
-                            const float2 a = E[lane * es + i], b = E[(lane + 32) * es + i];
+                            const float2 a = E[lane * ES + i], b = E[(lane + 32) * ES + i];
                             v[2 * i] = make_float2(a.x, b.x);
                             v[2 * i + 1] = make_float2(a.y, b.y);
                         }
                     }
-                    break;
                 }
-                case P_OTF: if constexpr (FIRST <= P_OTF && P_OTF < LAST) {  // lane 0: the packed real columns kx = 0, N/2
+            }
+            if constexpr (FIRST <= P_OTF && P_OTF < LAST) {
+                if (pass == P_OTF) {  // column lane; lane 0: real columns 0 and N/2 packed
 #pragma unroll
-                    for (int ky = 0; ky < kN; ++ky) v[ky] = E[ky * es + lane];
-                    break;
+                    for (int ky = 0; ky < kN; ++ky) v[ky] = E[ky * ES + lane];
                 }
-                case P_SEED: if constexpr (FIRST <= P_SEED && P_SEED < LAST) {  // lane 0: columns 0 and N/2 packed as a + i b
+            }
+            if constexpr (FIRST <= P_SEED && P_SEED < LAST) {
+                if (pass == P_SEED) {  // conj of column lane of G; lane 0: columns 0 and N/2 as a + i b
+                    const float2* h = (const float2*)su->h;
 #pragma unroll
                     for (int ky = 0; ky < kN; ++ky) {
-                        const float2 a = U_H[ky * kNH + lane];
-                        const float2 b = lane == 0 ? U_H[ky * kNH + 32] : make_float2(0.f, 0.f);
-                        v[ky] = make_float2(a.x - b.y, -(a.y + b.x));  // conj(a + i b)
+                        const float2 a = h[ky * kNH + lane];
+                        const float2 b = lane == 0 ? h[ky * kNH + 32] : make_float2(0.f, 0.f);
+                        v[ky] = make_float2(a.x - b.y, -(a.y + b.x));
                     }
-                    break;
                 }
-                case P_C2R: if constexpr (FIRST <= P_C2R && P_C2R < LAST) {
-                    if (r == 0) {
-                        // rows lane and lane+32: Hermitian extension T[k] = conj T[N-k]
+            }
+            if constexpr (FIRST <= P_C2R && P_C2R < LAST) {
+                if (pass == P_C2R) {
+                    if (r == 0) {  // conj of T_lane + i T_(lane+32), Hermitian-extended rows
 #pragma unroll
                         for (int k = 0; k < kN; ++k) {
                             float2 a, b;
                             if (k == 0) {
-                                a = make_float2(E[lane * es].x, 0.f);
-                                b = make_float2(E[(lane + 32) * es].x, 0.f);
+                                a = make_float2(E[lane * ES].x, 0.f);
+                                b = make_float2(E[(lane + 32) * ES].x, 0.f);
                             } else if (k == kN / 2) {
-                                a = make_float2(E[lane * es].y, 0.f);
-                                b = make_float2(E[(lane + 32) * es].y, 0.f);
+                                a = make_float2(E[lane * ES].y, 0.f);
+                                b = make_float2(E[(lane + 32) * ES].y, 0.f);
                             } else if (k < kN / 2) {
-                                a = E[lane * es + k];
-                                b = E[(lane + 32) * es + k];
+                                a = E[lane * ES + k];
+                                b = E[(lane + 32) * ES + k];
                             } else {
-                                a = cconj(E[lane * es + (kN - k)]);
-                                b = cconj(E[(lane + 32) * es + (kN - k)]);
+                                a = cconj(E[lane * ES + (kN - k)]);
+                                b = cconj(E[(lane + 32) * ES + (kN - k)]);
                             }
-                            v[k] = make_float2(a.x - b.y, -(a.y + b.x));  // conj(a + i b)
+                            v[k] = make_float2(a.x - b.y, -(a.y + b.x));
                         }
-                    } else {
+                    } else {  // conj(g_q p) of row y
                         const int y = lane + 32 * (r - 1);
+                        const float2* pf = (const float2*)su->pf;
 #pragma unroll
                         for (int i = 0; i < kN / 2; ++i) {
-                            const float2 g = E[y * es + i];  // g_q at x = 2i, 2i+1
-                            const float2 p0 = U_PF[(2 * i) * kN + y], p1 = U_PF[(2 * i + 1) * kN + y];
+                            const float2 g = E[y * ES + i];  // g_q at x = 2i, 2i+1
+                            const float2 p0 = pf[(2 * i) * kN + y], p1 = pf[(2 * i + 1) * kN + y];
                             v[2 * i] = make_float2(g.x * p0.x, -g.x * p0.y);
                             v[2 * i + 1] = make_float2(g.y * p1.x, -g.y * p1.y);
                         }
                     }
-                    break;
                 }
-                default: if constexpr (FIRST <= P_ADJ && P_ADJ < LAST) {  // P_ADJ
+            }
+            if constexpr (FIRST <= P_ADJ && P_ADJ < LAST) {
+                if (pass == P_ADJ) {
+                    // conj of box column c; an inactive lane transforms a
+                    // column that no lane overwrites in this round
                     const int c = lane + 32 * r;
-                    const int cc = c < W ? c : 0;  // inactive lanes transform a dummy column
+                    const int cc = c < W ? c : (c < ES ? c : c - 32);
 #pragma unroll
-                    for (int y = 0; y < kN; ++y) v[y] = cconj(E[y * es + cc]);
-                    break;
+                    for (int y = 0; y < kN; ++y) v[y] = cconj(E[y * ES + cc]);
+                    if (c < W) {
+                        // the column's pupil factors (kept phasors, else the
+                        // phase) are copied into it while the transform runs
+                        const float2* pp = (const float2*)su->pp;
+                        if (pp) {
+#pragma unroll
+                            for (int yy = 0; yy < kN; ++yy)
+                                if (yy < W) cp_async8(&E[yy * ES + c], pp + yy * W + c);
+                        } else {
+                            const float* ph = (const float*)su->phi;
+                            const int ld = su->ld;
+#pragma unroll
+                            for (int yy = 0; yy < kN; ++yy)
+                                if (yy < W) cp_async4(&E[yy * ES + c].x, ph + yy * ld + c);
+                        }
+                    }
                 }
             }
             // --------------------------------------------------- transform
             fftreg::fft4<kN, -1>(v);
-            if (adj) {
+            if (pass >= P_SEED) {
 #pragma unroll
                 for (int i = 0; i < kN; ++i) v[i].y = -v[i].y;
             }
             // ----------------------------------------------------- store
-            switch (pass) {
-                case P_PUPIL: if constexpr (FIRST <= P_PUPIL && P_PUPIL < LAST) {
+            if constexpr (FIRST <= P_PUPIL && P_PUPIL < LAST) {
+                if (pass == P_PUPIL) {
                     const int c = lane + 32 * r;
                     if (c < W) {
 #pragma unroll
-                        for (int ky = 0; ky < kN; ++ky) E[ky * es + c] = v[ky];
+                        for (int ky = 0; ky < kN; ++ky) E[ky * ES + c] = v[ky];
                     }
-                    break;
                 }
-                case P_FIELD: if constexpr (FIRST <= P_FIELD && P_FIELD < LAST) {
-                    if (r < 2) {
+            }
+            if constexpr (FIRST <= P_FIELD && P_FIELD < LAST) {
+                if (pass == P_FIELD) {
+                    if (r < 2) {  // keep the field row; PSF row s = |p|^2 / (N^2 n_pup) as float pairs
                         const int y = lane + 32 * r;
-                        if (U_PF) {
+                        float2* pf = (float2*)su->pf;
+                        if (pf) {
 #pragma unroll
-                            for (int x = 0; x < kN; ++x) U_PF[x * kN + y] = v[x];
+                            for (int x = 0; x < kN; ++x) pf[x * kN + y] = v[x];
                         }
+                        const float iz = su->inv_z;
 #pragma unroll
                         for (int i = 0; i < kN / 2; ++i)
-                            E[y * es + i] = make_float2(
-                                (v[2 * i].x * v[2 * i].x + v[2 * i].y * v[2 * i].y) * U_INVZ,
-                                (v[2 * i + 1].x * v[2 * i + 1].x + v[2 * i + 1].y * v[2 * i + 1].y) * U_INVZ);
+                            E[y * ES + i] = make_float2((v[2 * i].x * v[2 * i].x + v[2 * i].y * v[2 * i].y) * iz,
+                                                        (v[2 * i + 1].x * v[2 * i + 1].x + v[2 * i + 1].y * v[2 * i + 1].y) * iz);
                     } else {
                         // split the transform of s_lane + i s_(lane+32); the real
                         // columns kx = 0 and N/2 share slot 0 as (S[0], S[N/2])
@@ -249,104 +292,92 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                             const float2 d = cscale(csub(z, zc), 0.5f);
                             const float2 b = make_float2(d.y, -d.x);
                             if (k == 0) {
-                                E[lane * es] = make_float2(a.x, 0.f);
-                                E[(lane + 32) * es] = make_float2(b.x, 0.f);
+                                E[lane * ES] = make_float2(a.x, 0.f);
+                                E[(lane + 32) * ES] = make_float2(b.x, 0.f);
                             } else if (k == kN / 2) {
-                                E[lane * es].y = a.x;
-                                E[(lane + 32) * es].y = b.x;
+                                E[lane * ES].y = a.x;
+                                E[(lane + 32) * ES].y = b.x;
                             } else {
-                                E[lane * es + k] = a;
-                                E[(lane + 32) * es + k] = b;
+                                E[lane * ES + k] = a;
+                                E[(lane + 32) * ES + k] = b;
                             }
                         }
                     }
-                    break;
                 }
-                case P_OTF: if constexpr (FIRST <= P_OTF && P_OTF < LAST) {
+            }
+            if constexpr (FIRST <= P_OTF && P_OTF < LAST) {
+                if (pass == P_OTF) {
                     // every lane writes its OTF column (lane 0 the packed
-                    // Z = F(s_col0 + i s_colN/2), overwritten below) and keeps
-                    // a copy in shared memory for the split of column 0
+                    // Z = F(s_col0 + i s_colN/2), replaced below) and keeps a
+                    // copy in shared memory for the split of column 0
+                    float2* h = (float2*)su->h;
 #pragma unroll
                     for (int ky = 0; ky < kN; ++ky) {
-                        U_H[ky * kNH + lane] = (lane == 0 || bit(ssupp[ky], lane)) ? v[ky] : make_float2(0.f, 0.f);
-                        E[ky * es + lane] = v[ky];
+                        h[ky * kNH + lane] = (lane == 0 || bit(ssupp[ky], lane)) ? v[ky] : make_float2(0.f, 0.f);
+                        E[ky * ES + lane] = v[ky];
                     }
                     __syncwarp();
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
                         const int ky = lane + 32 * i;
-                        const float2 z = E[ky * es];
-                        const float2 zc = cconj(E[((kN - ky) & (kN - 1)) * es]);
+                        const float2 z = E[ky * ES];
+                        const float2 zc = cconj(E[((kN - ky) & (kN - 1)) * ES]);
                         float2 h0 = cscale(cadd(z, zc), 0.5f);
                         const float2 d = cscale(csub(z, zc), 0.5f);
                         float2 h32 = make_float2(d.y, -d.x);
                         if (!bit(ssupp[ky], 0)) h0 = make_float2(0.f, 0.f);
                         if (!bit(ssupp[ky], 32)) h32 = make_float2(0.f, 0.f);
                         if (ky == 0) h0 = make_float2(1.f, 0.f);
-                        U_H[ky * kNH] = h0;
-                        U_H[ky * kNH + 32] = h32;
+                        h[ky * kNH] = h0;
+                        h[ky * kNH + 32] = h32;
                     }
-                    break;
                 }
-                case P_SEED: if constexpr (FIRST <= P_SEED && P_SEED < LAST) {  // lane 0 keeps (T_0, T_N/2), both real, packed
+            }
+            if constexpr (FIRST <= P_SEED && P_SEED < LAST) {
+                if (pass == P_SEED) {  // lane 0 keeps (T_0, T_N/2), both real, packed
 #pragma unroll
-                    for (int y = 0; y < kN; ++y) E[y * es + lane] = v[y];
-                    break;
+                    for (int y = 0; y < kN; ++y) E[y * ES + lane] = v[y];
                 }
-                case P_C2R: if constexpr (FIRST <= P_C2R && P_C2R < LAST) {
-                    if (r == 0) {
-                        const float sc = 2.0f * U_INVZ;
+            }
+            if constexpr (FIRST <= P_C2R && P_C2R < LAST) {
+                if (pass == P_C2R) {
+                    if (r == 0) {  // g_q rows lane and lane+32 as float pairs
+                        const float sc = 2.0f * su->inv_z;
 #pragma unroll
                         for (int i = 0; i < kN / 2; ++i) {
-                            E[lane * es + i] = make_float2(v[2 * i].x * sc, v[2 * i + 1].x * sc);
-                            E[(lane + 32) * es + i] = make_float2(v[2 * i].y * sc, v[2 * i + 1].y * sc);
+                            E[lane * ES + i] = make_float2(v[2 * i].x * sc, v[2 * i + 1].x * sc);
+                            E[(lane + 32) * ES + i] = make_float2(v[2 * i].y * sc, v[2 * i + 1].y * sc);
                         }
-                    } else {
+                    } else {  // box columns of the row's F^H
                         const int y = lane + 32 * (r - 1);
 #pragma unroll
                         for (int x = 0; x < kN; ++x)
-                            if (x < W) E[y * es + x] = v[x];
+                            if (x < W) E[y * ES + x] = v[x];
                     }
-                    break;
                 }
-                default: if constexpr (FIRST <= P_ADJ && P_ADJ < LAST) {  // P_ADJ
+            }
+            if constexpr (FIRST <= P_ADJ && P_ADJ < LAST) {
+                if (pass == P_ADJ) {  // dL/dphi = 2 Im(conj(P) G_P) on the pupil
                     const int c = lane + 32 * r;
                     if (c < W) {
-#pragma unroll
-                        for (int y = 0; y < kN; ++y)
-                            if (y < W) E[y * es + c] = v[y];
-                        const float* ph = U_PHI + c;
-                        float* gph = U_GPHI + c;
-                        const int ld = U_LD;
-                        float phv[kN];
-#pragma unroll
-                        for (int yy = 0; yy < kN; ++yy) phv[yy] = (yy < W) ? ph[yy * ld] : 0.f;
+                        float* gph = (float*)su->gphi + c;
+                        const int ld = su->ld;
+                        const bool kept = su->pp != nullptr;
+                        cp_async_wait();
 #pragma unroll
                         for (int yy = 0; yy < kN; ++yy) {
                             if (yy < W) {
-                                float gv = 0.f;
-                                if (bit(smask[yy], c)) {
-                                    const float2 pv = expi(phv[yy]);
-                                    const float2 gp = E[yy * es + c];
-                                    gv = 2.0f * (pv.x * gp.y - pv.y * gp.x);
-                                }
-                                gph[yy * ld] = gv;
+                                const float2 e = E[yy * ES + c];
+                                const float2 pv = kept ? e : expi(e.x);
+                                gph[yy * ld] = bit(smask[yy], c) ? 2.0f * (pv.x * v[yy].y - pv.y * v[yy].x) : 0.f;
                             }
                         }
                     }
-                    break;
                 }
             }
         }
         __syncwarp();
     }
-#undef U_W
-#undef U_LD
-#undef U_INVZ
-#undef U_PHI
-#undef U_GPHI
-#undef U_H
-#undef U_PF
 }
 
 // Frame reduction of one (patch, object) by one warp: per frequency u,
@@ -505,13 +536,13 @@ __device__ double reduce_object_warp(const FusedParams& prm, int p, int k) {
 // FIRST..LAST selects the forward (PUPIL, FIELD, OTF) or adjoint (SEED,
 // C2R, ADJ) passes. No CTA-level synchronisation: warps progress
 // independently, so different warps overlap different passes.
-template <int FIRST, int LAST>
-__global__ void __launch_bounds__(kThreads, 2) mfbd_pass_kernel(const FusedParams prm, int es) {
+template <int FIRST, int LAST, int ES>
+__global__ void __launch_bounds__(kThreads, 2) mfbd_pass_kernel(const FusedParams prm) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Unit sunit[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    float2* E = reinterpret_cast<float2*>(smem) + (size_t)warp * kN * es;
+    float2* E = reinterpret_cast<float2*>(smem) + (size_t)warp * kN * ES;
     volatile Unit* su = &sunit[warp];
     const int J = prm.J, K = prm.K;
     const long long units = (long long)prm.P * K * J;
@@ -532,6 +563,13 @@ __global__ void __launch_bounds__(kThreads, 2) mfbd_pass_kernel(const FusedParam
             su->gphi = FIRST >= P_SEED ? prm.gphi + ob.phi_off + pj * ob.phi_unit + ob.phi_org : nullptr;
             su->h = prm.gscr + (size_t)u * kHalf;
             su->pf = prm.pscr ? prm.pscr + (size_t)u * kN * kN : nullptr;
+            su->pp = prm.uscr ? prm.uscr + (size_t)u * prm.ustride : nullptr;
+            if (FIRST == P_SEED && u + stride < units) {  // next unit's seed, field, phasors into L2
+                const long long un = u + stride;
+                prefetch_l2(prm.gscr + (size_t)un * kHalf, (size_t)kHalf * sizeof(float2));
+                if (prm.pscr) prefetch_l2(prm.pscr + (size_t)un * kN * kN, (size_t)kN * kN * sizeof(float2));
+                if (prm.uscr) prefetch_l2(prm.uscr + (size_t)un * prm.ustride, (size_t)prm.ustride * sizeof(float2));
+            }
             if (FIRST == P_PUPIL && u + stride < units) {  // next unit's phase into L2
                 const long long un = u + stride;
                 const int jn = (int)(un % J), kn = (int)((un / J) % K);
@@ -542,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, 2) mfbd_pass_kernel(const FusedParam
             }
         }
         __syncwarp();
-        run_passes<FIRST, LAST>(su, E, es, ob.mask, ob.supp);
+        run_passes<FIRST, LAST, ES>(su, E, ob.mask, ob.supp);
     }
 }
 
@@ -569,8 +607,8 @@ __global__ void __launch_bounds__(32 * kMaxObjects) mfbd_reduce_kernel(const Fus
 
 FusedGeometry fused_geometry(int max_box) {
     FusedGeometry g;
-    const int es = max_box > kNH ? max_box : kNH;
-    g.xs = es | 1;
+    // exchange-buffer row strides compiled in (odd, >= N/2 + 1)
+    g.xs = max_box <= 33 ? 33 : max_box <= 37 ? 37 : max_box <= 45 ? 45 : 65;
     // up to kWarps warps, two CTAs per SM when their buffers fit in 227 KB
     const size_t per_warp = (size_t)kN * g.xs * sizeof(float2);
     int warps = (int)(((size_t)113 * 1024) / per_warp);
@@ -580,13 +618,12 @@ FusedGeometry fused_geometry(int max_box) {
     return g;
 }
 
-namespace {
-
-}  // namespace
-
 template <int FIRST, int LAST>
 cudaError_t launch_pass(const FusedParams& prm, const FusedGeometry& g, int sms, cudaStream_t s) {
-    auto* kern = mfbd_pass_kernel<FIRST, LAST>;
+    auto* kern = g.xs == 33 ? mfbd_pass_kernel<FIRST, LAST, 33>
+                 : g.xs == 37 ? mfbd_pass_kernel<FIRST, LAST, 37>
+                 : g.xs == 45 ? mfbd_pass_kernel<FIRST, LAST, 45>
+                              : mfbd_pass_kernel<FIRST, LAST, 65>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem_bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -597,7 +634,7 @@ cudaError_t launch_pass(const FusedParams& prm, const FusedGeometry& g, int sms,
     long long ctas = (long long)sms * per_sm;
     const long long need = (units + g.slots - 1) / g.slots;
     if (ctas > need) ctas = need;
-    kern<<<(int)ctas, g.slots * 32, g.smem_bytes, s>>>(prm, g.xs);
+    kern<<<(int)ctas, g.slots * 32, g.smem_bytes, s>>>(prm);
     return cudaGetLastError();
 }
 
@@ -629,7 +666,10 @@ cudaError_t launch_adjoint_passes(const FusedParams& prm, const FusedGeometry& g
 }
 
 int max_ctas_per_sm(const FusedGeometry& g) {
-    auto* kern = mfbd_pass_kernel<P_PUPIL, P_OTF + 1>;
+    auto* kern = g.xs == 33 ? mfbd_pass_kernel<P_PUPIL, P_OTF + 1, 33>
+                 : g.xs == 37 ? mfbd_pass_kernel<P_PUPIL, P_OTF + 1, 37>
+                 : g.xs == 45 ? mfbd_pass_kernel<P_PUPIL, P_OTF + 1, 45>
+                              : mfbd_pass_kernel<P_PUPIL, P_OTF + 1, 65>;
     int n = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem_bytes) != cudaSuccess)
         return 0;
