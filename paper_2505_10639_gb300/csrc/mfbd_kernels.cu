@@ -98,6 +98,7 @@ struct Unit {
     float2* pp;        // pupil phasors exp(i phi) on the box, [W][W]
     float2* h;         // [N][N/2+1]: H (forward), then the adjoint seed G
     float2* pf;        // field p = F P, [x][y]; null: not kept
+    const float2* hn;  // adjoint seed of the warp's next unit (L2 prefetch); null: none
     int W, ld;
     float inv_z;
 };
@@ -151,6 +152,10 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
 #pragma unroll 1
     for (int pass = FIRST; pass < LAST; ++pass) {
         const int nr = pass_rounds(pass, W);
+        if (FIRST >= P_SEED && lane == 0) {  // L2 prefetch about one pass ahead of use
+            if (pass == P_C2R && su->pp) prefetch_l2((const void*)su->pp, (size_t)W * W * sizeof(float2));
+            if (pass == P_ADJ && su->hn) prefetch_l2((const void*)su->hn, (size_t)kHalf * sizeof(float2));
+        }
 #pragma unroll 1
         for (int r = 0; r < nr; ++r) {
             float2 v[kN];
@@ -362,14 +367,22 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                     if (c < W) {
                         float* gph = (float*)su->gphi + c;
                         const int ld = su->ld;
-                        const bool kept = su->pp != nullptr;
                         cp_async_wait();
+                        if (su->pp) {
 #pragma unroll
-                        for (int yy = 0; yy < kN; ++yy) {
-                            if (yy < W) {
-                                const float2 e = E[yy * ES + c];
-                                const float2 pv = kept ? e : expi(e.x);
-                                gph[yy * ld] = bit(smask[yy], c) ? 2.0f * (pv.x * v[yy].y - pv.y * v[yy].x) : 0.f;
+                            for (int yy = 0; yy < kN; ++yy) {
+                                if (yy < W) {
+                                    const float2 pv = E[yy * ES + c];
+                                    gph[yy * ld] = bit(smask[yy], c) ? 2.0f * (pv.x * v[yy].y - pv.y * v[yy].x) : 0.f;
+                                }
+                            }
+                        } else {
+#pragma unroll
+                            for (int yy = 0; yy < kN; ++yy) {
+                                if (yy < W) {
+                                    const float2 pv = expi(E[yy * ES + c].x);
+                                    gph[yy * ld] = bit(smask[yy], c) ? 2.0f * (pv.x * v[yy].y - pv.y * v[yy].x) : 0.f;
+                                }
                             }
                         }
                     }
@@ -564,12 +577,9 @@ __global__ void __launch_bounds__(kThreads, 2) mfbd_pass_kernel(const FusedParam
             su->h = prm.gscr + (size_t)u * kHalf;
             su->pf = prm.pscr ? prm.pscr + (size_t)u * kN * kN : nullptr;
             su->pp = prm.uscr ? prm.uscr + (size_t)u * prm.ustride : nullptr;
-            if (FIRST == P_SEED && u + stride < units) {  // next unit's seed, field, phasors into L2
-                const long long un = u + stride;
-                prefetch_l2(prm.gscr + (size_t)un * kHalf, (size_t)kHalf * sizeof(float2));
-                if (prm.pscr) prefetch_l2(prm.pscr + (size_t)un * kN * kN, (size_t)kN * kN * sizeof(float2));
-                if (prm.uscr) prefetch_l2(prm.uscr + (size_t)un * prm.ustride, (size_t)prm.ustride * sizeof(float2));
-            }
+            su->hn = FIRST == P_SEED && u + stride < units ? prm.gscr + (size_t)(u + stride) * kHalf : nullptr;
+            if (FIRST == P_SEED && prm.pscr)  // this unit's field, used from the second C2R round on
+                prefetch_l2(prm.pscr + (size_t)u * kN * kN, (size_t)kN * kN * sizeof(float2));
             if (FIRST == P_PUPIL && u + stride < units) {  // next unit's phase into L2
                 const long long un = u + stride;
                 const int jn = (int)(un % J), kn = (int)((un / J) % K);
