@@ -38,8 +38,8 @@ struct ObjectData {
     long long phi_off = 0;
     long long part_off = 0;     // offset of this object's modal-adjoint partial sums
     float* d_basis = nullptr;   // [M][W*W]
-    uint64_t* d_mask = nullptr; // [W]
-    uint64_t* d_supp = nullptr; // [N]
+    uint64_t* d_mask = nullptr; // [W] box rows, then [N] box columns
+    uint64_t* d_supp = nullptr; // [N] rows, then [N] columns of the OTF support
 };
 
 }  // namespace
@@ -177,6 +177,8 @@ FusedParams fused_params(const mfbd_plan* p, const void* spectra, double* loss, 
         f.obj[k].phi_ld = p->obj[k].W;
         f.obj[k].mask = p->obj[k].d_mask;
         f.obj[k].supp = p->obj[k].d_supp;
+        f.obj[k].cmask = p->obj[k].d_mask + p->obj[k].W;
+        f.obj[k].csupp = p->obj[k].d_supp + p->N;
     }
     return f;
 }
@@ -399,15 +401,22 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
                         if (mask[(size_t)(o.x0 + yy) * n + (o.x0 + xx)])
                             hb[k][(size_t)m * o.W * o.W + (size_t)yy * o.W + xx] = (float)full[src];
                     }
-            hm[k].assign(o.W, 0);
+            // bit rows, then the same bits by column (a lane's column in one word)
+            hm[k].assign(o.W + n, 0);
             for (int yy = 0; yy < o.W; ++yy)
                 for (int xx = 0; xx < o.W; ++xx)
-                    if (mask[(size_t)(o.x0 + yy) * n + (o.x0 + xx)]) hm[k][yy] |= 1ull << xx;
+                    if (mask[(size_t)(o.x0 + yy) * n + (o.x0 + xx)]) {
+                        hm[k][yy] |= 1ull << xx;
+                        hm[k][o.W + xx] |= 1ull << yy;
+                    }
             std::vector<uint8_t> sup = mfbd_host::otf_support_half(mask, n);
-            hs[k].assign(n, 0);
+            hs[k].assign(2 * n, 0);
             for (int ky = 0; ky < n; ++ky)
                 for (int kx = 0; kx <= n / 2; ++kx)
-                    if (sup[(size_t)ky * (n / 2 + 1) + kx]) hs[k][ky] |= 1ull << kx;
+                    if (sup[(size_t)ky * (n / 2 + 1) + kx]) {
+                        hs[k][ky] |= 1ull << kx;
+                        hs[k][n + kx] |= 1ull << ky;
+                    }
             if ((st = dev_alloc(p, &o.d_basis, hb[k].size()))) throw st;
             if ((st = dev_alloc(p, &o.d_mask, hm[k].size()))) throw st;
             if ((st = dev_alloc(p, &o.d_supp, hs[k].size()))) throw st;

@@ -24,6 +24,8 @@ struct ObjParams {
     int phi_ld;              // row stride of that image: W or N
     const uint64_t* mask;    // [W] rows, bit t = pupil pixel at box column t
     const uint64_t* supp;    // [N] rows, bit kx = OTF support (kx <= N/2)
+    const uint64_t* cmask;   // [N] box columns c, bit y = pupil pixel at box (y, c); 0 for c >= W
+    const uint64_t* csupp;   // [N] columns kx <= N/2, bit ky = OTF support; the rest 0
 };
 
 struct FusedParams {

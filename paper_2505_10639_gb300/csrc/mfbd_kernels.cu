@@ -117,28 +117,25 @@ __device__ __forceinline__ bool bit(uint64_t w, int b) { return (w >> b) & 1ull;
 
 // ------------------------------------------------------------ load stages
 
-template <int ES>
-__device__ __forceinline__ void load_pupil(const volatile Unit* su, float2* E, const uint64_t* smask, int W, int c,
-                                           float2 (&v)[kN]) {
-    if (c < W) {
-        const float* ph = (const float*)su->phi + c;
-        float2* pp = (float2*)su->pp + c;
-        const int ld = su->ld;
-        float phv[kN];  // every phase load of the column is issued before use
+// Pupil column c of the box: P = exp(i phi) where the column mask `cm` has
+// bit y (zero outside the pupil and for c >= W); the phasors are also kept
+// for the adjoint when the unit has a phasor buffer.
+__device__ __forceinline__ void load_pupil(const volatile Unit* su, uint64_t cm, int W, int c, float2 (&v)[kN]) {
+    const float* ph = (const float*)su->phi + c;
+    float2* pp = (float2*)su->pp;
+    const int ld = su->ld;
+    float phv[kN];  // every phase load of the column is issued before use
 #pragma unroll
-        for (int yy = 0; yy < kN; ++yy) phv[yy] = (yy < W) ? ph[yy * ld] : 0.f;
+    for (int yy = 0; yy < kN; ++yy) phv[yy] = (c < W && yy < W) ? ph[yy * ld] : 0.f;
 #pragma unroll
-        for (int yy = 0; yy < kN; ++yy)
-            if (yy < W) E[yy * ES + c].x = phv[yy];
-#pragma unroll 4
-        for (int yy = 0; yy < W; ++yy) {
-            const float2 pv = bit(smask[yy], c) ? expi(E[yy * ES + c].x) : make_float2(0.f, 0.f);
-            E[yy * ES + c] = pv;
-            if (pp) pp[yy * W] = pv;
+    for (int yy = 0; yy < kN; ++yy) {
+        if (yy < W) {
+            v[yy] = bit(cm, yy) ? expi(phv[yy]) : make_float2(0.f, 0.f);
+            if (pp != nullptr && c < W) pp[yy * W + c] = v[yy];
+        } else {
+            v[yy] = make_float2(0.f, 0.f);
         }
     }
-#pragma unroll
-    for (int y = 0; y < kN; ++y) v[y] = (c < W && y < W) ? E[y * ES + c] : make_float2(0.f, 0.f);
 }
 
 // ----------------------------------------------------------- the machine
@@ -146,7 +143,7 @@ __device__ __forceinline__ void load_pupil(const volatile Unit* su, float2* E, c
 // Runs passes [FIRST, LAST) of one unit on the calling warp.
 template <int FIRST, int LAST, int ES>
 __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __restrict__ E,
-                                           const uint64_t* __restrict__ smask, const uint64_t* __restrict__ ssupp) {
+                                           const uint64_t* __restrict__ cmask, const uint64_t* __restrict__ csupp) {
     const int lane = threadIdx.x & 31;
     const int W = su->W;
 #pragma unroll 1
@@ -161,7 +158,7 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
             float2 v[kN];
             // ------------------------------------------------------ load
             if constexpr (FIRST <= P_PUPIL && P_PUPIL < LAST) {
-                if (pass == P_PUPIL) load_pupil<ES>(su, E, smask, W, lane + 32 * r, v);
+                if (pass == P_PUPIL) load_pupil(su, cmask[lane + 32 * r], W, lane + 32 * r, v);
             }
             if constexpr (FIRST <= P_FIELD && P_FIELD < LAST) {
                 if (pass == P_FIELD) {
@@ -316,12 +313,14 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                     // Z = F(s_col0 + i s_colN/2), replaced below) and keeps a
                     // copy in shared memory for the split of column 0
                     float2* h = (float2*)su->h;
+                    const uint64_t cs = lane == 0 ? ~0ull : csupp[lane];
 #pragma unroll
                     for (int ky = 0; ky < kN; ++ky) {
-                        h[ky * kNH + lane] = (lane == 0 || bit(ssupp[ky], lane)) ? v[ky] : make_float2(0.f, 0.f);
+                        h[ky * kNH + lane] = bit(cs, ky) ? v[ky] : make_float2(0.f, 0.f);
                         E[ky * ES + lane] = v[ky];
                     }
                     __syncwarp();
+                    const uint64_t cs0 = csupp[0], cs32 = csupp[kN / 2];
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
                         const int ky = lane + 32 * i;
@@ -330,8 +329,8 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                         float2 h0 = cscale(cadd(z, zc), 0.5f);
                         const float2 d = cscale(csub(z, zc), 0.5f);
                         float2 h32 = make_float2(d.y, -d.x);
-                        if (!bit(ssupp[ky], 0)) h0 = make_float2(0.f, 0.f);
-                        if (!bit(ssupp[ky], 32)) h32 = make_float2(0.f, 0.f);
+                        if (!bit(cs0, ky)) h0 = make_float2(0.f, 0.f);
+                        if (!bit(cs32, ky)) h32 = make_float2(0.f, 0.f);
                         if (ky == 0) h0 = make_float2(1.f, 0.f);
                         h[ky * kNH] = h0;
                         h[ky * kNH + 32] = h32;
@@ -367,13 +366,14 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                     if (c < W) {
                         float* gph = (float*)su->gphi + c;
                         const int ld = su->ld;
+                        const uint64_t cm = cmask[c];
                         cp_async_wait();
                         if (su->pp) {
 #pragma unroll
                             for (int yy = 0; yy < kN; ++yy) {
                                 if (yy < W) {
                                     const float2 pv = E[yy * ES + c];
-                                    gph[yy * ld] = bit(smask[yy], c) ? 2.0f * (pv.x * v[yy].y - pv.y * v[yy].x) : 0.f;
+                                    gph[yy * ld] = bit(cm, yy) ? 2.0f * (pv.x * v[yy].y - pv.y * v[yy].x) : 0.f;
                                 }
                             }
                         } else {
@@ -381,7 +381,7 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                             for (int yy = 0; yy < kN; ++yy) {
                                 if (yy < W) {
                                     const float2 pv = expi(E[yy * ES + c].x);
-                                    gph[yy * ld] = bit(smask[yy], c) ? 2.0f * (pv.x * v[yy].y - pv.y * v[yy].x) : 0.f;
+                                    gph[yy * ld] = bit(cm, yy) ? 2.0f * (pv.x * v[yy].y - pv.y * v[yy].x) : 0.f;
                                 }
                             }
                         }
@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 2) mfbd_pass_kernel(const FusedParam
             }
         }
         __syncwarp();
-        run_passes<FIRST, LAST, ES>(su, E, ob.mask, ob.supp);
+        run_passes<FIRST, LAST, ES>(su, E, ob.cmask, ob.csupp);
     }
 }
 

@@ -21,7 +21,7 @@
 using namespace mfbd_dev;
 
 // 16 MiB per device: 64 KiB of per-call constants (pupil and OTF-support
-// bit rows, frame weights) followed by the per-unit scratch of one batch of
+// bits by row and by column, frame weights) followed by the per-unit scratch of one batch of
 // patches: [Pb][K][J][N][N/2+1] complex64 OTFs / adjoint seeds, then
 // [Pb][K][J][N][N] complex64 fields.
 static __device__ __align__(256) unsigned char g_static_workspace[(size_t)16 << 20];
@@ -30,7 +30,7 @@ namespace {
 
 constexpr size_t kStaticBytes = sizeof(g_static_workspace);
 constexpr size_t kConstBytes = (size_t)64 << 10;
-constexpr size_t kBitsBytes = (size_t)kMaxObjects * 2 * kN * sizeof(uint64_t);  // 8 KiB
+constexpr size_t kBitsBytes = (size_t)kMaxObjects * 4 * kN * sizeof(uint64_t);  // 16 KiB
 constexpr int kMaxDevices = 64;
 
 std::mutex g_mu;
@@ -160,11 +160,19 @@ extern "C" int mfbd_phase_loss_grad_noalloc(const mfbd_plan_desc* desc, const fl
         support_rows(rows, supp);
         const int W = hi - lo + 1;
         max_box = max_box > W ? max_box : W;
-        uint64_t* mk = bits + (size_t)k * 2 * kN;
+        // per object: pupil rows of the box, OTF-support rows, then the
+        // same bits by column (box columns; support columns kx <= N/2)
+        uint64_t* mk = bits + (size_t)k * 4 * kN;
         for (int yy = 0; yy < W; ++yy) mk[yy] = rows[lo + yy] >> lo;
         if (W < 64)
             for (int yy = 0; yy < W; ++yy) mk[yy] &= (1ull << W) - 1;
         std::memcpy(mk + kN, supp, sizeof supp);
+        for (int yy = 0; yy < W; ++yy)
+            for (int xx = 0; xx < W; ++xx)
+                if ((mk[yy] >> xx) & 1ull) mk[2 * kN + xx] |= 1ull << yy;
+        for (int ky = 0; ky < kN; ++ky)
+            for (int kx = 0; kx <= kN / 2; ++kx)
+                if ((supp[ky] >> kx) & 1ull) mk[3 * kN + kx] |= 1ull << ky;
         ObjParams& ob = f.obj[k];
         ob.W = W;
         ob.x0 = lo;
@@ -173,8 +181,10 @@ extern "C" int mfbd_phase_loss_grad_noalloc(const mfbd_plan_desc* desc, const fl
         ob.phi_unit = (long long)kN * kN;
         ob.phi_org = lo * kN + lo;
         ob.phi_ld = kN;
-        ob.mask = reinterpret_cast<const uint64_t*>(base) + (size_t)k * 2 * kN;
+        ob.mask = reinterpret_cast<const uint64_t*>(base) + (size_t)k * 4 * kN;
         ob.supp = ob.mask + kN;
+        ob.cmask = ob.mask + 2 * kN;
+        ob.csupp = ob.mask + 3 * kN;
     }
     for (int i = 0; i < K * J; ++i) wts[i] = desc->frame_weight ? desc->frame_weight[i] : 1.0f;
     if ((e = cudaMemcpyAsync(base, g_host_consts, kBitsBytes + (size_t)K * J * sizeof(float),
