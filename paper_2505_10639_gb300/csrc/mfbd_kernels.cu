@@ -62,13 +62,8 @@ __device__ __forceinline__ float2 expi(float ph) {
     return make_float2(c, s);
 }
 
-// Asynchronous global -> shared copies of 4 or 8 bytes (both addresses
-// aligned to the size); complete for the issuing thread after cp_async_wait.
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
-                 "l"(__cvta_generic_to_global(gmem))
-                 : "memory");
-}
+// Asynchronous global -> shared copy of 8 bytes (both addresses 8-byte
+// aligned); complete for the issuing thread after cp_async_wait.
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
                  "l"(__cvta_generic_to_global(gmem))
@@ -235,21 +230,13 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                     const int cc = c < W ? c : (c < ES ? c : c - 32);
 #pragma unroll
                     for (int y = 0; y < kN; ++y) v[y] = cconj(E[y * ES + cc]);
-                    if (c < W) {
-                        // the column's pupil factors (kept phasors, else the
-                        // phase) are copied into it while the transform runs
-                        const float2* pp = (const float2*)su->pp;
-                        if (pp) {
+                    const float2* pp = (const float2*)su->pp;
+                    if (c < W && pp != nullptr) {
+                        // the column's kept phasors are copied into it while
+                        // the transform runs
 #pragma unroll
-                            for (int yy = 0; yy < kN; ++yy)
-                                if (yy < W) cp_async8(&E[yy * ES + c], pp + yy * W + c);
-                        } else {
-                            const float* ph = (const float*)su->phi;
-                            const int ld = su->ld;
-#pragma unroll
-                            for (int yy = 0; yy < kN; ++yy)
-                                if (yy < W) cp_async4(&E[yy * ES + c].x, ph + yy * ld + c);
-                        }
+                        for (int yy = 0; yy < kN; ++yy)
+                            if (yy < W) cp_async8(&E[yy * ES + c], pp + yy * W + c);
                     }
                 }
             }
@@ -376,13 +363,16 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                                     gph[yy * ld] = bit(cm, yy) ? 2.0f * (pv.x * v[yy].y - pv.y * v[yy].x) : 0.f;
                                 }
                             }
-                        } else {
+                        } else {  // no phasor buffer: G_P parked, phasors from the phase (compact loop)
 #pragma unroll
-                            for (int yy = 0; yy < kN; ++yy) {
-                                if (yy < W) {
-                                    const float2 pv = expi(E[yy * ES + c].x);
-                                    gph[yy * ld] = bit(cm, yy) ? 2.0f * (pv.x * v[yy].y - pv.y * v[yy].x) : 0.f;
-                                }
+                            for (int yy = 0; yy < kN; ++yy)
+                                if (yy < W) E[yy * ES + c] = v[yy];
+                            const float* ph = (const float*)su->phi + c;
+#pragma unroll 4
+                            for (int yy = 0; yy < W; ++yy) {
+                                const float2 pv = expi(ph[yy * ld]);
+                                const float2 g = E[yy * ES + c];
+                                gph[yy * ld] = bit(cm, yy) ? 2.0f * (pv.x * g.y - pv.y * g.x) : 0.f;
                             }
                         }
                     }

@@ -167,14 +167,18 @@ def test_zero_patches_is_a_noop():
     assert loss.numel() == 0 and grad.numel() == 0
 
 
-def test_more_patches_than_ctas_and_determinism(c2_slice):
-    """A ragged persistent schedule (P not a multiple of the CTA count,
-    several patches per CTA): every copy of a patch gives the same bits."""
+def test_more_units_than_warps_and_determinism(c2_slice):
+    """A ragged persistent schedule (units = patches x objects x frames not a
+    multiple of the warps resident, several units per warp): every copy of a
+    patch gives the same bits."""
     a32, d32, d_or = _inputs(c2_slice)
     ref = _oracle(c2_slice, a32, d_or)
-    reps = 107  # 321 patches
+    reps = 107  # 321 patches, 7704 units
     plan = _plan_for(c2_slice, n_patches=3 * reps)
-    assert plan.info()["ctas"] < 3 * reps
+    info = plan.info()
+    units = 3 * reps * len(c2_slice["diams"]) * c2_slice["n_frames"]
+    assert 2 * info["ctas"] * info["slots_per_cta"] < units
+    assert units % (info["ctas"] * info["slots_per_cta"]) != 0
     aa = np.tile(a32, (reps, 1, 1))
     dd = np.tile(d32, (reps, 1, 1, 1, 1))
     loss, grad, obj = _run_fused(plan, aa, dd)
