@@ -114,19 +114,21 @@ __device__ __forceinline__ bool bit(uint64_t w, int b) { return (w >> b) & 1ull;
 
 // Pupil column c of the box: P = exp(i phi) where the column mask `cm` has
 // bit y (zero outside the pupil and for c >= W); the phasors are also kept
-// for the adjoint when the unit has a phasor buffer.
+// for the adjoint when the unit has a phasor buffer. R >= W is the
+// compile-time bound on the box side.
+template <int R>
 __device__ __forceinline__ void load_pupil(const volatile Unit* su, uint64_t cm, int W, int c, float2 (&v)[kN]) {
     const float* ph = (const float*)su->phi + c;
     float2* pp = (float2*)su->pp;
     const int ld = su->ld;
-    float phv[kN];  // every phase load of the column is issued before use
+    float phv[R];  // every phase load of the column is issued before use
 #pragma unroll
-    for (int yy = 0; yy < kN; ++yy) phv[yy] = (c < W && yy < W) ? ph[yy * ld] : 0.f;
+    for (int yy = 0; yy < R; ++yy) phv[yy] = (c < W && yy < W) ? ph[yy * ld] : 0.f;
 #pragma unroll
     for (int yy = 0; yy < kN; ++yy) {
-        if (yy < W) {
+        if (yy < R) {
             v[yy] = bit(cm, yy) ? expi(phv[yy]) : make_float2(0.f, 0.f);
-            if (pp != nullptr && c < W) pp[yy * W + c] = v[yy];
+            if (pp != nullptr && c < W && yy < W) pp[yy * W + c] = v[yy];
         } else {
             v[yy] = make_float2(0.f, 0.f);
         }
@@ -139,6 +141,7 @@ __device__ __forceinline__ void load_pupil(const volatile Unit* su, uint64_t cm,
 template <int FIRST, int LAST, int ES>
 __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __restrict__ E,
                                            const uint64_t* __restrict__ cmask, const uint64_t* __restrict__ csupp) {
+    constexpr int R = ES < kN ? ES : kN;  // the box side W is at most R
     const int lane = threadIdx.x & 31;
     const int W = su->W;
 #pragma unroll 1
@@ -153,14 +156,14 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
             float2 v[kN];
             // ------------------------------------------------------ load
             if constexpr (FIRST <= P_PUPIL && P_PUPIL < LAST) {
-                if (pass == P_PUPIL) load_pupil(su, cmask[lane + 32 * r], W, lane + 32 * r, v);
+                if (pass == P_PUPIL) load_pupil<R>(su, cmask[lane + 32 * r], W, lane + 32 * r, v);
             }
             if constexpr (FIRST <= P_FIELD && P_FIELD < LAST) {
                 if (pass == P_FIELD) {
                     if (r < 2) {  // row y of the pupil's column transform (box columns [0, W))
                         const int y = lane + 32 * r;
 #pragma unroll
-                        for (int x = 0; x < kN; ++x) v[x] = (x < W) ? E[y * ES + x] : make_float2(0.f, 0.f);
+                        for (int x = 0; x < kN; ++x) v[x] = (x < R && x < W) ? E[y * ES + x] : make_float2(0.f, 0.f);
                     } else {  // two real PSF rows as one complex line
 #pragma unroll
                         for (int i = 0; i < kN / 2; ++i) {
@@ -236,7 +239,7 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                         // the transform runs
 #pragma unroll
                         for (int yy = 0; yy < kN; ++yy)
-                            if (yy < W) cp_async8(&E[yy * ES + c], pp + yy * W + c);
+                            if (yy < R && yy < W) cp_async8(&E[yy * ES + c], pp + yy * W + c);
                     }
                 }
             }
@@ -343,7 +346,7 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                         const int y = lane + 32 * (r - 1);
 #pragma unroll
                         for (int x = 0; x < kN; ++x)
-                            if (x < W) E[y * ES + x] = v[x];
+                            if (x < R && x < W) E[y * ES + x] = v[x];
                     }
                 }
             }
@@ -358,7 +361,7 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                         if (su->pp) {
 #pragma unroll
                             for (int yy = 0; yy < kN; ++yy) {
-                                if (yy < W) {
+                                if (yy < R && yy < W) {
                                     const float2 pv = E[yy * ES + c];
                                     gph[yy * ld] = bit(cm, yy) ? 2.0f * (pv.x * v[yy].y - pv.y * v[yy].x) : 0.f;
                                 }
@@ -366,7 +369,7 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                         } else {  // no phasor buffer: G_P parked, phasors from the phase (compact loop)
 #pragma unroll
                             for (int yy = 0; yy < kN; ++yy)
-                                if (yy < W) E[yy * ES + c] = v[yy];
+                                if (yy < R && yy < W) E[yy * ES + c] = v[yy];
                             const float* ph = (const float*)su->phi + c;
 #pragma unroll 4
                             for (int yy = 0; yy < W; ++yy) {
