@@ -326,8 +326,10 @@ def run_gpu(args, rank, local_rank, world):
 
 
 def run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, w):
-    """Same metric through the public API with host buffers: every step
-    copies its inputs from pinned host memory and reads back loss and grad."""
+    """Same metric through the public host-buffer call (mfbd_loss_grad_host):
+    every step copies its coefficients and spectra from pinned host memory
+    and reads loss and grad back, chunk by chunk, overlapped with the
+    kernels of other chunks."""
     import torch
     import torch.distributed as dist
     e0 = torch.cuda.Event(enable_timing=True)
@@ -336,15 +338,9 @@ def run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, 
     d_host = spectra.cpu().pin_memory()
     l_host = torch.empty_like(loss, device="cpu").pin_memory()
     g_host = torch.empty_like(grad, device="cpu").pin_memory()
-    a_dev = torch.empty_like(coeffs)
-    d_dev = torch.empty_like(spectra)
 
     def e2e_step():
-        a_dev.copy_(a_host, non_blocking=True)
-        d_dev.copy_(d_host, non_blocking=True)
-        plan.loss_grad(a_dev, d_dev, loss=loss, grad=grad)
-        l_host.copy_(loss, non_blocking=True)
-        g_host.copy_(grad, non_blocking=True)
+        plan.loss_grad_host(a_host, d_host, loss=l_host, grad=g_host, n_chunks=args.e2e_chunks, stream=stream)
 
     for _ in range(max(1, args.warmup)):
         e2e_step()
@@ -356,12 +352,17 @@ def run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, 
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
+    # the host-buffer results are the device call's bits
+    plan.loss_grad(coeffs, spectra, loss=loss, grad=grad)
+    torch.cuda.synchronize()
+    if not (torch.equal(loss.cpu(), l_host) and torch.equal(grad.cpu(), g_host)):
+        raise RuntimeError("host-buffer call differs from the device call")
     e2e_local = e0.elapsed_time(e1) / args.steps
     e2e_ms, _, e2e_value = aggregate(e2e_local, units_of(w), world, rmax, rsum)
     h2d = coeffs.numel() * 4 + spectra.numel() * 8
     d2h = loss.numel() * 8 + grad.numel() * 4
     return {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h}
+            "d2h_bytes_per_step": d2h, "chunks": args.e2e_chunks}
 
 
 def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
@@ -435,6 +436,8 @@ def main():
     ap.add_argument("--patches", type=int, default=0,
                     help="use only the first N patches of the field (smaller profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunks", type=int, default=0,
+                    help="patch chunks of the host-buffer call (copies overlap the kernels of other chunks)")
     args = ap.parse_args()
     if args.patches:
         WORKLOAD["n_patches"] = args.patches

@@ -132,6 +132,33 @@ int mfbd_backward(mfbd_plan_t plan, float* grad, void* stream);
 int mfbd_loss_grad(mfbd_plan_t plan, const float* coeffs, const void* spectra,
                    double* loss, void* object, float* grad, void* stream);
 
+/* mfbd_loss_grad (loss of Sec. 2.2.1, Eq. 12, object of Eq. 11 and dL/da)
+ * from HOST buffers, with the copies overlapped with the
+ * kernels: the patches go through in n_chunks chunks (n_chunks <= 0: about
+ * 320 patches per chunk, 1 to 8 chunks); the
+ * spectra of chunk c + 1 are copied to the device while chunk c is computed
+ * (a chunk's phases and forward passes run while its own spectra are still
+ * in flight: only the frame reduction reads them), and the loss, grad (and
+ * object) of each chunk are copied back while later chunks are computed.
+ * Same layouts as mfbd_loss_grad, all four (five)
+ * pointers host memory; page-locked (cudaHostAlloc / pinned) buffers are
+ * needed for the copies to overlap, pageable ones work but serialise. The
+ * results are the same bits as mfbd_loss_grad's on the same inputs (every
+ * kernel works per patch or per unit).
+ * Asynchronous like the other calls: the host buffers may be read or
+ * written until `stream` has completed the work queued by this call, which
+ * covers the last copy back. The plan keeps device staging (coefficients,
+ * loss and gradient of all patches, two chunks of spectra, the object when
+ * asked for, two copy streams) from the first call on; a later call needing
+ * larger staging synchronises the device and rebuilds it. Calls on one plan
+ * from different streams must be ordered by the caller. After this call
+ * mfbd_backward reports MFBD_ERR_STATE (the plan's per-unit buffers hold only
+ * the last chunk). Errors: MFBD_ERR_INVALID_ARG for a NULL plan, coeffs,
+ * spectra, loss or grad; a failed CUDA call returns its error and marks the
+ * plan failed. */
+int mfbd_loss_grad_host(mfbd_plan_t plan, const float* coeffs, const void* spectra,
+                        double* loss, void* object, float* grad, int n_chunks, void* stream);
+
 /* Forward model only: otf dev [P][K][J][N][N/2+1] complex64 = H_pkj
  * (Sec. 3.1, Eqs. 20-22, then H = F s), e.g. to synthesise data. */
 int mfbd_otf(mfbd_plan_t plan, const float* coeffs, void* otf, void* stream);

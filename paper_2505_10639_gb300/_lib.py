@@ -65,6 +65,7 @@ _SIGNATURES = {
     "mfbd_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "mfbd_backward": (ctypes.c_int, [_VP, _VP, _VP]),
     "mfbd_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "mfbd_loss_grad_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     "mfbd_otf": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "mfbd_describe_object": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.c_int, _VP, _VP, _VP, _VP]),
     "mfbd_status_string": (ctypes.c_char_p, [ctypes.c_int]),

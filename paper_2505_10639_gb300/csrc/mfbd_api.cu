@@ -66,6 +66,21 @@ struct mfbd_plan {
     bool failed = false;
     bool have_forward = false;
     std::vector<void*> allocations;
+    // host-buffer pipeline (mfbd_loss_grad_host), created on first use
+    struct HostPipe {
+        bool ready = false;
+        int chunk_patches = 0;            // patches per staging buffer
+        bool with_object = false;
+        float* d_coeffs = nullptr;        // [P][J][M]
+        void* d_spec[2] = {nullptr, nullptr};
+        double* d_loss = nullptr;         // [P]
+        float* d_grad = nullptr;          // [P][J][M]
+        void* d_object = nullptr;         // [P][K][N][ld] or null
+        cudaStream_t h2d = nullptr, d2h = nullptr;
+        cudaEvent_t ev_start = nullptr, ev_coeffs = nullptr, ev_end = nullptr, ev_done = nullptr;
+        cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_consumed[2] = {nullptr, nullptr};
+        std::vector<void*> allocations;
+    } host;
     // kernel timing (mfbd_plan_set_profiling)
     std::vector<cudaEvent_t> ev;    // 2 per pair
     std::vector<int> ev_kind;       // kind of each used pair
@@ -148,10 +163,12 @@ void release(mfbd_plan* p) {
     p->allocations.clear();
 }
 
-FusedParams fused_params(const mfbd_plan* p, const void* spectra, double* loss, void* object, float2* gscr,
-                         float2* pscr, float2* uscr) {
+// Kernel parameters for patches [p0, p0 + np): spectra, loss and object
+// point at patch p0; the per-unit scratch is reused from its start.
+FusedParams fused_params(const mfbd_plan* p, int p0, int np, const void* spectra, double* loss, void* object,
+                         float2* gscr, float2* pscr, float2* uscr) {
     FusedParams f{};
-    f.P = p->P;
+    f.P = np;
     f.K = p->K;
     f.J = p->J;
     f.M = p->M;
@@ -171,7 +188,7 @@ FusedParams fused_params(const mfbd_plan* p, const void* spectra, double* loss, 
         f.obj[k].W = p->obj[k].W;
         f.obj[k].x0 = p->obj[k].x0;
         f.obj[k].inv_z = p->obj[k].inv_z;
-        f.obj[k].phi_off = p->obj[k].phi_off;
+        f.obj[k].phi_off = p->obj[k].phi_off + (long long)p0 * p->J * p->obj[k].W * p->obj[k].W;
         f.obj[k].phi_unit = (long long)p->obj[k].W * p->obj[k].W;
         f.obj[k].phi_org = 0;
         f.obj[k].phi_ld = p->obj[k].W;
@@ -211,12 +228,13 @@ void prof_end(mfbd_plan_t p, int i, cudaStream_t s) {
     if (i >= 0) cudaEventRecord(p->ev[2 * i + 1], s);
 }
 
-int run_phase(mfbd_plan_t p, const float* coeffs, cudaStream_t s) {
+// Phases of patches [p0, p0 + np); coeffs points at patch p0.
+int run_phase(mfbd_plan_t p, const float* coeffs, cudaStream_t s, int p0, int np) {
     for (int k = 0; k < p->K; ++k) {
         const ObjectData& o = p->obj[k];
         const int pi = prof_begin(p, 0, s);
-        cudaError_t e = launch_phase_gemm(coeffs, p->P * p->J, p->M, o.d_basis, o.W * o.W, o.scale,
-                                          p->d_phi + o.phi_off, s);
+        cudaError_t e = launch_phase_gemm(coeffs, np * p->J, p->M, o.d_basis, o.W * o.W, o.scale,
+                                          p->d_phi + o.phi_off + (size_t)p0 * p->J * o.W * o.W, s);
         prof_end(p, pi, s);
         if (e != cudaSuccess) {
             p->failed = true;
@@ -226,8 +244,9 @@ int run_phase(mfbd_plan_t p, const float* coeffs, cudaStream_t s) {
     return MFBD_OK;
 }
 
-int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s) {
-    const int U = p->P * p->J;
+// dL/da of patches [p0, p0 + np); grad points at patch p0.
+int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s, int p0, int np) {
+    const int U = np * p->J;
     GradParts gp{};
     gp.K = p->K;
     const int pi = prof_begin(p, 4, s);
@@ -238,7 +257,8 @@ int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s) {
         gp.splits[k] = grad_splits(o.W * o.W, &chunk);
         gp.scale[k] = o.scale;
         gp.part[k] = p->d_gpart + o.part_off;
-        e = launch_grad_gemm(p->d_gphi + o.phi_off, U, o.W * o.W, o.d_basis, p->M, p->d_gpart + o.part_off, s);
+        e = launch_grad_gemm(p->d_gphi + o.phi_off + (size_t)p0 * p->J * o.W * o.W, U, o.W * o.W, o.d_basis, p->M,
+                             p->d_gpart + o.part_off, s);
     }
     if (e == cudaSuccess) e = launch_grad_combine(gp, U, p->M, grad, s);
     prof_end(p, pi, s);
@@ -249,22 +269,29 @@ int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s) {
     return MFBD_OK;
 }
 
-int run_fused(mfbd_plan_t p, int mode, const void* spectra, double* loss, void* object, float2* gscr,
-              cudaStream_t s) {
-    FusedParams f = mode == MODE_OTF ? fused_params(p, spectra, loss, object, gscr, nullptr, nullptr)
-                                     : fused_params(p, spectra, loss, object, p->d_gscr, p->d_pscr, p->d_uscr);
+// Kernels of an evaluation, selected by bit: the forward passes, the frame
+// reduction, the adjoint passes; OTF_ONLY writes the OTFs to `gscr` and keeps
+// nothing for the adjoint.
+enum Stage : int { ST_FWD = 1, ST_RED = 2, ST_ADJ = 4, ST_OTF_ONLY = 8 };
+
+// Pass and reduction kernels of `stages` for patches [p0, p0 + np).
+int run_fused(mfbd_plan_t p, int stages, const void* spectra, double* loss, void* object, float2* gscr,
+              cudaStream_t s, int p0, int np) {
+    FusedParams f = (stages & ST_OTF_ONLY)
+                        ? fused_params(p, p0, np, spectra, loss, object, gscr, nullptr, nullptr)
+                        : fused_params(p, p0, np, spectra, loss, object, p->d_gscr, p->d_pscr, p->d_uscr);
     cudaError_t e = cudaSuccess;
-    if (mode != MODE_BWD) {
+    if (stages & ST_FWD) {
         const int pi = prof_begin(p, 1, s);
         e = launch_forward_passes(f, p->geo, p->sms, s);
         prof_end(p, pi, s);
-        if (e == cudaSuccess && mode != MODE_OTF) {
-            const int pr = prof_begin(p, 2, s);
-            e = launch_reduction(f, p->sms, s);
-            prof_end(p, pr, s);
-        }
     }
-    if (e == cudaSuccess && (mode == MODE_BWD || mode == MODE_FUSED)) {
+    if (e == cudaSuccess && (stages & ST_RED)) {
+        const int pr = prof_begin(p, 2, s);
+        e = launch_reduction(f, p->sms, s);
+        prof_end(p, pr, s);
+    }
+    if (e == cudaSuccess && (stages & ST_ADJ)) {
         const int pb = prof_begin(p, 3, s);
         e = launch_adjoint_passes(f, p->geo, p->sms, s);
         prof_end(p, pb, s);
@@ -273,6 +300,66 @@ int run_fused(mfbd_plan_t p, int mode, const void* spectra, double* loss, void* 
         p->failed = true;
         return cuda_fail(e, "pass or reduction kernel");
     }
+    return MFBD_OK;
+}
+
+// ------------------------------------------------------- host-buffer pipeline
+
+void host_release(mfbd_plan* p) {
+    auto& h = p->host;
+    for (cudaStream_t st : {h.h2d, h.d2h})
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : {h.ev_start, h.ev_coeffs, h.ev_end, h.ev_done, h.ev_copied[0], h.ev_copied[1],
+                          h.ev_consumed[0], h.ev_consumed[1]})
+        if (e) cudaEventDestroy(e);
+    for (void* a : h.allocations) cudaFree(a);
+    h = mfbd_plan::HostPipe{};
+}
+
+size_t spectrum_patch_bytes(const mfbd_plan* p) {
+    const int ld = (p->flags & MFBD_FLAG_FULL_SPECTRUM) ? p->N : p->N / 2 + 1;
+    return (size_t)p->K * p->J * p->N * ld * sizeof(float2);
+}
+
+size_t object_patch_bytes(const mfbd_plan* p) {
+    const int ld = (p->flags & MFBD_FLAG_FULL_SPECTRUM) ? p->N : p->N / 2 + 1;
+    return (size_t)p->K * p->N * ld * sizeof(float2);
+}
+
+// Device staging of the host pipeline for `chunk` patches per buffer; kept
+// across calls and rebuilt (after a device synchronisation) only when a call
+// needs more.
+int host_setup(mfbd_plan* p, int chunk, bool with_object) {
+    auto& h = p->host;
+    if (h.ready && h.chunk_patches >= chunk && (h.with_object || !with_object)) return MFBD_OK;
+    cudaDeviceSynchronize();
+    host_release(p);
+    auto alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMalloc(ptr, bytes > 0 ? bytes : 16);
+        if (e == cudaSuccess) h.allocations.push_back(*ptr);
+        return e;
+    };
+    const size_t cm = (size_t)p->P * p->J * p->M;
+    cudaError_t e = cudaSuccess;
+    if ((e = alloc((void**)&h.d_coeffs, cm * sizeof(float))) || (e = alloc((void**)&h.d_grad, cm * sizeof(float))) ||
+        (e = alloc((void**)&h.d_loss, (size_t)p->P * sizeof(double))) ||
+        (e = alloc(&h.d_spec[0], (size_t)chunk * spectrum_patch_bytes(p))) ||
+        (e = alloc(&h.d_spec[1], (size_t)chunk * spectrum_patch_bytes(p))) ||
+        (with_object && (e = alloc(&h.d_object, (size_t)p->P * object_patch_bytes(p)))) ||
+        (e = cudaStreamCreateWithFlags(&h.h2d, cudaStreamNonBlocking)) ||
+        (e = cudaStreamCreateWithFlags(&h.d2h, cudaStreamNonBlocking))) {
+        host_release(p);
+        return cuda_fail(e, "host pipeline setup");
+    }
+    for (cudaEvent_t* ev : {&h.ev_start, &h.ev_coeffs, &h.ev_end, &h.ev_done, &h.ev_copied[0], &h.ev_copied[1],
+                            &h.ev_consumed[0], &h.ev_consumed[1]})
+        if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming))) {
+            host_release(p);
+            return cuda_fail(e, "host pipeline events");
+        }
+    h.ready = true;
+    h.chunk_patches = chunk;
+    h.with_object = with_object;
     return MFBD_OK;
 }
 
@@ -508,6 +595,7 @@ int mfbd_plan_destroy(mfbd_plan_t p) {
     cudaSetDevice(p->device);
     cudaDeviceSynchronize();
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    host_release(p);
     release(p);
     delete p;
     return MFBD_OK;
@@ -542,8 +630,8 @@ int mfbd_forward(mfbd_plan_t p, const float* coeffs, const void* spectra, double
     if (!coeffs || !spectra || !loss) return fail(MFBD_ERR_INVALID_ARG, "coeffs, spectra and loss are required");
     if ((st = set_device(p))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if ((st = run_phase(p, coeffs, s))) return st;
-    if ((st = run_fused(p, MODE_FWD, spectra, loss, object, p->d_gscr, s))) return st;
+    if ((st = run_phase(p, coeffs, s, 0, p->P))) return st;
+    if ((st = run_fused(p, ST_FWD | ST_RED, spectra, loss, object, p->d_gscr, s, 0, p->P))) return st;
     p->have_forward = true;
     return MFBD_OK;
 }
@@ -556,8 +644,8 @@ int mfbd_backward(mfbd_plan_t p, float* grad, void* stream) {
     if (!grad) return fail(MFBD_ERR_INVALID_ARG, "grad is NULL");
     if ((st = set_device(p))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if ((st = run_fused(p, MODE_BWD, nullptr, nullptr, nullptr, p->d_gscr, s))) return st;
-    return run_grad(p, grad, s);
+    if ((st = run_fused(p, ST_ADJ, nullptr, nullptr, nullptr, p->d_gscr, s, 0, p->P))) return st;
+    return run_grad(p, grad, s, 0, p->P);
 }
 
 int mfbd_loss_grad(mfbd_plan_t p, const float* coeffs, const void* spectra, double* loss, void* object,
@@ -569,10 +657,83 @@ int mfbd_loss_grad(mfbd_plan_t p, const float* coeffs, const void* spectra, doub
         return fail(MFBD_ERR_INVALID_ARG, "coeffs, spectra, loss and grad are required");
     if ((st = set_device(p))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if ((st = run_phase(p, coeffs, s))) return st;
-    if ((st = run_fused(p, MODE_FUSED, spectra, loss, object, p->d_gscr, s))) return st;
-    if ((st = run_grad(p, grad, s))) return st;
+    if ((st = run_phase(p, coeffs, s, 0, p->P))) return st;
+    if ((st = run_fused(p, ST_FWD | ST_RED | ST_ADJ, spectra, loss, object, p->d_gscr, s, 0, p->P))) return st;
+    if ((st = run_grad(p, grad, s, 0, p->P))) return st;
     p->have_forward = true;
+    return MFBD_OK;
+}
+
+int mfbd_loss_grad_host(mfbd_plan_t p, const float* coeffs, const void* spectra, double* loss, void* object,
+                        float* grad, int n_chunks, void* stream) {
+    int st = check_plan(p);
+    if (st) return st;
+    if (p->P == 0) return MFBD_OK;
+    if (!coeffs || !spectra || !loss || !grad)
+        return fail(MFBD_ERR_INVALID_ARG, "coeffs, spectra, loss and grad are required");
+    if ((st = set_device(p))) return st;
+    const int P = p->P, J = p->J, M = p->M;
+    if (n_chunks <= 0) {  // ~320 patches per chunk keeps every kernel of a chunk device-filling
+        n_chunks = P / 320;
+        n_chunks = n_chunks < 1 ? 1 : (n_chunks > 8 ? 8 : n_chunks);
+    }
+    if (n_chunks > P) n_chunks = P;
+    const int cp = (P + n_chunks - 1) / n_chunks;  // patches per chunk (the last may have fewer)
+    n_chunks = (P + cp - 1) / cp;
+    if ((st = host_setup(p, cp, object != nullptr))) {
+        p->failed = true;
+        return st;
+    }
+    auto& h = p->host;
+    const size_t sp = spectrum_patch_bytes(p), op = object_patch_bytes(p);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+#define MFBD_HOST_TRY(call)                        \
+    if ((e = (call)) != cudaSuccess) {             \
+        p->failed = true;                          \
+        return cuda_fail(e, "host pipeline");      \
+    }
+    // the copies start after the work already queued on `stream`
+    MFBD_HOST_TRY(cudaEventRecord(h.ev_start, s));
+    MFBD_HOST_TRY(cudaStreamWaitEvent(h.h2d, h.ev_start, 0));
+    MFBD_HOST_TRY(cudaStreamWaitEvent(h.d2h, h.ev_start, 0));
+    MFBD_HOST_TRY(cudaMemcpyAsync(h.d_coeffs, coeffs, (size_t)P * J * M * sizeof(float), cudaMemcpyHostToDevice,
+                                  h.h2d));
+    MFBD_HOST_TRY(cudaEventRecord(h.ev_coeffs, h.h2d));
+    MFBD_HOST_TRY(cudaStreamWaitEvent(s, h.ev_coeffs, 0));
+    for (int c = 0; c < n_chunks; ++c) {
+        const int b = c & 1, p0 = c * cp, np = P - p0 < cp ? P - p0 : cp;
+        // chunk c's spectra go into the buffer chunk c - 2 read; its
+        // reduction kernel is the only reader
+        if (c >= 2) MFBD_HOST_TRY(cudaStreamWaitEvent(h.h2d, h.ev_consumed[b], 0));
+        MFBD_HOST_TRY(cudaMemcpyAsync(h.d_spec[b], static_cast<const char*>(spectra) + (size_t)p0 * sp,
+                                      (size_t)np * sp, cudaMemcpyHostToDevice, h.h2d));
+        MFBD_HOST_TRY(cudaEventRecord(h.ev_copied[b], h.h2d));
+        void* obj = object && h.d_object ? static_cast<char*>(h.d_object) + (size_t)p0 * op : nullptr;
+        // phases and forward passes need only the coefficients: they run
+        // while the chunk's spectra are still in flight
+        if ((st = run_phase(p, h.d_coeffs + (size_t)p0 * J * M, s, p0, np))) return st;
+        if ((st = run_fused(p, ST_FWD, nullptr, nullptr, nullptr, p->d_gscr, s, p0, np))) return st;
+        MFBD_HOST_TRY(cudaStreamWaitEvent(s, h.ev_copied[b], 0));
+        if ((st = run_fused(p, ST_RED, h.d_spec[b], h.d_loss + p0, obj, p->d_gscr, s, p0, np))) return st;
+        MFBD_HOST_TRY(cudaEventRecord(h.ev_consumed[b], s));
+        if ((st = run_fused(p, ST_ADJ, nullptr, nullptr, nullptr, p->d_gscr, s, p0, np))) return st;
+        if ((st = run_grad(p, h.d_grad + (size_t)p0 * J * M, s, p0, np))) return st;
+        MFBD_HOST_TRY(cudaEventRecord(h.ev_done, s));
+        MFBD_HOST_TRY(cudaStreamWaitEvent(h.d2h, h.ev_done, 0));
+        MFBD_HOST_TRY(cudaMemcpyAsync(loss + p0, h.d_loss + p0, (size_t)np * sizeof(double), cudaMemcpyDeviceToHost,
+                                      h.d2h));
+        MFBD_HOST_TRY(cudaMemcpyAsync(grad + (size_t)p0 * J * M, h.d_grad + (size_t)p0 * J * M,
+                                      (size_t)np * J * M * sizeof(float), cudaMemcpyDeviceToHost, h.d2h));
+        if (obj)
+            MFBD_HOST_TRY(cudaMemcpyAsync(static_cast<char*>(object) + (size_t)p0 * op, obj, (size_t)np * op,
+                                          cudaMemcpyDeviceToHost, h.d2h));
+    }
+    // `stream` completes only after the last read-back
+    MFBD_HOST_TRY(cudaEventRecord(h.ev_end, h.d2h));
+    MFBD_HOST_TRY(cudaStreamWaitEvent(s, h.ev_end, 0));
+#undef MFBD_HOST_TRY
+    p->have_forward = false;  // the per-unit buffers hold the last chunk only
     return MFBD_OK;
 }
 
@@ -584,8 +745,8 @@ int mfbd_otf(mfbd_plan_t p, const float* coeffs, void* otf, void* stream) {
     if ((st = set_device(p))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     p->have_forward = false;  // the phases now belong to these coefficients
-    if ((st = run_phase(p, coeffs, s))) return st;
-    return run_fused(p, MODE_OTF, nullptr, nullptr, nullptr, static_cast<float2*>(otf), s);
+    if ((st = run_phase(p, coeffs, s, 0, p->P))) return st;
+    return run_fused(p, ST_FWD | ST_OTF_ONLY, nullptr, nullptr, nullptr, static_cast<float2*>(otf), s, 0, p->P);
 }
 
 }  // extern "C"

@@ -62,6 +62,18 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _host(t, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise ValueError("%s must be a CPU tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _dev(t, dtype, shape, name):
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise ValueError("%s must be a CUDA tensor" % name)
@@ -157,6 +169,27 @@ class Plan:
             _dev(loss, torch.float64, (self.n_patches,), "loss"),
             _dev(obj, torch.complex64, self.object_shape(), "object") if obj is not None else None,
             _dev(grad, torch.float32, self.coeff_shape(), "grad"), _stream(stream)), "mfbd_loss_grad")
+        return loss, grad, obj
+
+    def loss_grad_host(self, coeffs, spectra, loss=None, grad=None, obj=None, want_object=False, n_chunks=0,
+                       stream=None):
+        """mfbd_loss_grad_host: the same outputs from CPU tensors (pin them for
+        the copies to overlap with the kernels). Asynchronous: synchronise
+        `stream` before reading the outputs or reusing the inputs."""
+        pin = torch.cuda.is_available()
+        if loss is None:
+            loss = torch.empty(self.n_patches, dtype=torch.float64, pin_memory=pin)
+        if grad is None:
+            grad = torch.empty(self.coeff_shape(), dtype=torch.float32, pin_memory=pin)
+        if obj is None and want_object:
+            obj = torch.empty(self.object_shape(), dtype=torch.complex64, pin_memory=pin)
+        _lib.check(self._lib.mfbd_loss_grad_host(
+            self._h, _host(coeffs, torch.float32, self.coeff_shape(), "coeffs"),
+            _host(spectra, torch.complex64, self.spectra_shape(), "spectra"),
+            _host(loss, torch.float64, (self.n_patches,), "loss"),
+            _host(obj, torch.complex64, self.object_shape(), "object") if obj is not None else None,
+            _host(grad, torch.float32, self.coeff_shape(), "grad"), ctypes.c_int(int(n_chunks)),
+            _stream(stream)), "mfbd_loss_grad_host")
         return loss, grad, obj
 
     def otf(self, coeffs, out=None, stream=None):

@@ -82,6 +82,7 @@ def test_unsupported_size_and_null_arguments(lib):
     assert lib.mfbd_plan_create(None, ctypes.byref(d.desc), None) == _lib.MFBD_ERR_INVALID_ARG
     assert lib.mfbd_forward(None, None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
     assert lib.mfbd_backward(None, None, None) == _lib.MFBD_ERR_INVALID_ARG
+    assert lib.mfbd_loss_grad_host(None, None, None, None, None, None, 4, None) == _lib.MFBD_ERR_INVALID_ARG
     assert lib.mfbd_plan_destroy(None) == _lib.MFBD_OK
 
 

@@ -221,3 +221,30 @@ def test_gradient_central_differences_on_gpu(c1):
             vals.append(loss.cpu().numpy()[0])
         fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(fd - g[0, j, m]) <= 1e-2 * abs(g[0, j, m]), (j, m, fd, g[0, j, m])
+
+
+@pytest.mark.parametrize("n_chunks", [1, 4, 0])
+def test_host_pipeline_equals_device_call(c2_slice, n_chunks):
+    """mfbd_loss_grad_host (pinned host buffers, chunked copies overlapped with
+    the kernels; 10 patches in chunks of 10, 3 + 3 + 3 + 1, or the default)
+    gives the bits of mfbd_loss_grad, and mfbd_backward is refused after it."""
+    a32, d32, _ = _inputs(c2_slice)
+    reps = 4
+    aa = np.ascontiguousarray(np.tile(a32, (reps, 1, 1))[:10])
+    dd = np.ascontiguousarray(np.tile(d32, (reps, 1, 1, 1, 1))[:10])
+    plan = _plan_for(c2_slice, n_patches=10)
+    loss, grad, obj = _run_fused(plan, aa, dd)
+    ah = torch.from_numpy(aa).pin_memory()
+    dh = torch.from_numpy(dd).pin_memory()
+    lh, gh, oh = plan.loss_grad_host(ah, dh, want_object=True, n_chunks=n_chunks)
+    torch.cuda.current_stream().synchronize()
+    assert np.array_equal(lh.numpy(), loss)
+    assert np.array_equal(gh.numpy(), grad)
+    assert np.array_equal(oh.numpy().astype(np.complex128), obj)
+    from paper_2505_10639_gb300._lib import MFBDError
+    with pytest.raises(MFBDError):
+        plan.backward()
+    # a second call on the same plan (staging reused) without the object
+    lh2, gh2, _ = plan.loss_grad_host(ah, dh, n_chunks=n_chunks)
+    torch.cuda.current_stream().synchronize()
+    assert np.array_equal(lh2.numpy(), loss) and np.array_equal(gh2.numpy(), grad)
