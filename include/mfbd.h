@@ -65,12 +65,19 @@ typedef enum {
 } mfbd_basis;
 
 typedef enum {
-    MFBD_PREC_FP32 = 0,      /* phase projection, FFTs, adjoint in FP32 */
-    MFBD_PREC_BF16_PHASE = 1 /* phase projection on BF16 tensor cores */
+    MFBD_PREC_FP32 = 0,      /* FFTs, adjoint in FP32; the phase projection on the
+                              * tensor cores with every operand split into three
+                              * BF16 planes (FP32-accurate), or on the SIMT kernel */
+    MFBD_PREC_BF16_PHASE = 1 /* phase projection phi = B a on the tensor cores with
+                              * BF16 operands and FP32 accumulation; the rest as
+                              * MFBD_PREC_FP32 */
 } mfbd_precision;
 
 /* flags */
 #define MFBD_FLAG_FULL_SPECTRUM 0x1u /* spectra/object are [N][N], else [N][N/2+1] */
+#define MFBD_FLAG_SIMT_PROJECTION 0x2u /* FP32 phase projection on the SIMT kernel instead
+                                        * of the tensor cores (comparison runs; not with
+                                        * MFBD_PREC_BF16_PHASE) */
 
 typedef struct {
     int n_pix;      /* N, patch size in pixels (64) */

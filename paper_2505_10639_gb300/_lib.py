@@ -21,6 +21,7 @@ MFBD_BASIS_USER = 2
 MFBD_PREC_FP32 = 0
 MFBD_PREC_BF16_PHASE = 1
 MFBD_FLAG_FULL_SPECTRUM = 0x1
+MFBD_FLAG_SIMT_PROJECTION = 0x2
 
 
 class PlanDesc(ctypes.Structure):

@@ -40,6 +40,10 @@ struct ObjectData {
     float* d_basis = nullptr;   // [M][W*W]
     uint64_t* d_mask = nullptr; // [W] box rows, then [N] box columns
     uint64_t* d_supp = nullptr; // [N] rows, then [N] columns of the OTF support
+    // tensor-core phase projection: the box basis as BF16 planes in the MMA
+    // tile layout, [n_tiles][planes][Nt * Mp]; planes == 0: SIMT kernel
+    uint16_t* d_basis_tc = nullptr;
+    int tc_planes = 0;
 };
 
 }  // namespace
@@ -47,7 +51,10 @@ struct ObjectData {
 struct mfbd_plan {
     int N = 0, P = 0, K = 0, J = 0, M = 0;
     unsigned flags = 0;
+    int precision = MFBD_PREC_FP32;
     double gamma = 0;
+    int* d_err = nullptr;       // set by a tensor-core kernel whose MMA wait gave up
+    uint16_t* d_acoef = nullptr;  // coefficients as BF16 planes in the MMA tile layout
     int device = 0;
     ObjectData obj[kMaxObjects];
     float* d_weights = nullptr;
@@ -119,10 +126,63 @@ int validate(const mfbd_plan_desc* d) {
                 return fail(MFBD_ERR_INVALID_ARG, "frame weights must be finite and >= 0");
     if (d->precision != MFBD_PREC_FP32 && d->precision != MFBD_PREC_BF16_PHASE)
         return fail(MFBD_ERR_INVALID_ARG, "unknown precision");
-    if (d->flags & ~MFBD_FLAG_FULL_SPECTRUM) return fail(MFBD_ERR_INVALID_ARG, "unknown flags");
+    if (d->flags & ~(MFBD_FLAG_FULL_SPECTRUM | MFBD_FLAG_SIMT_PROJECTION))
+        return fail(MFBD_ERR_INVALID_ARG, "unknown flags");
     if (d->n_pix != kN) return fail(MFBD_ERR_UNSUPPORTED, "this build supports n_pix == 64");
-    if (d->precision != MFBD_PREC_FP32) return fail(MFBD_ERR_UNSUPPORTED, "BF16 phase path not built");
+    if (d->precision == MFBD_PREC_BF16_PHASE && (d->flags & MFBD_FLAG_SIMT_PROJECTION))
+        return fail(MFBD_ERR_INVALID_ARG, "the BF16 phase projection runs on the tensor cores only");
     return MFBD_OK;
+}
+
+// BF16 bits of x, rounded to nearest even (finite x).
+uint16_t bf16_round(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_float(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float x;
+    std::memcpy(&x, &u, 4);
+    return x;
+}
+
+// Tensor-core layout of object o's box basis `hb` ([M][W^2] float): for each
+// tile of 128 pixels and each BF16 plane (x = x0 + x1 + x2, each plane
+// the rounding of what the previous ones leave; one plane for the BF16 phase
+// path), the 128 x Mp operand in the no-swizzle K-major core-matrix order
+// (8 pixels x 8 modes per 128-byte core matrix, core matrices along the modes
+// 128 bytes apart, 8-pixel groups Mp * 16 bytes apart). Returns false (SIMT
+// kernel) when the projection is forced onto the SIMT kernel or its tiles do
+// not fit in shared memory.
+bool tc_projection_layout(const mfbd_plan* p, ObjectData& o, const std::vector<float>& hb,
+                          std::vector<uint16_t>* out) {
+    if (p->flags & MFBD_FLAG_SIMT_PROJECTION) return false;
+    const int planes = p->precision == MFBD_PREC_BF16_PHASE ? 1 : 3;
+    const int Mp = (p->M + 15) / 16 * 16, npix = o.W * o.W;
+    if (phase_mma_smem(p->M, planes) > (size_t)200 * 1024) return false;
+    const int nt = 128;  // pixels per tile (the MMA's M)
+    const int tiles = (npix + nt - 1) / nt;
+    out->assign((size_t)tiles * planes * nt * Mp, 0);
+    for (int t = 0; t < tiles; ++t)
+        for (int r = 0; r < nt; ++r) {
+            const int i = t * nt + r;
+            if (i >= npix) break;
+            for (int m = 0; m < p->M; ++m) {
+                const float x = hb[(size_t)m * npix + i];
+                float left = x;
+                for (int q = 0; q < planes; ++q) {
+                    const uint16_t b = bf16_round(left);
+                    left -= bf16_float(b);
+                    const size_t off = (size_t)(r / 8) * Mp * 8 + (size_t)(m / 8) * 64 + (size_t)(r % 8) * 8 + (m % 8);
+                    (*out)[((size_t)t * planes + q) * nt * Mp + off] = b;
+                }
+            }
+        }
+    o.tc_planes = planes;
+    return true;
 }
 
 // full-grid double basis [M][N][N] of object k
@@ -233,8 +293,14 @@ int run_phase(mfbd_plan_t p, const float* coeffs, cudaStream_t s, int p0, int np
     for (int k = 0; k < p->K; ++k) {
         const ObjectData& o = p->obj[k];
         const int pi = prof_begin(p, 0, s);
-        cudaError_t e = launch_phase_gemm(coeffs, np * p->J, p->M, o.d_basis, o.W * o.W, o.scale,
-                                          p->d_phi + o.phi_off + (size_t)p0 * p->J * o.W * o.W, s);
+        float* out = p->d_phi + o.phi_off + (size_t)p0 * p->J * o.W * o.W;
+        cudaError_t e = cudaSuccess;
+        if (o.tc_planes > 0 && k == 0)  // the coefficients are shared by all objects: split once
+            e = launch_split_coeffs(coeffs, np * p->J, p->M, o.tc_planes, p->d_acoef, s);
+        if (e == cudaSuccess)
+            e = o.tc_planes > 0 ? launch_phase_mma(p->d_acoef, np * p->J, p->M, o.d_basis_tc, o.W * o.W, o.tc_planes,
+                                                   o.scale, out, p->d_err, p->sms, s)
+                                : launch_phase_gemm(coeffs, np * p->J, p->M, o.d_basis, o.W * o.W, o.scale, out, s);
         prof_end(p, pi, s);
         if (e != cudaSuccess) {
             p->failed = true;
@@ -443,6 +509,7 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
     p->J = d->n_frames;
     p->M = d->n_modes;
     p->flags = d->flags;
+    p->precision = d->precision;
     p->gamma = d->gamma;
     p->device = dev;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -456,6 +523,9 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
             throw cuda_fail(e, "upload weights");
 
         std::vector<std::vector<float>> hb(p->K);
+        std::vector<std::vector<uint16_t>> htc(p->K);
+        if ((st = dev_alloc(p, &p->d_err, 1))) throw st;
+        if ((e = cudaMemsetAsync(p->d_err, 0, sizeof(int), s))) throw cuda_fail(e, "clear error flag");
         std::vector<std::vector<uint64_t>> hm(p->K), hs(p->K);
         long long phi_floats = 0;
         int max_box = 1;
@@ -505,6 +575,11 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
                         hs[k][n + kx] |= 1ull << ky;
                     }
             if ((st = dev_alloc(p, &o.d_basis, hb[k].size()))) throw st;
+            if (tc_projection_layout(p, o, hb[k], &htc[k])) {
+                if ((st = dev_alloc(p, &o.d_basis_tc, htc[k].size()))) throw st;
+                if ((e = cudaMemcpyAsync(o.d_basis_tc, htc[k].data(), htc[k].size() * 2, cudaMemcpyHostToDevice, s)))
+                    throw cuda_fail(e, "upload tensor-core basis");
+            }
             if ((st = dev_alloc(p, &o.d_mask, hm[k].size()))) throw st;
             if ((st = dev_alloc(p, &o.d_supp, hs[k].size()))) throw st;
             if ((e = cudaMemcpyAsync(o.d_basis, hb[k].data(), hb[k].size() * sizeof(float), cudaMemcpyHostToDevice, s)) ||
@@ -513,6 +588,9 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
                 throw cuda_fail(e, "upload plan data");
         }
         p->phi_floats = phi_floats;
+        if (p->obj[0].tc_planes > 0 &&
+            (st = dev_alloc(p, &p->d_acoef, split_coeffs_elems(p->P * p->J, p->M, p->obj[0].tc_planes))))
+            throw st;
         long long part_floats = 0;
         for (int k = 0; k < p->K; ++k) {
             int chunk = 0;

@@ -68,6 +68,17 @@ cudaError_t launch_fused(const FusedParams& prm, int mode, const FusedGeometry& 
 cudaError_t launch_phase_gemm(const float* a, int U, int M, const float* basis, int npix,
                               float scale, float* phase, cudaStream_t s);
 
+// The same on the tensor cores (tcgen05, BF16 operands, FP32 accumulation).
+// launch_split_coeffs writes the coefficients as `planes` BF16 planes (3:
+// FP32-accurate split, 1: BF16) in the MMA tile layout (split_coeffs_elems
+// elements); bt holds the basis the same way in 128-pixel tiles; err is set
+// when an MMA wait gives up. phase_mma_smem: dynamic shared memory of a CTA.
+size_t phase_mma_smem(int M, int planes);
+size_t split_coeffs_elems(int U, int M, int planes);
+cudaError_t launch_split_coeffs(const float* a, int U, int M, int planes, uint16_t* at, cudaStream_t s);
+cudaError_t launch_phase_mma(const uint16_t* at, int U, int M, const uint16_t* bt, int npix, int planes,
+                             float scale, float* phase, int* err, int sms, cudaStream_t s);
+
 // Modal adjoint, split over pixels: part[z][u][m] = sum over chunk z of
 // gphi[u][i] basis[m][i]; grad_splits gives the number of chunks (and the
 // chunk length) for npix pixels.

@@ -25,7 +25,9 @@ class _Desc:
     """A PlanDesc plus the host arrays it points into (kept alive)."""
 
     def __init__(self, n_pix, n_patches, diams, wavelengths, n_frames, n_modes, basis, gamma,
-                 weights, obscuration, user_basis, precision, full_spectrum):
+                 weights, obscuration, user_basis, precision, full_spectrum, projection="tensor"):
+        if projection not in ("tensor", "simt"):
+            raise ValueError("projection must be 'tensor' or 'simt'")
         k = len(diams)
         self.diams = np.ascontiguousarray(diams, dtype=np.float32)
         self.wl = np.ascontiguousarray(wavelengths, dtype=np.float64)
@@ -37,7 +39,8 @@ class _Desc:
             central_obscuration=obscuration, basis=_BASIS[basis],
             user_basis=_fptr(self.user, ctypes.c_float), gamma=gamma,
             frame_weight=_fptr(self.weights, ctypes.c_float), precision=_PREC[precision],
-            flags=_lib.MFBD_FLAG_FULL_SPECTRUM if full_spectrum else 0)
+            flags=(_lib.MFBD_FLAG_FULL_SPECTRUM if full_spectrum else 0)
+            | (_lib.MFBD_FLAG_SIMT_PROJECTION if projection == "simt" else 0))
 
 
 def describe_object(obj, n_pix, diams, wavelengths, n_frames, n_modes, basis="kl", gamma=1e-3,
@@ -95,10 +98,10 @@ class Plan:
 
     def __init__(self, n_pix, n_patches, diams, wavelengths, n_frames, n_modes, basis="kl",
                  gamma=1e-3, weights=None, obscuration=0.0, user_basis=None, precision="fp32",
-                 full_spectrum=False, stream=None):
+                 full_spectrum=False, projection="tensor", stream=None):
         self._lib = _lib.load()
         self._d = _Desc(n_pix, n_patches, diams, wavelengths, n_frames, n_modes, basis, gamma, weights,
-                        obscuration, user_basis, precision, full_spectrum)
+                        obscuration, user_basis, precision, full_spectrum, projection)
         self.n_pix, self.n_patches, self.n_objects = n_pix, n_patches, len(diams)
         self.n_frames, self.n_modes = n_frames, n_modes
         self.full_spectrum = full_spectrum
