@@ -23,7 +23,6 @@
 // instruction writes 32 consecutive pixels of one unit's phase row.
 #include "mfbd_internal.h"
 
-#include <cuda_bf16.h>
 #include <cstdint>
 
 namespace mfbd_dev {
@@ -58,6 +57,25 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t 
         "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
+// The MMAs of one tile or chunk from one thread: the plane pairs of weight
+// >= 2^-16 in decreasing weight (one pair with one plane), `ksteps` K-steps of
+// 16 each. da0 / db0 describe plane 0 of A / B; a plane is a_plane / b_plane
+// bytes further and a K-step 256 bytes (the descriptor's address field counts
+// 16-byte units, and no shared-memory address overflows it).
+__device__ __forceinline__ void issue_mmas(uint32_t tmem_d, uint64_t da0, uint64_t db0, uint32_t a_plane,
+                                           uint32_t b_plane, int ksteps, int planes, uint32_t idesc, bool accumulate) {
+    const uint32_t pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+    const int npairs = planes == 3 ? 6 : 1;
+    uint32_t acc = accumulate ? 1u : 0u;
+    for (int pp = 0; pp < npairs; ++pp) {
+        const uint64_t da = da0 + ((pa[pp] * a_plane) >> 4), db = db0 + ((pb[pp] * b_plane) >> 4);
+        for (int s = 0; s < ksteps; ++s) {
+            mma_bf16(tmem_d, da + (uint64_t)(s * 16), db + (uint64_t)(s * 16), idesc, acc);
+            acc = 1u;
+        }
+    }
+}
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(__cvta_generic_to_global(gmem))
                  : "memory");
@@ -79,12 +97,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
     return done != 0;
 }
 
-__device__ __forceinline__ uint16_t bf16_bits(float x) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    return *reinterpret_cast<const uint16_t*>(&h);
+// x = x0 + x1 + x2 + r: each plane the BF16 rounding (to nearest even, by
+// integer arithmetic on the bits; x finite) of what the previous planes
+// leave; every subtraction is exact.
+__device__ __forceinline__ uint32_t bf16_round_bits(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
 }
 
-__device__ __forceinline__ float bf16_value(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+__device__ __forceinline__ void bf16_split3(float x, uint32_t& b0, uint32_t& b1, uint32_t& b2) {
+    b0 = bf16_round_bits(x);
+    const float r1 = x - __uint_as_float(b0 << 16);
+    b1 = bf16_round_bits(r1);
+    b2 = bf16_round_bits(r1 - __uint_as_float(b1 << 16));
+}
 
 // Coefficients [U][M] float -> BF16 planes in the MMA layout,
 // [n_tiles][planes][128 units x Mp modes]; one thread per (unit, 8 modes).
@@ -97,27 +123,21 @@ __global__ void __launch_bounds__(256) split_coeffs_kernel(const float* __restri
          idx += (long long)gridDim.x * blockDim.x) {
         const int kc = (int)(idx % kcs);
         const long long u = idx / kcs;
-        uint16_t h[3][8];
+        uint32_t h[3][8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int m = kc * 8 + e;
-            const float x = (u < U && m < M) ? a[u * M + m] : 0.f;
-            const uint16_t b0 = bf16_bits(x);
-            const float r1 = x - bf16_value(b0);
-            const uint16_t b1 = bf16_bits(r1);
-            h[0][e] = b0;
-            h[1][e] = b1;
-            h[2][e] = bf16_bits(r1 - bf16_value(b1));
+            bf16_split3((u < U && m < M) ? a[u * M + m] : 0.f, h[0][e], h[1][e], h[2][e]);
         }
         const long long t = u / kTile;
         const int r = (int)(u % kTile);
         const size_t off = (size_t)(r >> 3) * Mp * 8 + (size_t)kc * 64 + (size_t)(r & 7) * 8;  // elements
         for (int p = 0; p < planes; ++p) {
             uint4 v;
-            v.x = (uint32_t)h[p][0] | ((uint32_t)h[p][1] << 16);
-            v.y = (uint32_t)h[p][2] | ((uint32_t)h[p][3] << 16);
-            v.z = (uint32_t)h[p][4] | ((uint32_t)h[p][5] << 16);
-            v.w = (uint32_t)h[p][6] | ((uint32_t)h[p][7] << 16);
+            v.x = h[p][0] | (h[p][1] << 16);
+            v.y = h[p][2] | (h[p][3] << 16);
+            v.z = h[p][4] | (h[p][5] << 16);
+            v.w = h[p][6] | (h[p][7] << 16);
             *reinterpret_cast<uint4*>(out + ((size_t)t * planes + p) * kTile * Mp + off) = v;
         }
     }
@@ -217,18 +237,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_mma_kernel(const PhaseMma
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) {
-            // plane pairs in decreasing weight; plane 0 x plane 0 starts the accumulation
-            const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
-            const int npairs = planes == 3 ? 6 : 1;
-            uint32_t acc = 0;
-            for (int pp = 0; pp < npairs; ++pp)
-                for (int s = 0; s < Mp / 16; ++s) {
-                    // A: basis (pixel rows) plane pb, B: coefficients (unit rows) plane pa
-                    const uint64_t da = smem_desc(smem_addr(sP + pb[pp] * plane_bytes) + s * 256, 128, sbo);
-                    const uint64_t db = smem_desc(smem_addr(sU[buf] + pa[pp] * plane_bytes) + s * 256, 128, sbo);
-                    mma_bf16(tmem + (uint32_t)(buf * kTile), da, db, idesc, acc);
-                    acc = 1;
-                }
+            // A: basis (pixel rows), B: coefficients (unit rows); a fresh accumulator per tile
+            issue_mmas(tmem + (uint32_t)(buf * kTile), smem_desc(smem_addr(sP), 128, sbo),
+                       smem_desc(smem_addr(sU[buf]), 128, sbo), plane_bytes, plane_bytes, Mp / 16, planes, idesc,
+                       false);
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_addr(&mbar[buf]))
                          : "memory");
