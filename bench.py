@@ -283,8 +283,12 @@ def run_gpu(args, rank, local_rank, world):
     seed = SEED + rank
     plan = Plan(w["n_pix"], w["n_patches"], w["diams"], w["wavelengths"], w["n_frames"], w["n_modes"],
                 basis=w["basis"], gamma=gamma_of(w))
+    coeffs, spectra = make_gpu_inputs(plan, w, seed)  # the data always come from the FP32 forward model
+    if args.precision != "fp32" or args.projection != "tensor":
+        plan.close()
+        plan = Plan(w["n_pix"], w["n_patches"], w["diams"], w["wavelengths"], w["n_frames"], w["n_modes"],
+                    basis=w["basis"], gamma=gamma_of(w), precision=args.precision, projection=args.projection)
     info = plan.info()
-    coeffs, spectra = make_gpu_inputs(plan, w, seed)
     loss = torch.empty(w["n_patches"], dtype=torch.float64, device=plan.device)
     grad = torch.empty(plan.coeff_shape(), dtype=torch.float32, device=plan.device)
     stream = torch.cuda.current_stream()
@@ -410,7 +414,8 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w["workload"], "patch_px": w["n_pix"], "patches": w["n_patches"],
                    "objects": len(w["diams"]), "frames": w["n_frames"], "modes": w["n_modes"],
-                   "basis": w["basis"], "pupil_px": w["diams"], "precision": "fp32",
+                   "basis": w["basis"], "pupil_px": w["diams"], "precision": args.precision,
+                   "projection": args.projection,
                    "units_per_step": units_of(w),
                    "l2": "inputs larger than L2 (%.0f MB spectra)" % (units_of(w) * 64 * 33 * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -436,12 +441,20 @@ def main():
     ap.add_argument("--patches", type=int, default=0,
                     help="use only the first N patches of the field (smaller profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16_phase"],
+                    help="bf16_phase: the phase projection with BF16 operands on the tensor cores")
+    ap.add_argument("--projection", default="tensor", choices=["tensor", "simt"],
+                    help="FP32 phase projection on the tensor cores (three BF16 planes) or the SIMT kernel")
     ap.add_argument("--e2e-chunks", type=int, default=0,
                     help="patch chunks of the host-buffer call (copies overlap the kernels of other chunks)")
     args = ap.parse_args()
     if args.patches:
         WORKLOAD["n_patches"] = args.patches
         WORKLOAD["workload"] += "_first%d" % args.patches
+    if args.precision == "bf16_phase":
+        WORKLOAD["workload"] += "_bf16phase"
+    elif args.projection == "simt":
+        WORKLOAD["workload"] += "_simtphase"
     args.warmup = max(3, args.warmup)
     rank, local_rank, world = dist_env()
 
