@@ -40,6 +40,13 @@ WORKLOAD = dict(workload="fov1024_64px_961patches_2obj_12frames_44kl", fov=1024,
                 n_patches=961, diams=[36.0, 28.0], wavelengths=[6563.0, 8542.0], n_frames=12,
                 n_modes=44, basis="kl", d_over_r0=5.0, noise_sigma=1e-3)
 FP32_LANES_PER_SM = 128
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of each
+# kernel, from one ncu capture of the first 400 patches of this workload
+# (profiles/pass_kernels_fov1024_64px_400patches.md); a launch's traffic is
+# this times its units (the traffic is per unit: no cross-unit reuse)
+NCU_DRAM_BYTES_PER_UNIT = {"forward_passes": (72.987e6 + 503.382e6) / 9600,
+                           "adjoint_passes": (659.338e6 + 33.887e6) / 9600,
+                           "reduction": (324.479e6 + 120.270e6) / 9600}
 METRIC = "loss+grad evals/s (patch*obj*frame units at 64px)"
 UNIT = "units/s"
 
@@ -394,15 +401,18 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
         t = per_launch(kind)
         a = work / (t * 1e-3) / 1e12 if t > 0 else 0.0
         kernels[name] = {"bound": "alu", "ms": t, "achieved": a, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": a / alu_peak, "work_per_launch": work}
+                         "frac": a / alu_peak, "work_per_launch": work,
+                         "traffic": NCU_DRAM_BYTES_PER_UNIT[name] * units_of(w)}
     t = per_launch("reduction")
     a = red_bytes / (t * 1e-3) / 1e9 if t > 0 else 0.0
     kernels["reduction"] = {"bound": "hbm", "ms": t, "achieved": a, "peak": hbm_peak, "unit": "GB/s",
-                            "frac": a / hbm_peak, "work_per_launch": red_bytes}
+                            "frac": a / hbm_peak, "work_per_launch": red_bytes,
+                            "traffic": NCU_DRAM_BYTES_PER_UNIT["reduction"] * units_of(w)}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     dk = kernels[dom]
     roofline = {"bound": dk["bound"], "kernel": dom, "achieved": dk["achieved"], "peak": dk["peak"],
-                "unit": dk["unit"], "frac": dk["frac"], "traffic": None,
+                "unit": dk["unit"], "frac": dk["frac"], "traffic": dk["traffic"],
+                "traffic_basis": "ncu DRAM bytes per unit (400-patch capture) x units per launch",
                 "peak_basis": ("FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock)"
                                % (n_sm, FP32_LANES_PER_SM, sm_max)) if dk["bound"] == "alu"
                 else "HBM copy bandwidth of MEASURED_PEAKS.json",
