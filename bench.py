@@ -41,9 +41,9 @@ WORKLOAD = dict(workload="fov1024_64px_961patches_2obj_12frames_44kl", fov=1024,
                 n_modes=44, basis="kl", d_over_r0=5.0, noise_sigma=1e-3)
 FP32_LANES_PER_SM = 128
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of each
-# kernel, from one ncu capture of the first 400 patches of this workload
-# (profiles/pass_kernels_fov1024_64px_400patches.md); a launch's traffic is
-# this times its units (the traffic is per unit: no cross-unit reuse)
+# kernel, from one ncu capture (--set full) of the first 400 patches of this
+# workload; a launch's traffic is this times its units (the traffic is per
+# unit: no cross-unit reuse)
 NCU_DRAM_BYTES_PER_UNIT = {"forward_passes": (72.987e6 + 503.382e6) / 9600,
                            "adjoint_passes": (659.338e6 + 33.887e6) / 9600,
                            "reduction": (324.479e6 + 120.270e6) / 9600}
