@@ -79,48 +79,90 @@ __global__ void __launch_bounds__(256, 2) phase_gemm_kernel(const float* __restr
     }
 }
 
-// part[z][u][m] = sum_{i in chunk z} gphi[u][i] basis[m][i]: 64 x 48 output
-// tile per CTA of 64 threads, 8 x 6 per thread, pixels in chunks of 32
-// staged in shared memory; the pixel range is split over blockIdx.z.
-constexpr int kGU = 64, kGM = 48, kGK = 32;
+// part[z][u][m] = sum_{i in chunk z} gphi[u][i] basis[m][i]: 128 x 48 output
+// tile per CTA of 128 threads, 8 x 6 per thread, pixels in steps of 32 staged
+// in shared memory (two buffers; the next step's operands are loaded into
+// registers while the current one is computed). A thread loads row u = t of
+// the dL/dphi step and stores it transposed, As[i][u]: the 32 lanes of a warp
+// write 32 consecutive u of one i (no bank conflicts). Every object's pixel
+// range is split into chunks; blockIdx.z runs over all (object, chunk).
+constexpr int kGU = 128, kGM = 48, kGK = 32, kGT = 128;
 
-__global__ void __launch_bounds__(64) grad_gemm_kernel(const float* __restrict__ gphi, int U, int npix,
-                                                       const float* __restrict__ basis, int M, int chunk,
-                                                       float* __restrict__ part) {
-    __shared__ __align__(16) float As[kGK][kGU + 4];  // [i][u]
-    __shared__ __align__(16) float Bs[kGK][kGM + 4];  // [i][m]
-    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+__global__ void __launch_bounds__(kGT, 3) grad_gemm_kernel(const GradJob job, int U, int M) {
+    __shared__ __align__(16) float As[2][kGK][kGU + 4];  // [i][u]
+    __shared__ __align__(16) float Bs[2][kGK][kGM + 4];  // [i][m]
+    int k = 0;
+    while (k + 1 < job.K && (int)blockIdx.z >= job.split0[k + 1]) ++k;
+    const float* __restrict__ gphi = job.gphi[k];
+    const float* __restrict__ basis = job.basis[k];
+    const int npix = job.npix[k], chunk = job.chunk[k], vec = job.vec[k];
+    const int z = (int)blockIdx.z - job.split0[k];
+    float* __restrict__ part = job.part[k];
+    const int t = threadIdx.x;
+    const int tx = t & 7, ty = t >> 3;  // 8 x 6 outputs: u = ty * 8 .., m = tx * 6 ..
     const int u0 = blockIdx.y * kGU, m0 = blockIdx.x * kGM;
-    const int ib = blockIdx.z * chunk;
+    const int ib = z * chunk;
     const int ie = ib + chunk < npix ? ib + chunk : npix;
+    float ra[kGK];      // row u0 + t of the next step
+    float rb[3][4];     // (m, 4 pixels) groups of the next step's basis
+    auto load = [&](int i0) {
+        const int u = u0 + t;
+        const float* g = gphi + (size_t)u * npix + i0;
+        if (vec && u < U && i0 + kGK <= ie) {
+#pragma unroll
+            for (int q = 0; q < kGK / 4; ++q) {
+                const float4 v = *reinterpret_cast<const float4*>(g + 4 * q);
+                ra[4 * q] = v.x;
+                ra[4 * q + 1] = v.y;
+                ra[4 * q + 2] = v.z;
+                ra[4 * q + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kGK; ++i) ra[i] = (u < U && i0 + i < ie) ? g[i] : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int idx = t + kGT * r;  // < 384 = 48 modes x 8 groups of 4 pixels
+            const int mm = idx % kGM, q = idx / kGM;
+            const int m = m0 + mm, i = i0 + 4 * q;
+            const float* bsrc = basis + (size_t)m * npix + i;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) rb[r][e] = (m < M && i + e < ie) ? bsrc[e] : 0.f;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int i = 0; i < kGK; ++i) As[buf][i][t] = ra[i];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int idx = t + kGT * r;
+            const int mm = idx % kGM, q = idx / kGM;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) Bs[buf][4 * q + e][mm] = rb[r][e];
+        }
+    };
     float acc[8][6];
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
         for (int c = 0; c < 6; ++c) acc[r][c] = 0.f;
+    if (ib < ie) {
+        load(ib);
+        store(0);
+    }
+    __syncthreads();
+    int buf = 0;
     for (int i0 = ib; i0 < ie; i0 += kGK) {
-#pragma unroll 8
-        for (int t = 0; t < kGK * kGU / 64; ++t) {  // 32 consecutive pixels of one row per 32 threads
-            const int idx = threadIdx.x + 64 * t;
-            const int ii = idx & (kGK - 1), rr = idx >> 5;
-            const int u = u0 + rr, i = i0 + ii;
-            As[ii][rr] = (u < U && i < ie) ? gphi[(size_t)u * npix + i] : 0.f;
-        }
-#pragma unroll 8
-        for (int t = 0; t < kGK * kGM / 64; ++t) {
-            const int idx = threadIdx.x + 64 * t;
-            const int ii = idx & (kGK - 1), rr = idx >> 5;
-            const int m = m0 + rr, i = i0 + ii;
-            Bs[ii][rr] = (m < M && i < ie) ? basis[(size_t)m * npix + i] : 0.f;
-        }
-        __syncthreads();
+        const bool more = i0 + kGK < ie;
+        if (more) load(i0 + kGK);  // in flight during this step's FMAs
 #pragma unroll 8
         for (int k = 0; k < kGK; ++k) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&As[k][ty * 8]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&As[k][ty * 8 + 4]);
-            const float2 b0 = *reinterpret_cast<const float2*>(&Bs[k][tx * 6]);
-            const float2 b1 = *reinterpret_cast<const float2*>(&Bs[k][tx * 6 + 2]);
-            const float2 b2 = *reinterpret_cast<const float2*>(&Bs[k][tx * 6 + 4]);
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 8 + 4]);
+            const float2 b0 = *reinterpret_cast<const float2*>(&Bs[buf][k][tx * 6]);
+            const float2 b1 = *reinterpret_cast<const float2*>(&Bs[buf][k][tx * 6 + 2]);
+            const float2 b2 = *reinterpret_cast<const float2*>(&Bs[buf][k][tx * 6 + 4]);
             const float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float br[6] = {b0.x, b0.y, b1.x, b1.y, b2.x, b2.y};
 #pragma unroll
@@ -128,7 +170,9 @@ __global__ void __launch_bounds__(64) grad_gemm_kernel(const float* __restrict__
 #pragma unroll
                 for (int c = 0; c < 6; ++c) acc[r][c] = fmaf(ar[r], br[c], acc[r][c]);
         }
+        if (more) store(buf ^ 1);  // the other buffer was last read before the previous barrier
         __syncthreads();
+        buf ^= 1;
     }
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -137,7 +181,7 @@ __global__ void __launch_bounds__(64) grad_gemm_kernel(const float* __restrict__
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const int m = m0 + tx * 6 + c;
-            if (m < M) part[((size_t)blockIdx.z * U + u) * M + m] = acc[r][c];
+            if (m < M) part[((size_t)z * U + u) * M + m] = acc[r][c];
         }
     }
 }
@@ -157,14 +201,23 @@ __global__ void __launch_bounds__(256) grad_combine_kernel(const GradParts gp, s
 
 }  // namespace
 
-int grad_splits(int npix, int* chunk) {
-    // pixel chunks of about 160 (a multiple of the 32-pixel staging step)
-    int splits = (npix + 80) / 160;
-    if (splits < 1) splits = 1;
-    int c = (npix + splits - 1) / splits;
-    c = (c + kGK - 1) / kGK * kGK;
-    *chunk = c;
-    return (npix + c - 1) / c;
+void grad_layout(int K, const int* npix, int U, int sms, int* chunk, int* splits) {
+    // about one wave of CTAs (3 per SM) over all objects, the chunks of every
+    // object about equally long (a multiple of the 32-pixel step)
+    const int n_ut = (U + kGU - 1) / kGU > 0 ? (U + kGU - 1) / kGU : 1;
+    long long total = 0;
+    for (int k = 0; k < K; ++k) total += npix[k];
+    long long want = 3LL * sms / n_ut;
+    if (want < K) want = K;
+    for (int k = 0; k < K; ++k) {
+        long long sk = total > 0 ? (npix[k] * want + total / 2) / total : 1;
+        if (sk < 1) sk = 1;
+        long long c = (npix[k] + sk - 1) / sk;
+        c = (c + kGK - 1) / kGK * kGK;
+        if (c < kGK) c = kGK;
+        chunk[k] = (int)c;
+        splits[k] = npix[k] > 0 ? (int)((npix[k] + c - 1) / c) : 1;
+    }
 }
 
 cudaError_t launch_phase_gemm(const float* a, int U, int M, const float* basis, int npix, float scale,
@@ -176,13 +229,16 @@ cudaError_t launch_phase_gemm(const float* a, int U, int M, const float* basis, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_grad_gemm(const float* gphi, int U, int npix, const float* basis, int M, float* part,
-                             cudaStream_t s) {
+cudaError_t launch_grad_gemm(GradJob job, int U, int M, cudaStream_t s) {
     if (U == 0) return cudaSuccess;
-    int chunk = 0;
-    const int splits = grad_splits(npix, &chunk);
-    dim3 grid((M + kGM - 1) / kGM, (U + kGU - 1) / kGU, splits);
-    grad_gemm_kernel<<<grid, 64, 0, s>>>(gphi, U, npix, basis, M, chunk, part);
+    job.split0[0] = 0;
+    for (int k = 0; k < job.K; ++k) {
+        job.split0[k + 1] = job.split0[k] + job.splits[k];
+        // whole float4 steps need 16-byte aligned rows
+        job.vec[k] = (job.npix[k] % 4 == 0) && (reinterpret_cast<uintptr_t>(job.gphi[k]) % 16 == 0);
+    }
+    dim3 grid((M + kGM - 1) / kGM, (U + kGU - 1) / kGU, job.split0[job.K]);
+    grad_gemm_kernel<<<grid, kGT, 0, s>>>(job, U, M);
     return cudaGetLastError();
 }
 

@@ -37,6 +37,7 @@ struct ObjectData {
     float scale = 1.f, inv_z = 0.f;
     long long phi_off = 0;
     long long part_off = 0;     // offset of this object's modal-adjoint partial sums
+    int g_chunk = 0, g_splits = 0;  // modal-adjoint pixel chunks for all P*J units (sizes part buffer)
     float* d_basis = nullptr;   // [M][W*W]
     uint64_t* d_mask = nullptr; // [W] box rows, then [N] box columns
     uint64_t* d_supp = nullptr; // [N] rows, then [N] columns of the OTF support
@@ -313,19 +314,34 @@ int run_phase(mfbd_plan_t p, const float* coeffs, cudaStream_t s, int p0, int np
 // dL/da of patches [p0, p0 + np); grad points at patch p0.
 int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s, int p0, int np) {
     const int U = np * p->J;
+    GradJob job{};
+    job.K = p->K;
+    int npix[kMaxObjects], chunk[kMaxObjects], splits[kMaxObjects];
+    for (int k = 0; k < p->K; ++k) npix[k] = p->obj[k].W * p->obj[k].W;
+    // chunks for this call's units, if the plan's partial-sum buffers hold them
+    grad_layout(p->K, npix, U, p->sms, chunk, splits);
+    for (int k = 0; k < p->K; ++k)
+        if ((long long)splits[k] * U > (long long)p->obj[k].g_splits * p->P * p->J)
+            for (int q = 0; q < p->K; ++q) {
+                chunk[q] = p->obj[q].g_chunk;
+                splits[q] = p->obj[q].g_splits;
+            }
     GradParts gp{};
     gp.K = p->K;
-    const int pi = prof_begin(p, 4, s);
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < p->K && e == cudaSuccess; ++k) {
+    for (int k = 0; k < p->K; ++k) {
         const ObjectData& o = p->obj[k];
-        int chunk = 0;
-        gp.splits[k] = grad_splits(o.W * o.W, &chunk);
+        job.gphi[k] = p->d_gphi + o.phi_off + (size_t)p0 * p->J * o.W * o.W;
+        job.basis[k] = o.d_basis;
+        job.npix[k] = npix[k];
+        job.chunk[k] = chunk[k];
+        job.splits[k] = splits[k];
+        job.part[k] = p->d_gpart + o.part_off;
+        gp.splits[k] = splits[k];
         gp.scale[k] = o.scale;
-        gp.part[k] = p->d_gpart + o.part_off;
-        e = launch_grad_gemm(p->d_gphi + o.phi_off + (size_t)p0 * p->J * o.W * o.W, U, o.W * o.W, o.d_basis, p->M,
-                             p->d_gpart + o.part_off, s);
+        gp.part[k] = job.part[k];
     }
+    const int pi = prof_begin(p, 4, s);
+    cudaError_t e = launch_grad_gemm(job, U, p->M, s);
     if (e == cudaSuccess) e = launch_grad_combine(gp, U, p->M, grad, s);
     prof_end(p, pi, s);
     if (e != cudaSuccess) {
@@ -592,10 +608,16 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
             (st = dev_alloc(p, &p->d_acoef, split_coeffs_elems(p->P * p->J, p->M, p->obj[0].tc_planes))))
             throw st;
         long long part_floats = 0;
-        for (int k = 0; k < p->K; ++k) {
-            int chunk = 0;
-            p->obj[k].part_off = part_floats;
-            part_floats += (long long)grad_splits(p->obj[k].W * p->obj[k].W, &chunk) * p->P * p->J * p->M;
+        {
+            int npix[kMaxObjects], chunk[kMaxObjects], splits[kMaxObjects];
+            for (int k = 0; k < p->K; ++k) npix[k] = p->obj[k].W * p->obj[k].W;
+            grad_layout(p->K, npix, p->P * p->J, prop.multiProcessorCount, chunk, splits);
+            for (int k = 0; k < p->K; ++k) {
+                p->obj[k].g_chunk = chunk[k];
+                p->obj[k].g_splits = splits[k];
+                p->obj[k].part_off = part_floats;
+                part_floats += (long long)splits[k] * p->P * p->J * p->M;
+            }
         }
         if ((st = dev_alloc(p, &p->d_gpart, (size_t)part_floats))) throw st;
         if ((st = dev_alloc(p, &p->d_phi, (size_t)phi_floats))) throw st;

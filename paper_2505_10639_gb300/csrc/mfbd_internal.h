@@ -79,12 +79,23 @@ cudaError_t launch_split_coeffs(const float* a, int U, int M, int planes, uint16
 cudaError_t launch_phase_mma(const uint16_t* at, int U, int M, const uint16_t* bt, int npix, int planes,
                              float scale, float* phase, int* err, int sms, cudaStream_t s);
 
-// Modal adjoint, split over pixels: part[z][u][m] = sum over chunk z of
-// gphi[u][i] basis[m][i]; grad_splits gives the number of chunks (and the
-// chunk length) for npix pixels.
-int grad_splits(int npix, int* chunk);
-cudaError_t launch_grad_gemm(const float* gphi, int U, int npix, const float* basis, int M, float* part,
-                             cudaStream_t s);
+// Modal adjoint, one launch for all objects: part_k[z][u][m] = sum over
+// pixel chunk z of object k of gphi_k[u][i] basis_k[m][i]. grad_layout picks
+// the chunk length and the number of chunks of every object for U units on
+// `sms` SMs (the partial-sum buffers hold splits[k] x U x M floats).
+struct GradJob {
+    int K;
+    const float* gphi[kMaxObjects];
+    const float* basis[kMaxObjects];
+    int npix[kMaxObjects];
+    int chunk[kMaxObjects];
+    int splits[kMaxObjects];
+    float* part[kMaxObjects];
+    int split0[kMaxObjects + 1];  // filled by launch_grad_gemm
+    int vec[kMaxObjects];         // filled by launch_grad_gemm
+};
+void grad_layout(int K, const int* npix, int U, int sms, int* chunk, int* splits);
+cudaError_t launch_grad_gemm(GradJob job, int U, int M, cudaStream_t s);
 
 // grad[u][m] = sum_k scale_k sum_z part_k[z][u][m] (fixed summation order)
 struct GradParts {
