@@ -110,6 +110,43 @@ __device__ __forceinline__ int pass_rounds(int pass, int W) {
 
 __device__ __forceinline__ bool bit(uint64_t w, int b) { return (w >> b) & 1ull; }
 
+// ----------------------------------------------- quarter-line transforms
+
+// Boxes 33..40 px wide leave 1..8 columns after the first round of 32. Those
+// are transformed by 4 lanes each instead of one lane per column (in the
+// PUPIL pass): lane
+// l = lane & 3 holds a[n] = x[4 n + l] (n < 16), transforms it with a 16-point
+// FFT, multiplies A_l[k] by exp(-2 pi i l k / 64), and the 4-point DFT over
+// the lanes (two xor-shuffle stages) leaves X[k + 16 q] in lane l, with
+// q = ((l & 1) << 1) | (l >> 1). Forward transform.
+constexpr int kSplitMaxW = 40;
+
+__device__ __forceinline__ int split_q(int l) { return ((l & 1) << 1) | (l >> 1); }
+
+__device__ __forceinline__ void fft64_quarters(float2 (&a)[kN / 4], int l) {
+    fftreg::fft4<kN / 4, -1>(a);
+    fftreg::static_for<1, kN / 4>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        constexpr fftreg::SinCos w1 = fftreg::sincos_2pi(-k, kN), w2 = fftreg::sincos_2pi(-2 * k, kN),
+                                 w3 = fftreg::sincos_2pi(-3 * k, kN);
+        const float c = l == 0 ? 1.f : l == 1 ? (float)w1.c : l == 2 ? (float)w2.c : (float)w3.c;
+        const float sn = l == 0 ? 0.f : l == 1 ? (float)w1.s : l == 2 ? (float)w2.s : (float)w3.s;
+        a[k] = make_float2(a[k].x * c - a[k].y * sn, a[k].x * sn + a[k].y * c);
+    });
+    const float s2 = (l & 2) ? -1.f : 1.f, s1 = (l & 1) ? -1.f : 1.f;
+    const bool rot = l == 3;
+#pragma unroll
+    for (int k = 0; k < kN / 4; ++k) {
+        // lanes l and l ^ 2: l < 2 keeps the sum, l >= 2 the difference (times -i for l = 3)
+        const float ox = __shfl_xor_sync(0xffffffffu, a[k].x, 2), oy = __shfl_xor_sync(0xffffffffu, a[k].y, 2);
+        const float tx = fmaf(s2, a[k].x, ox), ty = fmaf(s2, a[k].y, oy);
+        const float ux = rot ? ty : tx, uy = rot ? -tx : ty;
+        // lanes l and l ^ 1: even l the sum, odd l the difference
+        const float px = __shfl_xor_sync(0xffffffffu, ux, 1), py = __shfl_xor_sync(0xffffffffu, uy, 1);
+        a[k] = make_float2(fmaf(s1, ux, px), fmaf(s1, uy, py));
+    }
+}
+
 // ------------------------------------------------------------ load stages
 
 // Pupil column c of the box: P = exp(i phi) where the column mask `cm` has
@@ -135,6 +172,36 @@ __device__ __forceinline__ void load_pupil(const volatile Unit* su, uint64_t cm,
     }
 }
 
+// Second PUPIL round of a box 33..40 px wide: columns 32..W-1, four lanes
+// per column (lane >> 2 picks the column). (The ADJ pass keeps the generic
+// second round: the quarter transform there pushes the adjoint kernel past
+// its register budget.)
+template <int ES>
+__device__ __forceinline__ void quarter_round_pupil(const volatile Unit* su, float2* __restrict__ E,
+                                                    const uint64_t* __restrict__ cmask, int W, int lane) {
+    const int l = lane & 3, q = split_q(l), c = 32 + (lane >> 2);
+    const bool active = c < W;
+    const int ld = su->ld;
+    const float* ph = (const float*)su->phi + c;
+    float2* pp = (float2*)su->pp;
+    const uint64_t cm = active ? cmask[c] : 0ull;
+    float2 a[kN / 4];
+    float phv[kN / 4];  // exp(i phi) on rows 4 n + l of column c
+#pragma unroll
+    for (int n = 0; n < kN / 4; ++n) phv[n] = (active && 4 * n + l < W) ? ph[(4 * n + l) * ld] : 0.f;
+#pragma unroll
+    for (int n = 0; n < kN / 4; ++n) {
+        const int y = 4 * n + l;
+        a[n] = bit(cm, y) ? expi(phv[n]) : make_float2(0.f, 0.f);
+        if (pp != nullptr && active && y < W) pp[y * W + c] = a[n];
+    }
+    fft64_quarters(a, l);
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < kN / 4; ++k) E[(k + 16 * q) * ES + c] = a[k];
+    }
+}
+
 // ----------------------------------------------------------- the machine
 
 // Runs passes [FIRST, LAST) of one unit on the calling warp.
@@ -153,6 +220,12 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
         }
 #pragma unroll 1
         for (int r = 0; r < nr; ++r) {
+            if constexpr (FIRST <= P_PUPIL && P_PUPIL < LAST) {
+                if (pass == P_PUPIL && r == 1 && W <= kSplitMaxW) {
+                    quarter_round_pupil<ES>(su, E, cmask, W, lane);
+                    continue;
+                }
+            }
             float2 v[kN];
             // ------------------------------------------------------ load
             if constexpr (FIRST <= P_PUPIL && P_PUPIL < LAST) {
