@@ -13,7 +13,7 @@
 extern "C" {
 #endif
 
-/* kind selects the transform, all of length 64, unnormalised:
+/* kind selects the transform (length 64 unless stated), unnormalised:
  *   0  complex forward  in: 64 complex (128 floats)  out: 64 complex
  *   1  complex adjoint  in: 64 complex               out: 64 complex
  *   2  real-to-complex  in: 64 floats                out: 33 complex (66 floats)
@@ -21,6 +21,8 @@ extern "C" {
  *   4  complex forward, length 32
  *   5  complex forward, length 64, radix-4 network
  *   6  complex adjoint, length 64, radix-4 network
+ *   7  complex forward, length 48 (three 16-point FFTs and a radix-3 stage)
+ *   8  complex adjoint, length 48
  * Forward: X[k] = sum x[n] exp(-2 pi i n k / N); adjoint uses exp(+...).
  * Returns 0 (MFBD_OK) or 1 (MFBD_ERR_INVALID_ARG) for an unknown kind or
  * NULL pointers. */

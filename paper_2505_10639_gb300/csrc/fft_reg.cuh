@@ -191,6 +191,42 @@ MFBD_HD void fft4(float2 (&a)[N]) {
     static_for<0, N>([&](auto i) { a[decltype(i)::value] = b[decltype(i)::value]; });
 }
 
+// In-place 48-point FFT (natural order in and out): three 16-point FFTs of
+// x[3n + r], each output twiddled by exp(DIR 2 pi i r k / 48), then a 3-point
+// DFT over r: X[k + 16 q] = sum_r W3^(r q) (W48^(r k) A_r[k]).
+template <int DIR>
+MFBD_HD void fft48(float2 (&a)[48]) {
+    float2 b[3][16];
+    static_for<0, 48>([&](auto i) {
+        constexpr int I = decltype(i)::value;
+        b[I % 3][I / 3] = a[I];
+    });
+    fft4<16, DIR>(b[0]);
+    fft4<16, DIR>(b[1]);
+    fft4<16, DIR>(b[2]);
+    constexpr float c3 = -0.5f;
+    constexpr float s3 = (float)(DIR * 0.86602540378443864676);  // DIR sin(2 pi / 3)
+    static_for<0, 16>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        const float2 x0 = b[0][k];
+        const float2 x1 = twmul<48, k, DIR>(b[1][k]);
+        const float2 x2 = twmul<48, 2 * k, DIR>(b[2][k]);
+        const float2 sum = cadd(x1, x2), dif = csub(x1, x2);
+        a[k] = cadd(x0, sum);
+        const float2 m = make_float2(x0.x + c3 * sum.x, x0.y + c3 * sum.y);
+        const float2 r = make_float2(-s3 * dif.y, s3 * dif.x);  // i s3 (x1 - x2)
+        a[k + 16] = cadd(m, r);
+        a[k + 32] = csub(m, r);
+    });
+}
+
+// Length-L line FFT for the line lengths used (48, 64).
+template <int L, int DIR>
+MFBD_HD void fft_line(float2 (&a)[L]) {
+    if constexpr (L == 48) fft48<DIR>(a);
+    else fft4<L, DIR>(a);
+}
+
 // Real-to-complex forward FFT of N real samples -> X[0..N/2] (X[0], X[N/2]
 // real), by one N/2-point complex FFT of z[n] = r[2n] + i r[2n+1]:
 //   E[k] = (Z[k] + conj Z[H-k]) / 2,  O[k] = (Z[k] - conj Z[H-k]) / (2i),

@@ -46,6 +46,15 @@ extern "C" int mfbd_test_fft_host(int kind, const float* in, float* out) {
             for (int i = 0; i < 64; ++i) { out[2 * i] = a[i].x; out[2 * i + 1] = a[i].y; }
             return 0;
         }
+        case 7:
+        case 8: {
+            float2 a[48];
+            for (int i = 0; i < 48; ++i) a[i] = make_float2(in[2 * i], in[2 * i + 1]);
+            if (kind == 7) fftreg::fft48<-1>(a);
+            else fftreg::fft48<+1>(a);
+            for (int i = 0; i < 48; ++i) { out[2 * i] = a[i].x; out[2 * i + 1] = a[i].y; }
+            return 0;
+        }
         default:
             return 1;
     }

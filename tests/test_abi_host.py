@@ -147,6 +147,10 @@ def test_register_ffts_match_oracle(lib, seed):
         ref = dft.fft_radix2(z.astype(np.complex128), sign=sign)
         got = o[0::2] + 1j * o[1::2]
         assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
+    for kind, sign in ((7, -1), (8, +1)):  # 48 points: radix-3 stage over radix-4 16-point FFTs
+        o = _host_fft(lib, kind, zin[:96], 96)
+        ref = dft.dft_naive(z[:48].astype(np.complex128), sign=sign)
+        assert np.abs(o[0::2] + 1j * o[1::2] - ref).max() <= 2e-6 * np.abs(ref).max()
     o = _host_fft(lib, 4, zin[:64], 64)
     ref = dft.fft_radix2(z[:32].astype(np.complex128))
     assert np.abs(o[0::2] + 1j * o[1::2] - ref).max() <= 2e-6 * np.abs(ref).max()
