@@ -27,7 +27,7 @@
  *   failed: later compute calls on it return MFBD_ERR_STATE.
  * - There is no CPU fallback: without a usable CUDA device the compute calls
  *   return MFBD_ERR_UNSUPPORTED (or MFBD_ERR_CUDA) and compute nothing.
- * - Grids: the patch size N (n_pix) is 64 in this version. Images are
+ * - Grids: the patch size N (n_pix) is 48, 64, 96 or 128. Images are
  *   [row y][column x], row-major. Spectra are unnormalised forward DFTs
  *   X[ky][kx] = sum_{y,x} x[y][x] exp(-2 pi i (ky y + kx x) / N), stored as
  *   interleaved complex64 (float re, float im). A "half spectrum" is the
@@ -78,9 +78,17 @@ typedef enum {
 #define MFBD_FLAG_SIMT_PROJECTION 0x2u /* FP32 phase projection on the SIMT kernel instead
                                         * of the tensor cores (comparison runs; not with
                                         * MFBD_PREC_BF16_PHASE) */
+#define MFBD_FLAG_RECOMPUTE_BACKWARD 0x4u /* the adjoint recomputes the field F P and the
+                                           * pupil phasors instead of keeping them from
+                                           * the forward pass: 8 N^2 + 8 W^2 fewer bytes of
+                                           * device memory per (patch, object, frame), about
+                                           * 40 % more adjoint work */
+#define MFBD_FLAG_GENERIC_KERNELS 0x8u /* run N = 64 on the kernels of the other patch
+                                        * sizes (one CTA per unit) instead of the 64-pixel
+                                        * pass machine (comparison runs) */
 
 typedef struct {
-    int n_pix;      /* N, patch size in pixels (64) */
+    int n_pix;      /* N, patch size in pixels: 48, 64, 96 or 128 */
     int n_patches;  /* P >= 0 (0: every compute call is a no-op) */
     int n_objects;  /* K, 1..8 */
     int n_frames;   /* J, 1..1024 (frames x diversity channels) */
@@ -203,7 +211,7 @@ int mfbd_plan_read_profile(mfbd_plan_t plan, double* ms, long long* launches, in
  * the inputs and outputs, and the kernel's working memory is one 16 MiB
  * array compiled into the library, held by every GPU that loads it until
  * the process exits.
- *   desc        host: n_pix (64), n_patches, n_objects, n_frames, pupil
+ *   desc        host: n_pix (64 only), n_patches, n_objects, n_frames, pupil
  *               diameters, obscuration, gamma, frame weights and flags are
  *               used; n_modes, basis, user_basis, wavelength and precision
  *               are ignored (the wavefront is given as a phase).

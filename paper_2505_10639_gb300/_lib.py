@@ -22,6 +22,8 @@ MFBD_PREC_FP32 = 0
 MFBD_PREC_BF16_PHASE = 1
 MFBD_FLAG_FULL_SPECTRUM = 0x1
 MFBD_FLAG_SIMT_PROJECTION = 0x2
+MFBD_FLAG_RECOMPUTE_BACKWARD = 0x4
+MFBD_FLAG_GENERIC_KERNELS = 0x8
 
 
 class PlanDesc(ctypes.Structure):

@@ -40,6 +40,9 @@ struct ObjectData {
     int g_chunk = 0, g_splits = 0;  // modal-adjoint pixel chunks for all P*J units (sizes part buffer)
     float* d_basis = nullptr;   // [M][W*W]
     uint64_t* d_mask = nullptr; // [W] box rows, then [N] box columns
+    uint32_t* d_gmask = nullptr;  // general sizes: [W][mw] box mask rows
+    uint32_t* d_gsupp = nullptr;  // general sizes: [N][sw] OTF-support rows
+    int mw = 0;
     uint64_t* d_supp = nullptr; // [N] rows, then [N] columns of the OTF support
     // tensor-core phase projection: the box basis as BF16 planes in the MMA
     // tile layout, [n_tiles][planes][Nt * Mp]; planes == 0: SIMT kernel
@@ -53,6 +56,8 @@ struct mfbd_plan {
     int N = 0, P = 0, K = 0, J = 0, M = 0;
     unsigned flags = 0;
     int precision = MFBD_PREC_FP32;
+    bool generic = false;       // CTA-per-unit kernels (N != 64, recompute, or on request)
+    int es = 0, es2 = 0, sw = 0;  // their exchange-buffer strides and support-row words
     double gamma = 0;
     int* d_err = nullptr;       // set by a tensor-core kernel whose MMA wait gave up
     uint16_t* d_acoef = nullptr;  // coefficients as BF16 planes in the MMA tile layout
@@ -127,9 +132,11 @@ int validate(const mfbd_plan_desc* d) {
                 return fail(MFBD_ERR_INVALID_ARG, "frame weights must be finite and >= 0");
     if (d->precision != MFBD_PREC_FP32 && d->precision != MFBD_PREC_BF16_PHASE)
         return fail(MFBD_ERR_INVALID_ARG, "unknown precision");
-    if (d->flags & ~(MFBD_FLAG_FULL_SPECTRUM | MFBD_FLAG_SIMT_PROJECTION))
+    if (d->flags & ~(MFBD_FLAG_FULL_SPECTRUM | MFBD_FLAG_SIMT_PROJECTION | MFBD_FLAG_RECOMPUTE_BACKWARD |
+                     MFBD_FLAG_GENERIC_KERNELS))
         return fail(MFBD_ERR_INVALID_ARG, "unknown flags");
-    if (d->n_pix != kN) return fail(MFBD_ERR_UNSUPPORTED, "this build supports n_pix == 64");
+    if (d->n_pix != 48 && d->n_pix != 64 && d->n_pix != 96 && d->n_pix != 128)
+        return fail(MFBD_ERR_UNSUPPORTED, "n_pix must be 48, 64, 96 or 128");
     if (d->precision == MFBD_PREC_BF16_PHASE && (d->flags & MFBD_FLAG_SIMT_PROJECTION))
         return fail(MFBD_ERR_INVALID_ARG, "the BF16 phase projection runs on the tensor cores only");
     return MFBD_OK;
@@ -356,9 +363,66 @@ int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s, int p0, int np) {
 // nothing for the adjoint.
 enum Stage : int { ST_FWD = 1, ST_RED = 2, ST_ADJ = 4, ST_OTF_ONLY = 8 };
 
+// General patch sizes: the same stages on the CTA-per-unit kernels.
+int run_generic(mfbd_plan_t p, int stages, const void* spectra, double* loss, void* object, float2* gscr,
+                cudaStream_t s, int p0, int np) {
+    GenericParams g{};
+    g.P = np;
+    g.K = p->K;
+    g.J = p->J;
+    g.N = p->N;
+    g.sw = p->sw;
+    g.gamma = p->gamma;
+    g.weights = p->d_weights;
+    g.phi = p->d_phi;
+    g.gphi = p->d_gphi;
+    const bool otf_only = (stages & ST_OTF_ONLY) != 0;
+    g.gscr = otf_only ? gscr : p->d_gscr;
+    g.pscr = otf_only ? nullptr : p->d_pscr;
+    g.uscr = otf_only ? nullptr : p->d_uscr;
+    g.ustride = p->ustride;
+    g.spectra = static_cast<const float2*>(spectra);
+    g.spec_ld = (p->flags & MFBD_FLAG_FULL_SPECTRUM) ? p->N : p->N / 2 + 1;
+    g.loss = loss;
+    g.object = static_cast<float2*>(object);
+    g.es = p->es;
+    g.es2 = p->es2;
+    for (int k = 0; k < p->K; ++k) {
+        const ObjectData& o = p->obj[k];
+        g.obj[k].W = o.W;
+        g.obj[k].phi_off = o.phi_off + (long long)p0 * p->J * o.W * o.W;
+        g.obj[k].inv_z = o.inv_z;
+        g.obj[k].mask = o.d_gmask;
+        g.obj[k].mw = o.mw;
+        g.obj[k].supp = o.d_gsupp;
+    }
+    cudaError_t e = cudaSuccess;
+    if (stages & ST_FWD) {
+        const int pi = prof_begin(p, 1, s);
+        e = launch_generic_forward(g, p->sms, s);
+        prof_end(p, pi, s);
+    }
+    if (e == cudaSuccess && (stages & ST_RED)) {
+        const int pr = prof_begin(p, 2, s);
+        e = launch_generic_reduction(g, p->sms, s);
+        prof_end(p, pr, s);
+    }
+    if (e == cudaSuccess && (stages & ST_ADJ)) {
+        const int pb = prof_begin(p, 3, s);
+        e = launch_generic_adjoint(g, p->sms, s);
+        prof_end(p, pb, s);
+    }
+    if (e != cudaSuccess) {
+        p->failed = true;
+        return cuda_fail(e, "pass or reduction kernel");
+    }
+    return MFBD_OK;
+}
+
 // Pass and reduction kernels of `stages` for patches [p0, p0 + np).
 int run_fused(mfbd_plan_t p, int stages, const void* spectra, double* loss, void* object, float2* gscr,
               cudaStream_t s, int p0, int np) {
+    if (p->generic) return run_generic(p, stages, spectra, loss, object, gscr, s, p0, np);
     FusedParams f = (stages & ST_OTF_ONLY)
                         ? fused_params(p, p0, np, spectra, loss, object, gscr, nullptr, nullptr)
                         : fused_params(p, p0, np, spectra, loss, object, p->d_gscr, p->d_pscr, p->d_uscr);
@@ -526,6 +590,7 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
     p->M = d->n_modes;
     p->flags = d->flags;
     p->precision = d->precision;
+    p->generic = d->n_pix != kN || (d->flags & (MFBD_FLAG_RECOMPUTE_BACKWARD | MFBD_FLAG_GENERIC_KERNELS));
     p->gamma = d->gamma;
     p->device = dev;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -543,6 +608,7 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
         if ((st = dev_alloc(p, &p->d_err, 1))) throw st;
         if ((e = cudaMemsetAsync(p->d_err, 0, sizeof(int), s))) throw cuda_fail(e, "clear error flag");
         std::vector<std::vector<uint64_t>> hm(p->K), hs(p->K);
+        std::vector<std::vector<uint32_t>> gm(p->K), gs(p->K);
         long long phi_floats = 0;
         int max_box = 1;
         for (int k = 0; k < p->K; ++k) {
@@ -574,34 +640,57 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
                         if (mask[(size_t)(o.x0 + yy) * n + (o.x0 + xx)])
                             hb[k][(size_t)m * o.W * o.W + (size_t)yy * o.W + xx] = (float)full[src];
                     }
-            // bit rows, then the same bits by column (a lane's column in one word)
-            hm[k].assign(o.W + n, 0);
-            for (int yy = 0; yy < o.W; ++yy)
-                for (int xx = 0; xx < o.W; ++xx)
-                    if (mask[(size_t)(o.x0 + yy) * n + (o.x0 + xx)]) {
-                        hm[k][yy] |= 1ull << xx;
-                        hm[k][o.W + xx] |= 1ull << yy;
-                    }
             std::vector<uint8_t> sup = mfbd_host::otf_support_half(mask, n);
-            hs[k].assign(2 * n, 0);
-            for (int ky = 0; ky < n; ++ky)
-                for (int kx = 0; kx <= n / 2; ++kx)
-                    if (sup[(size_t)ky * (n / 2 + 1) + kx]) {
-                        hs[k][ky] |= 1ull << kx;
-                        hs[k][n + kx] |= 1ull << ky;
-                    }
+            if (!p->generic) {
+                // bit rows, then the same bits by column (a lane's column in one word)
+                hm[k].assign(o.W + n, 0);
+                for (int yy = 0; yy < o.W; ++yy)
+                    for (int xx = 0; xx < o.W; ++xx)
+                        if (mask[(size_t)(o.x0 + yy) * n + (o.x0 + xx)]) {
+                            hm[k][yy] |= 1ull << xx;
+                            hm[k][o.W + xx] |= 1ull << yy;
+                        }
+                hs[k].assign(2 * n, 0);
+                for (int ky = 0; ky < n; ++ky)
+                    for (int kx = 0; kx <= n / 2; ++kx)
+                        if (sup[(size_t)ky * (n / 2 + 1) + kx]) {
+                            hs[k][ky] |= 1ull << kx;
+                            hs[k][n + kx] |= 1ull << ky;
+                        }
+            } else {
+                // 32-bit words: box rows [W][mw], support rows [N][sw]
+                o.mw = (o.W + 31) / 32;
+                p->sw = (n / 2 + 1 + 31) / 32;
+                gm[k].assign((size_t)o.W * o.mw, 0u);
+                for (int yy = 0; yy < o.W; ++yy)
+                    for (int xx = 0; xx < o.W; ++xx)
+                        if (mask[(size_t)(o.x0 + yy) * n + (o.x0 + xx)]) gm[k][yy * o.mw + xx / 32] |= 1u << (xx % 32);
+                gs[k].assign((size_t)n * p->sw, 0u);
+                for (int ky = 0; ky < n; ++ky)
+                    for (int kx = 0; kx <= n / 2; ++kx)
+                        if (sup[(size_t)ky * (n / 2 + 1) + kx]) gs[k][ky * p->sw + kx / 32] |= 1u << (kx % 32);
+                if ((st = dev_alloc(p, &o.d_gmask, gm[k].size()))) throw st;
+                if ((st = dev_alloc(p, &o.d_gsupp, gs[k].size()))) throw st;
+                if ((e = cudaMemcpyAsync(o.d_gmask, gm[k].data(), gm[k].size() * 4, cudaMemcpyHostToDevice, s)) ||
+                    (e = cudaMemcpyAsync(o.d_gsupp, gs[k].data(), gs[k].size() * 4, cudaMemcpyHostToDevice, s)))
+                    throw cuda_fail(e, "upload masks");
+            }
             if ((st = dev_alloc(p, &o.d_basis, hb[k].size()))) throw st;
             if (tc_projection_layout(p, o, hb[k], &htc[k])) {
                 if ((st = dev_alloc(p, &o.d_basis_tc, htc[k].size()))) throw st;
                 if ((e = cudaMemcpyAsync(o.d_basis_tc, htc[k].data(), htc[k].size() * 2, cudaMemcpyHostToDevice, s)))
                     throw cuda_fail(e, "upload tensor-core basis");
             }
-            if ((st = dev_alloc(p, &o.d_mask, hm[k].size()))) throw st;
-            if ((st = dev_alloc(p, &o.d_supp, hs[k].size()))) throw st;
-            if ((e = cudaMemcpyAsync(o.d_basis, hb[k].data(), hb[k].size() * sizeof(float), cudaMemcpyHostToDevice, s)) ||
-                (e = cudaMemcpyAsync(o.d_mask, hm[k].data(), hm[k].size() * 8, cudaMemcpyHostToDevice, s)) ||
-                (e = cudaMemcpyAsync(o.d_supp, hs[k].data(), hs[k].size() * 8, cudaMemcpyHostToDevice, s)))
+            if ((e = cudaMemcpyAsync(o.d_basis, hb[k].data(), hb[k].size() * sizeof(float), cudaMemcpyHostToDevice,
+                                     s)))
                 throw cuda_fail(e, "upload plan data");
+            if (!p->generic) {
+                if ((st = dev_alloc(p, &o.d_mask, hm[k].size()))) throw st;
+                if ((st = dev_alloc(p, &o.d_supp, hs[k].size()))) throw st;
+                if ((e = cudaMemcpyAsync(o.d_mask, hm[k].data(), hm[k].size() * 8, cudaMemcpyHostToDevice, s)) ||
+                    (e = cudaMemcpyAsync(o.d_supp, hs[k].data(), hs[k].size() * 8, cudaMemcpyHostToDevice, s)))
+                    throw cuda_fail(e, "upload plan data");
+            }
         }
         p->phi_floats = phi_floats;
         if (p->obj[0].tc_planes > 0 &&
@@ -622,16 +711,27 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
         if ((st = dev_alloc(p, &p->d_gpart, (size_t)part_floats))) throw st;
         if ((st = dev_alloc(p, &p->d_phi, (size_t)phi_floats))) throw st;
         if ((st = dev_alloc(p, &p->d_gphi, (size_t)phi_floats))) throw st;
-        if ((st = dev_alloc(p, &p->d_gscr, (size_t)p->P * p->K * p->J * kHalf))) throw st;
-        if ((st = dev_alloc(p, &p->d_pscr, (size_t)p->P * p->K * p->J * n * n))) throw st;
+        const bool keep = !(p->flags & MFBD_FLAG_RECOMPUTE_BACKWARD);
+        if ((st = dev_alloc(p, &p->d_gscr, (size_t)p->P * p->K * p->J * n * (n / 2 + 1)))) throw st;
+        if (keep && (st = dev_alloc(p, &p->d_pscr, (size_t)p->P * p->K * p->J * n * n))) throw st;
         p->ustride = (max_box * max_box + 31) & ~31;  // 256-byte aligned units
-        if ((st = dev_alloc(p, &p->d_uscr, (size_t)p->P * p->K * p->J * p->ustride))) throw st;
+        if (keep && (st = dev_alloc(p, &p->d_uscr, (size_t)p->P * p->K * p->J * p->ustride))) throw st;
 
-        p->geo = fused_geometry(max_box);
-        int per_sm = max_ctas_per_sm(p->geo);
-        if (per_sm < 1) throw fail(MFBD_ERR_UNSUPPORTED, "fused kernel does not fit on this device");
         p->sms = prop.multiProcessorCount;
-        p->ctas = prop.multiProcessorCount * per_sm;
+        if (!p->generic) {
+            p->geo = fused_geometry(max_box);
+            int per_sm = max_ctas_per_sm(p->geo);
+            if (per_sm < 1) throw fail(MFBD_ERR_UNSUPPORTED, "fused kernel does not fit on this device");
+            p->ctas = prop.multiProcessorCount * per_sm;
+        } else {
+            // odd row strides: column accesses do not conflict in shared memory
+            p->es = std::max(n / 2 + 1, max_box) | 1;
+            p->es2 = max_box | 1;
+            if (generic_smem(n, p->es, p->es2, !keep) > (size_t)227 * 1024)
+                throw fail(MFBD_ERR_UNSUPPORTED, "the pupil box is too large for the shared-memory buffers");
+            p->geo = FusedGeometry{};
+            p->ctas = prop.multiProcessorCount;
+        }
         if ((e = cudaStreamSynchronize(s))) throw cuda_fail(e, "plan upload");
     } catch (int status) {
         release(p);
@@ -714,7 +814,7 @@ int mfbd_plan_get_info(mfbd_plan_t p, mfbd_plan_info* info) {
         info->pupil_box[k] = p->obj[k].W;
     }
     info->workspace_bytes = p->workspace;
-    info->slots_per_cta = p->geo.slots;
+    info->slots_per_cta = p->generic ? 0 : p->geo.slots;
     info->ctas = p->ctas;
     return MFBD_OK;
 }

@@ -108,6 +108,41 @@ cudaError_t launch_grad_combine(const GradParts& gp, int U, int M, float* grad, 
 
 int max_ctas_per_sm(const FusedGeometry& g);
 
+// ------------------------------------------------- patch sizes 48, 96, 128
+// (and 64 on request): CTA-per-unit kernels, generic_kernels.cu.
+struct GenericObj {
+    int W;                  // side of the pupil's bounding box
+    long long phi_off;      // float offset of this object's [P*J][W*W] phase block
+    float inv_z;            // 1 / (N^2 n_pup)
+    const uint32_t* mask;   // [W][mw] box rows, bit c = pupil pixel at box column c
+    int mw;                 // words per mask row
+    const uint32_t* supp;   // [N][sw] OTF support rows over kx <= N/2
+};
+
+struct GenericParams {
+    int P, K, J, N;
+    int sw;                 // words per support row
+    double gamma;
+    const float* weights;   // [K][J]
+    const float* phi;       // box phases, per object at phi_off
+    float* gphi;            // dL/dphi, same layout
+    float2* gscr;           // [P][K][J][N][N/2+1]: OTF, then dL/dconj(H)
+    float2* pscr;           // [P][K][J][N x N] field p [x][y]; null: recomputed by the adjoint
+    float2* uscr;           // [P][K][J][ustride] pupil phasors; null: recomputed
+    int ustride;
+    const float2* spectra;  // D
+    int spec_ld;            // N/2 + 1 or N
+    double* loss;           // [P]
+    float2* object;         // [P][K][N][spec_ld] or null
+    int es, es2;            // shared-memory row strides (complex) of the exchange buffers
+    GenericObj obj[kMaxObjects];
+};
+
+size_t generic_smem(int N, int es, int es2, bool recompute);
+cudaError_t launch_generic_forward(const GenericParams& prm, int sms, cudaStream_t s);
+cudaError_t launch_generic_reduction(const GenericParams& prm, int sms, cudaStream_t s);
+cudaError_t launch_generic_adjoint(const GenericParams& prm, int sms, cudaStream_t s);
+
 // Record an error for mfbd_last_error() (fixed-size buffer, no allocation).
 int set_error(int status, const char* why);
 int set_cuda_error(cudaError_t e, const char* where);

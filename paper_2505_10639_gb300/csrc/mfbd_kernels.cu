@@ -35,6 +35,7 @@
 //   ADJ    W columns: column F^H -> G_P, dL/dphi = 2 Im(conj(P) G_P)
 #include "mfbd_internal.h"
 #include "fft_reg.cuh"
+#include "mfbd_device.cuh"
 
 namespace mfbd_dev {
 
@@ -50,17 +51,6 @@ constexpr int kWarps = 6;
 constexpr int kThreads = 32 * kWarps;
 
 enum Pass : int { P_PUPIL = 0, P_FIELD = 1, P_OTF = 2, P_SEED = 3, P_C2R = 4, P_ADJ = 5, P_END = 6 };
-
-// exp(i phi): reduction to [-pi, pi] by a two-constant Cody-Waite step
-// (2 pi = 6.2831854820251465 - 1.7484556e-7), then the SFU sine/cosine.
-__device__ __forceinline__ float2 expi(float ph) {
-    const float n = rintf(ph * 0.159154943091895336f);
-    float r = fmaf(n, -6.28318548202514648f, ph);
-    r = fmaf(n, 1.74845553e-7f, r);
-    float s, c;
-    __sincosf(r, &s, &c);
-    return make_float2(c, s);
-}
 
 // Asynchronous global -> shared copy of 8 bytes (both addresses 8-byte
 // aligned); complete for the issuing thread after cp_async_wait.
@@ -469,45 +459,6 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
 // frequency is redone with N, Q, O and r_j in FP64 -- except DC, whose seed
 // is zero and whose loss term is exact enough in FP32. Each lane sums its
 // loss terms with Kahan compensation; the warp combines them in FP64.
-constexpr float kCancel = 1e-3f;
-
-struct KahanSum {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        const float y = x - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-};
-
-__device__ __forceinline__ void fp64_frequency(int J, const float2* dp, size_t dstride, float2* hp, const float* w,
-                                               double gamma, bool seed, float& t, float2& o) {
-    double nx = 0.0, ny = 0.0, qd = gamma;
-    for (int j = 0; j < J; ++j) {
-        const float2 d = dp[(size_t)j * dstride];
-        const float2 h = hp[(size_t)j * kHalf];
-        const double wj = w[j];
-        nx += wj * ((double)d.x * h.x + (double)d.y * h.y);
-        ny += wj * ((double)d.y * h.x - (double)d.x * h.y);
-        qd += wj * ((double)h.x * h.x + (double)h.y * h.y);
-    }
-    const double ox = nx / qd, oy = ny / qd;
-    double tsum = 0.0;
-    for (int j = 0; j < J; ++j) {
-        const float2 d = dp[(size_t)j * dstride];
-        const float2 h = hp[(size_t)j * kHalf];
-        const double wj = w[j];
-        const double rx = (double)d.x - (ox * h.x - oy * h.y);
-        const double ry = (double)d.y - (ox * h.y + oy * h.x);
-        tsum += wj * (rx * rx + ry * ry);
-        hp[(size_t)j * kHalf] = seed ? make_float2((float)(-wj * (ox * rx + oy * ry)), (float)(-wj * (ox * ry - oy * rx)))
-                                     : make_float2(0.f, 0.f);
-    }
-    t = (float)(tsum + gamma * (ox * ox + oy * oy));
-    o = make_float2((float)ox, (float)oy);
-}
-
 // JM > 0: J <= JM, the J spectra and OTFs of a frequency are loaded once, all
 // at once, into registers. JM == 0: any J, streamed from memory twice.
 template <int JM>
@@ -554,7 +505,7 @@ __device__ double reduce_object_warp(const FusedParams& prm, int p, int k) {
             o = cscale(num, invq);
             const float t_est = e - (num.x * num.x + num.y * num.y) * invq;
             if (f != 0 && t_est < kCancel * e) {
-                fp64_frequency(J, dp, dstride, hp, w, prm.gamma, seed, t, o);
+                fp64_frequency(J, dp, dstride, hp, kHalf, w, prm.gamma, seed, t, o);
             } else {
                 float tsum = 0.f;
 #pragma unroll
@@ -582,7 +533,7 @@ __device__ double reduce_object_warp(const FusedParams& prm, int p, int k) {
             o = cscale(num, invq);
             const float t_est = e - (num.x * num.x + num.y * num.y) * invq;
             if (f != 0 && t_est < kCancel * e) {
-                fp64_frequency(J, dp, dstride, hp, w, prm.gamma, seed, t, o);
+                fp64_frequency(J, dp, dstride, hp, kHalf, w, prm.gamma, seed, t, o);
             } else {
                 float tsum = 0.f;
 #pragma unroll 4

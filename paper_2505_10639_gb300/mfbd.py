@@ -25,7 +25,8 @@ class _Desc:
     """A PlanDesc plus the host arrays it points into (kept alive)."""
 
     def __init__(self, n_pix, n_patches, diams, wavelengths, n_frames, n_modes, basis, gamma,
-                 weights, obscuration, user_basis, precision, full_spectrum, projection="tensor"):
+                 weights, obscuration, user_basis, precision, full_spectrum, projection="tensor",
+                 recompute=False, generic=False):
         if projection not in ("tensor", "simt"):
             raise ValueError("projection must be 'tensor' or 'simt'")
         k = len(diams)
@@ -40,7 +41,9 @@ class _Desc:
             user_basis=_fptr(self.user, ctypes.c_float), gamma=gamma,
             frame_weight=_fptr(self.weights, ctypes.c_float), precision=_PREC[precision],
             flags=(_lib.MFBD_FLAG_FULL_SPECTRUM if full_spectrum else 0)
-            | (_lib.MFBD_FLAG_SIMT_PROJECTION if projection == "simt" else 0))
+            | (_lib.MFBD_FLAG_SIMT_PROJECTION if projection == "simt" else 0)
+            | (_lib.MFBD_FLAG_RECOMPUTE_BACKWARD if recompute else 0)
+            | (_lib.MFBD_FLAG_GENERIC_KERNELS if generic else 0))
 
 
 def describe_object(obj, n_pix, diams, wavelengths, n_frames, n_modes, basis="kl", gamma=1e-3,
@@ -98,10 +101,10 @@ class Plan:
 
     def __init__(self, n_pix, n_patches, diams, wavelengths, n_frames, n_modes, basis="kl",
                  gamma=1e-3, weights=None, obscuration=0.0, user_basis=None, precision="fp32",
-                 full_spectrum=False, projection="tensor", stream=None):
+                 full_spectrum=False, projection="tensor", recompute=False, generic=False, stream=None):
         self._lib = _lib.load()
         self._d = _Desc(n_pix, n_patches, diams, wavelengths, n_frames, n_modes, basis, gamma, weights,
-                        obscuration, user_basis, precision, full_spectrum, projection)
+                        obscuration, user_basis, precision, full_spectrum, projection, recompute, generic)
         self.n_pix, self.n_patches, self.n_objects = n_pix, n_patches, len(diams)
         self.n_frames, self.n_modes = n_frames, n_modes
         self.full_spectrum = full_spectrum

@@ -76,7 +76,7 @@ def test_invalid_descriptors_are_rejected(lib, bad):
 
 
 def test_unsupported_size_and_null_arguments(lib):
-    d = _desc(n_pix=128, diams=[40.0])
+    d = _desc(n_pix=80, diams=[40.0])  # patch sizes: 48, 64, 96, 128
     out = ctypes.c_void_p()
     assert lib.mfbd_plan_create(ctypes.byref(out), ctypes.byref(d.desc), None) == _lib.MFBD_ERR_UNSUPPORTED
     assert lib.mfbd_plan_create(None, ctypes.byref(d.desc), None) == _lib.MFBD_ERR_INVALID_ARG

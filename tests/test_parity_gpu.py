@@ -289,3 +289,32 @@ def test_bf16_phase_error_against_oracle(c2_slice):
             eo = max(eo, np.linalg.norm((of - oo[p][k])[supp]) / np.linalg.norm(oo[p][k][supp]))
     print("bf16 phase: loss %.3e grad %.3e object %.3e" % (el, eg, eo))
     assert el <= BF16_LOSS_RTOL and eg <= BF16_GRAD_RTOL and eo <= BF16_OBJ_RTOL
+
+
+@pytest.mark.parametrize("recompute", [False, True])
+@pytest.mark.parametrize("n_pix,diams", [(48, (22.0,)), (96, (40.0, 30.0)), (128, (56.0, 44.0))])
+def test_general_patch_sizes(n_pix, diams, recompute):
+    """Patch sizes 48, 96 and 128 (one CTA per unit, lines over one or two
+    lanes), keeping or recomputing the field for the adjoint."""
+    wl = (6563.0, 8542.0)[:len(diams)]
+    case = cases.make_case(n_pix=n_pix, diams=diams, wavelengths=wl, n_frames=3, n_modes=12, basis="kl",
+                           n_patches=2, seed=20250518 + n_pix)
+    a32, d32, d_or = _inputs(case)
+    ref = _oracle(case, a32, d_or)
+    plan = _plan_for(case, recompute=recompute)
+    assert plan.info()["slots_per_cta"] == 0  # the general-size kernels
+    loss, grad, obj = _run_fused(plan, a32, d32)
+    _check(case, loss, grad, obj, ref)
+
+
+def test_general_kernels_match_64px_pass_machine(c2_slice):
+    """N = 64 on the general-size kernels (with and without recompute)
+    against the 64-pixel pass machine."""
+    a32, d32, _ = _inputs(c2_slice)
+    lf, gf, of = _run_fused(_plan_for(c2_slice), a32, d32)
+    for rec in (False, True):
+        lg, gg, og = _run_fused(_plan_for(c2_slice, generic=True, recompute=rec), a32, d32)
+        assert np.all(np.abs(lg - lf) <= 2e-6 * np.abs(lf))
+        for p in range(len(lf)):
+            assert np.linalg.norm(gg[p] - gf[p]) <= 2e-5 * np.linalg.norm(gf[p])
+        assert np.abs(og - of).max() <= 1e-5 * np.abs(of).max()
