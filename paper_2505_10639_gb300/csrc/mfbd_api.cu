@@ -323,16 +323,16 @@ int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s, int p0, int np) {
     const int U = np * p->J;
     GradJob job{};
     job.K = p->K;
+    // The plan's pixel chunks (laid out for all P*J units at create), for
+    // every call: the summation order of dL/da then does not depend on how
+    // many patches a call covers, so a chunked host-buffer call gives the
+    // same bits as one device call.
     int npix[kMaxObjects], chunk[kMaxObjects], splits[kMaxObjects];
-    for (int k = 0; k < p->K; ++k) npix[k] = p->obj[k].W * p->obj[k].W;
-    // chunks for this call's units, if the plan's partial-sum buffers hold them
-    grad_layout(p->K, npix, U, p->sms, chunk, splits);
-    for (int k = 0; k < p->K; ++k)
-        if ((long long)splits[k] * U > (long long)p->obj[k].g_splits * p->P * p->J)
-            for (int q = 0; q < p->K; ++q) {
-                chunk[q] = p->obj[q].g_chunk;
-                splits[q] = p->obj[q].g_splits;
-            }
+    for (int k = 0; k < p->K; ++k) {
+        npix[k] = p->obj[k].W * p->obj[k].W;
+        chunk[k] = p->obj[k].g_chunk;
+        splits[k] = p->obj[k].g_splits;
+    }
     GradParts gp{};
     gp.K = p->K;
     for (int k = 0; k < p->K; ++k) {

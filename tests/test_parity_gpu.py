@@ -259,6 +259,24 @@ def test_host_pipeline_equals_device_call(c2_slice, n_chunks):
     assert np.array_equal(lh2.numpy(), loss) and np.array_equal(gh2.numpy(), grad)
 
 
+def test_host_pipeline_bits_at_larger_field(c2_slice):
+    """160 patches in 4 host chunks of 40: a chunk covers a quarter of the
+    units, so a modal-adjoint pixel-chunk layout chosen per call would sum
+    dL/da in another order than the one-call path; the plan's fixed layout
+    keeps the bits equal."""
+    a32, d32, _ = _inputs(c2_slice)
+    reps = 54
+    aa = np.ascontiguousarray(np.tile(a32, (reps, 1, 1))[:160])
+    dd = np.ascontiguousarray(np.tile(d32, (reps, 1, 1, 1, 1))[:160])
+    plan = _plan_for(c2_slice, n_patches=160)
+    loss, grad, _ = _run_fused(plan, aa, dd, want_object=False)
+    lh, gh, _ = plan.loss_grad_host(torch.from_numpy(aa).pin_memory(), torch.from_numpy(dd).pin_memory(),
+                                    n_chunks=4)
+    torch.cuda.current_stream().synchronize()
+    assert np.array_equal(lh.numpy(), loss)
+    assert np.array_equal(gh.numpy(), grad)
+
+
 def test_tensor_projection_matches_simt_projection(c2_slice):
     """The FP32 phase projection on the tensor cores (three BF16 planes per
     operand) and on the SIMT kernel give the same loss and gradient to FP32
