@@ -35,15 +35,27 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-SEED = 20250517  # 20250515 + workload index 2
-WORKLOAD = dict(workload="fov1024_64px_961patches_2obj_12frames_44kl", fov=1024, n_pix=64, stride=32,
-                n_patches=961, diams=[36.0, 28.0], wavelengths=[6563.0, 8542.0], n_frames=12,
-                n_modes=44, basis="kl", d_over_r0=5.0, noise_sigma=1e-3)
+# Workloads: the 961-patch field of 64 px patches (the headline) and the
+# 3969-patch field of 128 px patches (4 objects, 32 frames, 100 KL modes,
+# BF16 phase projection, field and phasors recomputed in the backward pass).
+WORKLOADS = {
+    "fov1024_64px": dict(workload="fov1024_64px_961patches_2obj_12frames_44kl", seed=20250517, fov=1024,
+                         n_pix=64, stride=32, n_patches=961, diams=[36.0, 28.0], wavelengths=[6563.0, 8542.0],
+                         n_frames=12, n_modes=44, basis="kl", d_over_r0=5.0, noise_sigma=1e-3,
+                         precision="fp32", recompute=False, device_noise=False, cpu_patches=300),
+    "fov4096_128px": dict(workload="fov4096_128px_3969patches_4obj_32frames_100kl", seed=20250520, fov=4096,
+                          n_pix=128, stride=64, n_patches=3969, diams=[40.0, 48.0, 56.0, 64.0],
+                          wavelengths=[8542.0, 8542.0 * 40 / 48, 8542.0 * 40 / 56, 8542.0 * 40 / 64],
+                          n_frames=32, n_modes=100, basis="kl", d_over_r0=10.0, noise_sigma=1e-3,
+                          precision="bf16_phase", recompute=True, device_noise=True, cpu_patches=16),
+}
+WORKLOAD = dict(WORKLOADS["fov1024_64px"])
+SEED = WORKLOAD["seed"]  # 20250515 + workload index
 FP32_LANES_PER_SM = 128
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of each
-# kernel, from one ncu capture (--set full) of the first 400 patches of this
-# workload; a launch's traffic is this times its units (the traffic is per
-# unit: no cross-unit reuse)
+# kernel of the 64 px pass machine, from one ncu capture (--set full) of the
+# first 400 patches of the 961-patch workload; a launch's traffic is this
+# times its units (the traffic is per unit: no cross-unit reuse)
 NCU_DRAM_BYTES_PER_UNIT = {"forward_passes": (72.987e6 + 503.382e6) / 9600,
                            "adjoint_passes": (659.338e6 + 33.887e6) / 9600,
                            "reduction": (324.479e6 + 120.270e6) / 9600}
@@ -57,6 +69,15 @@ def gamma_of(w):
 
 def units_of(w):
     return w["n_patches"] * len(w["diams"]) * w["n_frames"]
+
+
+def unit_weight_64(n_pix):
+    """Work of one unit at n_pix relative to one at 64 px, N^2 log2 N^2."""
+    return (n_pix * n_pix * math.log2(n_pix * n_pix)) / (64 * 64 * 12.0)
+
+
+def units64_of(w):
+    return units_of(w) * unit_weight_64(w["n_pix"])
 
 
 # ------------------------------------------------------------ distributed
@@ -108,11 +129,15 @@ def object_patches(w, seed):
     return np.ascontiguousarray(np.swapaxes(pat, 0, 1))[: w["n_patches"]]
 
 
-def make_gpu_inputs(plan, w, seed):
-    """Synthetic spectra built on the GPU with the library's own OTF."""
+def make_gpu_inputs(w, seed, chunk=256):
+    """Synthetic spectra built on the GPU with the library's own OTF, chunk
+    by chunk of patches (a plan of `chunk` patches makes each chunk's OTFs):
+    D = F(o) H_true + F(n). The 961-patch workload draws its noise with the
+    numpy generator of `synth`; the 3969-patch one (8.3e9 noise samples)
+    with the seeded torch generator of `synth.noise_torch` on the device."""
     import torch
     from paper_2505_10639_gb300 import synth
-    from paper_2505_10639_gb300.mfbd import describe_object
+    from paper_2505_10639_gb300.mfbd import Plan, describe_object
     _, _, var, _ = describe_object(0, w["n_pix"], w["diams"], w["wavelengths"], w["n_frames"],
                                    w["n_modes"], basis=w["basis"])
     P, K, J, N = w["n_patches"], len(w["diams"]), w["n_frames"], w["n_pix"]
@@ -120,16 +145,31 @@ def make_gpu_inputs(plan, w, seed):
     a_eval = np.zeros_like(a_true)
     for p in range(P):
         a_true[p], a_eval[p] = per_patch_draws(w, seed, p, var)
-    dev = plan.device
-    h = plan.otf(torch.from_numpy(a_true).to(dev))
-    obj = torch.from_numpy(object_patches(w, seed)).to(dev)
-    spec = torch.fft.rfft2(obj.to(torch.float64)).to(torch.complex64)[:, :, None] * h
-    del h
-    for p in range(P):
-        n = torch.from_numpy(synth.noise(seed, (K, J, N, N), w["noise_sigma"], sub=p)).to(dev)
-        spec[p] += torch.fft.rfft2(n).to(torch.complex64)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    objs = object_patches(w, seed)
+    spec = torch.empty((P, K, J, N, N // 2 + 1), dtype=torch.complex64, device=dev)
+    chunk = min(chunk, P) if P > 0 else 1
+    dplan = Plan(N, chunk, w["diams"], w["wavelengths"], J, w["n_modes"], basis=w["basis"], gamma=gamma_of(w))
+    for p0 in range(0, P, chunk):
+        n = min(chunk, P - p0)
+        at = np.zeros((chunk, J, w["n_modes"]), np.float32)
+        at[:n] = a_true[p0:p0 + n]
+        h = dplan.otf(torch.from_numpy(at).to(dev))[:n]
+        obj = torch.from_numpy(objs[p0:p0 + n]).to(dev)
+        sp = torch.fft.rfft2(obj.to(torch.float64)).to(torch.complex64)[:, :, None] * h
+        del h
+        for q in range(n):
+            p = p0 + q
+            if w.get("device_noise"):
+                nz = synth.noise_torch(seed, (K, J, N, N), w["noise_sigma"], sub=p, device=dev)
+            else:
+                nz = torch.from_numpy(synth.noise(seed, (K, J, N, N), w["noise_sigma"], sub=p)).to(dev)
+            sp[q] += torch.fft.rfft2(nz).to(torch.complex64)
+        spec[p0:p0 + n] = sp
+        del sp
+    dplan.close()
     torch.cuda.synchronize()
-    return torch.from_numpy(a_eval).to(dev), spec.contiguous()
+    return torch.from_numpy(a_eval).to(dev), spec
 
 
 # ------------------------------------------------------------ clocks
@@ -224,7 +264,7 @@ def fp32_peak_tflops(n_sm, sm_mhz):
 def _oracle_worker(args):
     """Generate this worker's patches (untimed), wait at the barrier, then
     time the oracle's loss+object+gradient on them."""
-    (w, seed, patch_ids, barrier, queue) = args
+    (w, seed, patch_ids, objs, barrier, queue) = args
     from oracle import mfbd as omfbd
     from oracle import optics
     from paper_2505_10639_gb300 import synth
@@ -236,13 +276,12 @@ def _oracle_worker(args):
         var = v
     scales = [w["wavelengths"][0] / x for x in w["wavelengths"]]
     setup = omfbd.Setup(masks, bases, scales, np.ones((len(w["diams"]), w["n_frames"])), gamma_of(w))
-    objs = object_patches(w, seed)
     data = []
     K, J, N = len(w["diams"]), w["n_frames"], w["n_pix"]
-    for p in patch_ids:
+    for i, p in enumerate(patch_ids):
         a_true, a_eval = per_patch_draws(w, seed, p, var)
         noise = synth.noise(seed, (K, J, N, N), w["noise_sigma"], sub=p)
-        d = omfbd.synth_spectra(setup, a_true, objs[p], noise)
+        d = omfbd.synth_spectra(setup, a_true, objs[i], noise)
         data.append((a_eval.astype(np.float32).astype(np.float64), d.astype(np.complex64).astype(np.complex128)))
     barrier.wait()
     t0 = time.time()
@@ -258,9 +297,10 @@ def run_oracle_sample(w, seed, n_patches, cores):
     ids = list(range(n_patches))
     chunks = [ids[i::cores] for i in range(cores)]
     chunks = [c for c in chunks if c]
+    objs = object_patches(w, seed)  # the field once, in this process
     barrier = ctx.Barrier(len(chunks))
     queue = ctx.Queue()
-    procs = [ctx.Process(target=_oracle_worker, args=((w, seed, c, barrier, queue),)) for c in chunks]
+    procs = [ctx.Process(target=_oracle_worker, args=((w, seed, c, objs[c], barrier, queue),)) for c in chunks]
     for p in procs:
         p.start()
     res = [queue.get() for _ in procs]
@@ -273,11 +313,6 @@ def run_oracle_sample(w, seed, n_patches, cores):
     return units / (t1 - t0), t1 - t0, n, len(chunks)
 
 
-def cpu_sample_size(cores):
-    # ~0.05 s of CPU per patch: about 15 s of CPU work in total
-    return max(16, min(961, 300))
-
-
 # ------------------------------------------------------------ GPU leg
 
 def run_gpu(args, rank, local_rank, world):
@@ -288,13 +323,11 @@ def run_gpu(args, rank, local_rank, world):
     torch.cuda.set_device(local_rank)
     w = WORKLOAD
     seed = SEED + rank
+    # the data always come from the FP32 forward model
+    coeffs, spectra = make_gpu_inputs(w, seed)
     plan = Plan(w["n_pix"], w["n_patches"], w["diams"], w["wavelengths"], w["n_frames"], w["n_modes"],
-                basis=w["basis"], gamma=gamma_of(w))
-    coeffs, spectra = make_gpu_inputs(plan, w, seed)  # the data always come from the FP32 forward model
-    if args.precision != "fp32" or args.projection != "tensor":
-        plan.close()
-        plan = Plan(w["n_pix"], w["n_patches"], w["diams"], w["wavelengths"], w["n_frames"], w["n_modes"],
-                    basis=w["basis"], gamma=gamma_of(w), precision=args.precision, projection=args.projection)
+                basis=w["basis"], gamma=gamma_of(w), precision=args.precision, projection=args.projection,
+                recompute=args.recompute, generic=(args.kernels == "generic"))
     info = plan.info()
     loss = torch.empty(w["n_patches"], dtype=torch.float64, device=plan.device)
     grad = torch.empty(plan.coeff_shape(), dtype=torch.float32, device=plan.device)
@@ -328,7 +361,7 @@ def run_gpu(args, rank, local_rank, world):
     plan.set_profiling(False)
 
     rmax, rsum = (torch_reducers() if world > 1 else (None, None))
-    ms, units, value = aggregate(local_ms, units_of(w), world, rmax, rsum)
+    ms, units, value = aggregate(local_ms, units64_of(w), world, rmax, rsum)
 
     e2e = None
     if not args.no_e2e:
@@ -345,8 +378,10 @@ def run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, 
     import torch.distributed as dist
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    a_host = coeffs.cpu().pin_memory()
-    d_host = spectra.cpu().pin_memory()
+    a_host = torch.empty(coeffs.shape, dtype=coeffs.dtype, pin_memory=True)
+    a_host.copy_(coeffs)
+    d_host = torch.empty(spectra.shape, dtype=spectra.dtype, pin_memory=True)
+    d_host.copy_(spectra)
     l_host = torch.empty_like(loss, device="cpu").pin_memory()
     g_host = torch.empty_like(grad, device="cpu").pin_memory()
 
@@ -369,7 +404,7 @@ def run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, 
     if not (torch.equal(loss.cpu(), l_host) and torch.equal(grad.cpu(), g_host)):
         raise RuntimeError("host-buffer call differs from the device call")
     e2e_local = e0.elapsed_time(e1) / args.steps
-    e2e_ms, _, e2e_value = aggregate(e2e_local, units_of(w), world, rmax, rsum)
+    e2e_ms, _, e2e_value = aggregate(e2e_local, units64_of(w), world, rmax, rsum)
     h2d = coeffs.numel() * 4 + spectra.numel() * 8
     d2h = loss.numel() * 8 + grad.numel() * 4
     return {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d,
@@ -396,23 +431,27 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
         ms_, n_ = prof[kind]
         return ms_ / max(1, n_)
 
+    # DRAM traffic from the committed ncu capture of the 64 px pass machine;
+    # not measured for the other kernel families
+    ncu_ok = w["n_pix"] == 64 and args.kernels == "pass" and not args.recompute
     kernels = {}
     for name, kind, work in (("forward_passes", "forward", fwd_flops), ("adjoint_passes", "adjoint", adj_flops)):
         t = per_launch(kind)
         a = work / (t * 1e-3) / 1e12 if t > 0 else 0.0
         kernels[name] = {"bound": "alu", "ms": t, "achieved": a, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": a / alu_peak, "work_per_launch": work,
-                         "traffic": NCU_DRAM_BYTES_PER_UNIT[name] * units_of(w)}
+                         "traffic": NCU_DRAM_BYTES_PER_UNIT[name] * units_of(w) if ncu_ok else None}
     t = per_launch("reduction")
     a = red_bytes / (t * 1e-3) / 1e9 if t > 0 else 0.0
     kernels["reduction"] = {"bound": "hbm", "ms": t, "achieved": a, "peak": hbm_peak, "unit": "GB/s",
                             "frac": a / hbm_peak, "work_per_launch": red_bytes,
-                            "traffic": NCU_DRAM_BYTES_PER_UNIT["reduction"] * units_of(w)}
+                            "traffic": NCU_DRAM_BYTES_PER_UNIT["reduction"] * units_of(w) if ncu_ok else None}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     dk = kernels[dom]
     roofline = {"bound": dk["bound"], "kernel": dom, "achieved": dk["achieved"], "peak": dk["peak"],
                 "unit": dk["unit"], "frac": dk["frac"], "traffic": dk["traffic"],
-                "traffic_basis": "ncu DRAM bytes per unit (400-patch capture) x units per launch",
+                "traffic_basis": ("ncu DRAM bytes per unit (400-patch capture) x units per launch" if ncu_ok
+                                  else "not captured for this kernel family"),
                 "peak_basis": ("FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock)"
                                % (n_sm, FP32_LANES_PER_SM, sm_max)) if dk["bound"] == "alu"
                 else "HBM copy bandwidth of MEASURED_PEAKS.json",
@@ -424,10 +463,12 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w["workload"], "patch_px": w["n_pix"], "patches": w["n_patches"],
                    "objects": len(w["diams"]), "frames": w["n_frames"], "modes": w["n_modes"],
-                   "basis": w["basis"], "pupil_px": w["diams"], "precision": args.precision,
-                   "projection": args.projection,
-                   "units_per_step": units_of(w),
-                   "l2": "inputs larger than L2 (%.0f MB spectra)" % (units_of(w) * 64 * 33 * 8 / 1e6),
+                   "basis": w["basis"], "pupil_px": w["diams"], "d_over_r0": w["d_over_r0"],
+                   "precision": args.precision, "projection": args.projection, "recompute": args.recompute,
+                   "kernels": args.kernels, "units_per_step": units_of(w),
+                   "unit_weight_at_64px": unit_weight_64(w["n_pix"]),
+                   "l2": "inputs larger than L2 (%.0f MB spectra)"
+                         % (units_of(w) * w["n_pix"] * (w["n_pix"] // 2 + 1) * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": e2e,
         "roofline": roofline,
@@ -451,13 +492,26 @@ def main():
     ap.add_argument("--patches", type=int, default=0,
                     help="use only the first N patches of the field (smaller profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16_phase"],
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16_phase"],
                     help="bf16_phase: the phase projection with BF16 operands on the tensor cores")
     ap.add_argument("--projection", default="tensor", choices=["tensor", "simt"],
                     help="FP32 phase projection on the tensor cores (three BF16 planes) or the SIMT kernel")
     ap.add_argument("--e2e-chunks", type=int, default=0,
                     help="patch chunks of the host-buffer call (copies overlap the kernels of other chunks)")
+    ap.add_argument("--workload", default="fov1024_64px", choices=sorted(WORKLOADS),
+                    help="fov1024_64px: 961 patches of 64 px (default); fov4096_128px: 3969 patches of 128 px")
+    ap.add_argument("--kernels", default="pass", choices=["pass", "generic"],
+                    help="64 px: the warp-per-unit pass machine or the CTA-per-unit kernels of the other sizes")
+    ap.add_argument("--recompute", default=None, choices=["on", "off"],
+                    help="recompute the field and phasors in the backward pass (default: the workload's)")
     args = ap.parse_args()
+    WORKLOAD.clear()
+    WORKLOAD.update(WORKLOADS[args.workload])
+    global SEED
+    SEED = WORKLOAD["seed"]
+    if args.precision is None:
+        args.precision = WORKLOAD["precision"]
+    args.recompute = WORKLOAD["recompute"] if args.recompute is None else (args.recompute == "on")
     if args.patches:
         WORKLOAD["n_patches"] = args.patches
         WORKLOAD["workload"] += "_first%d" % args.patches
@@ -465,6 +519,10 @@ def main():
         WORKLOAD["workload"] += "_bf16phase"
     elif args.projection == "simt":
         WORKLOAD["workload"] += "_simtphase"
+    if args.recompute != WORKLOAD["recompute"]:
+        WORKLOAD["workload"] += "_recompute" if args.recompute else "_keep"
+    if args.kernels == "generic":
+        WORKLOAD["workload"] += "_ctaperunit"
     args.warmup = max(3, args.warmup)
     rank, local_rank, world = dist_env()
 
@@ -472,7 +530,7 @@ def main():
         if rank != 0:
             return 0
         cores = os.cpu_count() or 1
-        n = args.cpu_patches or cpu_sample_size(cores)
+        n = args.cpu_patches or WORKLOAD["cpu_patches"]
         total_t, total_u, rates = 0.0, 0, []
         for _ in range(args.warmup):
             pass  # the oracle has no warm state; warm-up steps are not needed
@@ -480,7 +538,7 @@ def main():
             rate, t, npat, used = run_oracle_sample(WORKLOAD, SEED, n, cores)
             rates.append(rate)
             total_t += t
-            total_u += npat * len(WORKLOAD["diams"]) * WORKLOAD["n_frames"]
+            total_u += npat * len(WORKLOAD["diams"]) * WORKLOAD["n_frames"] * unit_weight_64(WORKLOAD["n_pix"])
         value = total_u / total_t
         sample = "%d of %d patches (all %d objects x %d frames) per step" % (
             n, WORKLOAD["n_patches"], len(WORKLOAD["diams"]), WORKLOAD["n_frames"])
@@ -488,7 +546,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD["workload"], "patch_px": 64, "precision": "fp64 oracle"},
+                "config": {"workload": WORKLOAD["workload"], "patch_px": WORKLOAD["n_pix"],
+                           "precision": "fp64 oracle"},
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -501,11 +560,13 @@ def main():
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             cores = os.cpu_count() or 1
-            n = args.cpu_patches or cpu_sample_size(cores)
+            n = args.cpu_patches or WORKLOAD["cpu_patches"]
             rate, t, npat, used = run_oracle_sample(WORKLOAD, SEED, n, cores)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
-                                    "sample": "%d of %d patches (2 objects x 12 frames each), %.1f s wall"
-                                              % (npat, WORKLOAD["n_patches"], t)}
+                                    "sample": "%d of %d patches (%d objects x %d frames each), %.1f s wall"
+                                              % (npat, WORKLOAD["n_patches"], len(WORKLOAD["diams"]),
+                                                 WORKLOAD["n_frames"], t)}
+            line["cpu_baseline"]["value"] *= unit_weight_64(WORKLOAD["n_pix"])
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

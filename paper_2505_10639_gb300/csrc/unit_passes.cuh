@@ -1,0 +1,486 @@
+// Per-unit passes of the CTA-per-unit kernels (patch sizes 48, 64, 96, 128),
+// shared by the single-problem kernels (generic_kernels.cu) and the batched
+// persistent kernel (batch_kernels.cu).
+//
+// The passes are those of Sec. 3.1, Eqs. 20-22 and their adjoint: a line of
+// N points is held by S = 1 (N <= 64) or S = 2 (N = 96, 128) lanes, L = N / S
+// points each. A line transform runs a register FFT of L points on the
+// decimated samples x[S n + s] of each lane s and, for S = 2, one radix-2
+// stage across the lane pair by shuffles, leaving X[s L + k] in lane s
+// (decimation in time); the decimation-in-frequency twin takes X in that
+// blocked order and leaves x[S m + s]. A group of 64 S threads works on one
+// unit (patch, object, frame), 64 lines per round, with the 2-D transforms
+// exchanged through an N x es buffer in shared memory and the passes
+// separated by the group's barrier (the CTA's, or a named barrier when a CTA
+// runs two groups).
+//
+// RECOMPUTE (the adjoint's template flag): the field p = F P and the pupil
+// phasors are not kept by the forward passes; the adjoint recomputes the
+// column transforms of P into a second buffer and each row of p just before
+// it is needed.
+#pragma once
+
+#include <cstdint>
+
+#include "fft_reg.cuh"
+#include "mfbd_device.cuh"
+
+namespace mfbd_dev {
+namespace unitpass {
+
+using fftreg::cadd;
+using fftreg::cconj;
+using fftreg::cmul;
+using fftreg::cscale;
+using fftreg::csub;
+
+template <int N>
+struct Geo {
+    static constexpr int S = N > 64 ? 2 : 1;  // lanes per line
+    static constexpr int L = N / S;           // points per lane
+    static constexpr int NH = N / 2 + 1;
+    static constexpr int LINES = 64;          // lines per round
+    static constexpr int THREADS = LINES * S;
+};
+
+// Barrier of the threads that work on one unit: the whole CTA, or the named
+// barrier `id` of a group of n threads (n a multiple of 32).
+struct CtaBar {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct GroupBar {
+    int id, n;
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+    }
+};
+
+__device__ __forceinline__ bool wbit(const uint32_t* rows, int words, int r, int c) {
+    return (rows[r * words + (c >> 5)] >> (c & 31)) & 1u;
+}
+
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// Forward (DIR = -1) line transform, decimation in time: lane s holds
+// x[S n + s] on entry and X[s L + k] on exit.
+template <int N, int DIR>
+__device__ __forceinline__ void line_fft(float2 (&v)[Geo<N>::L], int sub) {
+    constexpr int S = Geo<N>::S, L = Geo<N>::L;
+    fftreg::fft_line<L, DIR>(v);
+    if constexpr (S == 2) {
+        fftreg::static_for<0, L>([&](auto kk) {
+            constexpr int k = decltype(kk)::value;
+            const float2 t = sub ? fftreg::twmul<N, k, DIR>(v[k]) : v[k];  // lane 1: W^k O[k]
+            const float2 o = shfl_xor2(t, 1);
+            v[k] = sub ? csub(o, t) : cadd(t, o);
+        });
+    }
+}
+
+// Decimation in frequency: lane s holds X[s L + k] on entry and the
+// transform's x[S m + s] on exit.
+template <int N, int DIR>
+__device__ __forceinline__ void line_fft_dif(float2 (&v)[Geo<N>::L], int sub) {
+    constexpr int S = Geo<N>::S, L = Geo<N>::L;
+    if constexpr (S == 2) {
+        fftreg::static_for<0, L>([&](auto kk) {
+            constexpr int k = decltype(kk)::value;
+            const float2 o = shfl_xor2(v[k], 1);
+            v[k] = sub ? fftreg::twmul<N, k, DIR>(csub(o, v[k])) : cadd(v[k], o);
+        });
+    }
+    fftreg::fft_line<L, DIR>(v);
+}
+
+// Conjugate partner Z[(N - kx) mod N] of the element k of lane `sub` (which
+// holds kx = sub L + k after line_fft), for every k.
+template <int N>
+__device__ __forceinline__ void conj_partners(const float2 (&v)[Geo<N>::L], float2 (&pc)[Geo<N>::L], int sub) {
+    constexpr int S = Geo<N>::S, L = Geo<N>::L;
+    fftreg::static_for<0, L>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        if constexpr (S == 1) {
+            pc[k] = cconj(v[(L - k) % L]);
+        } else if constexpr (k == 0) {
+            pc[k] = cconj(v[0]);  // kx = 0 or N/2: its own partner
+        } else {
+            pc[k] = cconj(shfl_xor2(v[L - k], 1));
+        }
+    });
+    (void)sub;
+}
+
+// Everything one unit's passes touch.
+struct UnitPtr {
+    const float* phi;       // [W][W] box phase
+    float* gphi;            // [W][W] dL/dphi (0 outside the pupil)
+    float2* h;              // [N][N/2+1]: OTF, then the adjoint seed
+    float2* pf;             // [N x N] field [x][y], or null (recomputed)
+    float2* pp;             // [W][W] phasors, or null (recomputed / not kept)
+    const uint32_t* mask;   // [W][mw] box rows, bit c = pupil pixel at box column c
+    int mw;
+    int W;
+    float inv_z;            // 1 / (N^2 n_pup)
+    const uint32_t* supp;   // [N][sw] OTF-support rows over kx <= N/2
+    int sw;
+};
+
+// PUPIL: the W box columns of P = exp(i phi) (zero-padded to N rows),
+// transformed along y into columns c of B (row stride bs); phasors kept
+// when `keep` and the unit has a buffer. t: thread index in the group.
+template <int N>
+__device__ __forceinline__ void pass_pupil(const UnitPtr& q, float2* B, int bs, bool keep, int t) {
+    constexpr int S = Geo<N>::S, L = Geo<N>::L;
+    const int sub = t % S, li = t / S;
+    for (int c0 = 0; c0 < q.W; c0 += Geo<N>::LINES) {
+        const int c = c0 + li;
+        const bool act = c < q.W;
+        float2 v[L];
+#pragma unroll
+        for (int n = 0; n < L; ++n) {
+            const int y = S * n + sub;
+            float2 val = make_float2(0.f, 0.f);
+            if (act && y < q.W) {
+                if (wbit(q.mask, q.mw, y, c)) val = expi(q.phi[y * q.W + c]);
+                if (keep && q.pp) q.pp[y * q.W + c] = val;
+            }
+            v[n] = val;
+        }
+        line_fft<N, -1>(v, sub);
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < L; ++k) B[(sub * L + k) * bs + c] = v[k];
+        }
+    }
+}
+
+// Forward passes of one unit: PUPIL, FIELD (field kept when q.pf), PSF rows,
+// OTF columns -> q.h (masked by the OTF support, H(0) = 1). E: the group's
+// N x es exchange buffer. Ends with the group's barrier.
+template <int N, class Bar>
+__device__ __forceinline__ void unit_forward(const UnitPtr& q, float2* E, int es, int t, Bar bar) {
+    constexpr int S = Geo<N>::S, L = Geo<N>::L, NH = Geo<N>::NH;
+    float* Ef = reinterpret_cast<float*>(E);
+    const int sub = t % S, li = t / S;
+    pass_pupil<N>(q, E, es, true, t);
+    bar();
+    // FIELD rows: p = F P along x; the PSF row |p|^2 / (N^2 n_pup) as floats
+    for (int y0 = 0; y0 < N; y0 += Geo<N>::LINES) {
+        const int y = y0 + li;
+        const bool act = y < N;
+        float2 v[L];
+#pragma unroll
+        for (int n = 0; n < L; ++n) {
+            const int x = S * n + sub;
+            v[n] = (act && x < q.W) ? E[y * es + x] : make_float2(0.f, 0.f);
+        }
+        line_fft<N, -1>(v, sub);
+        __syncwarp();  // both lanes of the line have read row y
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const int kx = sub * L + k;
+                if (q.pf) q.pf[(size_t)kx * N + y] = v[k];
+                Ef[(size_t)y * 2 * es + kx] = (v[k].x * v[k].x + v[k].y * v[k].y) * q.inv_z;
+            }
+        }
+    }
+    bar();
+    // PSF rows y and y + N/2 as one complex line; split into the two
+    // half spectra (kx <= N/2)
+    for (int y0 = 0; y0 < N / 2; y0 += Geo<N>::LINES) {
+        const int y = y0 + li;
+        const bool act = y < N / 2;
+        float2 v[L], pc[L];
+#pragma unroll
+        for (int n = 0; n < L; ++n) {
+            const int x = S * n + sub;
+            v[n] = act ? make_float2(Ef[(size_t)y * 2 * es + x], Ef[(size_t)(y + N / 2) * 2 * es + x])
+                       : make_float2(0.f, 0.f);
+        }
+        line_fft<N, -1>(v, sub);
+        conj_partners<N>(v, pc, sub);
+        __syncwarp();
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const int kx = sub * L + k;
+                if (kx <= N / 2) {
+                    const float2 a = cscale(cadd(v[k], pc[k]), 0.5f);
+                    const float2 d = cscale(csub(v[k], pc[k]), 0.5f);
+                    E[y * es + kx] = a;
+                    E[(y + N / 2) * es + kx] = make_float2(d.y, -d.x);
+                }
+            }
+        }
+    }
+    bar();
+    // OTF columns kx = 1 .. N/2 - 1; line 0 packs the real columns 0 and N/2
+    for (int l0 = 0; l0 < N / 2; l0 += Geo<N>::LINES) {
+        const int line = l0 + li;
+        const bool act = line < N / 2;
+        const int kx = line;
+        float2 v[L], pc[L];
+#pragma unroll
+        for (int n = 0; n < L; ++n) {
+            const int ky = S * n + sub;
+            if (!act) v[n] = make_float2(0.f, 0.f);
+            else if (kx == 0) v[n] = make_float2(E[ky * es].x, E[ky * es + N / 2].x);
+            else v[n] = E[ky * es + kx];
+        }
+        line_fft<N, -1>(v, sub);
+        conj_partners<N>(v, pc, sub);
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const int ky = sub * L + k;
+                if (kx > 0) {
+                    q.h[ky * NH + kx] = wbit(q.supp, q.sw, ky, kx) ? v[k] : make_float2(0.f, 0.f);
+                } else {
+                    float2 h0 = cscale(cadd(v[k], pc[k]), 0.5f);
+                    const float2 d = cscale(csub(v[k], pc[k]), 0.5f);
+                    float2 hn = make_float2(d.y, -d.x);
+                    if (!wbit(q.supp, q.sw, ky, 0)) h0 = make_float2(0.f, 0.f);
+                    if (!wbit(q.supp, q.sw, ky, N / 2)) hn = make_float2(0.f, 0.f);
+                    if (ky == 0) h0 = make_float2(1.f, 0.f);
+                    q.h[ky * NH] = h0;
+                    q.h[ky * NH + N / 2] = hn;
+                }
+            }
+        }
+    }
+    bar();
+}
+
+// Adjoint passes of one unit: SEED (columns of the seed G in q.h), C2R rows
+// -> g_q, rows of F^H(g_q p), ADJ columns -> q.gphi = 2 Im(conj(P) G_P) on
+// the pupil (0 elsewhere in the box). E2 (row stride es2): RECOMPUTE's
+// buffer for the column transforms of P. Ends with the group's barrier.
+template <int N, bool RECOMPUTE, class Bar>
+__device__ __forceinline__ void unit_adjoint(const UnitPtr& q, float2* E, int es, float2* E2, int es2, int t,
+                                             Bar bar) {
+    constexpr int S = Geo<N>::S, L = Geo<N>::L, NH = Geo<N>::NH;
+    float* Ef = reinterpret_cast<float*>(E);
+    const int sub = t % S, li = t / S;
+    // SEED: conj of the columns of G; line 0 packs the columns 0 and N/2
+    for (int l0 = 0; l0 < N / 2; l0 += Geo<N>::LINES) {
+        const int line = l0 + li;
+        const bool act = line < N / 2;
+        const int kx = line;
+        float2 v[L];
+#pragma unroll
+        for (int n = 0; n < L; ++n) {
+            const int ky = S * n + sub;
+            float2 g = make_float2(0.f, 0.f);
+            if (act) {
+                if (kx == 0) {
+                    const float2 a = q.h[ky * NH], b = q.h[ky * NH + N / 2];
+                    g = make_float2(a.x - b.y, a.y + b.x);  // a + i b
+                } else {
+                    g = q.h[ky * NH + kx];
+                }
+            }
+            v[n] = cconj(g);
+        }
+        line_fft<N, -1>(v, sub);
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < L; ++k) E[(sub * L + k) * es + kx] = cconj(v[k]);  // kx = 0: (T_0, T_N/2), both real
+        }
+    }
+    bar();
+    // C2R rows y and y + N/2: conj of T_y + i T_(y+N/2), Hermitian-extended
+    // along x; g_q rows (2 Re / (N^2 n_pup)) as floats
+    for (int y0 = 0; y0 < N / 2; y0 += Geo<N>::LINES) {
+        const int y = y0 + li;
+        const bool act = y < N / 2;
+        float2 v[L];
+#pragma unroll
+        for (int n = 0; n < L; ++n) {
+            const int x = S * n + sub;
+            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+            if (act) {
+                if (x == 0) {
+                    a = make_float2(E[y * es].x, 0.f);
+                    b = make_float2(E[(y + N / 2) * es].x, 0.f);
+                } else if (x == N / 2) {
+                    a = make_float2(E[y * es].y, 0.f);
+                    b = make_float2(E[(y + N / 2) * es].y, 0.f);
+                } else if (x < N / 2) {
+                    a = E[y * es + x];
+                    b = E[(y + N / 2) * es + x];
+                } else {
+                    a = cconj(E[y * es + N - x]);
+                    b = cconj(E[(y + N / 2) * es + N - x]);
+                }
+            }
+            v[n] = make_float2(a.x - b.y, -(a.y + b.x));  // conj(a + i b)
+        }
+        line_fft<N, -1>(v, sub);
+        __syncwarp();
+        if (act) {
+            const float sc = 2.0f * q.inv_z;
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const int x = sub * L + k;
+                Ef[(size_t)y * 2 * es + x] = v[k].x * sc;
+                Ef[(size_t)(y + N / 2) * 2 * es + x] = -v[k].y * sc;
+            }
+        }
+    }
+    bar();
+    if constexpr (RECOMPUTE) {
+        pass_pupil<N>(q, E2, es2, false, t);
+        bar();
+    }
+    // rows of F^H(g_q p), kept on the box columns x < W
+    for (int y0 = 0; y0 < N; y0 += Geo<N>::LINES) {
+        const int y = y0 + li;
+        const bool act = y < N;
+        float2 v[L];
+        int pos_mul, pos_add;  // output element k sits at x = pos_mul k + pos_add
+        if constexpr (!RECOMPUTE) {
+#pragma unroll
+            for (int n = 0; n < L; ++n) {
+                const int x = S * n + sub;
+                float2 w = make_float2(0.f, 0.f);
+                if (act) {
+                    const float g = Ef[(size_t)y * 2 * es + x];
+                    const float2 pv = q.pf[(size_t)x * N + y];
+                    w = make_float2(g * pv.x, -g * pv.y);  // conj(g_q p)
+                }
+                v[n] = w;
+            }
+            line_fft<N, -1>(v, sub);
+            pos_mul = 1;
+            pos_add = sub * L;
+        } else {
+            // p row y from the recomputed columns (blocked order kx = sub L + k)
+#pragma unroll
+            for (int n = 0; n < L; ++n) {
+                const int x = S * n + sub;
+                v[n] = (act && x < q.W) ? E2[y * es2 + x] : make_float2(0.f, 0.f);
+            }
+            line_fft<N, -1>(v, sub);
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const int kx = sub * L + k;
+                const float g = act ? Ef[(size_t)y * 2 * es + kx] : 0.f;
+                v[k] = make_float2(g * v[k].x, -g * v[k].y);
+            }
+            line_fft_dif<N, -1>(v, sub);
+            pos_mul = S;
+            pos_add = sub;
+        }
+        __syncwarp();
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const int x = pos_mul * k + pos_add;
+                if (x < q.W) E[y * es + x] = cconj(v[k]);
+            }
+        }
+    }
+    bar();
+    // ADJ: box columns of F^H along y; dL/dphi = 2 Im(conj(P) G_P) on the pupil
+    for (int c0 = 0; c0 < q.W; c0 += Geo<N>::LINES) {
+        const int c = c0 + li;
+        const bool act = c < q.W;
+        float2 v[L];
+#pragma unroll
+        for (int n = 0; n < L; ++n) {
+            const int y = S * n + sub;
+            v[n] = act ? cconj(E[y * es + c]) : make_float2(0.f, 0.f);
+        }
+        line_fft<N, -1>(v, sub);
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const int y = sub * L + k;
+                if (y < q.W) {
+                    float gv = 0.f;
+                    if (wbit(q.mask, q.mw, y, c)) {
+                        const float2 pv = q.pp ? q.pp[y * q.W + c] : expi(q.phi[y * q.W + c]);
+                        const float2 g = cconj(v[k]);
+                        gv = 2.0f * (pv.x * g.y - pv.y * g.x);
+                    }
+                    q.gphi[y * q.W + c] = gv;
+                }
+            }
+        }
+    }
+    bar();
+}
+
+// Frame reduction of one (patch, object) by one warp, any patch size: the
+// residual form of Eq. 12 in FP32 with FP64 where it would cancel, Kahan sums
+// per lane and an FP64 warp combine; writes the object (Eq. 11) when `obj`
+// is not null and the adjoint seeds G_j = -w_j conj(O) (D_j - O H_j) over H_j.
+// Returns the (patch, object) loss on every lane.
+struct RedPtr {
+    int N, J, spec_ld;      // spectra / object row stride: N/2 + 1 or N
+    double gamma;
+    const float2* d;        // frame 0 of D; frames N spec_ld apart
+    float2* h;              // frame 0 of H; frames N (N/2 + 1) apart
+    const float* w;         // [J] frame weights
+    const uint32_t* supp;   // [N][sw] OTF support rows
+    int sw;
+    float2* obj;            // [N][spec_ld] or null
+};
+
+__device__ __forceinline__ double reduce_warp(const RedPtr& r, int lane) {
+    const int N = r.N, NH = N / 2 + 1, half = N * NH, J = r.J;
+    const size_t dstride = (size_t)N * r.spec_ld;
+    const float gam = (float)r.gamma;
+    KahanSum acc;
+    for (int f = lane; f < half; f += 32) {
+        const int ky = f / NH, kx = f - ky * NH;
+        const size_t doff = (size_t)ky * r.spec_ld + kx;
+        const float2* dp = r.d + doff;
+        float2* hp = r.h + f;
+        const bool seed = (f != 0) && wbit(r.supp, r.sw, ky, kx);
+        float2 num = make_float2(0.f, 0.f), o;
+        float e = 0.f, qs = 0.f, tval;
+        for (int j = 0; j < J; ++j) {
+            const float2 d = dp[(size_t)j * dstride];
+            const float2 h = hp[(size_t)j * half];
+            const float wj = r.w[j];
+            num.x += wj * (d.x * h.x + d.y * h.y);
+            num.y += wj * (d.y * h.x - d.x * h.y);
+            e += wj * (d.x * d.x + d.y * d.y);
+            qs += wj * (h.x * h.x + h.y * h.y);
+        }
+        qs += gam;
+        const float invq = 1.0f / qs;
+        o = cscale(num, invq);
+        const float t_est = e - (num.x * num.x + num.y * num.y) * invq;
+        if (f != 0 && t_est < kCancel * e) {
+            fp64_frequency(J, dp, dstride, hp, half, r.w, r.gamma, seed, tval, o);
+        } else {
+            float tsum = 0.f;
+            for (int j = 0; j < J; ++j) {
+                const float2 d = dp[(size_t)j * dstride];
+                const float2 h = hp[(size_t)j * half];
+                const float wj = r.w[j];
+                const float2 res = csub(d, cmul(o, h));
+                tsum += wj * (res.x * res.x + res.y * res.y);
+                hp[(size_t)j * half] = seed ? cscale(cmul(cconj(o), res), -wj) : make_float2(0.f, 0.f);
+            }
+            tval = tsum + gam * (o.x * o.x + o.y * o.y);
+        }
+        acc.add((kx == 0 || kx == N / 2) ? tval : 2.0f * tval);
+        if (r.obj) {
+            r.obj[doff] = o;
+            if (r.spec_ld == N && kx > 0 && kx < N / 2) r.obj[(size_t)((N - ky) % N) * N + (N - kx)] = cconj(o);
+        }
+    }
+    double v = (double)acc.s - (double)acc.c;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+}  // namespace unitpass
+}  // namespace mfbd_dev

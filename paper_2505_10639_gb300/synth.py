@@ -78,3 +78,12 @@ def noise(seed, shape, sigma, sub=0):
 
 def uniform(seed, shape, lo=0.0, hi=1.0, sub=0):
     return rng(seed, "misc", sub).uniform(lo, hi, shape)
+
+
+def noise_torch(seed, shape, sigma, sub=0, device="cuda"):
+    """White Gaussian noise drawn on `device` by torch's seeded generator
+    (for fields too large to draw on the host), keyed by (seed, sub)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed((int(seed) * 1000003 + 7919 * int(sub) + _STREAMS["noise"]) & 0x7FFFFFFFFFFFFFFF)
+    return torch.randn(shape, generator=g, device=device, dtype=torch.float64) * sigma
