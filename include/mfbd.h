@@ -239,6 +239,104 @@ int mfbd_plan_read_profile(mfbd_plan_t plan, double* ms, long long* launches, in
 int mfbd_phase_loss_grad_noalloc(const mfbd_plan_desc* desc, const float* phase, const void* spectra,
                                  double* loss, void* object, float* grad_phase, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Uneven batches: many problems of different sizes in one persistent launch
+ * ------------------------------------------------------------------------
+ * A batch holds n problems, each described by an mfbd_plan_desc of its own
+ * (patch size 48, 64, 96 or 128, patches, objects, frames, modes, pupils,
+ * wavelengths, basis, gamma, weights; FP32 precision, half spectra and no
+ * flags). Its loss, Wiener object and dL/da are those of Sec. 2.2.1
+ * (Eqs. 11, 12) with the forward model of Sec. 3.1 (Eqs. 20-22), computed per
+ * problem as mfbd_loss_grad computes them for a plan.
+ *
+ * Caller buffers are the problems' buffers of mfbd_loss_grad packed one after
+ * the other in problem order (mfbd_batch_get_offsets gives each problem's
+ * start, in elements):
+ *   coeffs  dev float      [sum_i P_i J_i M_i]
+ *   spectra dev complex64  [sum_i P_i K_i J_i N_i (N_i/2+1)]
+ *   loss    dev double     [sum_i P_i]
+ *   object  dev complex64  [sum_i P_i K_i N_i (N_i/2+1)] or NULL
+ *   grad    dev float      like coeffs
+ *
+ * One evaluation is one launch of a persistent kernel over a list of work
+ * items (per patch: phases, forward passes per frame, frame reduction,
+ * adjoint passes per frame, modal adjoint), in which an item waits (bounded)
+ * for the items of its patch that it depends on; or, in the staged schedule,
+ * five launches (one per kind of item) that never wait. The schedule (mode,
+ * window of units over which the kinds of item are interleaved, CTAs per SM)
+ * is set by mfbd_batch_set_schedule or chosen by timing in
+ * mfbd_batch_autotune. mfbd_batch_loss_grad does no host synchronisation and
+ * no allocation, so it can be captured in a CUDA graph (a memset node and the
+ * kernel node(s)). Evaluations of one batch must not overlap on the GPU (they
+ * share the batch's scratch and counters). */
+#define MFBD_BATCH_ONE_LAUNCH 0 /* one launch; items wait for their dependencies */
+#define MFBD_BATCH_STAGED 1     /* one launch per kind of item; no waits */
+
+typedef struct mfbd_batch* mfbd_batch_t;
+
+typedef struct {
+    int n_problems;
+    long long n_patches, n_units, n_items;
+    long long coeff_floats, spectra_complex, loss_doubles, object_complex;  /* packed sizes */
+    size_t workspace_bytes;  /* device memory owned by the batch */
+    int mode;                /* MFBD_BATCH_ONE_LAUNCH or MFBD_BATCH_STAGED */
+    int window_units;        /* one-launch interleaving window, 64 px units (0: kind-major) */
+    int ctas_per_sm, max_ctas_per_sm, ctas;
+    int smem_bytes;          /* dynamic shared memory per CTA */
+} mfbd_batch_info;
+
+/* Create a batch from n_problems host descriptors: validates each (as
+ * mfbd_plan_create), builds the pupils, bases (shared between problems with
+ * the same sampling; Zernike sets are shared across mode counts) and OTF
+ * supports on the host, uploads them, allocates the scratch (per unit: OTF
+ * and seed N (N/2+1), field N^2 complex64; phases and dL/dphi on the pupil
+ * box) and the work list, and synchronises `stream` once. The default
+ * schedule is one launch with windows of 8192 units and the most CTAs per
+ * SM that fit. Errors: MFBD_ERR_INVALID_ARG / MFBD_ERR_UNSUPPORTED for a bad
+ * or unsupported descriptor (mfbd_last_error names it), MFBD_ERR_OOM,
+ * MFBD_ERR_CUDA without a usable device. */
+int mfbd_batch_create(mfbd_batch_t* out, const mfbd_plan_desc* problems, int n_problems, void* stream);
+
+/* Release a batch (synchronises the device). NULL is OK. */
+int mfbd_batch_destroy(mfbd_batch_t batch);
+
+int mfbd_batch_get_info(mfbd_batch_t batch, mfbd_batch_info* info);
+
+/* Start of each problem in the packed buffers, host arrays [n_problems] of
+ * element offsets (any may be NULL). */
+int mfbd_batch_get_offsets(mfbd_batch_t batch, long long* coeffs, long long* spectra, long long* loss,
+                           long long* object);
+
+/* Set the schedule: mode MFBD_BATCH_ONE_LAUNCH or MFBD_BATCH_STAGED,
+ * window_units (one launch: the kinds of item of about this many 64 px units
+ * are interleaved with the next window's; <= 0: all items of a kind before
+ * the next kind), ctas_per_sm (1..max_ctas_per_sm, 0: the maximum).
+ * Synchronises the device (the work list is rewritten). */
+int mfbd_batch_set_schedule(mfbd_batch_t batch, int mode, int window_units, int ctas_per_sm);
+
+/* Loss, object (or NULL) and dL/da of every problem (layouts above),
+ * asynchronous on `stream`. A dependency wait that gives up (it cannot in a
+ * correct launch; the bound guards against a fault elsewhere) sets the
+ * batch's error flag, reported by mfbd_batch_check. */
+int mfbd_batch_loss_grad(mfbd_batch_t batch, const float* coeffs, const void* spectra, double* loss,
+                         void* object, float* grad, void* stream);
+
+/* Forward model only (Sec. 3.1, Eqs. 20-22, then H = F s) of every problem:
+ * otf dev complex64, packed like spectra (the same offsets), = H_pkj, e.g. to
+ * synthesise data. Runs the phase and forward-pass items of the schedule. */
+int mfbd_batch_otf(mfbd_batch_t batch, const float* coeffs, void* otf, void* stream);
+
+/* Synchronise `stream`, then MFBD_ERR_TIMEOUT if a wait of an earlier
+ * evaluation gave up (the flag is cleared), else MFBD_OK. */
+int mfbd_batch_check(mfbd_batch_t batch, void* stream);
+
+/* Autotuner: times each candidate schedule (one launch with windows of 0,
+ * 2048, 8192 and 32768 units, and staged; at the most CTAs per SM and one
+ * fewer) on these inputs, `reps` evaluations each after one warm-up, keeps
+ * the fastest and returns. Synchronises; outputs hold the last evaluation. */
+int mfbd_batch_autotune(mfbd_batch_t batch, const float* coeffs, const void* spectra, double* loss,
+                        void* object, float* grad, int reps, void* stream);
+
 /* Static description of a status code (never NULL). */
 const char* mfbd_status_string(int status);
 

@@ -24,6 +24,8 @@ MFBD_FLAG_FULL_SPECTRUM = 0x1
 MFBD_FLAG_SIMT_PROJECTION = 0x2
 MFBD_FLAG_RECOMPUTE_BACKWARD = 0x4
 MFBD_FLAG_GENERIC_KERNELS = 0x8
+MFBD_BATCH_ONE_LAUNCH = 0
+MFBD_BATCH_STAGED = 1
 
 
 class PlanDesc(ctypes.Structure):
@@ -60,6 +62,26 @@ class PlanInfo(ctypes.Structure):
     ]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_problems", ctypes.c_int),
+        ("n_patches", ctypes.c_longlong),
+        ("n_units", ctypes.c_longlong),
+        ("n_items", ctypes.c_longlong),
+        ("coeff_floats", ctypes.c_longlong),
+        ("spectra_complex", ctypes.c_longlong),
+        ("loss_doubles", ctypes.c_longlong),
+        ("object_complex", ctypes.c_longlong),
+        ("workspace_bytes", ctypes.c_size_t),
+        ("mode", ctypes.c_int),
+        ("window_units", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int),
+        ("max_ctas_per_sm", ctypes.c_int),
+        ("ctas", ctypes.c_int),
+        ("smem_bytes", ctypes.c_int),
+    ]
+
+
 _VP = ctypes.c_void_p
 _SIGNATURES = {
     "mfbd_plan_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(PlanDesc), _VP]),
@@ -77,6 +99,17 @@ _SIGNATURES = {
     "mfbd_plan_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "mfbd_plan_read_profile": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
     "mfbd_phase_loss_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(PlanDesc), _VP, _VP, _VP, _VP, _VP, _VP]),
+    "mfbd_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(PlanDesc), ctypes.c_int, _VP]),
+    "mfbd_batch_destroy": (ctypes.c_int, [_VP]),
+    "mfbd_batch_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(BatchInfo)]),
+    "mfbd_batch_get_offsets": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "mfbd_batch_set_schedule": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "mfbd_batch_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "mfbd_batch_otf": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "mfbd_batch_check": (ctypes.c_int, [_VP, _VP]),
+    "mfbd_batch_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
+    "mfbd_test_batch_items": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_longlong,
+                                             _VP]),
 }
 
 _lib = None

@@ -512,6 +512,7 @@ int host_setup(mfbd_plan* p, int chunk, bool with_object) {
 }  // namespace
 
 namespace mfbd_dev {
+int validate_desc(const mfbd_plan_desc* d) { return validate(d); }
 int set_error(int status, const char* why) { return fail(status, why); }
 int set_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
 }  // namespace mfbd_dev

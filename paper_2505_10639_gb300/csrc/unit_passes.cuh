@@ -112,7 +112,9 @@ __device__ __forceinline__ void conj_partners(const float2 (&v)[Geo<N>::L], floa
     (void)sub;
 }
 
-// Everything one unit's passes touch.
+// Everything one unit's passes touch. Per-unit data written by another CTA
+// (phases, OTF / seed, field, phasors) is read through L2 (ld.global.cg):
+// the batched kernel reads it in the launch that writes it.
 struct UnitPtr {
     const float* phi;       // [W][W] box phase
     float* gphi;            // [W][W] dL/dphi (0 outside the pupil)
@@ -143,7 +145,7 @@ __device__ __forceinline__ void pass_pupil(const UnitPtr& q, float2* B, int bs, 
             const int y = S * n + sub;
             float2 val = make_float2(0.f, 0.f);
             if (act && y < q.W) {
-                if (wbit(q.mask, q.mw, y, c)) val = expi(q.phi[y * q.W + c]);
+                if (wbit(q.mask, q.mw, y, c)) val = expi(__ldcg(q.phi + y * q.W + c));
                 if (keep && q.pp) q.pp[y * q.W + c] = val;
             }
             v[n] = val;
@@ -276,10 +278,10 @@ __device__ __forceinline__ void unit_adjoint(const UnitPtr& q, float2* E, int es
             float2 g = make_float2(0.f, 0.f);
             if (act) {
                 if (kx == 0) {
-                    const float2 a = q.h[ky * NH], b = q.h[ky * NH + N / 2];
+                    const float2 a = __ldcg(q.h + ky * NH), b = __ldcg(q.h + ky * NH + N / 2);
                     g = make_float2(a.x - b.y, a.y + b.x);  // a + i b
                 } else {
-                    g = q.h[ky * NH + kx];
+                    g = __ldcg(q.h + ky * NH + kx);
                 }
             }
             v[n] = cconj(g);
@@ -348,7 +350,7 @@ __device__ __forceinline__ void unit_adjoint(const UnitPtr& q, float2* E, int es
                 float2 w = make_float2(0.f, 0.f);
                 if (act) {
                     const float g = Ef[(size_t)y * 2 * es + x];
-                    const float2 pv = q.pf[(size_t)x * N + y];
+                    const float2 pv = __ldcg(q.pf + (size_t)x * N + y);
                     w = make_float2(g * pv.x, -g * pv.y);  // conj(g_q p)
                 }
                 v[n] = w;
@@ -402,7 +404,7 @@ __device__ __forceinline__ void unit_adjoint(const UnitPtr& q, float2* E, int es
                 if (y < q.W) {
                     float gv = 0.f;
                     if (wbit(q.mask, q.mw, y, c)) {
-                        const float2 pv = q.pp ? q.pp[y * q.W + c] : expi(q.phi[y * q.W + c]);
+                        const float2 pv = q.pp ? __ldcg(q.pp + y * q.W + c) : expi(__ldcg(q.phi + y * q.W + c));
                         const float2 g = cconj(v[k]);
                         gv = 2.0f * (pv.x * g.y - pv.y * g.x);
                     }
@@ -445,7 +447,7 @@ __device__ __forceinline__ double reduce_warp(const RedPtr& r, int lane) {
         float e = 0.f, qs = 0.f, tval;
         for (int j = 0; j < J; ++j) {
             const float2 d = dp[(size_t)j * dstride];
-            const float2 h = hp[(size_t)j * half];
+            const float2 h = __ldcg(hp + (size_t)j * half);
             const float wj = r.w[j];
             num.x += wj * (d.x * h.x + d.y * h.y);
             num.y += wj * (d.y * h.x - d.x * h.y);
@@ -462,7 +464,7 @@ __device__ __forceinline__ double reduce_warp(const RedPtr& r, int lane) {
             float tsum = 0.f;
             for (int j = 0; j < J; ++j) {
                 const float2 d = dp[(size_t)j * dstride];
-                const float2 h = hp[(size_t)j * half];
+                const float2 h = __ldcg(hp + (size_t)j * half);
                 const float wj = r.w[j];
                 const float2 res = csub(d, cmul(o, h));
                 tsum += wj * (res.x * res.x + res.y * res.y);

@@ -261,6 +261,168 @@ def phase_loss_grad_noalloc(phase, spectra, n_patches, diams, n_frames, gamma, w
     return loss, grad_phase, obj
 
 
+class Problem:
+    """One problem of a Batch: the arguments of Plan (FP32, half spectra)."""
+
+    def __init__(self, n_pix, n_patches, diams, wavelengths, n_frames, n_modes, basis="zernike",
+                 gamma=1e-3, weights=None, obscuration=0.0, user_basis=None):
+        self.n_pix, self.n_patches, self.n_frames, self.n_modes = n_pix, n_patches, n_frames, n_modes
+        self.diams, self.wavelengths = list(diams), list(wavelengths)
+        self.n_objects = len(diams)
+        self.basis, self.gamma, self.weights, self.obscuration = basis, gamma, weights, obscuration
+        self.user_basis = user_basis
+
+    def desc(self):
+        return _Desc(self.n_pix, self.n_patches, self.diams, self.wavelengths, self.n_frames, self.n_modes,
+                     self.basis, self.gamma, self.weights, self.obscuration, self.user_basis, "fp32", False)
+
+    def coeff_shape(self):
+        return (self.n_patches, self.n_frames, self.n_modes)
+
+    def spectra_shape(self):
+        return (self.n_patches, self.n_objects, self.n_frames, self.n_pix, self.n_pix // 2 + 1)
+
+    def object_shape(self):
+        return (self.n_patches, self.n_objects, self.n_pix, self.n_pix // 2 + 1)
+
+
+class Batch:
+    """An uneven batch (mfbd_batch_*): many problems, one persistent launch.
+
+    Buffers are flat tensors holding the problems' buffers one after the
+    other (``pack`` / ``unpack`` convert from and to per-problem tensors):
+    coeffs and grad float32 [coeff_floats], spectra complex64
+    [spectra_complex], loss float64 [loss_doubles], object complex64
+    [object_complex] (sizes from ``info()``)."""
+
+    def __init__(self, problems, stream=None):
+        self._lib = _lib.load()
+        self.problems = list(problems)
+        self._descs = [p.desc() for p in self.problems]
+        arr = (_lib.PlanDesc * max(1, len(self._descs)))()
+        for i, d in enumerate(self._descs):
+            arr[i] = d.desc
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        handle = ctypes.c_void_p()
+        _lib.check(self._lib.mfbd_batch_create(ctypes.byref(handle), arr, len(self._descs), _stream(stream)),
+                   "mfbd_batch_create")
+        self._h = handle
+        n = len(self.problems)
+        self.offsets = {k: np.zeros(max(1, n), np.int64) for k in ("coeffs", "spectra", "loss", "object")}
+        _lib.check(self._lib.mfbd_batch_get_offsets(self._h, self.offsets["coeffs"].ctypes.data,
+                                                    self.offsets["spectra"].ctypes.data,
+                                                    self.offsets["loss"].ctypes.data,
+                                                    self.offsets["object"].ctypes.data), "mfbd_batch_get_offsets")
+        self._info = self.info()
+
+    def info(self):
+        inf = _lib.BatchInfo()
+        _lib.check(self._lib.mfbd_batch_get_info(self._h, ctypes.byref(inf)), "mfbd_batch_get_info")
+        return {name: getattr(inf, name) for name, _ in _lib.BatchInfo._fields_}
+
+    # ------------------------------------------------------------ packing
+    @staticmethod
+    def pack(tensors, kind=None):
+        """Concatenate per-problem tensors (coeffs or spectra) into one flat tensor."""
+        return torch.cat([t.reshape(-1) for t in tensors]).contiguous()
+
+    def unpack(self, flat, kind):
+        """Split a flat buffer (coeffs, grad, spectra, loss, object) into per-problem views."""
+        shape_of = {"coeffs": Problem.coeff_shape, "grad": Problem.coeff_shape,
+                    "spectra": Problem.spectra_shape, "object": Problem.object_shape,
+                    "loss": lambda p: (p.n_patches,)}[kind]
+        off = self.offsets["coeffs" if kind == "grad" else kind]
+        out = []
+        for i, p in enumerate(self.problems):
+            shp = shape_of(p)
+            n = int(np.prod(shp))
+            out.append(flat[int(off[i]):int(off[i]) + n].view(shp))
+        return out
+
+    # ------------------------------------------------------------ calls
+    def _bufs(self, coeffs, spectra, loss, grad, obj):
+        inf = self._info
+        return (_dev(coeffs, torch.float32, (inf["coeff_floats"],), "coeffs"),
+                _dev(spectra, torch.complex64, (inf["spectra_complex"],), "spectra"),
+                _dev(loss, torch.float64, (inf["loss_doubles"],), "loss"),
+                _dev(obj, torch.complex64, (inf["object_complex"],), "object") if obj is not None else None,
+                _dev(grad, torch.float32, (inf["coeff_floats"],), "grad"))
+
+    def outputs(self, want_object=False):
+        inf = self._info
+        loss = torch.empty(inf["loss_doubles"], dtype=torch.float64, device=self.device)
+        grad = torch.empty(inf["coeff_floats"], dtype=torch.float32, device=self.device)
+        obj = (torch.empty(inf["object_complex"], dtype=torch.complex64, device=self.device)
+               if want_object else None)
+        return loss, grad, obj
+
+    def loss_grad(self, coeffs, spectra, loss=None, grad=None, obj=None, want_object=False, stream=None):
+        """mfbd_batch_loss_grad -> (loss, grad, object or None), flat."""
+        if loss is None or grad is None or (want_object and obj is None):
+            l2, g2, o2 = self.outputs(want_object and obj is None)
+            loss = l2 if loss is None else loss
+            grad = g2 if grad is None else grad
+            obj = o2 if obj is None else obj
+        a, d, lo, ob, g = self._bufs(coeffs, spectra, loss, grad, obj)
+        _lib.check(self._lib.mfbd_batch_loss_grad(self._h, a, d, lo, ob, g, _stream(stream)),
+                   "mfbd_batch_loss_grad")
+        return loss, grad, obj
+
+    def otf(self, coeffs, out=None, stream=None):
+        """mfbd_batch_otf -> H of every problem, flat, packed like the spectra."""
+        inf = self._info
+        if out is None:
+            out = torch.empty(inf["spectra_complex"], dtype=torch.complex64, device=self.device)
+        _lib.check(self._lib.mfbd_batch_otf(self._h, _dev(coeffs, torch.float32, (inf["coeff_floats"],), "coeffs"),
+                                            _dev(out, torch.complex64, (inf["spectra_complex"],), "otf"),
+                                            _stream(stream)), "mfbd_batch_otf")
+        return out
+
+    def check(self, stream=None):
+        """mfbd_batch_check: synchronise and raise if a dependency wait gave up."""
+        _lib.check(self._lib.mfbd_batch_check(self._h, _stream(stream)), "mfbd_batch_check")
+
+    def set_schedule(self, mode="one_launch", window_units=0, ctas_per_sm=0):
+        m = {"one_launch": _lib.MFBD_BATCH_ONE_LAUNCH, "staged": _lib.MFBD_BATCH_STAGED}[mode]
+        _lib.check(self._lib.mfbd_batch_set_schedule(self._h, m, int(window_units), int(ctas_per_sm)),
+                   "mfbd_batch_set_schedule")
+        self._info = self.info()
+
+    def autotune(self, coeffs, spectra, loss, grad, obj=None, reps=2, stream=None):
+        """mfbd_batch_autotune: time the candidate schedules, keep the fastest."""
+        a, d, lo, ob, g = self._bufs(coeffs, spectra, loss, grad, obj)
+        _lib.check(self._lib.mfbd_batch_autotune(self._h, a, d, lo, ob, g, int(reps), _stream(stream)),
+                   "mfbd_batch_autotune")
+        self._info = self.info()
+        return self._info
+
+    def capture(self, coeffs, spectra, loss, grad, obj=None):
+        """A CUDA graph of one evaluation on these buffers (the counter
+        memset and the launch(es) of the current schedule); replay() re-runs
+        it."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.loss_grad(coeffs, spectra, loss=loss, grad=grad, obj=obj, stream=side)  # warm-up
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.loss_grad(coeffs, spectra, loss=loss, grad=grad, obj=obj)
+        return graph
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mfbd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class MOMFBDLoss(torch.autograd.Function):
     """loss[P] = MOMFBD loss of every patch as a differentiable function of
     the modal coefficients (spectra are data: no gradient)."""

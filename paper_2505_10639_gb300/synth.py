@@ -87,3 +87,23 @@ def noise_torch(seed, shape, sigma, sub=0, device="cuda"):
     g = torch.Generator(device=device)
     g.manual_seed((int(seed) * 1000003 + 7919 * int(sub) + _STREAMS["noise"]) & 0x7FFFFFFFFFFFFFFF)
     return torch.randn(shape, generator=g, device=device, dtype=torch.float64) * sigma
+
+
+def uneven_problems(seed, n, sizes=(48, 64, 96, 128), objects=(1, 3), frames=(8, 24), modes=(20, 66),
+                    pupil_frac=(0.35, 0.5), wavelength0=6563.0):
+    """Sizes of an uneven batch of n problems (one patch each), drawn
+    uniformly: patch size from `sizes`, objects, frames and modes from the
+    inclusive ranges; each object's pupil diameter 2 round(U(pupil_frac) N / 2)
+    px and its wavelength wavelength0 * D_0 / D_k (pupil diameter in pixels
+    inversely proportional to the wavelength)."""
+    g = rng(seed, "misc", 7)
+    out = []
+    for _ in range(n):
+        npx = int(sizes[g.integers(0, len(sizes))])
+        k = int(g.integers(objects[0], objects[1] + 1))
+        j = int(g.integers(frames[0], frames[1] + 1))
+        m = int(g.integers(modes[0], modes[1] + 1))
+        diams = [float(2 * round(g.uniform(*pupil_frac) * npx / 2)) for _ in range(k)]
+        wls = [wavelength0 * diams[0] / d for d in diams]
+        out.append(dict(n_pix=npx, n_objects=k, n_frames=j, n_modes=m, diams=diams, wavelengths=wls))
+    return out

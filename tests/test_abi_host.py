@@ -183,3 +183,80 @@ def test_noalloc_entry_point_checks_arguments_on_host(lib):
     assert f(ctypes.byref(d.desc), None, None, None, None, None, None) == _lib.MFBD_OK
     d = _desc()
     assert f(ctypes.byref(d.desc), None, None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
+
+
+# ------------------------------------------------------------ batches
+
+def _batch_items(lib, sizes, mode, window):
+    s = np.ascontiguousarray(np.array(sizes, np.int32).reshape(-1, 4))
+    count = ctypes.c_longlong()
+    assert lib.mfbd_test_batch_items(s.ctypes.data, len(s), mode, window, None, 0, ctypes.byref(count)) == 0
+    out = np.zeros((count.value, 5), np.int32)
+    assert lib.mfbd_test_batch_items(s.ctypes.data, len(s), mode, window, out.ctypes.data, count.value,
+                                     ctypes.byref(count)) == 0
+    return out
+
+
+@pytest.mark.parametrize("mode,window", [(_lib.MFBD_BATCH_ONE_LAUNCH, 0), (_lib.MFBD_BATCH_ONE_LAUNCH, 40),
+                                         (_lib.MFBD_BATCH_ONE_LAUNCH, 1), (_lib.MFBD_BATCH_STAGED, 0)])
+def test_batch_work_list_covers_every_unit_once_after_its_dependencies(lib, mode, window):
+    """The batch work list: one phase, reduction and modal-adjoint item per
+    patch, every unit in exactly one forward and one adjoint item (pairs only
+    for N <= 64 and only within one object), and in one-launch mode every
+    item after the items it waits for (the progress argument of the kernel)."""
+    sizes = [(48, 2, 1, 5), (64, 1, 2, 4), (96, 3, 1, 3), (128, 1, 3, 2), (64, 2, 1, 1), (128, 0, 2, 3)]
+    items = _batch_items(lib, sizes, mode, window)
+    pos, seen_f, seen_a = {}, {}, {}
+    for idx, (kind, prob, patch, kj, pair) in enumerate(items):
+        n, p, k_, j_ = sizes[prob]
+        assert 0 <= patch < p
+        if kind in (1, 3):
+            assert pair in (0, 1)
+            if pair:
+                assert n <= 64 and (kj % j_) + 1 < j_
+            for u in range(kj, kj + 1 + pair):
+                d = seen_f if kind == 1 else seen_a
+                assert (prob, patch, u) not in d
+                d[(prob, patch, u)] = idx
+        else:
+            assert (kind, prob, patch) not in pos
+            pos[(kind, prob, patch)] = idx
+    for prob, (n, p, k_, j_) in enumerate(sizes):
+        for patch in range(p):
+            for kind in (0, 2, 4):
+                assert (kind, prob, patch) in pos
+            for u in range(k_ * j_):
+                f, a = seen_f[(prob, patch, u)], seen_a[(prob, patch, u)]
+                if mode == _lib.MFBD_BATCH_ONE_LAUNCH:
+                    assert pos[(0, prob, patch)] < f < pos[(2, prob, patch)] < a < pos[(4, prob, patch)]
+    assert len(seen_f) == sum(p * k * j for _, p, k, j in sizes) == len(seen_a)
+    if mode == _lib.MFBD_BATCH_STAGED:
+        assert list(items[:, 0]) == sorted(items[:, 0])
+
+
+def test_batch_create_validates_without_gpu(lib):
+    out = ctypes.c_void_p()
+    assert lib.mfbd_batch_create(None, None, 0, None) == _lib.MFBD_ERR_INVALID_ARG
+    bad = _desc(n_pix=80, diams=[30.0])
+    assert lib.mfbd_batch_create(ctypes.byref(out), ctypes.byref(bad.desc), 1, None) == _lib.MFBD_ERR_UNSUPPORTED
+    bf = _desc(precision="bf16_phase")
+    assert lib.mfbd_batch_create(ctypes.byref(out), ctypes.byref(bf.desc), 1, None) == _lib.MFBD_ERR_UNSUPPORTED
+    fs = _desc(full_spectrum=True)
+    assert lib.mfbd_batch_create(ctypes.byref(out), ctypes.byref(fs.desc), 1, None) == _lib.MFBD_ERR_UNSUPPORTED
+    if not torch.cuda.is_available():
+        ok = _desc()
+        st = lib.mfbd_batch_create(ctypes.byref(out), ctypes.byref(ok.desc), 1, None)
+        assert st in (_lib.MFBD_ERR_CUDA, _lib.MFBD_ERR_UNSUPPORTED) and not out.value
+
+
+def test_uneven_problem_draws():
+    from paper_2505_10639_gb300 import synth
+    probs = synth.uneven_problems(20250518, 400)
+    assert {p["n_pix"] for p in probs} == {48, 64, 96, 128}
+    for p in probs:
+        assert 1 <= p["n_objects"] <= 3 and 8 <= p["n_frames"] <= 24 and 20 <= p["n_modes"] <= 66
+        assert len(p["diams"]) == p["n_objects"]
+        for d, wl in zip(p["diams"], p["wavelengths"]):
+            assert d % 2 == 0 and 0.35 * p["n_pix"] - 1 <= d <= 0.5 * p["n_pix"] + 1
+            assert abs(d * wl - p["diams"][0] * p["wavelengths"][0]) < 1e-6 * d * wl
+    assert probs == synth.uneven_problems(20250518, 400)
