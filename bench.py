@@ -48,6 +48,9 @@ WORKLOADS = {
                           wavelengths=[8542.0, 8542.0 * 40 / 48, 8542.0 * 40 / 56, 8542.0 * 40 / 64],
                           n_frames=32, n_modes=100, basis="kl", d_over_r0=10.0, noise_sigma=1e-3,
                           precision="bf16_phase", recompute=True, device_noise=True, cpu_patches=16),
+    "batched2000": dict(workload="batched_2000problems_48to128px_1to3obj_8to24frames_20to66zernike",
+                        seed=20250518, n_problems=2000, basis="zernike", d_over_r0=5.0, noise_sigma=1e-3,
+                        n_pix=64, precision="fp32", recompute=False, cpu_patches=32),
 }
 WORKLOAD = dict(WORKLOADS["fov1024_64px"])
 SEED = WORKLOAD["seed"]  # 20250515 + workload index
@@ -481,6 +484,234 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
     return line
 
 
+# ------------------------------------------------------------ uneven batch
+
+def batch_problems(w):
+    from paper_2505_10639_gb300 import synth
+    return synth.uneven_problems(w["seed"], w["n_problems"])
+
+
+def batch_gamma(n_pix, w):
+    return 1e-3 * n_pix ** 2 * w["noise_sigma"] ** 2
+
+
+def batch_units64(probs):
+    return sum(p["n_objects"] * p["n_frames"] * unit_weight_64(p["n_pix"]) for p in probs)
+
+
+def batch_flops(probs):
+    """Algorithmic FP32 flops of one evaluation: the pass flops of every unit
+    (pass_flops_per_unit) plus the phase projection and modal adjoint,
+    2 n_box M flops each per unit (n_box = W^2, the pupil's box)."""
+    from paper_2505_10639_gb300.mfbd import describe_object
+    tot = 0.0
+    cache = {}
+    for p in probs:
+        for k, d in enumerate(p["diams"]):
+            key = (p["n_pix"], d)
+            if key not in cache:
+                mask, _, _, _ = describe_object(0, p["n_pix"], [d], [1.0], 1, 1, basis="zernike")
+                ys, xs = np.nonzero(mask)
+                w_box = int(max(ys.max() - ys.min(), xs.max() - xs.min()) + 1)
+                cache[key] = (int(mask.sum()), w_box)
+            npup, w_box = cache[key]
+            f, a = pass_flops_per_unit(p["n_pix"], npup)
+            tot += p["n_frames"] * (f + a + 4.0 * w_box * w_box * p["n_modes"])
+    return tot
+
+
+def make_batch_inputs(batch, probs, w):
+    """Coefficients (Kolmogorov draws at the evaluation point) and spectra
+    D = F(o) H_true + F(n), built on the device with the batch's own OTF."""
+    import torch
+    from paper_2505_10639_gb300 import synth
+    from paper_2505_10639_gb300.mfbd import Batch, describe_object
+    _, _, var, _ = describe_object(0, 64, [32.0], [1.0], 1, 66, basis="zernike")  # Noll variances, a prefix per M
+    dev = batch.device
+    a_true, a_eval = [], []
+    for i, p in enumerate(probs):
+        v = var[:p["n_modes"]]
+        t = synth.kolmogorov_coeffs(w["seed"], v, w["d_over_r0"], (1, p["n_frames"]), sub=2 * i)
+        e = t + 0.3 * synth.kolmogorov_coeffs(w["seed"], v, w["d_over_r0"], (1, p["n_frames"]), sub=2 * i + 1)
+        a_true.append(torch.from_numpy(t.astype(np.float32)))
+        a_eval.append(torch.from_numpy(e.astype(np.float32)))
+    h = batch.otf(Batch.pack(a_true).to(dev))
+    hs = batch.unpack(h, "spectra")
+    for i, p in enumerate(probs):
+        n, k, j = p["n_pix"], p["n_objects"], p["n_frames"]
+        o = torch.from_numpy(synth.object_field(w["seed"], (1, k, n, n), sub=i)).to(dev)
+        nz = synth.noise_torch(w["seed"], (1, k, j, n, n), w["noise_sigma"], sub=i, device=dev)
+        hs[i].mul_(torch.fft.rfft2(o).to(torch.complex64)[:, :, None]).add_(torch.fft.rfft2(nz).to(torch.complex64))
+    torch.cuda.synchronize()
+    return Batch.pack(a_eval).to(dev), h
+
+
+def _oracle_batch_worker(args):
+    (w, items, barrier, queue) = args
+    from oracle import mfbd as omfbd
+    from oracle import optics
+    from paper_2505_10639_gb300 import synth
+    data = []
+    for i, p in items:
+        n, k, j, m = p["n_pix"], p["n_objects"], p["n_frames"], p["n_modes"]
+        masks = [optics.pupil_mask(n, d) for d in p["diams"]]
+        bases = [optics.zernike_basis(n, d, range(2, m + 2)) for d in p["diams"]]
+        scales = [p["wavelengths"][0] / x for x in p["wavelengths"]]
+        setup = omfbd.Setup(masks, bases, scales, np.ones((k, j)), batch_gamma(n, w))
+        var = optics.mode_variances("zernike", m)
+        t = synth.kolmogorov_coeffs(w["seed"], var, w["d_over_r0"], (1, j), sub=2 * i)
+        e = t + 0.3 * synth.kolmogorov_coeffs(w["seed"], var, w["d_over_r0"], (1, j), sub=2 * i + 1)
+        o = synth.object_field(w["seed"], (1, k, n, n), sub=i)
+        nz = synth.noise(w["seed"], (k, j, n, n), w["noise_sigma"], sub=i)
+        d = omfbd.synth_spectra(setup, t[0], o[0], nz)
+        data.append((setup, e[0].astype(np.float32).astype(np.float64), d.astype(np.complex64).astype(np.complex128),
+                     k * j * unit_weight_64(n)))
+    barrier.wait()
+    t0 = time.time()
+    for setup, a, d, _ in data:
+        omfbd.loss_object_grad_patch(setup, a, d)
+    t1 = time.time()
+    queue.put((t0, t1, len(items), sum(x[3] for x in data)))
+
+
+def run_oracle_batch_sample(w, n_problems, cores):
+    """The FP64 oracle on the first n_problems problems, spread over the
+    host cores (spawned workers); returns 64 px units/s, seconds, problems,
+    workers."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    probs = batch_problems(w)[:n_problems]
+    items = list(enumerate(probs))
+    chunks = [c for c in (items[i::cores] for i in range(cores)) if c]
+    barrier = ctx.Barrier(len(chunks))
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_batch_worker, args=((w, c, barrier, queue),)) for c in chunks]
+    for p in procs:
+        p.start()
+    res = [queue.get() for _ in procs]
+    for p in procs:
+        p.join()
+    t0, t1 = min(r[0] for r in res), max(r[1] for r in res)
+    units = sum(r[3] for r in res)
+    return units / (t1 - t0), t1 - t0, sum(r[2] for r in res), len(chunks)
+
+
+def run_gpu_batch(args, rank, local_rank, world):
+    """One evaluation of the 2000-problem uneven batch per step: the captured
+    CUDA graph of mfbd_batch_loss_grad (counter memset + one persistent
+    launch, or the autotuner's schedule) replayed, inputs resident."""
+    import torch
+    import torch.distributed as dist
+    from paper_2505_10639_gb300.mfbd import Batch, Problem
+
+    torch.cuda.set_device(local_rank)
+    w = dict(WORKLOAD)
+    w["seed"] = w["seed"] + rank
+    probs = batch_problems(w)
+    batch = Batch([Problem(p["n_pix"], 1, p["diams"], p["wavelengths"], p["n_frames"], p["n_modes"],
+                           basis="zernike", gamma=batch_gamma(p["n_pix"], w)) for p in probs])
+    coeffs, spectra = make_batch_inputs(batch, probs, w)
+    loss, grad, _ = batch.outputs()
+    tuned = batch.autotune(coeffs, spectra, loss, grad, reps=2)
+    if args.batch_schedule != "auto":
+        mode, win = args.batch_schedule.split(":") if ":" in args.batch_schedule else (args.batch_schedule, "0")
+        batch.set_schedule(mode, int(win), 0)
+    info = batch.info()
+    graph = batch.capture(coeffs, spectra, loss, grad)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        graph.replay()
+    batch.check()
+    if not np.isfinite(loss.cpu().numpy()).all():
+        raise RuntimeError("non-finite loss")
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    clocks.start()
+    time.sleep(0.2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    batch.check()
+    local_ms = e0.elapsed_time(e1) / args.steps
+    rmax, rsum = (torch_reducers() if world > 1 else (None, None))
+    u64 = batch_units64(probs)
+    ms, _, value = aggregate(local_ms, u64, world, rmax, rsum)
+
+    e2e = None
+    if not args.no_e2e:
+        # through the public API from pinned host buffers: H2D of coefficients
+        # and spectra, the evaluation, D2H of loss and gradient, every step
+        a_h = torch.empty(coeffs.shape, dtype=coeffs.dtype, pin_memory=True)
+        a_h.copy_(coeffs)
+        d_h = torch.empty(spectra.shape, dtype=spectra.dtype, pin_memory=True)
+        d_h.copy_(spectra)
+        l_h = torch.empty(loss.shape, dtype=loss.dtype, pin_memory=True)
+        g_h = torch.empty(grad.shape, dtype=grad.dtype, pin_memory=True)
+        a_d, d_d = torch.empty_like(coeffs), torch.empty_like(spectra)
+
+        def e2e_step():
+            a_d.copy_(a_h, non_blocking=True)
+            d_d.copy_(d_h, non_blocking=True)
+            batch.loss_grad(a_d, d_d, loss=loss, grad=grad)
+            l_h.copy_(loss, non_blocking=True)
+            g_h.copy_(grad, non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms, _, e2e_value = aggregate(f0.elapsed_time(f1) / args.steps, u64, world, rmax, rsum)
+        e2e = {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": coeffs.numel() * 4 + spectra.numel() * 8,
+               "d2h_bytes_per_step": loss.numel() * 8 + grad.numel() * 4}
+
+    peaks = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    alu_peak = fp32_peak_tflops(n_sm, peaks.get("sm_max_mhz", 2070.0))
+    flops = batch_flops(probs)
+    achieved = flops / (local_ms * 1e-3) / 1e12
+    units = sum(p["n_objects"] * p["n_frames"] for p in probs)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["workload"], "problems": len(probs), "units_per_step": units,
+                   "units64_per_step": u64, "problems_per_s": len(probs) / (ms * 1e-3),
+                   "patch_px": sorted({p["n_pix"] for p in probs}), "basis": "zernike",
+                   "schedule": {"mode": ["one_launch", "staged"][info["mode"]], "window_units": info["window_units"],
+                                "ctas_per_sm": info["ctas_per_sm"], "autotuned": args.batch_schedule == "auto"},
+                   "graph": "captured CUDA graph replayed per step",
+                   "l2": "inputs larger than L2 (%.0f MB spectra)" % (spectra.numel() * 8 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": e2e,
+        "roofline": {"bound": "alu", "kernel": "batch_kernel", "achieved": achieved, "peak": alu_peak,
+                     "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                     "traffic_basis": "not captured for this kernel",
+                     "peak_basis": "FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock)"
+                                   % (n_sm, FP32_LANES_PER_SM, peaks.get("sm_max_mhz", 2070.0)),
+                     "work_per_launch": flops, "kernel_ms": local_ms},
+        "gpu_launches": args.steps * (1 if info["mode"] == 0 else 5),
+        "clocks": clk,
+        "batch": {k: info[k] for k in ("n_items", "workspace_bytes", "ctas", "smem_bytes", "max_ctas_per_sm")},
+    }
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -499,11 +730,14 @@ def main():
     ap.add_argument("--e2e-chunks", type=int, default=0,
                     help="patch chunks of the host-buffer call (copies overlap the kernels of other chunks)")
     ap.add_argument("--workload", default="fov1024_64px", choices=sorted(WORKLOADS),
-                    help="fov1024_64px: 961 patches of 64 px (default); fov4096_128px: 3969 patches of 128 px")
+                    help="fov1024_64px: 961 patches of 64 px (default); fov4096_128px: 3969 patches of "
+                         "128 px; batched2000: 2000 uneven problems in one persistent launch")
     ap.add_argument("--kernels", default="pass", choices=["pass", "generic"],
                     help="64 px: the warp-per-unit pass machine or the CTA-per-unit kernels of the other sizes")
     ap.add_argument("--recompute", default=None, choices=["on", "off"],
                     help="recompute the field and phasors in the backward pass (default: the workload's)")
+    ap.add_argument("--batch-schedule", default="auto",
+                    help="batched2000: auto (autotuner), one_launch:<window units> or staged")
     args = ap.parse_args()
     WORKLOAD.clear()
     WORKLOAD.update(WORKLOADS[args.workload])
@@ -526,6 +760,26 @@ def main():
     args.warmup = max(3, args.warmup)
     rank, local_rank, world = dist_env()
 
+    if args.impl == "reference" and args.workload == "batched2000":
+        if rank != 0:
+            return 0
+        cores = os.cpu_count() or 1
+        n = args.cpu_patches or WORKLOAD["cpu_patches"]
+        total_t, total_u = 0.0, 0.0
+        for _ in range(args.steps):
+            rate, t, nprob, used = run_oracle_batch_sample(WORKLOAD, n, cores)
+            total_t += t
+            total_u += rate * t
+        value = total_u / total_t
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOAD["workload"], "precision": "fp64 oracle"},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                                 "sample": "the first %d of %d problems per step" % (n, WORKLOAD["n_problems"])},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
     if args.impl == "reference":
         if rank != 0:
             return 0
@@ -556,6 +810,20 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    if args.workload == "batched2000":
+        line = run_gpu_batch(args, rank, local_rank, world)
+        if rank == 0:
+            if world == 1 and not args.no_cpu_baseline:
+                n = args.cpu_patches or WORKLOAD["cpu_patches"]
+                rate, t, nprob, used = run_oracle_batch_sample(WORKLOAD, n, os.cpu_count() or 1)
+                line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+                                        "sample": "the first %d of %d problems, %.1f s wall"
+                                                  % (nprob, WORKLOAD["n_problems"], t)}
+            print(json.dumps(line))
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
     line = run_gpu(args, rank, local_rank, world)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:

@@ -21,9 +21,12 @@
 // barrier. Larger patches use all 128 threads on one unit.
 //
 // Data written by one CTA and read by another inside the launch (phases,
-// OTFs and seeds, fields, dL/dphi) is read through L2 (ld.global.cg), and
-// every per-unit and per-patch scratch block starts on a 256-byte boundary,
-// so that no L1 line holds a block that another CTA writes later.
+// OTFs and seeds, fields, dL/dphi) is published by the writer's barrier,
+// fence and counter increment and acquired by the reader's thread 0
+// (ld.acquire.gpu, fence) before its CTA barrier: the PTX memory model then
+// orders the readers' plain loads after the writes. Every per-unit and
+// per-patch scratch block also starts on a 256-byte boundary, so no cache
+// line is shared by blocks of different writers.
 #include "batch_internal.h"
 #include "unit_passes.cuh"
 
@@ -162,7 +165,7 @@ __device__ void item_grad(const BatchParams& prm, const BatchProblem& pr, int p)
             for (int i = 0; i < npix; ++i) {
                 const float b = ob.bt[(size_t)i * ob.ldt + m];
 #pragma unroll
-                for (int jj = 0; jj < kJC; ++jj) part[jj] = fmaf(__ldcg(row[jj] + i), b, part[jj]);
+                for (int jj = 0; jj < kJC; ++jj) part[jj] = fmaf(row[jj][i], b, part[jj]);
             }
 #pragma unroll
             for (int jj = 0; jj < kJC; ++jj) acc[jj] = fmaf(ob.scale, part[jj], acc[jj]);

@@ -41,7 +41,7 @@ __device__ __forceinline__ void fp64_frequency(int J, const float2* dp, size_t d
     double nx = 0.0, ny = 0.0, qd = gamma;
     for (int j = 0; j < J; ++j) {
         const float2 d = dp[(size_t)j * dstride];
-        const float2 h = __ldcg(hp + (size_t)j * hstride);
+        const float2 h = hp[(size_t)j * hstride];
         const double wj = w[j];
         nx += wj * ((double)d.x * h.x + (double)d.y * h.y);
         ny += wj * ((double)d.y * h.x - (double)d.x * h.y);
@@ -51,7 +51,7 @@ __device__ __forceinline__ void fp64_frequency(int J, const float2* dp, size_t d
     double tsum = 0.0;
     for (int j = 0; j < J; ++j) {
         const float2 d = dp[(size_t)j * dstride];
-        const float2 h = __ldcg(hp + (size_t)j * hstride);
+        const float2 h = hp[(size_t)j * hstride];
         const double wj = w[j];
         const double rx = (double)d.x - (ox * h.x - oy * h.y);
         const double ry = (double)d.y - (ox * h.y + oy * h.x);

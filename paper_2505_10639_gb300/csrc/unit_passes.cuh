@@ -94,27 +94,19 @@ __device__ __forceinline__ void line_fft_dif(float2 (&v)[Geo<N>::L], int sub) {
     fftreg::fft_line<L, DIR>(v);
 }
 
-// Conjugate partner Z[(N - kx) mod N] of the element k of lane `sub` (which
-// holds kx = sub L + k after line_fft), for every k.
-template <int N>
-__device__ __forceinline__ void conj_partners(const float2 (&v)[Geo<N>::L], float2 (&pc)[Geo<N>::L], int sub) {
+// Conjugate partner conj Z[(N - kx) mod N] of element K of this lane (which
+// holds kx = sub L + K after line_fft). With S = 2 it comes from the pair
+// lane by a shuffle that every lane of the warp executes; the callers take
+// one partner at a time so that no second register array is live.
+template <int N, int K>
+__device__ __forceinline__ float2 conj_partner(const float2 (&v)[Geo<N>::L]) {
     constexpr int S = Geo<N>::S, L = Geo<N>::L;
-    fftreg::static_for<0, L>([&](auto kk) {
-        constexpr int k = decltype(kk)::value;
-        if constexpr (S == 1) {
-            pc[k] = cconj(v[(L - k) % L]);
-        } else if constexpr (k == 0) {
-            pc[k] = cconj(v[0]);  // kx = 0 or N/2: its own partner
-        } else {
-            pc[k] = cconj(shfl_xor2(v[L - k], 1));
-        }
-    });
-    (void)sub;
+    if constexpr (S == 1) return cconj(v[(L - K) % L]);
+    else if constexpr (K == 0) return cconj(v[0]);  // kx = 0 or N/2: its own partner
+    else return cconj(shfl_xor2(v[L - K], 1));
 }
 
-// Everything one unit's passes touch. Per-unit data written by another CTA
-// (phases, OTF / seed, field, phasors) is read through L2 (ld.global.cg):
-// the batched kernel reads it in the launch that writes it.
+// Everything one unit's passes touch.
 struct UnitPtr {
     const float* phi;       // [W][W] box phase
     float* gphi;            // [W][W] dL/dphi (0 outside the pupil)
@@ -145,7 +137,7 @@ __device__ __forceinline__ void pass_pupil(const UnitPtr& q, float2* B, int bs, 
             const int y = S * n + sub;
             float2 val = make_float2(0.f, 0.f);
             if (act && y < q.W) {
-                if (wbit(q.mask, q.mw, y, c)) val = expi(__ldcg(q.phi + y * q.W + c));
+                if (wbit(q.mask, q.mw, y, c)) val = expi(q.phi[y * q.W + c]);
                 if (keep && q.pp) q.pp[y * q.W + c] = val;
             }
             v[n] = val;
@@ -195,7 +187,7 @@ __device__ __forceinline__ void unit_forward(const UnitPtr& q, float2* E, int es
     for (int y0 = 0; y0 < N / 2; y0 += Geo<N>::LINES) {
         const int y = y0 + li;
         const bool act = y < N / 2;
-        float2 v[L], pc[L];
+        float2 v[L];
 #pragma unroll
         for (int n = 0; n < L; ++n) {
             const int x = S * n + sub;
@@ -203,20 +195,18 @@ __device__ __forceinline__ void unit_forward(const UnitPtr& q, float2* E, int es
                        : make_float2(0.f, 0.f);
         }
         line_fft<N, -1>(v, sub);
-        conj_partners<N>(v, pc, sub);
         __syncwarp();
-        if (act) {
-#pragma unroll
-            for (int k = 0; k < L; ++k) {
-                const int kx = sub * L + k;
-                if (kx <= N / 2) {
-                    const float2 a = cscale(cadd(v[k], pc[k]), 0.5f);
-                    const float2 d = cscale(csub(v[k], pc[k]), 0.5f);
-                    E[y * es + kx] = a;
-                    E[(y + N / 2) * es + kx] = make_float2(d.y, -d.x);
-                }
+        fftreg::static_for<0, L>([&](auto kk) {
+            constexpr int k = decltype(kk)::value;
+            const float2 pc = conj_partner<N, k>(v);
+            const int kx = sub * L + k;
+            if (act && kx <= N / 2) {
+                const float2 a = cscale(cadd(v[k], pc), 0.5f);
+                const float2 d = cscale(csub(v[k], pc), 0.5f);
+                E[y * es + kx] = a;
+                E[(y + N / 2) * es + kx] = make_float2(d.y, -d.x);
             }
-        }
+        });
     }
     bar();
     // OTF columns kx = 1 .. N/2 - 1; line 0 packs the real columns 0 and N/2
@@ -224,7 +214,7 @@ __device__ __forceinline__ void unit_forward(const UnitPtr& q, float2* E, int es
         const int line = l0 + li;
         const bool act = line < N / 2;
         const int kx = line;
-        float2 v[L], pc[L];
+        float2 v[L];
 #pragma unroll
         for (int n = 0; n < L; ++n) {
             const int ky = S * n + sub;
@@ -233,16 +223,16 @@ __device__ __forceinline__ void unit_forward(const UnitPtr& q, float2* E, int es
             else v[n] = E[ky * es + kx];
         }
         line_fft<N, -1>(v, sub);
-        conj_partners<N>(v, pc, sub);
-        if (act) {
-#pragma unroll
-            for (int k = 0; k < L; ++k) {
-                const int ky = sub * L + k;
+        fftreg::static_for<0, L>([&](auto kk) {
+            constexpr int k = decltype(kk)::value;
+            const float2 pc = conj_partner<N, k>(v);
+            const int ky = sub * L + k;
+            if (act) {
                 if (kx > 0) {
                     q.h[ky * NH + kx] = wbit(q.supp, q.sw, ky, kx) ? v[k] : make_float2(0.f, 0.f);
                 } else {
-                    float2 h0 = cscale(cadd(v[k], pc[k]), 0.5f);
-                    const float2 d = cscale(csub(v[k], pc[k]), 0.5f);
+                    float2 h0 = cscale(cadd(v[k], pc), 0.5f);
+                    const float2 d = cscale(csub(v[k], pc), 0.5f);
                     float2 hn = make_float2(d.y, -d.x);
                     if (!wbit(q.supp, q.sw, ky, 0)) h0 = make_float2(0.f, 0.f);
                     if (!wbit(q.supp, q.sw, ky, N / 2)) hn = make_float2(0.f, 0.f);
@@ -251,7 +241,7 @@ __device__ __forceinline__ void unit_forward(const UnitPtr& q, float2* E, int es
                     q.h[ky * NH + N / 2] = hn;
                 }
             }
-        }
+        });
     }
     bar();
 }
@@ -278,10 +268,10 @@ __device__ __forceinline__ void unit_adjoint(const UnitPtr& q, float2* E, int es
             float2 g = make_float2(0.f, 0.f);
             if (act) {
                 if (kx == 0) {
-                    const float2 a = __ldcg(q.h + ky * NH), b = __ldcg(q.h + ky * NH + N / 2);
+                    const float2 a = q.h[ky * NH], b = q.h[ky * NH + N / 2];
                     g = make_float2(a.x - b.y, a.y + b.x);  // a + i b
                 } else {
-                    g = __ldcg(q.h + ky * NH + kx);
+                    g = q.h[ky * NH + kx];
                 }
             }
             v[n] = cconj(g);
@@ -350,7 +340,7 @@ __device__ __forceinline__ void unit_adjoint(const UnitPtr& q, float2* E, int es
                 float2 w = make_float2(0.f, 0.f);
                 if (act) {
                     const float g = Ef[(size_t)y * 2 * es + x];
-                    const float2 pv = __ldcg(q.pf + (size_t)x * N + y);
+                    const float2 pv = q.pf[(size_t)x * N + y];
                     w = make_float2(g * pv.x, -g * pv.y);  // conj(g_q p)
                 }
                 v[n] = w;
@@ -404,7 +394,7 @@ __device__ __forceinline__ void unit_adjoint(const UnitPtr& q, float2* E, int es
                 if (y < q.W) {
                     float gv = 0.f;
                     if (wbit(q.mask, q.mw, y, c)) {
-                        const float2 pv = q.pp ? __ldcg(q.pp + y * q.W + c) : expi(__ldcg(q.phi + y * q.W + c));
+                        const float2 pv = q.pp ? q.pp[y * q.W + c] : expi(q.phi[y * q.W + c]);
                         const float2 g = cconj(v[k]);
                         gv = 2.0f * (pv.x * g.y - pv.y * g.x);
                     }
@@ -447,7 +437,7 @@ __device__ __forceinline__ double reduce_warp(const RedPtr& r, int lane) {
         float e = 0.f, qs = 0.f, tval;
         for (int j = 0; j < J; ++j) {
             const float2 d = dp[(size_t)j * dstride];
-            const float2 h = __ldcg(hp + (size_t)j * half);
+            const float2 h = hp[(size_t)j * half];
             const float wj = r.w[j];
             num.x += wj * (d.x * h.x + d.y * h.y);
             num.y += wj * (d.y * h.x - d.x * h.y);
@@ -464,7 +454,7 @@ __device__ __forceinline__ double reduce_warp(const RedPtr& r, int lane) {
             float tsum = 0.f;
             for (int j = 0; j < J; ++j) {
                 const float2 d = dp[(size_t)j * dstride];
-                const float2 h = __ldcg(hp + (size_t)j * half);
+                const float2 h = hp[(size_t)j * half];
                 const float wj = r.w[j];
                 const float2 res = csub(d, cmul(o, h));
                 tsum += wj * (res.x * res.x + res.y * res.y);
