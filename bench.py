@@ -488,7 +488,7 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
 
 def batch_problems(w):
     from paper_2505_10639_gb300 import synth
-    return synth.uneven_problems(w["seed"], w["n_problems"])
+    return synth.uneven_problems(w["seed"], 2000)[: w["n_problems"]]
 
 
 def batch_gamma(n_pix, w):
@@ -612,10 +612,11 @@ def run_gpu_batch(args, rank, local_rank, world):
                            basis="zernike", gamma=batch_gamma(p["n_pix"], w)) for p in probs])
     coeffs, spectra = make_batch_inputs(batch, probs, w)
     loss, grad, _ = batch.outputs()
-    tuned = batch.autotune(coeffs, spectra, loss, grad, reps=2)
-    if args.batch_schedule != "auto":
-        mode, win = args.batch_schedule.split(":") if ":" in args.batch_schedule else (args.batch_schedule, "0")
-        batch.set_schedule(mode, int(win), 0)
+    if args.batch_schedule == "auto":
+        batch.autotune(coeffs, spectra, loss, grad, reps=2)
+    else:
+        parts = args.batch_schedule.split(":") + ["0", "0"]
+        batch.set_schedule(parts[0], int(parts[1]), 0, int(parts[2]))
     info = batch.info()
     graph = batch.capture(coeffs, spectra, loss, grad)
     stream = torch.cuda.current_stream()
@@ -694,7 +695,8 @@ def run_gpu_batch(args, rank, local_rank, world):
                    "units64_per_step": u64, "problems_per_s": len(probs) / (ms * 1e-3),
                    "patch_px": sorted({p["n_pix"] for p in probs}), "basis": "zernike",
                    "schedule": {"mode": ["one_launch", "staged"][info["mode"]], "window_units": info["window_units"],
-                                "ctas_per_sm": info["ctas_per_sm"], "autotuned": args.batch_schedule == "auto"},
+                                "ctas_per_sm": info["ctas_per_sm"], "kernel_variant": info["variant"],
+                                "autotuned": args.batch_schedule == "auto"},
                    "graph": "captured CUDA graph replayed per step",
                    "l2": "inputs larger than L2 (%.0f MB spectra)" % (spectra.numel() * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -736,8 +738,10 @@ def main():
                     help="64 px: the warp-per-unit pass machine or the CTA-per-unit kernels of the other sizes")
     ap.add_argument("--recompute", default=None, choices=["on", "off"],
                     help="recompute the field and phasors in the backward pass (default: the workload's)")
+    ap.add_argument("--problems", type=int, default=0,
+                    help="batched2000: use only the first N problems (smaller profiling cases)")
     ap.add_argument("--batch-schedule", default="auto",
-                    help="batched2000: auto (autotuner), one_launch:<window units> or staged")
+                    help="batched2000: auto (autotuner) or <one_launch|staged>:<window units>:<kernel variant>")
     args = ap.parse_args()
     WORKLOAD.clear()
     WORKLOAD.update(WORKLOADS[args.workload])
@@ -746,6 +750,9 @@ def main():
     if args.precision is None:
         args.precision = WORKLOAD["precision"]
     args.recompute = WORKLOAD["recompute"] if args.recompute is None else (args.recompute == "on")
+    if args.problems and args.workload == "batched2000":
+        WORKLOAD["n_problems"] = args.problems
+        WORKLOAD["workload"] += "_first%d" % args.problems
     if args.patches:
         WORKLOAD["n_patches"] = args.patches
         WORKLOAD["workload"] += "_first%d" % args.patches

@@ -283,6 +283,7 @@ typedef struct {
     int window_units;        /* one-launch interleaving window, 64 px units (0: kind-major) */
     int ctas_per_sm, max_ctas_per_sm, ctas;
     int smem_bytes;          /* dynamic shared memory per CTA */
+    int variant;             /* kernel variant (register budget), see mfbd_batch_set_schedule */
 } mfbd_batch_info;
 
 /* Create a batch from n_problems host descriptors: validates each (as
@@ -310,9 +311,12 @@ int mfbd_batch_get_offsets(mfbd_batch_t batch, long long* coeffs, long long* spe
 /* Set the schedule: mode MFBD_BATCH_ONE_LAUNCH or MFBD_BATCH_STAGED,
  * window_units (one launch: the kinds of item of about this many 64 px units
  * are interleaved with the next window's; <= 0: all items of a kind before
- * the next kind), ctas_per_sm (1..max_ctas_per_sm, 0: the maximum).
- * Synchronises the device (the work list is rewritten). */
-int mfbd_batch_set_schedule(mfbd_batch_t batch, int mode, int window_units, int ctas_per_sm);
+ * the next kind), ctas_per_sm (1..max_ctas_per_sm of the variant, 0: the
+ * maximum), variant (0: the kernel compiled with up to 255 registers a
+ * thread, 2 CTAs of 128 threads per SM; 1: up to 170 registers, 3 CTAs per
+ * SM, the 96 and 128 px passes spilling). Synchronises the device (the work
+ * list is rewritten). */
+int mfbd_batch_set_schedule(mfbd_batch_t batch, int mode, int window_units, int ctas_per_sm, int variant);
 
 /* Loss, object (or NULL) and dL/da of every problem (layouts above),
  * asynchronous on `stream`. A dependency wait that gives up (it cannot in a
@@ -331,8 +335,8 @@ int mfbd_batch_otf(mfbd_batch_t batch, const float* coeffs, void* otf, void* str
 int mfbd_batch_check(mfbd_batch_t batch, void* stream);
 
 /* Autotuner: times each candidate schedule (one launch with windows of 0,
- * 2048, 8192 and 32768 units, and staged; at the most CTAs per SM and one
- * fewer) on these inputs, `reps` evaluations each after one warm-up, keeps
+ * 2048, 8192 and 32768 units, and staged; each kernel variant at its most
+ * CTAs per SM) on these inputs, `reps` evaluations each after one warm-up, keeps
  * the fastest and returns. Synchronises; outputs hold the last evaluation. */
 int mfbd_batch_autotune(mfbd_batch_t batch, const float* coeffs, const void* spectra, double* loss,
                         void* object, float* grad, int reps, void* stream);

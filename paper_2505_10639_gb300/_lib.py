@@ -79,6 +79,7 @@ class BatchInfo(ctypes.Structure):
         ("max_ctas_per_sm", ctypes.c_int),
         ("ctas", ctypes.c_int),
         ("smem_bytes", ctypes.c_int),
+        ("variant", ctypes.c_int),
     ]
 
 
@@ -103,7 +104,7 @@ _SIGNATURES = {
     "mfbd_batch_destroy": (ctypes.c_int, [_VP]),
     "mfbd_batch_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(BatchInfo)]),
     "mfbd_batch_get_offsets": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
-    "mfbd_batch_set_schedule": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "mfbd_batch_set_schedule": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mfbd_batch_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "mfbd_batch_otf": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "mfbd_batch_check": (ctypes.c_int, [_VP, _VP]),

@@ -45,9 +45,9 @@ struct mfbd_batch {
     long long patches = 0, units = 0;
     int es_small = 33, es_large = 65;
     size_t smem = 0;
-    int max_per_sm = 0;
+    int max_per_sm_v[2] = {0, 0};       // CTAs per SM of each kernel variant
     // schedule
-    int mode = MFBD_BATCH_ONE_LAUNCH, window_units = 0, ctas_per_sm = 0;
+    int mode = MFBD_BATCH_ONE_LAUNCH, window_units = 0, ctas_per_sm = 0, variant = 0;
     std::vector<int> stage_begin;       // staged mode: first item of each kind, then the end
     long long n_items = 0;
     // device memory
@@ -89,7 +89,7 @@ void batch_release(mfbd_batch* b) {
 // Relative cost of a unit of size N (for ordering items, largest first).
 int unit_cost(int N) { return N * N; }
 
-// The item list of a schedule. Per patch: P, the F items (frames in pairs
+// The item list of a schedule. Per patch: P, the F items (frames in fours
 // when N <= 64), R, the A items, G. Staged: all P, all F, all R, all A, all
 // G (each a launch). One launch: the patches are cut into windows of about
 // `window` 64 px units (0: one window) and window w's kind s goes into block
@@ -113,9 +113,9 @@ std::vector<BatchItem> build_items(const mfbd_batch* b, int mode, int window, st
             for (int k = 0; k < pr.K; ++k)
                 for (int j = 0; j < pr.J;) {
                     it.kj = k * pr.J + j;
-                    it.pair = (pr.N <= 64 && j + 1 < pr.J) ? 1 : 0;
+                    it.extra = pr.N <= 64 ? std::min(3, pr.J - 1 - j) : 0;
                     out.push_back(it);
-                    j += 1 + it.pair;
+                    j += 1 + it.extra;
                 }
         } else {
             out.push_back(it);
@@ -163,10 +163,13 @@ std::vector<BatchItem> build_items(const mfbd_batch* b, int mode, int window, st
     return items;
 }
 
-int apply_schedule(mfbd_batch* b, int mode, int window, int ctas_per_sm) {
+int apply_schedule(mfbd_batch* b, int mode, int window, int ctas_per_sm, int variant) {
     if (mode != MFBD_BATCH_ONE_LAUNCH && mode != MFBD_BATCH_STAGED)
         return set_error(MFBD_ERR_INVALID_ARG, "unknown batch schedule mode");
-    if (ctas_per_sm < 0 || ctas_per_sm > b->max_per_sm)
+    if (variant != 0 && variant != 1) return set_error(MFBD_ERR_INVALID_ARG, "unknown batch kernel variant");
+    if (b->max_per_sm_v[variant] < 1)
+        return set_error(MFBD_ERR_UNSUPPORTED, "this batch kernel variant does not fit on this device");
+    if (ctas_per_sm < 0 || ctas_per_sm > b->max_per_sm_v[variant])
         return set_error(MFBD_ERR_INVALID_ARG, "ctas_per_sm out of range for this batch");
     std::vector<int> sb;
     std::vector<BatchItem> items = build_items(b, mode, window, &sb);
@@ -178,7 +181,8 @@ int apply_schedule(mfbd_batch* b, int mode, int window, int ctas_per_sm) {
     }
     b->mode = mode;
     b->window_units = mode == MFBD_BATCH_STAGED ? 0 : std::max(0, window);
-    b->ctas_per_sm = ctas_per_sm == 0 ? b->max_per_sm : ctas_per_sm;
+    b->ctas_per_sm = ctas_per_sm == 0 ? b->max_per_sm_v[variant] : ctas_per_sm;
+    b->variant = variant;
     b->stage_begin = sb;
     return MFBD_OK;
 }
@@ -222,7 +226,8 @@ int run_batch(mfbd_batch_t b, const float* coeffs, const void* spectra, double* 
         prm.n_items = (int)b->n_items;
         prm.wait = 1;
         prm.ticket = b->d_ctr + (size_t)b->patches * BC_COUNT;
-        if (e == cudaSuccess) e = launch_batch(prm, (int)std::min<long long>(cap, b->n_items), b->smem, s);
+        if (e == cudaSuccess)
+            e = launch_batch(prm, (int)std::min<long long>(cap, b->n_items), b->smem, b->variant, s);
     } else {
         for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
             if (!((kinds >> st) & 1)) continue;
@@ -230,7 +235,7 @@ int run_batch(mfbd_batch_t b, const float* coeffs, const void* spectra, double* 
             prm.n_items = b->stage_begin[st + 1] - b->stage_begin[st];
             prm.wait = 0;
             prm.ticket = b->d_ctr + (size_t)b->patches * BC_COUNT + st;
-            e = launch_batch(prm, (int)std::min<long long>(cap, std::max(1, prm.n_items)), b->smem, s);
+            e = launch_batch(prm, (int)std::min<long long>(cap, std::max(1, prm.n_items)), b->smem, b->variant, s);
         }
     }
     if (e != cudaSuccess) {
@@ -443,8 +448,10 @@ int mfbd_batch_create(mfbd_batch_t* out, const mfbd_plan_desc* problems, int n_p
         b->smem = batch_smem(b->es_small, b->es_large);
         if (b->smem > (size_t)227 * 1024)
             throw set_error(MFBD_ERR_UNSUPPORTED, "a pupil box is too large for the batch kernel's shared memory");
-        b->max_per_sm = batch_max_ctas_per_sm(b->smem);
-        if (b->max_per_sm < 1) throw set_error(MFBD_ERR_UNSUPPORTED, "the batch kernel does not fit on this device");
+        b->max_per_sm_v[0] = batch_max_ctas_per_sm(b->smem, 0);
+        b->max_per_sm_v[1] = batch_max_ctas_per_sm(b->smem, 1);
+        if (b->max_per_sm_v[0] < 1)
+            throw set_error(MFBD_ERR_UNSUPPORTED, "the batch kernel does not fit on this device");
         // weights, problem table, scratch
         float* d_w = nullptr;
         if ((st = balloc(b, &d_w, (size_t)std::max(1ll, w_total)))) throw st;
@@ -470,7 +477,7 @@ int mfbd_batch_create(mfbd_batch_t* out, const mfbd_plan_desc* problems, int n_p
         if ((e = cudaStreamSynchronize(s))) throw set_cuda_error(e, "batch upload");
         staging.clear();
         // default schedule: one launch, windows of about 8192 64 px units
-        if ((st = apply_schedule(b, MFBD_BATCH_ONE_LAUNCH, 8192, 0))) throw st;
+        if ((st = apply_schedule(b, MFBD_BATCH_ONE_LAUNCH, 8192, 0, 0))) throw st;
     } catch (int status) {
         batch_release(b);
         delete b;
@@ -507,7 +514,8 @@ int mfbd_batch_get_info(mfbd_batch_t b, mfbd_batch_info* info) {
     info->mode = b->mode;
     info->window_units = b->window_units;
     info->ctas_per_sm = b->ctas_per_sm;
-    info->max_ctas_per_sm = b->max_per_sm;
+    info->max_ctas_per_sm = b->max_per_sm_v[b->variant];
+    info->variant = b->variant;
     info->ctas = b->sms * b->ctas_per_sm;
     info->smem_bytes = (int)b->smem;
     return MFBD_OK;
@@ -524,12 +532,12 @@ int mfbd_batch_get_offsets(mfbd_batch_t b, long long* coeffs, long long* spectra
     return MFBD_OK;
 }
 
-int mfbd_batch_set_schedule(mfbd_batch_t b, int mode, int window_units, int ctas_per_sm) {
+int mfbd_batch_set_schedule(mfbd_batch_t b, int mode, int window_units, int ctas_per_sm, int variant) {
     int st = check_batch(b);
     if (st) return st;
     cudaError_t e = cudaDeviceSynchronize();  // no launch may be reading the item list
     if (e != cudaSuccess) return set_cuda_error(e, "synchronise before a schedule change");
-    return apply_schedule(b, mode, window_units, ctas_per_sm);
+    return apply_schedule(b, mode, window_units, ctas_per_sm, variant);
 }
 
 int mfbd_batch_loss_grad(mfbd_batch_t b, const float* coeffs, const void* spectra, double* loss, void* object,
@@ -590,7 +598,7 @@ int mfbd_test_batch_items(const int* sizes, int n, int mode, int window_units, i
         r[1] = v[i].prob;
         r[2] = v[i].patch;
         r[3] = v[i].kj;
-        r[4] = v[i].pair;
+        r[4] = v[i].extra;
     }
     return MFBD_OK;
 }
@@ -602,22 +610,23 @@ int mfbd_batch_autotune(mfbd_batch_t b, const float* coeffs, const void* spectra
     if (reps < 1) reps = 2;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     struct Cand {
-        int mode, window, cps;
+        int mode, window, cps, variant;
     };
     std::vector<Cand> cands;
-    const int mx = b->max_per_sm;
-    for (int cps = mx; cps >= 1 && cps >= mx - 1; --cps) {
-        for (int w : {0, 2048, 8192, 32768}) cands.push_back({MFBD_BATCH_ONE_LAUNCH, w, cps});
-        cands.push_back({MFBD_BATCH_STAGED, 0, cps});
+    for (int v = 0; v < 2; ++v) {
+        const int mx = b->max_per_sm_v[v];
+        if (mx < 1) continue;
+        for (int w : {0, 2048, 8192, 32768}) cands.push_back({MFBD_BATCH_ONE_LAUNCH, w, mx, v});
+        cands.push_back({MFBD_BATCH_STAGED, 0, mx, v});
     }
     if ((int)cands.size() > kMaxSchedules) cands.resize(kMaxSchedules);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    Cand best_c = {b->mode, b->window_units, b->ctas_per_sm};
+    Cand best_c = {b->mode, b->window_units, b->ctas_per_sm, b->variant};
     for (const Cand& c : cands) {
-        if ((st = mfbd_batch_set_schedule(b, c.mode, c.window, c.cps))) break;
+        if ((st = mfbd_batch_set_schedule(b, c.mode, c.window, c.cps, c.variant))) break;
         if ((st = run_loss_grad(b, coeffs, spectra, loss, object, grad, s))) break;  // warm-up
         cudaEventRecord(e0, s);
         for (int r = 0; r < reps && !st; ++r) st = run_loss_grad(b, coeffs, spectra, loss, object, grad, s);
@@ -634,7 +643,7 @@ int mfbd_batch_autotune(mfbd_batch_t b, const float* coeffs, const void* spectra
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st) return st;
-    return mfbd_batch_set_schedule(b, best_c.mode, best_c.window, best_c.cps);
+    return mfbd_batch_set_schedule(b, best_c.mode, best_c.window, best_c.cps, best_c.variant);
 }
 
 }  // extern "C"

@@ -46,9 +46,9 @@ struct BatchProblem {
     BatchObj obj[kMaxObjects];
 };
 
-// Work items. F and A cover one unit (patch, object, frame), or two frames
-// of one (patch, object) when N <= 64 (two 64-thread groups per CTA); P, R
-// and G cover one patch.
+// Work items. F and A cover one unit (patch, object, frame), or up to four
+// frames of one (patch, object) when N <= 64 (one warp per unit); P, R and G
+// cover one patch.
 enum BatchKind : int {
     BK_PROJ = 0,   // phases of every object and frame of a patch (Eq. 22)
     BK_FWD = 1,    // forward passes of a unit (Eqs. 20-21, OTF)
@@ -62,7 +62,7 @@ struct BatchItem {
     int prob;       // problem index
     int patch;      // patch within the problem
     int kj;         // F, A: k * J + j of the first unit; P, R, G: 0
-    int pair;       // F, A: 1 if the item also covers frame j + 1 (N <= 64)
+    int extra;      // F, A: further frames j + 1 .. j + extra in the item (N <= 64: 0..3)
     int pad[3];
 };
 
@@ -92,10 +92,11 @@ struct BatchParams {
 };
 
 size_t batch_smem(int es_small, int es_large);
-// Also sets the kernel's dynamic shared-memory limit to `smem` (required
-// before launch_batch).
-int batch_max_ctas_per_sm(size_t smem);
+// Kernel variants: 0, a register budget of up to 255 a thread (2 CTAs per
+// SM); 1, up to 170 (3 CTAs per SM). Also sets the variant's dynamic
+// shared-memory limit to `smem` (required before launch_batch).
+int batch_max_ctas_per_sm(size_t smem, int variant);
 // One launch of `ctas` CTAs over items [item0, item0 + n_items).
-cudaError_t launch_batch(const BatchParams& prm, int ctas, size_t smem, cudaStream_t s);
+cudaError_t launch_batch(const BatchParams& prm, int ctas, size_t smem, int variant, cudaStream_t s);
 
 }  // namespace mfbd_dev

@@ -16,9 +16,10 @@
 // the host launches each kind's range of the list separately and nothing
 // waits.
 //
-// F and A items of patches of N <= 64 px cover two frames of one (patch,
-// object): the CTA's two 64-thread groups each run one unit with a named
-// barrier. Larger patches use all 128 threads on one unit.
+// F and A items of patches of N <= 64 px cover up to four frames of one
+// (patch, object): each of the CTA's four warps runs one unit on its own
+// exchange buffer with warp synchronisation only. Larger patches use all 128
+// threads on one unit.
 //
 // Data written by one CTA and read by another inside the launch (phases,
 // OTFs and seeds, fields, dL/dphi) is published by the writer's barrier,
@@ -86,24 +87,25 @@ __device__ __forceinline__ UnitPtr batch_unit(const BatchParams& prm, const Batc
     return q;
 }
 
-// F or A item: one unit per 64-thread group (N <= 64, two groups when the
-// item is a pair) or one unit on the whole CTA.
+// F or A item: one unit per warp (N <= 64: up to four frames of one (patch,
+// object), 32 lines per round, warp synchronisation only) or one unit on the
+// whole CTA (N = 96, 128: 64 lines of two lanes per round, CTA barriers).
 template <int N, bool ADJ>
 __device__ void item_unit(const BatchParams& prm, const BatchProblem& pr, const BatchItem& it, float2* smem) {
     const int t = threadIdx.x;
     if constexpr (N <= 64) {
-        const int g = t >> 6, tg = t & 63;
-        if (g == 1 && !it.pair) return;
-        const int kj = it.kj + g, k = kj / pr.J, j = kj - k * pr.J;
+        const int w = t >> 5, lane = t & 31;
+        if (w > it.extra) return;
+        const int kj = it.kj + w, k = kj / pr.J, j = kj - k * pr.J;
         const UnitPtr q = batch_unit<N>(prm, pr, it.patch, k, j);
-        float2* E = smem + (size_t)g * N * prm.es_small;
-        if constexpr (ADJ) unit_adjoint<N, false>(q, E, prm.es_small, nullptr, 0, tg, GroupBar{1 + g, 64});
-        else unit_forward<N>(q, E, prm.es_small, tg, GroupBar{1 + g, 64});
+        float2* E = smem + (size_t)w * N * prm.es_small;
+        if constexpr (ADJ) unit_adjoint<N, 32, false>(q, E, prm.es_small, nullptr, 0, lane, WarpBar{});
+        else unit_forward<N, 32>(q, E, prm.es_small, lane, WarpBar{});
     } else {
         const int k = it.kj / pr.J, j = it.kj - k * pr.J;
         const UnitPtr q = batch_unit<N>(prm, pr, it.patch, k, j);
-        if constexpr (ADJ) unit_adjoint<N, false>(q, smem, prm.es_large, nullptr, 0, t, CtaBar{});
-        else unit_forward<N>(q, smem, prm.es_large, t, CtaBar{});
+        if constexpr (ADJ) unit_adjoint<N, 64, false>(q, smem, prm.es_large, nullptr, 0, t, CtaBar{});
+        else unit_forward<N, 64>(q, smem, prm.es_large, t, CtaBar{});
     }
 }
 
@@ -216,7 +218,11 @@ __device__ void dispatch_unit(const BatchParams& prm, const BatchProblem& pr, co
     }
 }
 
-__global__ void __launch_bounds__(kBT) batch_kernel(const BatchParams prm) {
+// MINB: CTAs per SM the register budget is set for (2: up to 255 registers a
+// thread; 3: up to 170, the 96 and 128 px passes then spill). The autotuner
+// picks one.
+template <int MINB>
+__global__ void __launch_bounds__(kBT, MINB) batch_kernel(const BatchParams prm) {
     extern __shared__ __align__(16) unsigned char bsm[];
     float2* smem = reinterpret_cast<float2*>(bsm);
     __shared__ int s_item, s_ok;
@@ -256,7 +262,7 @@ __global__ void __launch_bounds__(kBT) batch_kernel(const BatchParams prm) {
         __syncthreads();  // the item's writes precede the signal; s_item is free again
         if (prm.wait && threadIdx.x == 0 && it.kind != BK_GRAD) {
             __threadfence();
-            const int n = (it.kind == BK_FWD || it.kind == BK_ADJ) ? 1 + it.pair : 1;
+            const int n = (it.kind == BK_FWD || it.kind == BK_ADJ) ? 1 + it.extra : 1;
             const int slot = it.kind == BK_PROJ ? BC_PROJ : it.kind == BK_FWD ? BC_FWD : it.kind == BK_RED ? BC_RED
                                                                                                       : BC_ADJ;
             atomicAdd(ctr + slot, n);
@@ -267,24 +273,32 @@ __global__ void __launch_bounds__(kBT) batch_kernel(const BatchParams prm) {
 }  // namespace
 
 size_t batch_smem(int es_small, int es_large) {
-    // two 64-pixel groups, one 128-pixel unit, or the P item's coefficient tile
-    const size_t small = (size_t)2 * 64 * es_small * sizeof(float2);
+    // four 64-pixel warps, one 128-pixel unit, or the P item's coefficient tile
+    const size_t small = (size_t)(kBT / 32) * 64 * es_small * sizeof(float2);
     const size_t large = (size_t)128 * es_large * sizeof(float2);
     const size_t proj = (size_t)kJC * 256 * sizeof(float);
     return std::max(std::max(small, large), proj);
 }
 
-int batch_max_ctas_per_sm(size_t smem) {
-    if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+template <int MINB>
+int max_ctas(size_t smem) {
+    if (cudaFuncSetAttribute(batch_kernel<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
         return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBT, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<MINB>, kBT, smem) != cudaSuccess)
+        return 0;
     return per_sm;
 }
 
-cudaError_t launch_batch(const BatchParams& prm, int ctas, size_t smem, cudaStream_t s) {
+int batch_max_ctas_per_sm(size_t smem, int variant) {
+    return variant == 1 ? max_ctas<3>(smem) : max_ctas<2>(smem);
+}
+
+cudaError_t launch_batch(const BatchParams& prm, int ctas, size_t smem, int variant, cudaStream_t s) {
     if (prm.n_items == 0) return cudaSuccess;
-    batch_kernel<<<ctas, kBT, smem, s>>>(prm);
+    if (variant == 1) batch_kernel<3><<<ctas, kBT, smem, s>>>(prm);
+    else batch_kernel<2><<<ctas, kBT, smem, s>>>(prm);
     return cudaGetLastError();
 }
 

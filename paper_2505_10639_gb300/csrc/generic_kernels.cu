@@ -1,6 +1,6 @@
 // Pass and reduction kernels of one problem for the patch sizes other than
 // 64 (48, 96, 128), and for 64 on request: one CTA per unit (patch, object,
-// frame), persistent over the units. The passes themselves (Sec. 3.1,
+// frame), persistent over the units; for N <= 64 the CTA is one warp. The passes themselves (Sec. 3.1,
 // Eqs. 20-22 and their adjoint) are in unit_passes.cuh.
 #include "mfbd_internal.h"
 #include "unit_passes.cuh"
@@ -35,23 +35,40 @@ __device__ __forceinline__ UnitPtr unit_ptr(const GenericParams& prm, long long 
     return q;
 }
 
+// Threads of a CTA: N <= 64, one warp working on one unit at a time (32
+// lines per round, no CTA barrier); N = 96, 128, 128 threads on one unit (64
+// lines of two lanes per round).
 template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) generic_forward_kernel(const GenericParams prm) {
+struct Cta {
+    static constexpr bool WARP = N <= 64;
+    static constexpr int THREADS = WARP ? 32 : Geo<N>::THREADS;
+    static constexpr int LINES = WARP ? 32 : Geo<N>::LINES;
+    static constexpr int MIN_CTAS = WARP ? 12 : 1;  // 12 warps per SM: at most 170 registers a thread
+};
+
+template <int N>
+__global__ void __launch_bounds__(Cta<N>::THREADS, Cta<N>::MIN_CTAS) generic_forward_kernel(const GenericParams prm) {
     extern __shared__ __align__(16) unsigned char gsm[];
     float2* E = reinterpret_cast<float2*>(gsm);
     const long long units = (long long)prm.P * prm.K * prm.J;
-    for (long long u = blockIdx.x; u < units; u += gridDim.x)
-        unit_forward<N>(unit_ptr<N>(prm, u), E, prm.es, threadIdx.x, CtaBar{});
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        if constexpr (Cta<N>::WARP) unit_forward<N, 32>(unit_ptr<N>(prm, u), E, prm.es, threadIdx.x, WarpBar{});
+        else unit_forward<N, 64>(unit_ptr<N>(prm, u), E, prm.es, threadIdx.x, CtaBar{});
+    }
 }
 
 template <int N, bool RECOMPUTE>
-__global__ void __launch_bounds__(Geo<N>::THREADS) generic_adjoint_kernel(const GenericParams prm) {
+__global__ void __launch_bounds__(Cta<N>::THREADS, Cta<N>::MIN_CTAS) generic_adjoint_kernel(const GenericParams prm) {
     extern __shared__ __align__(16) unsigned char gsm[];
     float2* E = reinterpret_cast<float2*>(gsm);
     float2* E2 = E + (size_t)N * prm.es;  // RECOMPUTE: column transforms of P
     const long long units = (long long)prm.P * prm.K * prm.J;
-    for (long long u = blockIdx.x; u < units; u += gridDim.x)
-        unit_adjoint<N, RECOMPUTE>(unit_ptr<N>(prm, u), E, prm.es, E2, prm.es2, threadIdx.x, CtaBar{});
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        if constexpr (Cta<N>::WARP)
+            unit_adjoint<N, 32, RECOMPUTE>(unit_ptr<N>(prm, u), E, prm.es, E2, prm.es2, threadIdx.x, WarpBar{});
+        else
+            unit_adjoint<N, 64, RECOMPUTE>(unit_ptr<N>(prm, u), E, prm.es, E2, prm.es2, threadIdx.x, CtaBar{});
+    }
 }
 
 // One CTA per patch (persistent over patches), one warp per object; the
@@ -112,10 +129,10 @@ cudaError_t launch_generic_forward(const GenericParams& prm, int sms, cudaStream
     if (units == 0) return cudaSuccess;
     const size_t smem = generic_smem(prm.N, prm.es, prm.es2, false);
     switch (prm.N) {
-        case 48: return launch_persistent(generic_forward_kernel<48>, Geo<48>::THREADS, smem, units, sms, prm, s);
-        case 64: return launch_persistent(generic_forward_kernel<64>, Geo<64>::THREADS, smem, units, sms, prm, s);
-        case 96: return launch_persistent(generic_forward_kernel<96>, Geo<96>::THREADS, smem, units, sms, prm, s);
-        case 128: return launch_persistent(generic_forward_kernel<128>, Geo<128>::THREADS, smem, units, sms, prm, s);
+        case 48: return launch_persistent(generic_forward_kernel<48>, Cta<48>::THREADS, smem, units, sms, prm, s);
+        case 64: return launch_persistent(generic_forward_kernel<64>, Cta<64>::THREADS, smem, units, sms, prm, s);
+        case 96: return launch_persistent(generic_forward_kernel<96>, Cta<96>::THREADS, smem, units, sms, prm, s);
+        case 128: return launch_persistent(generic_forward_kernel<128>, Cta<128>::THREADS, smem, units, sms, prm, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -127,8 +144,8 @@ cudaError_t launch_generic_adjoint(const GenericParams& prm, int sms, cudaStream
     const size_t smem = generic_smem(prm.N, prm.es, prm.es2, rec);
 #define MFBD_ADJ(NN)                                                                                            \
     case NN:                                                                                                    \
-        return rec ? launch_persistent(generic_adjoint_kernel<NN, true>, Geo<NN>::THREADS, smem, units, sms, prm, s) \
-                   : launch_persistent(generic_adjoint_kernel<NN, false>, Geo<NN>::THREADS, smem, units, sms, prm, s);
+        return rec ? launch_persistent(generic_adjoint_kernel<NN, true>, Cta<NN>::THREADS, smem, units, sms, prm, s) \
+                   : launch_persistent(generic_adjoint_kernel<NN, false>, Cta<NN>::THREADS, smem, units, sms, prm, s);
     switch (prm.N) {
         MFBD_ADJ(48)
         MFBD_ADJ(64)

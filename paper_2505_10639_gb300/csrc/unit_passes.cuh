@@ -8,11 +8,12 @@
 // decimated samples x[S n + s] of each lane s and, for S = 2, one radix-2
 // stage across the lane pair by shuffles, leaving X[s L + k] in lane s
 // (decimation in time); the decimation-in-frequency twin takes X in that
-// blocked order and leaves x[S m + s]. A group of 64 S threads works on one
-// unit (patch, object, frame), 64 lines per round, with the 2-D transforms
-// exchanged through an N x es buffer in shared memory and the passes
-// separated by the group's barrier (the CTA's, or a named barrier when a CTA
-// runs two groups).
+// blocked order and leaves x[S m + s]. A group of LINES * S threads works on
+// one unit (patch, object, frame), LINES lines per round, with the 2-D
+// transforms exchanged through an N x es buffer in shared memory and the
+// passes separated by the group's barrier: one warp (LINES = 32, N <= 64,
+// __syncwarp), or 128 threads (LINES = 64, N = 96, 128: the CTA's barrier or
+// a named barrier).
 //
 // RECOMPUTE (the adjoint's template flag): the field p = F P and the pupil
 // phasors are not kept by the forward passes; the adjoint recomputes the
@@ -39,7 +40,7 @@ struct Geo {
     static constexpr int S = N > 64 ? 2 : 1;  // lanes per line
     static constexpr int L = N / S;           // points per lane
     static constexpr int NH = N / 2 + 1;
-    static constexpr int LINES = 64;          // lines per round
+    static constexpr int LINES = 64;          // lines per round of a 64 S-thread group
     static constexpr int THREADS = LINES * S;
 };
 
@@ -47,6 +48,9 @@ struct Geo {
 // barrier `id` of a group of n threads (n a multiple of 32).
 struct CtaBar {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct WarpBar {  // a group of one warp (32 lines per round, N <= 64)
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
 };
 struct GroupBar {
     int id, n;
@@ -124,11 +128,11 @@ struct UnitPtr {
 // PUPIL: the W box columns of P = exp(i phi) (zero-padded to N rows),
 // transformed along y into columns c of B (row stride bs); phasors kept
 // when `keep` and the unit has a buffer. t: thread index in the group.
-template <int N>
+template <int N, int LINES>
 __device__ __forceinline__ void pass_pupil(const UnitPtr& q, float2* B, int bs, bool keep, int t) {
     constexpr int S = Geo<N>::S, L = Geo<N>::L;
     const int sub = t % S, li = t / S;
-    for (int c0 = 0; c0 < q.W; c0 += Geo<N>::LINES) {
+    for (int c0 = 0; c0 < q.W; c0 += LINES) {
         const int c = c0 + li;
         const bool act = c < q.W;
         float2 v[L];
@@ -153,15 +157,15 @@ __device__ __forceinline__ void pass_pupil(const UnitPtr& q, float2* B, int bs, 
 // Forward passes of one unit: PUPIL, FIELD (field kept when q.pf), PSF rows,
 // OTF columns -> q.h (masked by the OTF support, H(0) = 1). E: the group's
 // N x es exchange buffer. Ends with the group's barrier.
-template <int N, class Bar>
+template <int N, int LINES, class Bar>
 __device__ __forceinline__ void unit_forward(const UnitPtr& q, float2* E, int es, int t, Bar bar) {
     constexpr int S = Geo<N>::S, L = Geo<N>::L, NH = Geo<N>::NH;
     float* Ef = reinterpret_cast<float*>(E);
     const int sub = t % S, li = t / S;
-    pass_pupil<N>(q, E, es, true, t);
+    pass_pupil<N, LINES>(q, E, es, true, t);
     bar();
     // FIELD rows: p = F P along x; the PSF row |p|^2 / (N^2 n_pup) as floats
-    for (int y0 = 0; y0 < N; y0 += Geo<N>::LINES) {
+    for (int y0 = 0; y0 < N; y0 += LINES) {
         const int y = y0 + li;
         const bool act = y < N;
         float2 v[L];
@@ -184,7 +188,7 @@ __device__ __forceinline__ void unit_forward(const UnitPtr& q, float2* E, int es
     bar();
     // PSF rows y and y + N/2 as one complex line; split into the two
     // half spectra (kx <= N/2)
-    for (int y0 = 0; y0 < N / 2; y0 += Geo<N>::LINES) {
+    for (int y0 = 0; y0 < N / 2; y0 += LINES) {
         const int y = y0 + li;
         const bool act = y < N / 2;
         float2 v[L];
@@ -210,7 +214,7 @@ __device__ __forceinline__ void unit_forward(const UnitPtr& q, float2* E, int es
     }
     bar();
     // OTF columns kx = 1 .. N/2 - 1; line 0 packs the real columns 0 and N/2
-    for (int l0 = 0; l0 < N / 2; l0 += Geo<N>::LINES) {
+    for (int l0 = 0; l0 < N / 2; l0 += LINES) {
         const int line = l0 + li;
         const bool act = line < N / 2;
         const int kx = line;
@@ -250,14 +254,14 @@ __device__ __forceinline__ void unit_forward(const UnitPtr& q, float2* E, int es
 // -> g_q, rows of F^H(g_q p), ADJ columns -> q.gphi = 2 Im(conj(P) G_P) on
 // the pupil (0 elsewhere in the box). E2 (row stride es2): RECOMPUTE's
 // buffer for the column transforms of P. Ends with the group's barrier.
-template <int N, bool RECOMPUTE, class Bar>
+template <int N, int LINES, bool RECOMPUTE, class Bar>
 __device__ __forceinline__ void unit_adjoint(const UnitPtr& q, float2* E, int es, float2* E2, int es2, int t,
                                              Bar bar) {
     constexpr int S = Geo<N>::S, L = Geo<N>::L, NH = Geo<N>::NH;
     float* Ef = reinterpret_cast<float*>(E);
     const int sub = t % S, li = t / S;
     // SEED: conj of the columns of G; line 0 packs the columns 0 and N/2
-    for (int l0 = 0; l0 < N / 2; l0 += Geo<N>::LINES) {
+    for (int l0 = 0; l0 < N / 2; l0 += LINES) {
         const int line = l0 + li;
         const bool act = line < N / 2;
         const int kx = line;
@@ -285,7 +289,7 @@ __device__ __forceinline__ void unit_adjoint(const UnitPtr& q, float2* E, int es
     bar();
     // C2R rows y and y + N/2: conj of T_y + i T_(y+N/2), Hermitian-extended
     // along x; g_q rows (2 Re / (N^2 n_pup)) as floats
-    for (int y0 = 0; y0 < N / 2; y0 += Geo<N>::LINES) {
+    for (int y0 = 0; y0 < N / 2; y0 += LINES) {
         const int y = y0 + li;
         const bool act = y < N / 2;
         float2 v[L];
@@ -324,11 +328,11 @@ __device__ __forceinline__ void unit_adjoint(const UnitPtr& q, float2* E, int es
     }
     bar();
     if constexpr (RECOMPUTE) {
-        pass_pupil<N>(q, E2, es2, false, t);
+        pass_pupil<N, LINES>(q, E2, es2, false, t);
         bar();
     }
     // rows of F^H(g_q p), kept on the box columns x < W
-    for (int y0 = 0; y0 < N; y0 += Geo<N>::LINES) {
+    for (int y0 = 0; y0 < N; y0 += LINES) {
         const int y = y0 + li;
         const bool act = y < N;
         float2 v[L];
@@ -377,7 +381,7 @@ __device__ __forceinline__ void unit_adjoint(const UnitPtr& q, float2* E, int es
     }
     bar();
     // ADJ: box columns of F^H along y; dL/dphi = 2 Im(conj(P) G_P) on the pupil
-    for (int c0 = 0; c0 < q.W; c0 += Geo<N>::LINES) {
+    for (int c0 = 0; c0 < q.W; c0 += LINES) {
         const int c = c0 + li;
         const bool act = c < q.W;
         float2 v[L];

@@ -382,9 +382,9 @@ class Batch:
         """mfbd_batch_check: synchronise and raise if a dependency wait gave up."""
         _lib.check(self._lib.mfbd_batch_check(self._h, _stream(stream)), "mfbd_batch_check")
 
-    def set_schedule(self, mode="one_launch", window_units=0, ctas_per_sm=0):
+    def set_schedule(self, mode="one_launch", window_units=0, ctas_per_sm=0, variant=0):
         m = {"one_launch": _lib.MFBD_BATCH_ONE_LAUNCH, "staged": _lib.MFBD_BATCH_STAGED}[mode]
-        _lib.check(self._lib.mfbd_batch_set_schedule(self._h, m, int(window_units), int(ctas_per_sm)),
+        _lib.check(self._lib.mfbd_batch_set_schedule(self._h, m, int(window_units), int(ctas_per_sm), int(variant)),
                    "mfbd_batch_set_schedule")
         self._info = self.info()
 

@@ -84,16 +84,17 @@ def test_small_uneven_batch_against_oracle(small_batch):
 
 def test_schedules_graph_and_autotune_give_the_same_bits(small_batch):
     """Every item computes the same arithmetic whatever the schedule: one
-    launch with any window, staged launches, a CUDA-graph replay and the
-    autotuned schedule all give identical bits."""
+    launch with any window, staged launches, either kernel variant (register
+    budget), a CUDA-graph replay and the autotuned schedule all give
+    identical bits."""
     b, coeffs, spectra = _make_batch(small_batch)
     ref = [t.cpu() for t in _run(b, coeffs, spectra)]
-    for mode, window, cps in (("one_launch", 0, 0), ("one_launch", 1, 1), ("one_launch", 100000, 0),
-                              ("staged", 0, 0)):
-        b.set_schedule(mode, window, cps)
+    for mode, window, cps, var in (("one_launch", 0, 0, 0), ("one_launch", 1, 1, 0), ("one_launch", 100000, 0, 0),
+                                   ("staged", 0, 0, 0), ("one_launch", 8192, 0, 1), ("staged", 0, 0, 1)):
+        b.set_schedule(mode, window, cps, var)
         out = _run(b, coeffs, spectra)
         for x, y in zip(out, ref):
-            assert torch.equal(x.cpu(), y), (mode, window, cps)
+            assert torch.equal(x.cpu(), y), (mode, window, cps, var)
     loss, grad, obj = b.outputs(want_object=True)
     graph = b.capture(coeffs, spectra, loss, grad, obj)
     for _ in range(2):
