@@ -32,6 +32,8 @@ struct SharedObj {
     float* bt = nullptr;       // [W*W][M]
     uint32_t* mask = nullptr;  // [W][mw]
     uint32_t* supp = nullptr;  // [N][sw]
+    uint64_t* cmask = nullptr; // [W][2] box columns
+    uint64_t* csupp = nullptr; // [N/2+1][2] support columns
 };
 
 }  // namespace
@@ -366,6 +368,18 @@ int mfbd_batch_create(mfbd_batch_t* out, const mfbd_plan_desc* problems, int n_p
             if ((st = balloc(b, &so.mask, mwords))) throw st;
             so.supp = so.mask + (size_t)W * so.mw;
             upload(hm, so.mask, mwords * sizeof(uint32_t));
+            const size_t cwords = (size_t)2 * W + 2 * (n / 2 + 1);
+            staging.emplace_back(cwords * sizeof(uint64_t), 0);
+            uint64_t* hc = reinterpret_cast<uint64_t*>(staging.back().data());
+            for (int yy = 0; yy < W; ++yy)
+                for (int xx = 0; xx < W; ++xx)
+                    if (mask[(size_t)(lo + yy) * n + (lo + xx)]) hc[2 * xx + yy / 64] |= 1ull << (yy % 64);
+            for (int ky = 0; ky < n; ++ky)
+                for (int kx = 0; kx <= n / 2; ++kx)
+                    if (sup[(size_t)ky * (n / 2 + 1) + kx]) hc[2 * W + 2 * kx + ky / 64] |= 1ull << (ky % 64);
+            if ((st = balloc(b, &so.cmask, cwords))) throw st;
+            so.csupp = so.cmask + 2 * W;
+            upload(hc, so.cmask, cwords * sizeof(uint64_t));
             return so;
         };
 
@@ -434,6 +448,8 @@ int mfbd_batch_create(mfbd_batch_t* out, const mfbd_plan_desc* problems, int n_p
                 ob.bt = so.bt;
                 ob.mask = so.mask;
                 ob.supp = so.supp;
+                ob.cmask = so.cmask;
+                ob.csupp = so.csupp;
                 ob.phi_koff = koff;
                 koff += (long long)pr.J * phi_stride(so.W);
                 if (n <= 64) max_small = std::max(max_small, so.W);

@@ -25,6 +25,8 @@ struct BatchObj {
     const float* bt;        // [W*W][ldt] the same, transposed
     const uint32_t* mask;   // [W][mw] box rows
     const uint32_t* supp;   // [N][sw] OTF-support rows over kx <= N/2
+    const uint64_t* cmask;  // [W][2] box columns: bit y = pupil pixel
+    const uint64_t* csupp;  // [N/2+1][2] half-spectrum columns: bit ky = OTF support
     long long phi_koff;     // floats from a patch's phase block to this object's [J][stride(W)]
 };
 

@@ -84,6 +84,8 @@ __device__ __forceinline__ UnitPtr batch_unit(const BatchParams& prm, const Batc
     q.inv_z = ob.inv_z;
     q.supp = ob.supp;
     q.sw = pr.sw;
+    q.cmask = ob.cmask;
+    q.csupp = ob.csupp;
     return q;
 }
 

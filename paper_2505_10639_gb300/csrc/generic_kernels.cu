@@ -32,6 +32,8 @@ __device__ __forceinline__ UnitPtr unit_ptr(const GenericParams& prm, long long 
     q.inv_z = ob.inv_z;
     q.supp = ob.supp;
     q.sw = prm.sw;
+    q.cmask = ob.cmask;
+    q.csupp = ob.csupp;
     return q;
 }
 
@@ -61,7 +63,9 @@ template <int N, bool RECOMPUTE>
 __global__ void __launch_bounds__(Cta<N>::THREADS, Cta<N>::MIN_CTAS) generic_adjoint_kernel(const GenericParams prm) {
     extern __shared__ __align__(16) unsigned char gsm[];
     float2* E = reinterpret_cast<float2*>(gsm);
-    float2* E2 = E + (size_t)N * prm.es;  // RECOMPUTE: column transforms of P
+    // RECOMPUTE: the column transforms of P, in this CTA's global buffer (kept
+    // in L2) so that shared memory holds one exchange buffer
+    float2* E2 = RECOMPUTE ? prm.e2scr + (size_t)blockIdx.x * N * prm.es2 : nullptr;
     const long long units = (long long)prm.P * prm.K * prm.J;
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
         if constexpr (Cta<N>::WARP)
@@ -104,15 +108,24 @@ __global__ void __launch_bounds__(32 * kMaxObjects) generic_reduce_kernel(const 
 }
 
 template <class Kern>
-cudaError_t launch_persistent(Kern kern, int threads, size_t smem, long long units, int sms, const GenericParams& prm,
-                              cudaStream_t s) {
+cudaError_t persistent_ctas(Kern kern, int threads, size_t smem, int sms, long long* ctas) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    long long ctas = (long long)sms * per_sm;
+    *ctas = (long long)sms * per_sm;
+    return cudaSuccess;
+}
+
+template <class Kern>
+cudaError_t launch_persistent(Kern kern, int threads, size_t smem, long long units, int sms, const GenericParams& prm,
+                              cudaStream_t s, int max_ctas = 0) {
+    long long ctas = 0;
+    cudaError_t e = persistent_ctas(kern, threads, smem, sms, &ctas);
+    if (e != cudaSuccess) return e;
+    if (max_ctas > 0 && ctas > max_ctas) ctas = max_ctas;
     if (ctas > units) ctas = units;
     kern<<<(int)ctas, threads, smem, s>>>(prm);
     return cudaGetLastError();
@@ -121,7 +134,23 @@ cudaError_t launch_persistent(Kern kern, int threads, size_t smem, long long uni
 }  // namespace
 
 size_t generic_smem(int N, int es, int es2, bool recompute) {
-    return (size_t)N * es * sizeof(float2) + (recompute ? (size_t)N * es2 * sizeof(float2) : 0);
+    (void)es2;
+    (void)recompute;  // the recompute buffer is in global memory (e2scr)
+    return (size_t)N * es * sizeof(float2);
+}
+
+int generic_adjoint_ctas(int N, int es, int sms) {
+    const size_t smem = generic_smem(N, es, 0, true);
+    long long c = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (N) {
+        case 48: e = persistent_ctas(generic_adjoint_kernel<48, true>, Cta<48>::THREADS, smem, sms, &c); break;
+        case 64: e = persistent_ctas(generic_adjoint_kernel<64, true>, Cta<64>::THREADS, smem, sms, &c); break;
+        case 96: e = persistent_ctas(generic_adjoint_kernel<96, true>, Cta<96>::THREADS, smem, sms, &c); break;
+        case 128: e = persistent_ctas(generic_adjoint_kernel<128, true>, Cta<128>::THREADS, smem, sms, &c); break;
+        default: break;
+    }
+    return e == cudaSuccess ? (int)c : 0;
 }
 
 cudaError_t launch_generic_forward(const GenericParams& prm, int sms, cudaStream_t s) {
@@ -141,10 +170,12 @@ cudaError_t launch_generic_adjoint(const GenericParams& prm, int sms, cudaStream
     const long long units = (long long)prm.P * prm.K * prm.J;
     if (units == 0) return cudaSuccess;
     const bool rec = prm.pscr == nullptr;
+    if (rec && (!prm.e2scr || prm.e2_ctas < 1)) return cudaErrorInvalidValue;
     const size_t smem = generic_smem(prm.N, prm.es, prm.es2, rec);
 #define MFBD_ADJ(NN)                                                                                            \
     case NN:                                                                                                    \
-        return rec ? launch_persistent(generic_adjoint_kernel<NN, true>, Cta<NN>::THREADS, smem, units, sms, prm, s) \
+        return rec ? launch_persistent(generic_adjoint_kernel<NN, true>, Cta<NN>::THREADS, smem, units, sms, prm, s, \
+                                       prm.e2_ctas)                                                              \
                    : launch_persistent(generic_adjoint_kernel<NN, false>, Cta<NN>::THREADS, smem, units, sms, prm, s);
     switch (prm.N) {
         MFBD_ADJ(48)

@@ -42,6 +42,7 @@ struct ObjectData {
     uint64_t* d_mask = nullptr; // [W] box rows, then [N] box columns
     uint32_t* d_gmask = nullptr;  // general sizes: [W][mw] box mask rows
     uint32_t* d_gsupp = nullptr;  // general sizes: [N][sw] OTF-support rows
+    uint64_t* d_gcol = nullptr;   // general sizes: [W][2] box-column mask words, then [N/2+1][2] support columns
     int mw = 0;
     uint64_t* d_supp = nullptr; // [N] rows, then [N] columns of the OTF support
     // tensor-core phase projection: the box basis as BF16 planes in the MMA
@@ -70,6 +71,8 @@ struct mfbd_plan {
     float2* d_gscr = nullptr;   // per unit [P][K][J][N][N/2+1]: OTF, then adjoint seed
     float2* d_pscr = nullptr;   // per unit [P][K][J][N*N]: field
     float2* d_uscr = nullptr;   // per unit [P][K][J][ustride]: pupil phasors on the box
+    float2* d_e2scr = nullptr;  // recompute, CTA-per-unit kernels: per-CTA second buffers [e2_ctas][N * es2]
+    int e2_ctas = 0;
     int ustride = 0;
     long long phi_floats = 0;
     size_t workspace = 0;
@@ -387,6 +390,8 @@ int run_generic(mfbd_plan_t p, int stages, const void* spectra, double* loss, vo
     g.object = static_cast<float2*>(object);
     g.es = p->es;
     g.es2 = p->es2;
+    g.e2scr = p->d_e2scr;
+    g.e2_ctas = p->e2_ctas;
     for (int k = 0; k < p->K; ++k) {
         const ObjectData& o = p->obj[k];
         g.obj[k].W = o.W;
@@ -395,6 +400,8 @@ int run_generic(mfbd_plan_t p, int stages, const void* spectra, double* loss, vo
         g.obj[k].mask = o.d_gmask;
         g.obj[k].mw = o.mw;
         g.obj[k].supp = o.d_gsupp;
+        g.obj[k].cmask = o.d_gcol;
+        g.obj[k].csupp = o.d_gcol ? o.d_gcol + 2 * o.W : nullptr;
     }
     cudaError_t e = cudaSuccess;
     if (stages & ST_FWD) {
@@ -610,6 +617,7 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
         if ((e = cudaMemsetAsync(p->d_err, 0, sizeof(int), s))) throw cuda_fail(e, "clear error flag");
         std::vector<std::vector<uint64_t>> hm(p->K), hs(p->K);
         std::vector<std::vector<uint32_t>> gm(p->K), gs(p->K);
+        std::vector<std::vector<uint64_t>> gc(p->K);
         long long phi_floats = 0;
         int max_box = 1;
         for (int k = 0; k < p->K; ++k) {
@@ -670,6 +678,16 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
                 for (int ky = 0; ky < n; ++ky)
                     for (int kx = 0; kx <= n / 2; ++kx)
                         if (sup[(size_t)ky * (n / 2 + 1) + kx]) gs[k][ky * p->sw + kx / 32] |= 1u << (kx % 32);
+                gc[k].assign((size_t)2 * o.W + 2 * (n / 2 + 1), 0ull);
+                for (int yy = 0; yy < o.W; ++yy)
+                    for (int xx = 0; xx < o.W; ++xx)
+                        if (mask[(size_t)(o.x0 + yy) * n + (o.x0 + xx)]) gc[k][2 * xx + yy / 64] |= 1ull << (yy % 64);
+                for (int ky = 0; ky < n; ++ky)
+                    for (int kx = 0; kx <= n / 2; ++kx)
+                        if (sup[(size_t)ky * (n / 2 + 1) + kx]) gc[k][2 * o.W + 2 * kx + ky / 64] |= 1ull << (ky % 64);
+                if ((st = dev_alloc(p, &o.d_gcol, gc[k].size()))) throw st;
+                if ((e = cudaMemcpyAsync(o.d_gcol, gc[k].data(), gc[k].size() * 8, cudaMemcpyHostToDevice, s)))
+                    throw cuda_fail(e, "upload column masks");
                 if ((st = dev_alloc(p, &o.d_gmask, gm[k].size()))) throw st;
                 if ((st = dev_alloc(p, &o.d_gsupp, gs[k].size()))) throw st;
                 if ((e = cudaMemcpyAsync(o.d_gmask, gm[k].data(), gm[k].size() * 4, cudaMemcpyHostToDevice, s)) ||
@@ -730,6 +748,11 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
             p->es2 = max_box | 1;
             if (generic_smem(n, p->es, p->es2, !keep) > (size_t)227 * 1024)
                 throw fail(MFBD_ERR_UNSUPPORTED, "the pupil box is too large for the shared-memory buffers");
+            if (!keep) {
+                p->e2_ctas = generic_adjoint_ctas(n, p->es, prop.multiProcessorCount);
+                if (p->e2_ctas < 1) throw fail(MFBD_ERR_UNSUPPORTED, "the adjoint kernel does not fit on this device");
+                if ((st = dev_alloc(p, &p->d_e2scr, (size_t)p->e2_ctas * n * p->es2))) throw st;
+            }
             p->geo = FusedGeometry{};
             p->ctas = prop.multiProcessorCount;
         }

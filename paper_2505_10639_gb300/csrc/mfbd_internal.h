@@ -117,6 +117,8 @@ struct GenericObj {
     const uint32_t* mask;   // [W][mw] box rows, bit c = pupil pixel at box column c
     int mw;                 // words per mask row
     const uint32_t* supp;   // [N][sw] OTF support rows over kx <= N/2
+    const uint64_t* cmask;  // [W][2] box columns: bit y = pupil pixel
+    const uint64_t* csupp;  // [N/2+1][2] half-spectrum columns: bit ky = OTF support
 };
 
 struct GenericParams {
@@ -134,11 +136,15 @@ struct GenericParams {
     int spec_ld;            // N/2 + 1 or N
     double* loss;           // [P]
     float2* object;         // [P][K][N][spec_ld] or null
-    int es, es2;            // shared-memory row strides (complex) of the exchange buffers
+    int es, es2;            // row strides (complex) of the exchange buffers
+    float2* e2scr;          // recompute: per-CTA second buffers [ctas][N * es2] in global memory (L2)
+    int e2_ctas;            // CTAs e2scr has room for
     GenericObj obj[kMaxObjects];
 };
 
 size_t generic_smem(int N, int es, int es2, bool recompute);
+// CTAs of the recompute adjoint launch on `sms` SMs (the size of e2scr).
+int generic_adjoint_ctas(int N, int es, int sms);
 cudaError_t launch_generic_forward(const GenericParams& prm, int sms, cudaStream_t s);
 cudaError_t launch_generic_reduction(const GenericParams& prm, int sms, cudaStream_t s);
 cudaError_t launch_generic_adjoint(const GenericParams& prm, int sms, cudaStream_t s);

@@ -63,6 +63,11 @@ __device__ __forceinline__ bool wbit(const uint32_t* rows, int words, int r, int
     return (rows[r * words + (c >> 5)] >> (c & 31)) & 1u;
 }
 
+// Bit i (< 128) of a column held as two 64-bit words.
+__device__ __forceinline__ bool cbit(uint64_t w0, uint64_t w1, int i) {
+    return ((i < 64 ? w0 >> i : w1 >> (i - 64)) & 1ull) != 0;
+}
+
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
@@ -123,6 +128,8 @@ struct UnitPtr {
     float inv_z;            // 1 / (N^2 n_pup)
     const uint32_t* supp;   // [N][sw] OTF-support rows over kx <= N/2
     int sw;
+    const uint64_t* cmask;  // [W][2] box column c: bit y = pupil pixel at box (y, c)
+    const uint64_t* csupp;  // [N/2+1][2] column kx: bit ky = OTF support
 };
 
 // PUPIL: the W box columns of P = exp(i phi) (zero-padded to N rows),
@@ -135,13 +142,14 @@ __device__ __forceinline__ void pass_pupil(const UnitPtr& q, float2* B, int bs, 
     for (int c0 = 0; c0 < q.W; c0 += LINES) {
         const int c = c0 + li;
         const bool act = c < q.W;
+        const uint64_t m0 = act ? q.cmask[2 * c] : 0ull, m1 = act ? q.cmask[2 * c + 1] : 0ull;
         float2 v[L];
 #pragma unroll
         for (int n = 0; n < L; ++n) {
             const int y = S * n + sub;
             float2 val = make_float2(0.f, 0.f);
             if (act && y < q.W) {
-                if (wbit(q.mask, q.mw, y, c)) val = expi(q.phi[y * q.W + c]);
+                if (cbit(m0, m1, y)) val = expi(q.phi[y * q.W + c]);
                 if (keep && q.pp) q.pp[y * q.W + c] = val;
             }
             v[n] = val;
@@ -227,19 +235,21 @@ __device__ __forceinline__ void unit_forward(const UnitPtr& q, float2* E, int es
             else v[n] = E[ky * es + kx];
         }
         line_fft<N, -1>(v, sub);
+        const uint64_t s0 = act ? q.csupp[2 * kx] : 0ull, s1 = act ? q.csupp[2 * kx + 1] : 0ull;
+        const uint64_t n0 = act && kx == 0 ? q.csupp[N] : 0ull, n1 = act && kx == 0 ? q.csupp[N + 1] : 0ull;
         fftreg::static_for<0, L>([&](auto kk) {
             constexpr int k = decltype(kk)::value;
             const float2 pc = conj_partner<N, k>(v);
             const int ky = sub * L + k;
             if (act) {
                 if (kx > 0) {
-                    q.h[ky * NH + kx] = wbit(q.supp, q.sw, ky, kx) ? v[k] : make_float2(0.f, 0.f);
+                    q.h[ky * NH + kx] = cbit(s0, s1, ky) ? v[k] : make_float2(0.f, 0.f);
                 } else {
                     float2 h0 = cscale(cadd(v[k], pc), 0.5f);
                     const float2 d = cscale(csub(v[k], pc), 0.5f);
                     float2 hn = make_float2(d.y, -d.x);
-                    if (!wbit(q.supp, q.sw, ky, 0)) h0 = make_float2(0.f, 0.f);
-                    if (!wbit(q.supp, q.sw, ky, N / 2)) hn = make_float2(0.f, 0.f);
+                    if (!cbit(s0, s1, ky)) h0 = make_float2(0.f, 0.f);
+                    if (!cbit(n0, n1, ky)) hn = make_float2(0.f, 0.f);
                     if (ky == 0) h0 = make_float2(1.f, 0.f);
                     q.h[ky * NH] = h0;
                     q.h[ky * NH + N / 2] = hn;
@@ -392,12 +402,13 @@ __device__ __forceinline__ void unit_adjoint(const UnitPtr& q, float2* E, int es
         }
         line_fft<N, -1>(v, sub);
         if (act) {
+            const uint64_t m0 = q.cmask[2 * c], m1 = q.cmask[2 * c + 1];
 #pragma unroll
             for (int k = 0; k < L; ++k) {
                 const int y = sub * L + k;
                 if (y < q.W) {
                     float gv = 0.f;
-                    if (wbit(q.mask, q.mw, y, c)) {
+                    if (cbit(m0, m1, y)) {
                         const float2 pv = q.pp ? q.pp[y * q.W + c] : expi(q.phi[y * q.W + c]);
                         const float2 g = cconj(v[k]);
                         gv = 2.0f * (pv.x * g.y - pv.y * g.x);
