@@ -23,10 +23,6 @@ extern "C" {
  *   6  complex adjoint, length 64, radix-4 network
  *   7  complex forward, length 48 (three 16-point FFTs and a radix-3 stage)
  *   8  complex adjoint, length 48
- *   9  complex forward, length 32 (two 16-point FFTs and a radix-2 stage)
- *  10  complex adjoint, length 32
- *  11  complex forward, length 24 (three 8-point FFTs and a radix-3 stage)
- *  12  complex adjoint, length 24
  * Forward: X[k] = sum x[n] exp(-2 pi i n k / N); adjoint uses exp(+...).
  * Returns 0 (MFBD_OK) or 1 (MFBD_ERR_INVALID_ARG) for an unknown kind or
  * NULL pointers. */

@@ -106,8 +106,8 @@ __device__ void item_unit(const BatchParams& prm, const BatchProblem& pr, const 
     } else {
         const int k = it.kj / pr.J, j = it.kj - k * pr.J;
         const UnitPtr q = batch_unit<N>(prm, pr, it.patch, k, j);
-        if constexpr (ADJ) unit_adjoint<N, Geo<N>::LINES, false>(q, smem, prm.es_large, nullptr, 0, t, CtaBar{});
-        else unit_forward<N, Geo<N>::LINES>(q, smem, prm.es_large, t, CtaBar{});
+        if constexpr (ADJ) unit_adjoint<N, 64, false>(q, smem, prm.es_large, nullptr, 0, t, CtaBar{});
+        else unit_forward<N, 64>(q, smem, prm.es_large, t, CtaBar{});
     }
 }
 

@@ -220,69 +220,10 @@ MFBD_HD void fft48(float2 (&a)[48]) {
     });
 }
 
-// exp(DIR * 2 pi i K / L) as a constant.
-template <int L, int K, int DIR>
-MFBD_HD float2 twconst() {
-    constexpr int k = ((K % L) + L) % L;
-    constexpr SinCos sc = sincos_2pi(k, L);
-    return make_float2((float)sc.c, (float)(DIR * sc.s));
-}
-
-// In-place 32-point FFT (natural order in and out): 16-point FFTs of the even
-// and odd samples, then X[k] = E[k] + W32^k O[k], X[k + 16] = E[k] - W32^k O[k].
-template <int DIR>
-MFBD_HD void fft32(float2 (&a)[32]) {
-    float2 e[16], o[16];
-    static_for<0, 16>([&](auto i) {
-        constexpr int I = decltype(i)::value;
-        e[I] = a[2 * I];
-        o[I] = a[2 * I + 1];
-    });
-    fft4<16, DIR>(e);
-    fft4<16, DIR>(o);
-    static_for<0, 16>([&](auto kk) {
-        constexpr int k = decltype(kk)::value;
-        const float2 t = twmul<32, k, DIR>(o[k]);
-        a[k] = cadd(e[k], t);
-        a[k + 16] = csub(e[k], t);
-    });
-}
-
-// In-place 24-point FFT (natural order in and out): three 8-point FFTs of
-// x[3n + r], each output twiddled by exp(DIR 2 pi i r k / 24), then a 3-point
-// DFT over r, as fft48.
-template <int DIR>
-MFBD_HD void fft24(float2 (&a)[24]) {
-    float2 b[3][8];
-    static_for<0, 24>([&](auto i) {
-        constexpr int I = decltype(i)::value;
-        b[I % 3][I / 3] = a[I];
-    });
-    fft<8, DIR>(b[0]);
-    fft<8, DIR>(b[1]);
-    fft<8, DIR>(b[2]);
-    constexpr float c3 = -0.5f;
-    constexpr float s3 = (float)(DIR * 0.86602540378443864676);  // DIR sin(2 pi / 3)
-    static_for<0, 8>([&](auto kk) {
-        constexpr int k = decltype(kk)::value;
-        const float2 x0 = b[0][k];
-        const float2 x1 = twmul<24, k, DIR>(b[1][k]);
-        const float2 x2 = twmul<24, 2 * k, DIR>(b[2][k]);
-        const float2 sum = cadd(x1, x2), dif = csub(x1, x2);
-        a[k] = cadd(x0, sum);
-        const float2 m = make_float2(x0.x + c3 * sum.x, x0.y + c3 * sum.y);
-        const float2 r = make_float2(-s3 * dif.y, s3 * dif.x);  // i s3 (x1 - x2)
-        a[k + 8] = cadd(m, r);
-        a[k + 16] = csub(m, r);
-    });
-}
-
-// Length-L line FFT for the line lengths used (24, 32, 48, 64).
+// Length-L line FFT for the line lengths used (48, 64).
 template <int L, int DIR>
 MFBD_HD void fft_line(float2 (&a)[L]) {
     if constexpr (L == 48) fft48<DIR>(a);
-    else if constexpr (L == 24) fft24<DIR>(a);
-    else if constexpr (L == 32) fft32<DIR>(a);
     else fft4<L, DIR>(a);
 }
 

@@ -45,7 +45,7 @@ struct Cta {
     static constexpr bool WARP = N <= 64;
     static constexpr int THREADS = WARP ? 32 : Geo<N>::THREADS;
     static constexpr int LINES = WARP ? 32 : Geo<N>::LINES;
-    static constexpr int MIN_CTAS = WARP ? 12 : 3;  // 12 warps per SM: at most 170 registers a thread
+    static constexpr int MIN_CTAS = WARP ? 12 : 1;  // 12 warps per SM: at most 170 registers a thread
 };
 
 template <int N>
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(Cta<N>::THREADS, Cta<N>::MIN_CTAS) generic_for
     const long long units = (long long)prm.P * prm.K * prm.J;
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
         if constexpr (Cta<N>::WARP) unit_forward<N, 32>(unit_ptr<N>(prm, u), E, prm.es, threadIdx.x, WarpBar{});
-        else unit_forward<N, Geo<N>::LINES>(unit_ptr<N>(prm, u), E, prm.es, threadIdx.x, CtaBar{});
+        else unit_forward<N, 64>(unit_ptr<N>(prm, u), E, prm.es, threadIdx.x, CtaBar{});
     }
 }
 
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(Cta<N>::THREADS, Cta<N>::MIN_CTAS) generic_adj
         if constexpr (Cta<N>::WARP)
             unit_adjoint<N, 32, RECOMPUTE>(unit_ptr<N>(prm, u), E, prm.es, E2, prm.es2, threadIdx.x, WarpBar{});
         else
-            unit_adjoint<N, Geo<N>::LINES, RECOMPUTE>(unit_ptr<N>(prm, u), E, prm.es, E2, prm.es2, threadIdx.x, CtaBar{});
+            unit_adjoint<N, 64, RECOMPUTE>(unit_ptr<N>(prm, u), E, prm.es, E2, prm.es2, threadIdx.x, CtaBar{});
     }
 }
 

@@ -55,24 +55,6 @@ extern "C" int mfbd_test_fft_host(int kind, const float* in, float* out) {
             for (int i = 0; i < 48; ++i) { out[2 * i] = a[i].x; out[2 * i + 1] = a[i].y; }
             return 0;
         }
-        case 9:
-        case 10: {
-            float2 a[32];
-            for (int i = 0; i < 32; ++i) a[i] = make_float2(in[2 * i], in[2 * i + 1]);
-            if (kind == 9) fftreg::fft32<-1>(a);
-            else fftreg::fft32<+1>(a);
-            for (int i = 0; i < 32; ++i) { out[2 * i] = a[i].x; out[2 * i + 1] = a[i].y; }
-            return 0;
-        }
-        case 11:
-        case 12: {
-            float2 a[24];
-            for (int i = 0; i < 24; ++i) a[i] = make_float2(in[2 * i], in[2 * i + 1]);
-            if (kind == 11) fftreg::fft24<-1>(a);
-            else fftreg::fft24<+1>(a);
-            for (int i = 0; i < 24; ++i) { out[2 * i] = a[i].x; out[2 * i + 1] = a[i].y; }
-            return 0;
-        }
         default:
             return 1;
     }

@@ -3,18 +3,17 @@
 // persistent kernel (batch_kernels.cu).
 //
 // The passes are those of Sec. 3.1, Eqs. 20-22 and their adjoint: a line of
-// N points is held by S = 1 (N <= 64) or S = 4 (N = 96, 128) lanes, L = N / S
+// N points is held by S = 1 (N <= 64) or S = 2 (N = 96, 128) lanes, L = N / S
 // points each. A line transform runs a register FFT of L points on the
-// decimated samples x[S n + s] of each lane s and, for S = 4, a twiddle
-// W_N^(s k) and a 4-point DFT across the four lanes by two shuffle stages
-// (radix 2 on lane bit 1, then on lane bit 0), leaving X[s L + k] in lane s
+// decimated samples x[S n + s] of each lane s and, for S = 2, one radix-2
+// stage across the lane pair by shuffles, leaving X[s L + k] in lane s
 // (decimation in time); the decimation-in-frequency twin takes X in that
 // blocked order and leaves x[S m + s]. A group of LINES * S threads works on
 // one unit (patch, object, frame), LINES lines per round, with the 2-D
 // transforms exchanged through an N x es buffer in shared memory and the
 // passes separated by the group's barrier: one warp (LINES = 32, N <= 64,
-// __syncwarp), or 128 threads (32 lines of four lanes, N = 96, 128: the CTA's
-// barrier).
+// __syncwarp), or 128 threads (LINES = 64, N = 96, 128: the CTA's barrier or
+// a named barrier).
 //
 // RECOMPUTE (the adjoint's template flag): the field p = F P and the pupil
 // phasors are not kept by the forward passes; the adjoint recomputes the
@@ -38,11 +37,11 @@ using fftreg::csub;
 
 template <int N>
 struct Geo {
-    static constexpr int S = N > 64 ? 4 : 1;  // lanes per line
-    static constexpr int L = N / S;           // points per lane: 48, 64 (one lane), 24, 32 (four lanes)
+    static constexpr int S = N > 64 ? 2 : 1;  // lanes per line
+    static constexpr int L = N / S;           // points per lane
     static constexpr int NH = N / 2 + 1;
-    static constexpr int LINES = N > 64 ? 32 : 64;  // lines per round of a CTA-wide group
-    static constexpr int THREADS = LINES * S;       // 128 for N > 64
+    static constexpr int LINES = 64;          // lines per round of a 64 S-thread group
+    static constexpr int THREADS = LINES * S;
 };
 
 // Barrier of the threads that work on one unit: the whole CTA, or the named
@@ -73,87 +72,47 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
-// 4-point DFT across the four lanes of a line: lane s holds z_s and leaves
-// with Y_s = sum_r W_4^(r s) z_r (W_4 = exp(DIR 2 pi i / 4)). Radix 2 on lane
-// bit 1 (A = z_r + z_(r+2), B = z_r - z_(r+2) in lanes r and r + 2), then on
-// bit 0: Y_0 = A_0 + A_1, Y_2 = A_0 - A_1, Y_1 = B_0 + W_4 B_1,
-// Y_3 = B_0 - W_4 B_1, each lane receiving the one value it lacks.
-template <int DIR>
-__device__ __forceinline__ float2 xdft4(float2 z, int sub) {
-    const float2 o = shfl_xor2(z, 2);
-    const float2 a = sub < 2 ? cadd(z, o) : cadd(o, z);
-    const float2 b = sub < 2 ? csub(z, o) : csub(o, z);
-    const float2 r = shfl_xor2((sub & 1) ? a : b, 1);  // lanes 0, 2 get A_1; lanes 1, 3 get B_0
-    const float2 wb = DIR < 0 ? make_float2(b.y, -b.x) : make_float2(-b.y, b.x);  // W_4 B
-    switch (sub) {
-        case 0: return cadd(a, r);
-        case 1: return cadd(r, wb);
-        case 2: return csub(a, r);
-        default: return csub(r, wb);
-    }
-}
-
-// v * W_N^(sub K) for the lane's sub (0..3): one complex multiply by a
-// selected constant.
-template <int N, int K, int DIR>
-__device__ __forceinline__ float2 lane_twiddle(float2 v, int sub) {
-    if constexpr (K == 0) {
-        return v;
-    } else {
-        const float2 w1 = fftreg::twconst<N, K, DIR>(), w2 = fftreg::twconst<N, 2 * K, DIR>(),
-                     w3 = fftreg::twconst<N, 3 * K, DIR>();
-        const float2 w = sub == 1 ? w1 : (sub == 2 ? w2 : w3);
-        return sub == 0 ? v : cmul(v, w);
-    }
-}
-
 // Forward (DIR = -1) line transform, decimation in time: lane s holds
 // x[S n + s] on entry and X[s L + k] on exit.
 template <int N, int DIR>
 __device__ __forceinline__ void line_fft(float2 (&v)[Geo<N>::L], int sub) {
     constexpr int S = Geo<N>::S, L = Geo<N>::L;
     fftreg::fft_line<L, DIR>(v);
-    if constexpr (S == 4) {
+    if constexpr (S == 2) {
         fftreg::static_for<0, L>([&](auto kk) {
             constexpr int k = decltype(kk)::value;
-            v[k] = xdft4<DIR>(lane_twiddle<N, k, DIR>(v[k], sub), sub);
+            const float2 t = sub ? fftreg::twmul<N, k, DIR>(v[k]) : v[k];  // lane 1: W^k O[k]
+            const float2 o = shfl_xor2(t, 1);
+            v[k] = sub ? csub(o, t) : cadd(t, o);
         });
     }
 }
 
 // Decimation in frequency: lane s holds X[s L + k] on entry and the
-// transform's x[S m + s] on exit (the 4-point DFT across the lanes, the
-// twiddle, then the lane's L-point FFT).
+// transform's x[S m + s] on exit.
 template <int N, int DIR>
 __device__ __forceinline__ void line_fft_dif(float2 (&v)[Geo<N>::L], int sub) {
     constexpr int S = Geo<N>::S, L = Geo<N>::L;
-    if constexpr (S == 4) {
+    if constexpr (S == 2) {
         fftreg::static_for<0, L>([&](auto kk) {
             constexpr int k = decltype(kk)::value;
-            v[k] = lane_twiddle<N, k, DIR>(xdft4<DIR>(v[k], sub), sub);
+            const float2 o = shfl_xor2(v[k], 1);
+            v[k] = sub ? fftreg::twmul<N, k, DIR>(csub(o, v[k])) : cadd(v[k], o);
         });
     }
     fftreg::fft_line<L, DIR>(v);
 }
 
 // Conjugate partner conj Z[(N - kx) mod N] of element K of this lane (which
-// holds kx = sub L + K after line_fft). With S = 4 it comes from another lane
-// of the line by a shuffle that every lane of the warp executes (K > 0: lane
-// 3 - sub, element L - K; K = 0: lane (4 - sub) mod 4, element 0); the
-// callers take one partner at a time so that no second register array is
-// live.
+// holds kx = sub L + K after line_fft). With S = 2 it comes from the pair
+// lane by a shuffle that every lane of the warp executes; the callers take
+// one partner at a time so that no second register array is live.
 template <int N, int K>
-__device__ __forceinline__ float2 conj_partner(const float2 (&v)[Geo<N>::L], int sub) {
+__device__ __forceinline__ float2 conj_partner(const float2 (&v)[Geo<N>::L]) {
     constexpr int S = Geo<N>::S, L = Geo<N>::L;
-    if constexpr (S == 1) {
-        return cconj(v[(L - K) % L]);
-    } else if constexpr (K == 0) {
-        const int lane = threadIdx.x & 31;
-        const int src = (lane & ~3) | ((4 - sub) & 3);
-        return cconj(make_float2(__shfl_sync(0xffffffffu, v[0].x, src), __shfl_sync(0xffffffffu, v[0].y, src)));
-    } else {
-        return cconj(shfl_xor2(v[L - K], 3));
-    }
+    if constexpr (S == 1) return cconj(v[(L - K) % L]);
+    else if constexpr (K == 0) return cconj(v[0]);  // kx = 0 or N/2: its own partner
+    else return cconj(shfl_xor2(v[L - K], 1));
 }
 
 // Everything one unit's passes touch.
@@ -251,7 +210,7 @@ __device__ __forceinline__ void unit_forward(const UnitPtr& q, float2* E, int es
         __syncwarp();
         fftreg::static_for<0, L>([&](auto kk) {
             constexpr int k = decltype(kk)::value;
-            const float2 pc = conj_partner<N, k>(v, sub);
+            const float2 pc = conj_partner<N, k>(v);
             const int kx = sub * L + k;
             if (act && kx <= N / 2) {
                 const float2 a = cscale(cadd(v[k], pc), 0.5f);
@@ -280,7 +239,7 @@ __device__ __forceinline__ void unit_forward(const UnitPtr& q, float2* E, int es
         const uint64_t n0 = act && kx == 0 ? q.csupp[N] : 0ull, n1 = act && kx == 0 ? q.csupp[N + 1] : 0ull;
         fftreg::static_for<0, L>([&](auto kk) {
             constexpr int k = decltype(kk)::value;
-            const float2 pc = conj_partner<N, k>(v, sub);
+            const float2 pc = conj_partner<N, k>(v);
             const int ky = sub * L + k;
             if (act) {
                 if (kx > 0) {
