@@ -19,7 +19,10 @@
 // F and A items of patches of N <= 64 px cover up to four frames of one
 // (patch, object): each of the CTA's four warps runs one unit on its own
 // exchange buffer with warp synchronisation only. Larger patches use all 128
-// threads on one unit.
+// threads on one unit. Every pass runs as rounds with one register FFT per
+// (patch size, direction) (unit_forward_rounds, unit_adjoint_rounds): the
+// kernel holds all patch sizes and both directions, and the smaller code was
+// measured faster here (18.7 against 20.7 ms on the 2000-problem batch).
 //
 // Data written by one CTA and read by another inside the launch (phases,
 // OTFs and seeds, fields, dL/dphi) is published by the writer's barrier,
@@ -101,13 +104,13 @@ __device__ void item_unit(const BatchParams& prm, const BatchProblem& pr, const 
         const int kj = it.kj + w, k = kj / pr.J, j = kj - k * pr.J;
         const UnitPtr q = batch_unit<N>(prm, pr, it.patch, k, j);
         float2* E = smem + (size_t)w * N * prm.es_small;
-        if constexpr (ADJ) unit_adjoint<N, 32, false>(q, E, prm.es_small, nullptr, 0, lane, WarpBar{});
-        else unit_forward<N, 32>(q, E, prm.es_small, lane, WarpBar{});
+        if constexpr (ADJ) unit_adjoint_rounds<N, 32, false>(q, E, prm.es_small, nullptr, 0, lane, WarpBar{});
+        else unit_forward_rounds<N, 32>(q, E, prm.es_small, lane, WarpBar{});
     } else {
         const int k = it.kj / pr.J, j = it.kj - k * pr.J;
         const UnitPtr q = batch_unit<N>(prm, pr, it.patch, k, j);
-        if constexpr (ADJ) unit_adjoint<N, 64, false>(q, smem, prm.es_large, nullptr, 0, t, CtaBar{});
-        else unit_forward<N, 64>(q, smem, prm.es_large, t, CtaBar{});
+        if constexpr (ADJ) unit_adjoint_rounds<N, 64, false>(q, smem, prm.es_large, nullptr, 0, t, CtaBar{});
+        else unit_forward_rounds<N, 64>(q, smem, prm.es_large, t, CtaBar{});
     }
 }
 

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(Cta<N>::THREADS, Cta<N>::MIN_CTAS) generic_for
     float2* E = reinterpret_cast<float2*>(gsm);
     const long long units = (long long)prm.P * prm.K * prm.J;
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-        if constexpr (Cta<N>::WARP) unit_forward<N, 32>(unit_ptr<N>(prm, u), E, prm.es, threadIdx.x, WarpBar{});
+        if constexpr (Cta<N>::WARP) unit_forward_rounds<N, 32>(unit_ptr<N>(prm, u), E, prm.es, threadIdx.x, WarpBar{});
         else unit_forward<N, 64>(unit_ptr<N>(prm, u), E, prm.es, threadIdx.x, CtaBar{});
     }
 }

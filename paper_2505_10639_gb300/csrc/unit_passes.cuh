@@ -421,6 +421,295 @@ __device__ __forceinline__ void unit_adjoint(const UnitPtr& q, float2* E, int es
     bar();
 }
 
+// The passes of one unit. Forward: PUPIL (box columns of P = exp(i phi),
+// zero-padded, along y), FIELD (rows of p = F P along x; the field is kept
+// when q.pf; the PSF rows |p|^2 / (N^2 n_pup) as floats), PSF (rows y and
+// y + N/2 of the PSF as one complex line, split into two half spectra), OTF
+// (half-spectrum columns -> q.h, masked by the OTF support, H(0) = 1; line 0
+// packs the real columns 0 and N/2). Adjoint: SEED (conj of the columns of
+// the seed G in q.h), C2R (rows y and y + N/2, Hermitian-extended -> the g_q
+// rows 2 Re / (N^2 n_pup) as floats), RPUPIL (recompute only: PUPIL into the
+// second buffer E2), GP (rows of F^H(g_q p) on the box columns), ADJ (box
+// columns of F^H along y -> q.gphi = 2 Im(conj(P) G_P) on the pupil, 0
+// elsewhere in the box).
+enum Pass : int { PS_PUPIL = 0, PS_FIELD, PS_PSF, PS_OTF, PS_SEED, PS_C2R, PS_RPUPIL, PS_GP, PS_ADJ };
+
+__device__ __forceinline__ int pass_lines(int ps, int N, int W) {
+    return (ps == PS_PUPIL || ps == PS_RPUPIL || ps == PS_ADJ) ? W : (ps == PS_FIELD || ps == PS_GP) ? N : N / 2;
+}
+
+// The same forward passes as rounds of LINES lines: each round loads one
+// line per lane group (a branch on the pass), runs the one register FFT of
+// this function and stores (a branch on the pass), so the unrolled FFT
+// exists once in the code: smaller code, at the price of pass-generic
+// register allocation. Measured on GB300: faster for N <= 64 forward passes
+// and inside the batched kernel; slower for N = 96, 128 and for the N <= 64
+// adjoint on their own kernels. E: the group's N x es exchange buffer; t: thread index in the
+// group. Each pass ends with the group's barrier.
+template <int N, int LINES, class Bar>
+__device__ __forceinline__ void unit_forward_rounds(const UnitPtr& q, float2* E, int es, int t, Bar bar) {
+    constexpr int S = Geo<N>::S, L = Geo<N>::L, NH = Geo<N>::NH;
+    float* Ef = reinterpret_cast<float*>(E);
+    const int sub = t % S, li = t / S;
+    const int W = q.W;
+#pragma unroll 1
+    for (int ps = PS_PUPIL; ps <= PS_OTF; ++ps) {
+        const int lines = pass_lines(ps, N, W);
+#pragma unroll 1
+        for (int l0 = 0; l0 < lines; l0 += LINES) {
+            const int line = l0 + li;
+            const bool act = line < lines;
+            float2 v[L];
+            if (ps == PS_PUPIL) {
+                const uint64_t m0 = act ? q.cmask[2 * line] : 0ull, m1 = act ? q.cmask[2 * line + 1] : 0ull;
+#pragma unroll
+                for (int n = 0; n < L; ++n) {
+                    const int y = S * n + sub;
+                    float2 val = make_float2(0.f, 0.f);
+                    if (act && y < W) {
+                        if (cbit(m0, m1, y)) val = expi(q.phi[y * W + line]);
+                        if (q.pp) q.pp[y * W + line] = val;
+                    }
+                    v[n] = val;
+                }
+            } else if (ps == PS_FIELD) {
+#pragma unroll
+                for (int n = 0; n < L; ++n) {
+                    const int x = S * n + sub;
+                    v[n] = (act && x < W) ? E[line * es + x] : make_float2(0.f, 0.f);
+                }
+            } else if (ps == PS_PSF) {
+#pragma unroll
+                for (int n = 0; n < L; ++n) {
+                    const int x = S * n + sub;
+                    v[n] = act ? make_float2(Ef[(size_t)line * 2 * es + x], Ef[(size_t)(line + N / 2) * 2 * es + x])
+                               : make_float2(0.f, 0.f);
+                }
+            } else {  // PS_OTF
+#pragma unroll
+                for (int n = 0; n < L; ++n) {
+                    const int ky = S * n + sub;
+                    if (!act) v[n] = make_float2(0.f, 0.f);
+                    else if (line == 0) v[n] = make_float2(E[ky * es].x, E[ky * es + N / 2].x);
+                    else v[n] = E[ky * es + line];
+                }
+            }
+            line_fft<N, -1>(v, sub);
+            __syncwarp();  // every lane of the line has read it before any store
+            if (ps == PS_PUPIL) {
+                if (act) {
+#pragma unroll
+                    for (int k = 0; k < L; ++k) E[(sub * L + k) * es + line] = v[k];
+                }
+            } else if (ps == PS_FIELD) {
+                if (act) {
+#pragma unroll
+                    for (int k = 0; k < L; ++k) {
+                        const int kx = sub * L + k;
+                        if (q.pf) q.pf[(size_t)kx * N + line] = v[k];
+                        Ef[(size_t)line * 2 * es + kx] = (v[k].x * v[k].x + v[k].y * v[k].y) * q.inv_z;
+                    }
+                }
+            } else if (ps == PS_PSF) {
+                fftreg::static_for<0, L>([&](auto kk) {
+                    constexpr int k = decltype(kk)::value;
+                    const float2 pc = conj_partner<N, k>(v);
+                    const int kx = sub * L + k;
+                    if (act && kx <= N / 2) {
+                        const float2 a = cscale(cadd(v[k], pc), 0.5f);
+                        const float2 d = cscale(csub(v[k], pc), 0.5f);
+                        E[line * es + kx] = a;
+                        E[(line + N / 2) * es + kx] = make_float2(d.y, -d.x);
+                    }
+                });
+            } else {  // PS_OTF
+                const int kx = line;
+                const uint64_t s0 = act ? q.csupp[2 * kx] : 0ull, s1 = act ? q.csupp[2 * kx + 1] : 0ull;
+                const uint64_t n0 = act && kx == 0 ? q.csupp[N] : 0ull, n1 = act && kx == 0 ? q.csupp[N + 1] : 0ull;
+                fftreg::static_for<0, L>([&](auto kk) {
+                    constexpr int k = decltype(kk)::value;
+                    const float2 pc = conj_partner<N, k>(v);
+                    const int ky = sub * L + k;
+                    if (act) {
+                        if (kx > 0) {
+                            q.h[ky * NH + kx] = cbit(s0, s1, ky) ? v[k] : make_float2(0.f, 0.f);
+                        } else {
+                            float2 h0 = cscale(cadd(v[k], pc), 0.5f);
+                            const float2 d = cscale(csub(v[k], pc), 0.5f);
+                            float2 hn = make_float2(d.y, -d.x);
+                            if (!cbit(s0, s1, ky)) h0 = make_float2(0.f, 0.f);
+                            if (!cbit(n0, n1, ky)) hn = make_float2(0.f, 0.f);
+                            if (ky == 0) h0 = make_float2(1.f, 0.f);
+                            q.h[ky * NH] = h0;
+                            q.h[ky * NH + N / 2] = hn;
+                        }
+                    }
+                });
+            }
+        }
+        bar();
+    }
+}
+
+// The adjoint passes (SEED, C2R, RPUPIL when RECOMPUTE, GP, ADJ) as rounds
+// with one register FFT (and, for RECOMPUTE, its decimation-in-
+// frequency twin in GP). E2 (row stride es2): RECOMPUTE's buffer for the
+// column transforms of P. Each pass ends with the group's barrier.
+template <int N, int LINES, bool RECOMPUTE, class Bar>
+__device__ __forceinline__ void unit_adjoint_rounds(const UnitPtr& q, float2* E, int es, float2* E2, int es2, int t,
+                                             Bar bar) {
+    constexpr int S = Geo<N>::S, L = Geo<N>::L, NH = Geo<N>::NH;
+    float* Ef = reinterpret_cast<float*>(E);
+    const int sub = t % S, li = t / S;
+    const int W = q.W;
+#pragma unroll 1
+    for (int ps = PS_SEED; ps <= PS_ADJ; ++ps) {
+        if (!RECOMPUTE && ps == PS_RPUPIL) continue;
+        const int lines = pass_lines(ps, N, W);
+#pragma unroll 1
+        for (int l0 = 0; l0 < lines; l0 += LINES) {
+            const int line = l0 + li;
+            const bool act = line < lines;
+            float2 v[L];
+            if (ps == PS_SEED) {
+#pragma unroll
+                for (int n = 0; n < L; ++n) {
+                    const int ky = S * n + sub;
+                    float2 g = make_float2(0.f, 0.f);
+                    if (act) {
+                        if (line == 0) {
+                            const float2 a = q.h[ky * NH], b = q.h[ky * NH + N / 2];
+                            g = make_float2(a.x - b.y, a.y + b.x);  // a + i b
+                        } else {
+                            g = q.h[ky * NH + line];
+                        }
+                    }
+                    v[n] = cconj(g);
+                }
+            } else if (ps == PS_C2R) {
+#pragma unroll
+                for (int n = 0; n < L; ++n) {
+                    const int x = S * n + sub, y = line;
+                    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+                    if (act) {
+                        if (x == 0) {
+                            a = make_float2(E[y * es].x, 0.f);
+                            b = make_float2(E[(y + N / 2) * es].x, 0.f);
+                        } else if (x == N / 2) {
+                            a = make_float2(E[y * es].y, 0.f);
+                            b = make_float2(E[(y + N / 2) * es].y, 0.f);
+                        } else if (x < N / 2) {
+                            a = E[y * es + x];
+                            b = E[(y + N / 2) * es + x];
+                        } else {
+                            a = cconj(E[y * es + N - x]);
+                            b = cconj(E[(y + N / 2) * es + N - x]);
+                        }
+                    }
+                    v[n] = make_float2(a.x - b.y, -(a.y + b.x));  // conj(a + i b)
+                }
+            } else if (ps == PS_RPUPIL) {
+                const uint64_t m0 = act ? q.cmask[2 * line] : 0ull, m1 = act ? q.cmask[2 * line + 1] : 0ull;
+#pragma unroll
+                for (int n = 0; n < L; ++n) {
+                    const int y = S * n + sub;
+                    v[n] = (act && y < W && cbit(m0, m1, y)) ? expi(q.phi[y * W + line]) : make_float2(0.f, 0.f);
+                }
+            } else if (ps == PS_GP) {
+                if constexpr (!RECOMPUTE) {
+#pragma unroll
+                    for (int n = 0; n < L; ++n) {
+                        const int x = S * n + sub;
+                        float2 w = make_float2(0.f, 0.f);
+                        if (act) {
+                            const float g = Ef[(size_t)line * 2 * es + x];
+                            const float2 pv = q.pf[(size_t)x * N + line];
+                            w = make_float2(g * pv.x, -g * pv.y);  // conj(g_q p)
+                        }
+                        v[n] = w;
+                    }
+                } else {  // the field row from the recomputed columns, transformed below
+#pragma unroll
+                    for (int n = 0; n < L; ++n) {
+                        const int x = S * n + sub;
+                        v[n] = (act && x < W) ? E2[line * es2 + x] : make_float2(0.f, 0.f);
+                    }
+                }
+            } else {  // PS_ADJ
+#pragma unroll
+                for (int n = 0; n < L; ++n) {
+                    const int y = S * n + sub;
+                    v[n] = act ? cconj(E[y * es + line]) : make_float2(0.f, 0.f);
+                }
+            }
+            line_fft<N, -1>(v, sub);
+            bool dif = false;
+            if constexpr (RECOMPUTE) {
+                if (ps == PS_GP) {
+                    // conj(g_q p) on the row (blocked order kx = sub L + k), then F^H by the DIF twin
+#pragma unroll
+                    for (int k = 0; k < L; ++k) {
+                        const int kx = sub * L + k;
+                        const float g = act ? Ef[(size_t)line * 2 * es + kx] : 0.f;
+                        v[k] = make_float2(g * v[k].x, -g * v[k].y);
+                    }
+                    line_fft_dif<N, -1>(v, sub);
+                    dif = true;
+                }
+            }
+            __syncwarp();  // every lane of the line has read it before any store
+            if (ps == PS_SEED) {
+                if (act) {
+#pragma unroll
+                    for (int k = 0; k < L; ++k)
+                        E[(sub * L + k) * es + line] = cconj(v[k]);  // line 0: (T_0, T_N/2), both real
+                }
+            } else if (ps == PS_C2R) {
+                if (act) {
+                    const float sc = 2.0f * q.inv_z;
+#pragma unroll
+                    for (int k = 0; k < L; ++k) {
+                        const int x = sub * L + k;
+                        Ef[(size_t)line * 2 * es + x] = v[k].x * sc;
+                        Ef[(size_t)(line + N / 2) * 2 * es + x] = -v[k].y * sc;
+                    }
+                }
+            } else if (ps == PS_RPUPIL) {
+                if (act) {
+#pragma unroll
+                    for (int k = 0; k < L; ++k) E2[(sub * L + k) * es2 + line] = v[k];
+                }
+            } else if (ps == PS_GP) {
+                if (act) {
+#pragma unroll
+                    for (int k = 0; k < L; ++k) {
+                        const int x = dif ? S * k + sub : sub * L + k;
+                        if (x < W) E[line * es + x] = cconj(v[k]);
+                    }
+                }
+            } else {  // PS_ADJ
+                if (act) {
+                    const uint64_t m0 = q.cmask[2 * line], m1 = q.cmask[2 * line + 1];
+#pragma unroll
+                    for (int k = 0; k < L; ++k) {
+                        const int y = sub * L + k;
+                        if (y < W) {
+                            float gv = 0.f;
+                            if (cbit(m0, m1, y)) {
+                                const float2 pv = q.pp ? q.pp[y * W + line] : expi(q.phi[y * W + line]);
+                                const float2 g = cconj(v[k]);
+                                gv = 2.0f * (pv.x * g.y - pv.y * g.x);
+                            }
+                            q.gphi[y * W + line] = gv;
+                        }
+                    }
+                }
+            }
+        }
+        bar();
+    }
+}
+
 // Frame reduction of one (patch, object) by one warp, any patch size: the
 // residual form of Eq. 12 in FP32 with FP64 where it would cancel, Kahan sums
 // per lane and an FP64 warp combine; writes the object (Eq. 11) when `obj`
