@@ -34,7 +34,7 @@ int mfbd_test_fft_host(int kind, const float* in, float* out);
  * MFBD_BATCH_STAGED and window_units. Writes up to `cap` items as rows of 5
  * ints {kind (0 phases, 1 forward, 2 reduction, 3 adjoint, 4 modal adjoint),
  * problem, patch, k * J + j of the first unit, the number e of further
- * frames j + 1 .. j + e it covers} and the total in *count. Returns 0, or 1 for bad arguments. */
+ * units (k J + j) + 1 .. (k J + j) + e it covers} and the total in *count. Returns 0, or 1 for bad arguments. */
 int mfbd_test_batch_items(const int* sizes, int n, int mode, int window_units, int* items, long long cap,
                           long long* count);
 

@@ -91,8 +91,8 @@ void batch_release(mfbd_batch* b) {
 // Relative cost of a unit of size N (for ordering items, largest first).
 int unit_cost(int N) { return N * N; }
 
-// The item list of a schedule. Per patch: P, the F items (frames in fours
-// when N <= 64), R, the A items, G. Staged: all P, all F, all R, all A, all
+// The item list of a schedule. Per patch: P, the F items (units k J + j in
+// fours when N <= 64), R, the A items, G. Staged: all P, all F, all R, all A, all
 // G (each a launch). One launch: the patches are cut into windows of about
 // `window` 64 px units (0: one window) and window w's kind s goes into block
 // w + s, each block listing its older windows first, so an item's
@@ -112,13 +112,13 @@ std::vector<BatchItem> build_items(const mfbd_batch* b, int mode, int window, st
         it.prob = r.prob;
         it.patch = r.patch;
         if (kind == BK_FWD || kind == BK_ADJ) {
-            for (int k = 0; k < pr.K; ++k)
-                for (int j = 0; j < pr.J;) {
-                    it.kj = k * pr.J + j;
-                    it.extra = pr.N <= 64 ? std::min(3, pr.J - 1 - j) : 0;
-                    out.push_back(it);
-                    j += 1 + it.extra;
-                }
+            const int units = pr.K * pr.J;  // (k, j) flattened: a group of four may span two objects
+            for (int u = 0; u < units;) {
+                it.kj = u;
+                it.extra = pr.N <= 64 ? std::min(3, units - 1 - u) : 0;
+                out.push_back(it);
+                u += 1 + it.extra;
+            }
         } else {
             out.push_back(it);
         }

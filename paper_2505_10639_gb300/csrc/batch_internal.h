@@ -49,8 +49,8 @@ struct BatchProblem {
 };
 
 // Work items. F and A cover one unit (patch, object, frame), or up to four
-// frames of one (patch, object) when N <= 64 (one warp per unit); P, R and G
-// cover one patch.
+// consecutive units k J + j of one patch when N <= 64 (one warp per unit);
+// P, R and G cover one patch.
 enum BatchKind : int {
     BK_PROJ = 0,   // phases of every object and frame of a patch (Eq. 22)
     BK_FWD = 1,    // forward passes of a unit (Eqs. 20-21, OTF)
@@ -64,7 +64,7 @@ struct BatchItem {
     int prob;       // problem index
     int patch;      // patch within the problem
     int kj;         // F, A: k * J + j of the first unit; P, R, G: 0
-    int extra;      // F, A: further frames j + 1 .. j + extra in the item (N <= 64: 0..3)
+    int extra;      // F, A: further units kj + 1 .. kj + extra in the item (N <= 64: 0..3)
     int pad[3];
 };
 

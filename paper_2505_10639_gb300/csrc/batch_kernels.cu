@@ -16,8 +16,8 @@
 // the host launches each kind's range of the list separately and nothing
 // waits.
 //
-// F and A items of patches of N <= 64 px cover up to four frames of one
-// (patch, object): each of the CTA's four warps runs one unit on its own
+// F and A items of patches of N <= 64 px cover up to four consecutive units
+// (k J + j) of one patch: each of the CTA's four warps runs one unit on its own
 // exchange buffer with warp synchronisation only. Larger patches use all 128
 // threads on one unit. Every pass runs as rounds with one register FFT per
 // (patch size, direction) (unit_forward_rounds, unit_adjoint_rounds): the
@@ -92,8 +92,8 @@ __device__ __forceinline__ UnitPtr batch_unit(const BatchParams& prm, const Batc
     return q;
 }
 
-// F or A item: one unit per warp (N <= 64: up to four frames of one (patch,
-// object), 32 lines per round, warp synchronisation only) or one unit on the
+// F or A item: one unit per warp (N <= 64: up to four units of one patch,
+// 32 lines per round, warp synchronisation only) or one unit on the
 // whole CTA (N = 96, 128: 64 lines of two lanes per round, CTA barriers).
 template <int N, bool ADJ>
 __device__ void item_unit(const BatchParams& prm, const BatchProblem& pr, const BatchItem& it, float2* smem) {

@@ -202,7 +202,7 @@ def _batch_items(lib, sizes, mode, window):
 def test_batch_work_list_covers_every_unit_once_after_its_dependencies(lib, mode, window):
     """The batch work list: one phase, reduction and modal-adjoint item per
     patch, every unit in exactly one forward and one adjoint item (groups of
-    up to four frames only for N <= 64 and only within one object), and in
+    up to four units only for N <= 64 and only within one patch), and in
     one-launch mode every
     item after the items it waits for (the progress argument of the kernel)."""
     sizes = [(48, 2, 1, 5), (64, 1, 2, 4), (96, 3, 1, 3), (128, 1, 3, 2), (64, 2, 1, 1), (128, 0, 2, 3)]
@@ -214,7 +214,7 @@ def test_batch_work_list_covers_every_unit_once_after_its_dependencies(lib, mode
         if kind in (1, 3):
             assert 0 <= pair <= 3
             if pair:
-                assert n <= 64 and (kj % j_) + pair < j_
+                assert n <= 64 and kj + pair < k_ * j_
             for u in range(kj, kj + 1 + pair):
                 d = seen_f if kind == 1 else seen_a
                 assert (prob, patch, u) not in d
