@@ -147,49 +147,88 @@ __device__ void item_proj(const BatchParams& prm, const BatchProblem& pr, int p,
     }
 }
 
-// G item: grad[j][m] = sum_k c_k sum_i dL/dphi_kj[i] B_k[m][i], the objects
-// added in order; one thread per (mode, tile of kJC frames).
-__device__ void item_grad(const BatchParams& prm, const BatchProblem& pr, int p) {
+// G item: grad[j][m] = sum_k c_k sum_i dL/dphi_kj[i] B_k[m][i]. For each tile
+// of kJC frames and each block of up to kBT modes, the pixels of every object
+// go through in chunks of kGC, the chunk's dL/dphi (kJC x kGC) and basis rows
+// (kGC x modes) staged in shared memory; thread t takes mode t % MB of the
+// block and the chunk pixels i = t / MB (mod kBT / MB), holding kJC sums; the
+// objects' sums are added in order (each scaled by c_k), the pixel groups'
+// partial sums in group order.
+constexpr int kGC = 64;
+__device__ void item_grad(const BatchParams& prm, const BatchProblem& pr, int p, float* smf) {
     const int t = threadIdx.x, J = pr.J, M = pr.M;
-    const int tiles = (J + kJC - 1) / kJC;
+    const int MB = min(M, kBT), npg = kBT / MB;
+    const int mi = t % MB, pg = t / MB;
+    float* sg = smf;                    // [kJC][kGC]
+    float* sb = sg + kJC * kGC;         // [kGC][MB]
+    float* red = sb + kGC * kBT;        // [npg][kJC][MB]
     float* grad = prm.grad + pr.coeff_off + (size_t)p * J * M;
-    for (int idx = t; idx < M * tiles; idx += kBT) {
-        const int m = idx % M, jc = (idx / M) * kJC, nj = min(kJC, J - jc);
-        float acc[kJC];
+    for (int jc = 0; jc < J; jc += kJC) {
+        const int nj = min(kJC, J - jc);
+        for (int m0 = 0; m0 < M; m0 += MB) {
+            const int m = m0 + mi;
+            const bool act = pg < npg && m < M;
+            float acc[kJC];
 #pragma unroll
-        for (int jj = 0; jj < kJC; ++jj) acc[jj] = 0.f;
-        for (int k = 0; k < pr.K; ++k) {
-            const BatchObj& ob = pr.obj[k];
-            const int npix = ob.W * ob.W;
-            const long long us = unit_stride_phi(ob.W);
-            const float* g = prm.gphi + pr.phi_off + (long long)p * pr.phi_patch + ob.phi_koff + jc * us;
-            const float* row[kJC];
+            for (int jj = 0; jj < kJC; ++jj) acc[jj] = 0.f;
+            for (int k = 0; k < pr.K; ++k) {
+                const BatchObj& ob = pr.obj[k];
+                const int npix = ob.W * ob.W;
+                const long long us = unit_stride_phi(ob.W);
+                const float* g = prm.gphi + pr.phi_off + (long long)p * pr.phi_patch + ob.phi_koff + jc * us;
+                float part[kJC];
 #pragma unroll
-            for (int jj = 0; jj < kJC; ++jj) row[jj] = g + min(jj, nj - 1) * us;
-            float part[kJC];
+                for (int jj = 0; jj < kJC; ++jj) part[jj] = 0.f;
+                for (int i0 = 0; i0 < npix; i0 += kGC) {
+                    const int nc = min(kGC, npix - i0);
+                    __syncthreads();
+                    for (int e = t; e < kJC * kGC; e += kBT) {
+                        const int jj = e / kGC, ii = e - jj * kGC;
+                        sg[e] = (jj < nj && ii < nc) ? g[jj * us + i0 + ii] : 0.f;
+                    }
+                    for (int e = t; e < kGC * MB; e += kBT) {
+                        const int ii = e / MB, mm = e - ii * MB;
+                        sb[e] = (ii < nc && m0 + mm < M) ? ob.bt[(size_t)(i0 + ii) * ob.ldt + m0 + mm] : 0.f;
+                    }
+                    __syncthreads();
+                    if (act) {
+                        for (int ii = pg; ii < nc; ii += npg) {
+                            const float b = sb[ii * MB + mi];
 #pragma unroll
-            for (int jj = 0; jj < kJC; ++jj) part[jj] = 0.f;
-            for (int i = 0; i < npix; ++i) {
-                const float b = ob.bt[(size_t)i * ob.ldt + m];
+                            for (int jj = 0; jj < kJC; ++jj) part[jj] = fmaf(sg[jj * kGC + ii], b, part[jj]);
+                        }
+                    }
+                }
 #pragma unroll
-                for (int jj = 0; jj < kJC; ++jj) part[jj] = fmaf(row[jj][i], b, part[jj]);
+                for (int jj = 0; jj < kJC; ++jj) acc[jj] = fmaf(ob.scale, part[jj], acc[jj]);
             }
+            __syncthreads();
+            if (pg < npg) {
 #pragma unroll
-            for (int jj = 0; jj < kJC; ++jj) acc[jj] = fmaf(ob.scale, part[jj], acc[jj]);
+                for (int jj = 0; jj < kJC; ++jj) red[(pg * kJC + jj) * MB + mi] = acc[jj];
+            }
+            __syncthreads();
+            if (pg == 0 && m < M) {
+#pragma unroll
+                for (int jj = 0; jj < kJC; ++jj) {
+                    float v = 0.f;
+                    for (int q = 0; q < npg; ++q) v += red[(q * kJC + jj) * MB + mi];
+                    if (jj < nj) grad[(size_t)(jc + jj) * M + m] = v;
+                }
+            }
         }
-#pragma unroll
-        for (int jj = 0; jj < kJC; ++jj)
-            if (jj < nj) grad[(size_t)(jc + jj) * M + m] = acc[jj];
     }
 }
 
-// R item: one warp per object (objects k = warp, warp + 4, ...); the patch
-// loss adds the objects in order.
+// R item: the four warps share each object's frequencies (warp w takes
+// f = 32 w + lane + 128 i); the patch loss adds the warps' sums of an object
+// in warp order, then the objects in order.
 __device__ void item_reduce(const BatchParams& prm, const BatchProblem& pr, int p, double* sobj) {
+    constexpr int kW = kBT / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = pr.N, NH = N / 2 + 1, J = pr.J;
     const size_t dstride = (size_t)N * NH;
-    for (int k = warp; k < pr.K; k += kBT / 32) {
+    for (int k = 0; k < pr.K; ++k) {
         const size_t unit0 = ((size_t)p * pr.K + k) * J;
         RedPtr r;
         r.N = N;
@@ -202,13 +241,17 @@ __device__ void item_reduce(const BatchParams& prm, const BatchProblem& pr, int 
         r.supp = pr.obj[k].supp;
         r.sw = pr.sw;
         r.obj = prm.object ? prm.object + pr.obj_off + ((size_t)p * pr.K + k) * dstride : nullptr;
-        const double v = reduce_warp(r, lane);
-        if (lane == 0) sobj[k] = v;
+        const double v = reduce_warp(r, lane, 32 * warp, 32 * kW);
+        if (lane == 0) sobj[k * kW + warp] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot = 0.0;
-        for (int k = 0; k < pr.K; ++k) tot += sobj[k];
+        for (int k = 0; k < pr.K; ++k) {
+            double tk = 0.0;
+            for (int w = 0; w < kW; ++w) tk += sobj[k * kW + w];
+            tot += tk;
+        }
         prm.loss[pr.loss_off + p] = tot;
     }
 }
@@ -231,7 +274,7 @@ __global__ void __launch_bounds__(kBT, MINB) batch_kernel(const BatchParams prm)
     extern __shared__ __align__(16) unsigned char bsm[];
     float2* smem = reinterpret_cast<float2*>(bsm);
     __shared__ int s_item, s_ok;
-    __shared__ double sobj[kMaxObjects];
+    __shared__ double sobj[kMaxObjects * (kBT / 32)];
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(prm.ticket, 1);
         __syncthreads();
@@ -261,7 +304,7 @@ __global__ void __launch_bounds__(kBT, MINB) batch_kernel(const BatchParams prm)
                 case BK_FWD: dispatch_unit<false>(prm, pr, it, smem); break;
                 case BK_RED: item_reduce(prm, pr, it.patch, sobj); break;
                 case BK_ADJ: dispatch_unit<true>(prm, pr, it, smem); break;
-                default: item_grad(prm, pr, it.patch); break;
+                default: item_grad(prm, pr, it.patch, reinterpret_cast<float*>(bsm)); break;
             }
         }
         __syncthreads();  // the item's writes precede the signal; s_item is free again
@@ -278,11 +321,13 @@ __global__ void __launch_bounds__(kBT, MINB) batch_kernel(const BatchParams prm)
 }  // namespace
 
 size_t batch_smem(int es_small, int es_large) {
-    // four 64-pixel warps, one 128-pixel unit, or the P item's coefficient tile
+    // four 64-pixel warps, one 128-pixel unit, the P item's coefficient tile or
+    // the G item's staging
     const size_t small = (size_t)(kBT / 32) * 64 * es_small * sizeof(float2);
     const size_t large = (size_t)128 * es_large * sizeof(float2);
     const size_t proj = (size_t)kJC * 256 * sizeof(float);
-    return std::max(std::max(small, large), proj);
+    const size_t grad = (size_t)(kJC * kGC + kGC * kBT + kJC * kBT) * sizeof(float);
+    return std::max(std::max(small, large), std::max(proj, grad));
 }
 
 template <int MINB>

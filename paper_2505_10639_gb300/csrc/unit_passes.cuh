@@ -726,12 +726,15 @@ struct RedPtr {
     float2* obj;            // [N][spec_ld] or null
 };
 
-__device__ __forceinline__ double reduce_warp(const RedPtr& r, int lane) {
+// Lanes take the frequencies f0 + lane, f0 + lane + fstep, ... (fstep a
+// multiple of 32: several warps can share one (patch, object)); the returned
+// sum covers this warp's frequencies.
+__device__ __forceinline__ double reduce_warp(const RedPtr& r, int lane, int f0 = 0, int fstep = 32) {
     const int N = r.N, NH = N / 2 + 1, half = N * NH, J = r.J;
     const size_t dstride = (size_t)N * r.spec_ld;
     const float gam = (float)r.gamma;
     KahanSum acc;
-    for (int f = lane; f < half; f += 32) {
+    for (int f = f0 + lane; f < half; f += fstep) {
         const int ky = f / NH, kx = f - ky * NH;
         const size_t doff = (size_t)ky * r.spec_ld + kx;
         const float2* dp = r.d + doff;
@@ -739,6 +742,7 @@ __device__ __forceinline__ double reduce_warp(const RedPtr& r, int lane) {
         const bool seed = (f != 0) && wbit(r.supp, r.sw, ky, kx);
         float2 num = make_float2(0.f, 0.f), o;
         float e = 0.f, qs = 0.f, tval;
+#pragma unroll 4
         for (int j = 0; j < J; ++j) {
             const float2 d = dp[(size_t)j * dstride];
             const float2 h = hp[(size_t)j * half];
@@ -756,6 +760,7 @@ __device__ __forceinline__ double reduce_warp(const RedPtr& r, int lane) {
             fp64_frequency(J, dp, dstride, hp, half, r.w, r.gamma, seed, tval, o);
         } else {
             float tsum = 0.f;
+#pragma unroll 4
             for (int j = 0; j < J; ++j) {
                 const float2 d = dp[(size_t)j * dstride];
                 const float2 h = hp[(size_t)j * half];
