@@ -147,76 +147,41 @@ __device__ void item_proj(const BatchParams& prm, const BatchProblem& pr, int p,
     }
 }
 
-// G item: grad[j][m] = sum_k c_k sum_i dL/dphi_kj[i] B_k[m][i]. For each tile
-// of kJC frames and each block of up to kBT modes, the pixels of every object
-// go through in chunks of kGC, the chunk's dL/dphi (kJC x kGC) and basis rows
-// (kGC x modes) staged in shared memory; thread t takes mode t % MB of the
-// block and the chunk pixels i = t / MB (mod kBT / MB), holding kJC sums; the
-// objects' sums are added in order (each scaled by c_k), the pixel groups'
-// partial sums in group order.
-constexpr int kGC = 64;
-__device__ void item_grad(const BatchParams& prm, const BatchProblem& pr, int p, float* smf) {
+// G item: grad[j][m] = sum_k c_k sum_i dL/dphi_kj[i] B_k[m][i], the objects
+// added in order; one thread per (mode, tile of kJC frames). (Staging
+// dL/dphi and basis chunks in shared memory was measured slower: 5.7 against
+// 2.0 ms for the 2000-problem batch.)
+__device__ void item_grad(const BatchParams& prm, const BatchProblem& pr, int p) {
     const int t = threadIdx.x, J = pr.J, M = pr.M;
-    const int MB = min(M, kBT), npg = kBT / MB;
-    const int mi = t % MB, pg = t / MB;
-    float* sg = smf;                    // [kJC][kGC]
-    float* sb = sg + kJC * kGC;         // [kGC][MB]
-    float* red = sb + kGC * kBT;        // [npg][kJC][MB]
+    const int tiles = (J + kJC - 1) / kJC;
     float* grad = prm.grad + pr.coeff_off + (size_t)p * J * M;
-    for (int jc = 0; jc < J; jc += kJC) {
-        const int nj = min(kJC, J - jc);
-        for (int m0 = 0; m0 < M; m0 += MB) {
-            const int m = m0 + mi;
-            const bool act = pg < npg && m < M;
-            float acc[kJC];
+    for (int idx = t; idx < M * tiles; idx += kBT) {
+        const int m = idx % M, jc = (idx / M) * kJC, nj = min(kJC, J - jc);
+        float acc[kJC];
 #pragma unroll
-            for (int jj = 0; jj < kJC; ++jj) acc[jj] = 0.f;
-            for (int k = 0; k < pr.K; ++k) {
-                const BatchObj& ob = pr.obj[k];
-                const int npix = ob.W * ob.W;
-                const long long us = unit_stride_phi(ob.W);
-                const float* g = prm.gphi + pr.phi_off + (long long)p * pr.phi_patch + ob.phi_koff + jc * us;
-                float part[kJC];
+        for (int jj = 0; jj < kJC; ++jj) acc[jj] = 0.f;
+        for (int k = 0; k < pr.K; ++k) {
+            const BatchObj& ob = pr.obj[k];
+            const int npix = ob.W * ob.W;
+            const long long us = unit_stride_phi(ob.W);
+            const float* g = prm.gphi + pr.phi_off + (long long)p * pr.phi_patch + ob.phi_koff + jc * us;
+            const float* row[kJC];
 #pragma unroll
-                for (int jj = 0; jj < kJC; ++jj) part[jj] = 0.f;
-                for (int i0 = 0; i0 < npix; i0 += kGC) {
-                    const int nc = min(kGC, npix - i0);
-                    __syncthreads();
-                    for (int e = t; e < kJC * kGC; e += kBT) {
-                        const int jj = e / kGC, ii = e - jj * kGC;
-                        sg[e] = (jj < nj && ii < nc) ? g[jj * us + i0 + ii] : 0.f;
-                    }
-                    for (int e = t; e < kGC * MB; e += kBT) {
-                        const int ii = e / MB, mm = e - ii * MB;
-                        sb[e] = (ii < nc && m0 + mm < M) ? ob.bt[(size_t)(i0 + ii) * ob.ldt + m0 + mm] : 0.f;
-                    }
-                    __syncthreads();
-                    if (act) {
-                        for (int ii = pg; ii < nc; ii += npg) {
-                            const float b = sb[ii * MB + mi];
+            for (int jj = 0; jj < kJC; ++jj) row[jj] = g + min(jj, nj - 1) * us;
+            float part[kJC];
 #pragma unroll
-                            for (int jj = 0; jj < kJC; ++jj) part[jj] = fmaf(sg[jj * kGC + ii], b, part[jj]);
-                        }
-                    }
-                }
+            for (int jj = 0; jj < kJC; ++jj) part[jj] = 0.f;
+            for (int i = 0; i < npix; ++i) {
+                const float b = ob.bt[(size_t)i * ob.ldt + m];
 #pragma unroll
-                for (int jj = 0; jj < kJC; ++jj) acc[jj] = fmaf(ob.scale, part[jj], acc[jj]);
+                for (int jj = 0; jj < kJC; ++jj) part[jj] = fmaf(row[jj][i], b, part[jj]);
             }
-            __syncthreads();
-            if (pg < npg) {
 #pragma unroll
-                for (int jj = 0; jj < kJC; ++jj) red[(pg * kJC + jj) * MB + mi] = acc[jj];
-            }
-            __syncthreads();
-            if (pg == 0 && m < M) {
-#pragma unroll
-                for (int jj = 0; jj < kJC; ++jj) {
-                    float v = 0.f;
-                    for (int q = 0; q < npg; ++q) v += red[(q * kJC + jj) * MB + mi];
-                    if (jj < nj) grad[(size_t)(jc + jj) * M + m] = v;
-                }
-            }
+            for (int jj = 0; jj < kJC; ++jj) acc[jj] = fmaf(ob.scale, part[jj], acc[jj]);
         }
+#pragma unroll
+        for (int jj = 0; jj < kJC; ++jj)
+            if (jj < nj) grad[(size_t)(jc + jj) * M + m] = acc[jj];
     }
 }
 
@@ -304,7 +269,7 @@ __global__ void __launch_bounds__(kBT, MINB) batch_kernel(const BatchParams prm)
                 case BK_FWD: dispatch_unit<false>(prm, pr, it, smem); break;
                 case BK_RED: item_reduce(prm, pr, it.patch, sobj); break;
                 case BK_ADJ: dispatch_unit<true>(prm, pr, it, smem); break;
-                default: item_grad(prm, pr, it.patch, reinterpret_cast<float*>(bsm)); break;
+                default: item_grad(prm, pr, it.patch); break;
             }
         }
         __syncthreads();  // the item's writes precede the signal; s_item is free again
@@ -321,13 +286,11 @@ __global__ void __launch_bounds__(kBT, MINB) batch_kernel(const BatchParams prm)
 }  // namespace
 
 size_t batch_smem(int es_small, int es_large) {
-    // four 64-pixel warps, one 128-pixel unit, the P item's coefficient tile or
-    // the G item's staging
+    // four 64-pixel warps, one 128-pixel unit, or the P item's coefficient tile
     const size_t small = (size_t)(kBT / 32) * 64 * es_small * sizeof(float2);
     const size_t large = (size_t)128 * es_large * sizeof(float2);
     const size_t proj = (size_t)kJC * 256 * sizeof(float);
-    const size_t grad = (size_t)(kJC * kGC + kGC * kBT + kJC * kBT) * sizeof(float);
-    return std::max(std::max(small, large), std::max(proj, grad));
+    return std::max(std::max(small, large), proj);
 }
 
 template <int MINB>
