@@ -116,15 +116,20 @@ __device__ void item_unit(const BatchParams& prm, const BatchProblem& pr, const 
 
 // P item: phi_kj[i] = c_k sum_m a_j[m] B_k[m][i] on every box pixel i, for
 // every object and frame of the patch; kJC frames per register tile with
-// their coefficients staged in shared memory.
+// their coefficients staged in shared memory mode-major ([m][kJC]: two
+// 16-byte loads per mode).
 __device__ void item_proj(const BatchParams& prm, const BatchProblem& pr, int p, float* sa) {
     const int t = threadIdx.x, J = pr.J, M = pr.M;
     const float* a = prm.coeffs + pr.coeff_off + (size_t)p * J * M;
     for (int jc = 0; jc < J; jc += kJC) {
         const int nj = min(kJC, J - jc);
         __syncthreads();
-        for (int i = t; i < kJC * M; i += kBT) sa[i] = (i / M < nj) ? a[(size_t)jc * M + i] : 0.f;
+        for (int e = t; e < kJC * M; e += kBT) {
+            const int m = e / kJC, jj = e - m * kJC;
+            sa[e] = jj < nj ? a[(size_t)(jc + jj) * M + m] : 0.f;
+        }
         __syncthreads();
+        const float4* sa4 = reinterpret_cast<const float4*>(sa);
         for (int k = 0; k < pr.K; ++k) {
             const BatchObj& ob = pr.obj[k];
             const int npix = ob.W * ob.W;
@@ -136,8 +141,15 @@ __device__ void item_proj(const BatchParams& prm, const BatchProblem& pr, int p,
                 for (int jj = 0; jj < kJC; ++jj) acc[jj] = 0.f;
                 for (int m = 0; m < M; ++m) {
                     const float b = ob.bm[(size_t)m * npix + i];
-#pragma unroll
-                    for (int jj = 0; jj < kJC; ++jj) acc[jj] = fmaf(sa[jj * M + m], b, acc[jj]);
+                    const float4 c0 = sa4[2 * m], c1 = sa4[2 * m + 1];
+                    acc[0] = fmaf(c0.x, b, acc[0]);
+                    acc[1] = fmaf(c0.y, b, acc[1]);
+                    acc[2] = fmaf(c0.z, b, acc[2]);
+                    acc[3] = fmaf(c0.w, b, acc[3]);
+                    acc[4] = fmaf(c1.x, b, acc[4]);
+                    acc[5] = fmaf(c1.y, b, acc[5]);
+                    acc[6] = fmaf(c1.z, b, acc[6]);
+                    acc[7] = fmaf(c1.w, b, acc[7]);
                 }
 #pragma unroll
                 for (int jj = 0; jj < kJC; ++jj)
@@ -171,7 +183,22 @@ __device__ void item_grad(const BatchParams& prm, const BatchProblem& pr, int p)
             float part[kJC];
 #pragma unroll
             for (int jj = 0; jj < kJC; ++jj) part[jj] = 0.f;
-            for (int i = 0; i < npix; ++i) {
+            // four pixels per step: one 16-byte load of each frame's dL/dphi
+            // (rows are 256-byte aligned), then the tail
+            const int n4 = npix & ~3;
+            for (int i = 0; i < n4; i += 4) {
+                const float b0 = ob.bt[(size_t)i * ob.ldt + m], b1 = ob.bt[(size_t)(i + 1) * ob.ldt + m];
+                const float b2 = ob.bt[(size_t)(i + 2) * ob.ldt + m], b3 = ob.bt[(size_t)(i + 3) * ob.ldt + m];
+#pragma unroll
+                for (int jj = 0; jj < kJC; ++jj) {
+                    const float4 gv = *reinterpret_cast<const float4*>(row[jj] + i);
+                    float x = fmaf(gv.x, b0, part[jj]);
+                    x = fmaf(gv.y, b1, x);
+                    x = fmaf(gv.z, b2, x);
+                    part[jj] = fmaf(gv.w, b3, x);
+                }
+            }
+            for (int i = n4; i < npix; ++i) {
                 const float b = ob.bt[(size_t)i * ob.ldt + m];
 #pragma unroll
                 for (int jj = 0; jj < kJC; ++jj) part[jj] = fmaf(row[jj][i], b, part[jj]);
