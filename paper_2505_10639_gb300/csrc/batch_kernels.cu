@@ -233,7 +233,7 @@ __device__ void item_reduce(const BatchParams& prm, const BatchProblem& pr, int 
         r.supp = pr.obj[k].supp;
         r.sw = pr.sw;
         r.obj = prm.object ? prm.object + pr.obj_off + ((size_t)p * pr.K + k) * dstride : nullptr;
-        const double v = reduce_warp<24>(r, lane, 32 * warp, 32 * kW);
+        const double v = reduce_warp(r, lane, 32 * warp, 32 * kW);
         if (lane == 0) sobj[k * kW + warp] = v;
     }
     __syncthreads();

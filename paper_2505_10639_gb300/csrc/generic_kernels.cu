@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(32 * kMaxObjects) generic_reduce_kernel(const 
         r.supp = prm.obj[k].supp;
         r.sw = prm.sw;
         r.obj = prm.object ? prm.object + ((size_t)p * prm.K + k) * dstride : nullptr;
-        const double v = reduce_warp<32>(r, lane);
+        const double v = reduce_warp(r, lane);
         if (lane == 0) sobj[k] = v;
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -726,89 +726,56 @@ struct RedPtr {
     float2* obj;            // [N][spec_ld] or null
 };
 
-// One frequency: the frame sums, the object, the loss term and the seeds
-// written over H (FP64 where the FP32 residual would cancel). JR > 0: the
-// J <= JR frames of D and H are loaded once into registers (all loads issued
-// together) and the residual pass reuses them; JR = 0: two passes over
-// memory. The arithmetic and its order are the same either way.
-template <int JR>
-__device__ __forceinline__ float reduce_frequency(const RedPtr& r, int f, int J, size_t dstride, int half,
-                                                  float gam, float2& o) {
-    const int N = r.N, NH = N / 2 + 1;
-    const int ky = f / NH, kx = f - ky * NH;
-    const size_t doff = (size_t)ky * r.spec_ld + kx;
-    const float2* dp = r.d + doff;
-    float2* hp = r.h + f;
-    const bool seed = (f != 0) && wbit(r.supp, r.sw, ky, kx);
-    float2 num = make_float2(0.f, 0.f);
-    float e = 0.f, qs = 0.f, tval;
-    float2 dr[JR > 0 ? JR : 1], hr[JR > 0 ? JR : 1];
-    auto frame = [&](const float2& d, const float2& h, float wj) {
-        num.x += wj * (d.x * h.x + d.y * h.y);
-        num.y += wj * (d.y * h.x - d.x * h.y);
-        e += wj * (d.x * d.x + d.y * d.y);
-        qs += wj * (h.x * h.x + h.y * h.y);
-    };
-    if constexpr (JR > 0) {
-#pragma unroll
-        for (int j = 0; j < JR; ++j) {
-            if (j < J) {
-                dr[j] = dp[(size_t)j * dstride];
-                hr[j] = hp[(size_t)j * half];
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < JR; ++j)
-            if (j < J) frame(dr[j], hr[j], r.w[j]);
-    } else {
-#pragma unroll 4
-        for (int j = 0; j < J; ++j) frame(dp[(size_t)j * dstride], hp[(size_t)j * half], r.w[j]);
-    }
-    qs += gam;
-    const float invq = 1.0f / qs;
-    o = cscale(num, invq);
-    const float t_est = e - (num.x * num.x + num.y * num.y) * invq;
-    if (f != 0 && t_est < kCancel * e) {
-        fp64_frequency(J, dp, dstride, hp, half, r.w, r.gamma, seed, tval, o);
-    } else {
-        float tsum = 0.f;
-        auto residual = [&](const float2& d, const float2& h, float wj, int j) {
-            const float2 res = csub(d, cmul(o, h));
-            tsum += wj * (res.x * res.x + res.y * res.y);
-            hp[(size_t)j * half] = seed ? cscale(cmul(cconj(o), res), -wj) : make_float2(0.f, 0.f);
-        };
-        if constexpr (JR > 0) {
-#pragma unroll
-            for (int j = 0; j < JR; ++j)
-                if (j < J) residual(dr[j], hr[j], r.w[j], j);
-        } else {
-#pragma unroll 4
-            for (int j = 0; j < J; ++j) residual(dp[(size_t)j * dstride], hp[(size_t)j * half], r.w[j], j);
-        }
-        tval = tsum + gam * (o.x * o.x + o.y * o.y);
-    }
-    if (r.obj) {
-        r.obj[doff] = o;
-        if (r.spec_ld == N && kx > 0 && kx < N / 2) r.obj[(size_t)((N - ky) % N) * N + (N - kx)] = cconj(o);
-    }
-    return (kx == 0 || kx == N / 2) ? tval : 2.0f * tval;
-}
-
 // Lanes take the frequencies f0 + lane, f0 + lane + fstep, ... (fstep a
 // multiple of 32: several warps can share one (patch, object)); the returned
-// sum covers this warp's frequencies. JR: frames held in registers (see
-// reduce_frequency).
-template <int JR = 0>
+// sum covers this warp's frequencies.
 __device__ __forceinline__ double reduce_warp(const RedPtr& r, int lane, int f0 = 0, int fstep = 32) {
     const int N = r.N, NH = N / 2 + 1, half = N * NH, J = r.J;
     const size_t dstride = (size_t)N * r.spec_ld;
     const float gam = (float)r.gamma;
     KahanSum acc;
     for (int f = f0 + lane; f < half; f += fstep) {
-        float2 o;
-        const float t = (JR > 0 && J <= JR) ? reduce_frequency<JR>(r, f, J, dstride, half, gam, o)
-                                            : reduce_frequency<0>(r, f, J, dstride, half, gam, o);
-        acc.add(t);
+        const int ky = f / NH, kx = f - ky * NH;
+        const size_t doff = (size_t)ky * r.spec_ld + kx;
+        const float2* dp = r.d + doff;
+        float2* hp = r.h + f;
+        const bool seed = (f != 0) && wbit(r.supp, r.sw, ky, kx);
+        float2 num = make_float2(0.f, 0.f), o;
+        float e = 0.f, qs = 0.f, tval;
+#pragma unroll 4
+        for (int j = 0; j < J; ++j) {
+            const float2 d = dp[(size_t)j * dstride];
+            const float2 h = hp[(size_t)j * half];
+            const float wj = r.w[j];
+            num.x += wj * (d.x * h.x + d.y * h.y);
+            num.y += wj * (d.y * h.x - d.x * h.y);
+            e += wj * (d.x * d.x + d.y * d.y);
+            qs += wj * (h.x * h.x + h.y * h.y);
+        }
+        qs += gam;
+        const float invq = 1.0f / qs;
+        o = cscale(num, invq);
+        const float t_est = e - (num.x * num.x + num.y * num.y) * invq;
+        if (f != 0 && t_est < kCancel * e) {
+            fp64_frequency(J, dp, dstride, hp, half, r.w, r.gamma, seed, tval, o);
+        } else {
+            float tsum = 0.f;
+#pragma unroll 4
+            for (int j = 0; j < J; ++j) {
+                const float2 d = dp[(size_t)j * dstride];
+                const float2 h = hp[(size_t)j * half];
+                const float wj = r.w[j];
+                const float2 res = csub(d, cmul(o, h));
+                tsum += wj * (res.x * res.x + res.y * res.y);
+                hp[(size_t)j * half] = seed ? cscale(cmul(cconj(o), res), -wj) : make_float2(0.f, 0.f);
+            }
+            tval = tsum + gam * (o.x * o.x + o.y * o.y);
+        }
+        acc.add((kx == 0 || kx == N / 2) ? tval : 2.0f * tval);
+        if (r.obj) {
+            r.obj[doff] = o;
+            if (r.spec_ld == N && kx > 0 && kx < N / 2) r.obj[(size_t)((N - ky) % N) * N + (N - kx)] = cconj(o);
+        }
     }
     double v = (double)acc.s - (double)acc.c;
 #pragma unroll
