@@ -7,7 +7,8 @@ m = mode. Spectra are full N x N complex arrays in the forward-FFT
 convention of ``oracle.dft`` (index [ky][kx], unnormalised).
 
 Per object k and frame j (Sec. 3.1):
-  phi_kj(v) = c_k sum_m a_jm B_km(v)                      (Eq. 22)
+  phi_kj(v) = c_k sum_m a_jm B_km(v) [+ theta_kj(v)]      (Eq. 22; theta: the known
+                                                           diversity phase, Sec. 2.1)
   P_kj      = A_k exp(i phi_kj)                           (Eq. 20)
   s_kj      = |F P_kj|^2 / sum_x |F P_kj|^2               (Eq. 21, normalised)
   H_kj      = F s_kj
@@ -84,14 +85,17 @@ def loss_terms(d, h, w, gamma):
 
 
 class Setup:
-    """Per-object plan data: masks, sampled bases, phase scales, weights."""
+    """Per-object plan data: masks, sampled bases, phase scales, weights, and
+    optionally the known diversity phases theta [K][J, N, N] (radians) added
+    to the wavefront of object k in frame j (phase diversity, Sec. 2.1)."""
 
-    def __init__(self, masks, bases, scales, weights, gamma):
+    def __init__(self, masks, bases, scales, weights, gamma, diversity=None):
         self.masks = [np.asarray(m, bool) for m in masks]
         self.bases = [np.asarray(b, np.float64) for b in bases]
         self.scales = np.asarray(scales, np.float64)
         self.weights = np.asarray(weights, np.float64)  # [K, J]
         self.gamma = float(gamma)
+        self.diversity = None if diversity is None else [np.asarray(t, np.float64) for t in diversity]
 
     @property
     def n_objects(self):
@@ -104,6 +108,8 @@ def otf_patch(setup, coeffs):
     out = []
     for k in range(setup.n_objects):
         phi = phase(setup.bases[k], coeffs, setup.scales[k])
+        if setup.diversity is not None:
+            phi = phi + setup.diversity[k]  # phi_kj = c_k B_k a_j + theta_kj
         pup = pupil_function(setup.masks[k], phi)
         p, q, z, s = psf_from_pupil(pup)
         out.append(dict(P=pup, p=p, z=z, s=s, H=otf(s)))

@@ -190,6 +190,47 @@ def test_piston_invariance():
     assert np.abs(g0[:, -1]).max() <= 1e-8 * np.abs(g0).max()  # dL/d(piston) = 0
 
 
+# ---------------------------------------------- phase diversity (Sec. 2.1)
+
+def _diversity_case():
+    return cases.make_case(n_pix=32, diams=(14.0, 11.0), wavelengths=(6563.0, 8542.0), n_frames=3,
+                           n_modes=6, basis="zernike", seed=20250541)
+
+
+def test_modal_diversity_equals_shifted_coefficients():
+    """A diversity theta_kj = c_k B_k delta_j is the wavefront of delta_j:
+    the loss, object and dL/da at a equal those at a + delta with no
+    diversity (checks that theta is added, per object, unscaled)."""
+    c = _diversity_case()
+    s = c["setup"]
+    a = c["a_eval"][0]
+    delta = synth.kolmogorov_coeffs(7, np.ones(6), 5.0, (3,))
+    theta = [mfbd.phase(s.bases[k], delta, s.scales[k]) for k in range(2)]
+    sd = mfbd.Setup(s.masks, s.bases, s.scales, s.weights, s.gamma, diversity=theta)
+    l1, o1, g1 = mfbd.loss_object_grad_patch(sd, a, c["d"][0])
+    l0, o0, g0 = mfbd.loss_object_grad_patch(s, a + delta, c["d"][0])
+    assert abs(l1 - l0) <= 1e-11 * abs(l0)
+    assert np.abs(o1 - o0).max() <= 1e-10 * np.abs(o0).max()
+    assert np.abs(g1 - g0).max() <= 1e-9 * np.abs(g0).max()
+    # and it is not the same as no diversity, or as the diversity subtracted
+    lm, _, _ = mfbd.loss_object_grad_patch(s, a - delta, c["d"][0])
+    ln, _, _ = mfbd.loss_object_grad_patch(s, a, c["d"][0])
+    assert abs(lm - l1) > 1e-3 * abs(l1) and abs(ln - l1) > 1e-3 * abs(l1)
+
+
+def test_piston_diversity_changes_nothing():
+    c = _diversity_case()
+    s = c["setup"]
+    a = c["a_eval"][0]
+    theta = [np.full((3,) + s.masks[k].shape, 0.3 + 0.7 * k) for k in range(2)]
+    sd = mfbd.Setup(s.masks, s.bases, s.scales, s.weights, s.gamma, diversity=theta)
+    l1, o1, g1 = mfbd.loss_object_grad_patch(sd, a, c["d"][0])
+    l0, o0, g0 = mfbd.loss_object_grad_patch(s, a, c["d"][0])
+    assert abs(l1 - l0) <= 1e-11 * abs(l0)
+    assert np.abs(o1 - o0).max() <= 1e-10 * np.abs(o0).max()
+    assert np.abs(g1 - g0).max() <= 1e-9 * np.abs(g0).max()
+
+
 # ---------------------------------------------- P7: even-mode sign flip
 
 @pytest.mark.parametrize("basis", ["zernike", "kl"])
