@@ -178,6 +178,17 @@ int mfbd_loss_grad_host(mfbd_plan_t plan, const float* coeffs, const void* spect
  * (Sec. 3.1, Eqs. 20-22, then H = F s), e.g. to synthesise data. */
 int mfbd_otf(mfbd_plan_t plan, const float* coeffs, void* otf, void* stream);
 
+/* Phase diversity (Sec. 2.1): a known phase theta_kj added to the wavefront
+ * of object k in frame (diversity channel) j of every patch,
+ * phi_kj = c_k B_k a_j + theta_kj, e.g. a defocus in the diversity channels.
+ *   diversity host [K][J][N][N] float, radians, on the same grid as the pupil
+ *             (read on pupil pixels only); NULL removes it.
+ * Applies to every later evaluation and mfbd_otf on this plan (the forward
+ * model, the loss, the object and dL/da; theta does not depend on a). The
+ * first call allocates K x J x W_k^2 floats of device memory. Synchronises
+ * `stream` (before and after the upload). */
+int mfbd_plan_set_diversity(mfbd_plan_t plan, const float* diversity, void* stream);
+
 /* Host-only plan-time data (no GPU needed), for inspection and tests:
  *   mask     host [N][N] uint8, pupil k (1 inside), or NULL
  *   basis    host [M][N][N] float, modes of object k (0 outside pupil), or NULL

@@ -220,6 +220,25 @@ void grad_layout(int K, const int* npix, int U, int sms, int* chunk, int* splits
     }
 }
 
+// phase[u][i] += div[u mod J][i]: the known diversity phase of frame j
+// added to every patch's phase (phase diversity, Sec. 2.1).
+__global__ void __launch_bounds__(256) add_diversity_kernel(float* __restrict__ phase,
+                                                            const float* __restrict__ div, long long n, int J,
+                                                            int npix) {
+    const long long per = (long long)J * npix;
+    for (long long e = blockIdx.x * 256ll + threadIdx.x; e < n; e += (long long)gridDim.x * 256)
+        phase[e] += div[e % per];
+}
+
+cudaError_t launch_add_diversity(float* phase, const float* div, int U, int J, int npix, int sms, cudaStream_t s) {
+    const long long n = (long long)U * npix;
+    if (n == 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 8ll * sms) blocks = 8ll * sms;
+    add_diversity_kernel<<<(int)blocks, 256, 0, s>>>(phase, div, n, J, npix);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_phase_gemm(const float* a, int U, int M, const float* basis, int npix, float scale,
                               float* phase, cudaStream_t s) {
     if (U == 0) return cudaSuccess;

@@ -49,6 +49,8 @@ struct ObjectData {
     // tile layout, [n_tiles][planes][Nt * Mp]; planes == 0: SIMT kernel
     uint16_t* d_basis_tc = nullptr;
     int tc_planes = 0;
+    float* d_div = nullptr;       // known diversity phases [J][W*W] (phase diversity), or null
+    float* d_div_buf = nullptr;   // their buffer, allocated by the first mfbd_plan_set_diversity
 };
 
 }  // namespace
@@ -312,6 +314,8 @@ int run_phase(mfbd_plan_t p, const float* coeffs, cudaStream_t s, int p0, int np
             e = o.tc_planes > 0 ? launch_phase_mma(p->d_acoef, np * p->J, p->M, o.d_basis_tc, o.W * o.W, o.tc_planes,
                                                    o.scale, out, p->d_err, p->sms, s)
                                 : launch_phase_gemm(coeffs, np * p->J, p->M, o.d_basis, o.W * o.W, o.scale, out, s);
+        if (e == cudaSuccess && o.d_div)  // phi_kj = c_k B_k a_j + theta_kj
+            e = launch_add_diversity(out, o.d_div, np * p->J, p->J, o.W * o.W, p->sms, s);
         prof_end(p, pi, s);
         if (e != cudaSuccess) {
             p->failed = true;
@@ -822,6 +826,36 @@ int mfbd_plan_destroy(mfbd_plan_t p) {
     host_release(p);
     release(p);
     delete p;
+    return MFBD_OK;
+}
+
+int mfbd_plan_set_diversity(mfbd_plan_t p, const float* diversity, void* stream) {
+    int st = check_plan(p);
+    if (st) return st;
+    if ((st = set_device(p))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);  // no queued evaluation may be reading the old phases
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise before setting the diversity");
+    for (int k = 0; k < p->K; ++k) {
+        ObjectData& o = p->obj[k];
+        if (!diversity) {
+            o.d_div = nullptr;  // the buffer stays with the plan's allocations
+            continue;
+        }
+        const int n = p->N, W = o.W;
+        std::vector<float> hb((size_t)p->J * W * W, 0.f);
+        for (int j = 0; j < p->J; ++j)
+            for (int yy = 0; yy < W; ++yy)
+                for (int xx = 0; xx < W; ++xx) {
+                    const size_t g = (size_t)(o.x0 + yy) * n + (o.x0 + xx);
+                    hb[((size_t)j * W + yy) * W + xx] = diversity[((size_t)k * p->J + j) * n * n + g];
+                }
+        if (!o.d_div_buf && (st = dev_alloc(p, &o.d_div_buf, hb.size()))) return st;
+        if ((e = cudaMemcpyAsync(o.d_div_buf, hb.data(), hb.size() * sizeof(float), cudaMemcpyHostToDevice, s)))
+            return cuda_fail(e, "upload diversity");
+        o.d_div = o.d_div_buf;
+    }
+    if ((e = cudaStreamSynchronize(s))) return cuda_fail(e, "upload diversity");
     return MFBD_OK;
 }
 

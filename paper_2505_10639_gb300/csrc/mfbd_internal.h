@@ -64,6 +64,10 @@ cudaError_t launch_adjoint_passes(const FusedParams& prm, const FusedGeometry& g
 // FUSED: all three; OTF: forward only).
 cudaError_t launch_fused(const FusedParams& prm, int mode, const FusedGeometry& g, int sms, cudaStream_t s);
 
+// phase[u][i] += div[u mod J][i] for U units (U a multiple of J): the
+// known diversity phases of the J frames added to every patch's phases.
+cudaError_t launch_add_diversity(float* phase, const float* div, int U, int J, int npix, int sms, cudaStream_t s);
+
 // phase[u][i] = scale * sum_m a[u][m] basis[m][i]  (u < U, i < npix)
 cudaError_t launch_phase_gemm(const float* a, int U, int M, const float* basis, int npix,
                               float scale, float* phase, cudaStream_t s);

@@ -207,6 +207,19 @@ class Plan:
                    "mfbd_otf")
         return out
 
+    def set_diversity(self, diversity, stream=None):
+        """mfbd_plan_set_diversity: known phases theta [K, J, N, N] (radians,
+        host array) added to every patch's wavefronts, or None to remove them."""
+        if diversity is None:
+            ptr, keep = None, None
+        else:
+            keep = np.ascontiguousarray(diversity, dtype=np.float32)
+            if keep.shape != (self.n_objects, self.n_frames, self.n_pix, self.n_pix):
+                raise ValueError("diversity must have shape %s" % ((self.n_objects, self.n_frames, self.n_pix,
+                                                                    self.n_pix),))
+            ptr = ctypes.c_void_p(keep.ctypes.data)
+        _lib.check(self._lib.mfbd_plan_set_diversity(self._h, ptr, _stream(stream)), "mfbd_plan_set_diversity")
+
     def set_profiling(self, enable=True, max_launches=4096):
         """mfbd_plan_set_profiling: time every kernel with CUDA events."""
         _lib.check(self._lib.mfbd_plan_set_profiling(self._h, int(enable), int(max_launches)),
