@@ -380,3 +380,26 @@ def test_phase_diversity(n_pix, diams, generic):
     again = _run_fused(plan, a32, d32)
     for x, y in zip(again, plain):
         assert np.array_equal(x, y)
+
+
+def test_lbfgs_driven_from_the_host(c2_slice):
+    """torch's L-BFGS, driven from the host through the autograd function
+    (the optimiser of the 961-patch workload's description), lowers the loss
+    of every patch and its gradient from the evaluation point."""
+    from paper_2505_10639_gb300.mfbd import momfbd_loss
+    a32, d32, _ = _inputs(c2_slice)
+    plan = _plan_for(c2_slice)
+    d = torch.from_numpy(d32).cuda()
+    a = torch.from_numpy(a32).cuda().requires_grad_(True)
+    opt = torch.optim.LBFGS([a], lr=1.0, max_iter=50, history_size=10, line_search_fn="strong_wolfe")
+    l0 = momfbd_loss(a, d, plan).detach().clone()
+
+    def closure():
+        opt.zero_grad()
+        loss = momfbd_loss(a, d, plan).sum()
+        loss.backward()
+        return loss
+
+    opt.step(closure)
+    l1 = momfbd_loss(a, d, plan).detach()
+    assert torch.all(l1 < 0.9 * l0), (l0, l1)
