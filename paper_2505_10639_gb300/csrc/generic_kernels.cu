@@ -75,41 +75,32 @@ __global__ void __launch_bounds__(Cta<N>::THREADS, Cta<N>::MIN_CTAS) generic_adj
     }
 }
 
-// One CTA per patch (persistent over patches): its kRedWarps warps share
-// every object's frequencies (warp w takes f = 32 w + lane + 32 kRedWarps i);
-// the patch loss adds the warps' sums of an object in warp order, then the
-// objects in order.
-constexpr int kRedWarps = 8;
-__global__ void __launch_bounds__(32 * kRedWarps) generic_reduce_kernel(const GenericParams prm) {
-    __shared__ double sobj[kMaxObjects * kRedWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// One CTA per patch (persistent over patches), one warp per object; the
+// patch loss sums the objects in order.
+__global__ void __launch_bounds__(32 * kMaxObjects) generic_reduce_kernel(const GenericParams prm) {
+    __shared__ double sobj[kMaxObjects];
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = prm.N, half = N * (N / 2 + 1), J = prm.J;
     const size_t dstride = (size_t)N * prm.spec_ld;
     for (int p = blockIdx.x; p < prm.P; p += gridDim.x) {
-        for (int k = 0; k < prm.K; ++k) {
-            const size_t unit0 = ((size_t)p * prm.K + k) * J;
-            RedPtr r;
-            r.N = N;
-            r.J = J;
-            r.spec_ld = prm.spec_ld;
-            r.gamma = prm.gamma;
-            r.d = prm.spectra + unit0 * dstride;
-            r.h = prm.gscr + unit0 * half;
-            r.w = prm.weights + (size_t)k * J;
-            r.supp = prm.obj[k].supp;
-            r.sw = prm.sw;
-            r.obj = prm.object ? prm.object + ((size_t)p * prm.K + k) * dstride : nullptr;
-            const double v = reduce_warp(r, lane, 32 * warp, 32 * kRedWarps);
-            if (lane == 0) sobj[k * kRedWarps + warp] = v;
-        }
+        const size_t unit0 = ((size_t)p * prm.K + k) * J;
+        RedPtr r;
+        r.N = N;
+        r.J = J;
+        r.spec_ld = prm.spec_ld;
+        r.gamma = prm.gamma;
+        r.d = prm.spectra + unit0 * dstride;
+        r.h = prm.gscr + unit0 * half;
+        r.w = prm.weights + (size_t)k * J;
+        r.supp = prm.obj[k].supp;
+        r.sw = prm.sw;
+        r.obj = prm.object ? prm.object + ((size_t)p * prm.K + k) * dstride : nullptr;
+        const double v = reduce_warp(r, lane);
+        if (lane == 0) sobj[k] = v;
         __syncthreads();
         if (threadIdx.x == 0) {
             double tot = 0.0;
-            for (int k = 0; k < prm.K; ++k) {
-                double tk = 0.0;
-                for (int w = 0; w < kRedWarps; ++w) tk += sobj[k * kRedWarps + w];
-                tot += tk;
-            }
+            for (int i = 0; i < prm.K; ++i) tot += sobj[i];
             prm.loss[p] = tot;
         }
         __syncthreads();
@@ -198,7 +189,7 @@ cudaError_t launch_generic_adjoint(const GenericParams& prm, int sms, cudaStream
 
 cudaError_t launch_generic_reduction(const GenericParams& prm, int sms, cudaStream_t s) {
     if (prm.P == 0) return cudaSuccess;
-    const int threads = 32 * kRedWarps;
+    const int threads = 32 * prm.K;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, generic_reduce_kernel, threads, 0);
     if (e != cudaSuccess) return e;
