@@ -17,10 +17,13 @@ It is a plain, slow, obviously correct restatement of the paper
 * ``mfbd``   -- wavefront, pupil, PSF, OTF (Sec. 3.1, Eqs. 20-22), the
   Wiener object and the object-eliminated loss (Sec. 2.2.1, Eqs. 11-12), and
   the analytic gradient of that loss with respect to the modal coefficients.
+* ``patches`` -- the patch grid, mean-subtracted modified-Hanning
+  apodisation, data spectra of patches and the weighted merge of patch
+  objects into a mosaic (Sec. 5.2).
 
 Every function computes in float64/complex128. Each one is pinned by tests
 in ``tests/test_oracle_*.py`` against closed forms, invariants, brute force
 and published tables; none is "parity unpinned".
 """
 
-from . import dft, optics, mfbd  # noqa: F401
+from . import dft, optics, mfbd, patches  # noqa: F401

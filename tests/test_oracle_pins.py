@@ -520,3 +520,60 @@ def test_half_and_full_spectrum_roundtrip():
     half = mfbd.half_spectrum(full)
     assert half.shape == (2, 16, 9)
     assert np.allclose(mfbd.full_from_half(half, 16), full, atol=1e-12)
+
+
+# ---------------------------------------------- patches, apodisation, merge (Sec. 5.2)
+
+def test_hanning_window_shape():
+    from oracle import patches
+    assert np.array_equal(patches.hanning_window(64, 0), np.ones(64))
+    for n, b in ((64, 6), (48, 5), (128, 12)):
+        w = patches.hanning_window(n, b)
+        assert np.allclose(w, w[::-1], rtol=0, atol=1e-15)          # symmetric
+        assert np.all(w[b:n - b] == 1.0) and np.all((w > 0) & (w <= 1))
+        assert np.allclose(w[:b] + w[:b][::-1], 1.0, rtol=0, atol=1e-14)  # raised-cosine transition
+        assert np.all(np.diff(w[:b]) > 0)
+
+
+def test_patch_grid_of_the_961_patch_field():
+    from oracle import patches
+    g = patches.patch_grid(1024, 1024, 64, 32)
+    assert len(g) == 31 * 31 and g[0] == (0, 0) and g[-1] == (960, 960) and g[1] == (0, 32)
+    assert len(patches.patch_grid(4096, 4096, 128, 64)) == 63 * 63
+
+
+def test_spectra_from_frames_is_the_fft_of_the_apodised_patch():
+    from oracle import patches
+    g = np.random.default_rng(3)
+    frames = 1.0 + 0.1 * g.standard_normal((2, 3, 80, 112))
+    d = patches.spectra_from_frames(frames, 48, 16, 5)
+    grid = patches.patch_grid(80, 112, 48, 16)
+    assert d.shape == (len(grid), 2, 3, 48, 48)
+    w1 = patches.hanning_window(48, 5)
+    win = np.outer(w1, w1)
+    for p in (0, len(grid) - 1):
+        y0, x0 = grid[p]
+        tile = frames[1, 2, y0:y0 + 48, x0:x0 + 48]
+        apod = (tile - tile.mean()) * win + tile.mean()
+        assert np.allclose(d[p, 1, 2], np.fft.fft2(apod), rtol=0, atol=1e-10)
+    flat = np.full((1, 1, 64, 64), 3.25)
+    assert np.allclose(patches.apodize(flat[0, 0], 6), 3.25, rtol=0, atol=1e-14)  # a flat patch is unchanged
+
+
+def test_merge_of_unprocessed_patches_is_the_image():
+    """Patches cut from an image, taken to the Fourier domain and back
+    (object_images), merge into the same image wherever a patch covers it
+    (the weights form a partition of unity), and 0 elsewhere."""
+    from oracle import patches
+    g = np.random.default_rng(4)
+    img = g.standard_normal((2, 100, 90))
+    n, ov, b = 32, 16, 6
+    grid = patches.patch_grid(100, 90, n, ov)
+    tiles = np.array([[img[k, y0:y0 + n, x0:x0 + n] for k in range(2)] for y0, x0 in grid])
+    back = patches.object_images(np.fft.fft2(tiles))
+    assert np.allclose(back, tiles, rtol=0, atol=1e-12)
+    m = patches.merge(back, 100, 90, ov, b)
+    hmax = grid[-1][0] + n
+    wmax = grid[-1][1] + n
+    assert np.allclose(m[:, :hmax, :wmax], img[:, :hmax, :wmax], rtol=0, atol=1e-12)
+    assert np.all(m[:, hmax:, :] == 0) and np.all(m[:, :, wmax:] == 0)
