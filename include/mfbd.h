@@ -189,6 +189,39 @@ int mfbd_otf(mfbd_plan_t plan, const float* coeffs, void* otf, void* stream);
  * `stream` (before and after the upload). */
 int mfbd_plan_set_diversity(mfbd_plan_t plan, const float* diversity, void* stream);
 
+/* Data front end of a field (Sec. 5.2): the plan's spectra from frames.
+ *   frames  dev [K][J][height][width] float, the observed frames of every
+ *           object and frame.
+ * The field is cut into patches of n_pix px at stride n_pix - overlap, as
+ * many as fit from the first row and column (their number must be the
+ * plan's n_patches; patch p at row p / nx, column p % nx of the grid). In
+ * every patch and frame the patch mean is subtracted, the modified Hanning
+ * window applied (1 inside, a raised-cosine transition of `border` px at
+ * each edge evaluated at pixel centres: w[x] = (1 - cos(pi (x + 1/2) /
+ * border)) / 2 within `border` of an edge) and the mean added back;
+ *   spectra dev [P][K][J][N][N/2+1] complex64 receives the unnormalised DFT
+ *           of the result, in the layout mfbd_loss_grad reads.
+ * Half-spectrum plans only (MFBD_ERR_UNSUPPORTED otherwise);
+ * MFBD_ERR_INVALID_ARG for overlap outside [0, n_pix), border outside
+ * [0, n_pix / 2], a field smaller than a patch or a patch count that is not
+ * the plan's. Asynchronous; allocates nothing. */
+int mfbd_spectra_from_frames(mfbd_plan_t plan, const float* frames, int height, int width, int overlap,
+                             int border, void* spectra, void* stream);
+
+/* Back end (Sec. 5.2): the mosaic of the patch objects.
+ *   object dev [P][K][N][N/2+1] complex64, e.g. the Wiener objects of
+ *          mfbd_forward / mfbd_loss_grad;
+ *   image  dev [K][height][width] float receives, per pixel, the average of
+ *          the patches covering it (patch grid as mfbd_spectra_from_frames),
+ *          each patch object taken to the image domain by the inverse DFT
+ *          normalised by 1 / N^2 and weighted by the window of `border` px;
+ *          0 where no patch covers the pixel.
+ * Same argument checks as mfbd_spectra_from_frames. The first call
+ * allocates P x K x N^2 floats of plan scratch; later calls allocate
+ * nothing. Asynchronous. */
+int mfbd_merge_objects(mfbd_plan_t plan, const void* object, int height, int width, int overlap, int border,
+                       float* image, void* stream);
+
 /* Host-only plan-time data (no GPU needed), for inspection and tests:
  *   mask     host [N][N] uint8, pupil k (1 inside), or NULL
  *   basis    host [M][N][N] float, modes of object k (0 outside pupil), or NULL

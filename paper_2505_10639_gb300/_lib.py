@@ -101,6 +101,10 @@ _SIGNATURES = {
     "mfbd_plan_read_profile": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
     "mfbd_phase_loss_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(PlanDesc), _VP, _VP, _VP, _VP, _VP, _VP]),
     "mfbd_plan_set_diversity": (ctypes.c_int, [_VP, _VP, _VP]),
+    "mfbd_spectra_from_frames": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                _VP, _VP]),
+    "mfbd_merge_objects": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
+                                          _VP]),
     "mfbd_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(PlanDesc), ctypes.c_int, _VP]),
     "mfbd_batch_destroy": (ctypes.c_int, [_VP]),
     "mfbd_batch_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(BatchInfo)]),

@@ -1,0 +1,270 @@
+// Data front and back end of a field (Sec. 5.2, "Division in patches and
+// apodization"): the data spectra of every patch and frame from the frames,
+// and the mosaic of the patch objects.
+//
+// Spectra: one CTA per unit (patch, object, frame), persistent. The patch's
+// mean is subtracted, the modified Hanning window w[y] w[x] applied and the
+// mean added back; rows y and y + N/2 are transformed as one complex line
+// and split into two half spectra, then the half-spectrum columns (columns
+// 0 and N/2, real after the row transforms, packed as one line) are
+// transformed along y: the unnormalised 2-D DFT of the apodised patch,
+// kx <= N/2.
+//
+// Mosaic: (1) per (patch, object) the inverse 2-D DFT of the object's half
+// spectrum, normalised by 1/N^2: columns along ky (0 and N/2 packed, both
+// transforms real), then row pairs Hermitian-extended along kx; (2) per
+// mosaic pixel, the average of the patches covering it weighted by the
+// window, summed in patch order (deterministic).
+//
+// The window (a raised-cosine transition of `border` px at each edge,
+// evaluated at pixel centres) is computed per CTA in shared memory with
+// cosf.
+#include "mfbd_internal.h"
+#include "unit_passes.cuh"
+
+namespace mfbd_dev {
+
+namespace {
+
+using namespace unitpass;
+
+__device__ void window_to_smem(float* w, int n, int border) {
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+        const int e = x < n - 1 - x ? x : n - 1 - x;  // distance to the nearer edge
+        w[x] = e < border ? 0.5f * (1.0f - cosf(3.14159265358979f * ((float)e + 0.5f) / (float)border)) : 1.0f;
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::THREADS) spectra_kernel(const FrontParams prm) {
+    constexpr int S = Geo<N>::S, L = Geo<N>::L, NH = Geo<N>::NH, LINES = Geo<N>::LINES;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    float* win = reinterpret_cast<float*>(fsm);                     // [N]
+    double* red = reinterpret_cast<double*>(fsm + 16 * ((N * 4 + 15) / 16));  // [THREADS / 32]
+    float2* E = reinterpret_cast<float2*>(fsm + 16 * ((N * 4 + 15) / 16) + 16 * 8);
+    float* Ef = reinterpret_cast<float*>(E);
+    const int es = prm.es;
+    const int t = threadIdx.x, sub = t % S, li = t / S;
+    window_to_smem(win, N, prm.border);
+    const long long units = (long long)prm.P * prm.K * prm.J;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        const int j = (int)(u % prm.J);
+        const long long pk = u / prm.J;
+        const int k = (int)(pk % prm.K);
+        const int p = (int)(pk / prm.K);
+        const int y0 = (p / prm.nx) * prm.stride, x0 = (p % prm.nx) * prm.stride;
+        const float* F = prm.frames + ((size_t)k * prm.J + j) * prm.H * prm.Wimg + (size_t)y0 * prm.Wimg + x0;
+        // patch mean (FP64 sums, fixed order)
+        double acc = 0.0;
+        for (int e = t; e < N * N; e += Geo<N>::THREADS) acc += F[(size_t)(e / N) * prm.Wimg + e % N];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        __syncthreads();  // win ready; red free
+        if ((t & 31) == 0) red[t >> 5] = acc;
+        __syncthreads();
+        double tot = 0.0;
+        for (int w = 0; w < Geo<N>::THREADS / 32; ++w) tot += red[w];
+        const float m = (float)(tot / (N * N));
+        // rows y and y + N/2 of the apodised patch as one complex line
+        for (int y = li; y < N / 2; y += LINES) {
+            float2 v[L];
+#pragma unroll
+            for (int n = 0; n < L; ++n) {
+                const int x = S * n + sub;
+                const float a = (F[(size_t)y * prm.Wimg + x] - m) * win[y] * win[x] + m;
+                const float b = (F[(size_t)(y + N / 2) * prm.Wimg + x] - m) * win[y + N / 2] * win[x] + m;
+                v[n] = make_float2(a, b);
+            }
+            line_fft<N, -1>(v, sub);
+            fftreg::static_for<0, L>([&](auto kk) {
+                constexpr int kq = decltype(kk)::value;
+                const float2 pc = conj_partner<N, kq>(v);
+                const int kx = sub * L + kq;
+                if (kx <= N / 2) {
+                    const float2 ra = cscale(cadd(v[kq], pc), 0.5f);
+                    const float2 d = cscale(csub(v[kq], pc), 0.5f);
+                    E[y * es + kx] = ra;
+                    E[(y + N / 2) * es + kx] = make_float2(d.y, -d.x);
+                }
+            });
+        }
+        __syncthreads();
+        // columns kx = 1 .. N/2 - 1; line 0 packs the real columns 0 and N/2
+        float2* D = prm.spectra + (size_t)u * N * NH;
+        for (int kx = li; kx < N / 2; kx += LINES) {
+            float2 v[L];
+#pragma unroll
+            for (int n = 0; n < L; ++n) {
+                const int ky = S * n + sub;
+                v[n] = kx == 0 ? make_float2(E[ky * es].x, E[ky * es + N / 2].x) : E[ky * es + kx];
+            }
+            line_fft<N, -1>(v, sub);
+            fftreg::static_for<0, L>([&](auto kk) {
+                constexpr int kq = decltype(kk)::value;
+                const float2 pc = conj_partner<N, kq>(v);
+                const int ky = sub * L + kq;
+                if (kx > 0) {
+                    D[ky * NH + kx] = v[kq];
+                } else {
+                    const float2 d0 = cscale(cadd(v[kq], pc), 0.5f);
+                    const float2 d = cscale(csub(v[kq], pc), 0.5f);
+                    D[ky * NH] = d0;
+                    D[ky * NH + N / 2] = make_float2(d.y, -d.x);
+                }
+            });
+        }
+        __syncthreads();
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::THREADS) object_image_kernel(const FrontParams prm) {
+    constexpr int S = Geo<N>::S, L = Geo<N>::L, NH = Geo<N>::NH, LINES = Geo<N>::LINES;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    float2* E = reinterpret_cast<float2*>(fsm);
+    const int es = prm.es;
+    const int t = threadIdx.x, sub = t % S, li = t / S;
+    const float sc = 1.0f / (float)(N * N);
+    const long long units = (long long)prm.P * prm.K;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        const float2* O = prm.object + (size_t)u * N * NH;
+        // columns along ky: F^H of O[:, kx]; line 0 packs the columns 0 and
+        // N/2 (both inverse transforms are real)
+        for (int kx = li; kx < N / 2; kx += LINES) {
+            float2 v[L];
+#pragma unroll
+            for (int n = 0; n < L; ++n) {
+                const int ky = S * n + sub;
+                float2 z;
+                if (kx == 0) {
+                    const float2 a = O[ky * NH], b = O[ky * NH + N / 2];
+                    z = make_float2(a.x - b.y, a.y + b.x);  // a + i b
+                } else {
+                    z = O[ky * NH + kx];
+                }
+                v[n] = cconj(z);
+            }
+            line_fft<N, -1>(v, sub);
+#pragma unroll
+            for (int q = 0; q < L; ++q) E[(sub * L + q) * es + kx] = cconj(v[q]);
+        }
+        __syncthreads();
+        // rows y and y + N/2: F^H of the Hermitian-extended rows of T, packed
+        // as T_y + i T_(y+N/2); both results real
+        float* img = prm.oimg + (size_t)u * N * N;
+        for (int y = li; y < N / 2; y += LINES) {
+            float2 v[L];
+#pragma unroll
+            for (int n = 0; n < L; ++n) {
+                const int x = S * n + sub;
+                float2 a, b;
+                if (x == 0) {
+                    a = make_float2(E[y * es].x, 0.f);
+                    b = make_float2(E[(y + N / 2) * es].x, 0.f);
+                } else if (x == N / 2) {
+                    a = make_float2(E[y * es].y, 0.f);
+                    b = make_float2(E[(y + N / 2) * es].y, 0.f);
+                } else if (x < N / 2) {
+                    a = E[y * es + x];
+                    b = E[(y + N / 2) * es + x];
+                } else {
+                    a = cconj(E[y * es + N - x]);
+                    b = cconj(E[(y + N / 2) * es + N - x]);
+                }
+                v[n] = make_float2(a.x - b.y, -(a.y + b.x));  // conj(a + i b)
+            }
+            line_fft<N, -1>(v, sub);
+#pragma unroll
+            for (int q = 0; q < L; ++q) {
+                const int x = sub * L + q;
+                img[(size_t)y * N + x] = v[q].x * sc;
+                img[(size_t)(y + N / 2) * N + x] = -v[q].y * sc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) merge_kernel(const FrontParams prm) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    float* win = reinterpret_cast<float*>(fsm);
+    const int N = prm.N, s = prm.stride;
+    window_to_smem(win, N, prm.border);
+    __syncthreads();
+    const int ny = prm.P / prm.nx;
+    const long long pix = (long long)prm.H * prm.Wimg;
+    for (long long e = blockIdx.x * 256ll + threadIdx.x; e < pix * prm.K; e += (long long)gridDim.x * 256) {
+        const int k = (int)(e / pix);
+        const long long r = e - (long long)k * pix;
+        const int Y = (int)(r / prm.Wimg), X = (int)(r - (long long)Y * prm.Wimg);
+        const int iy0 = Y >= N ? (Y - N + s) / s : 0, iy1 = min(ny - 1, Y / s);
+        const int ix0 = X >= N ? (X - N + s) / s : 0, ix1 = min(prm.nx - 1, X / s);
+        float num = 0.f, den = 0.f;
+        for (int iy = iy0; iy <= iy1; ++iy)
+            for (int ix = ix0; ix <= ix1; ++ix) {
+                const int dy = Y - iy * s, dx = X - ix * s;
+                if (dy >= N || dx >= N) continue;
+                const float w = win[dy] * win[dx];
+                const int p = iy * prm.nx + ix;
+                num = fmaf(w, prm.oimg[(((size_t)p * prm.K + k) * N + dy) * N + dx], num);
+                den += w;
+            }
+        prm.image[e] = den > 0.f ? num / den : 0.f;
+    }
+}
+
+template <class Kern>
+cudaError_t launch_persistent_front(Kern kern, int threads, size_t smem, long long work, int sms, const FrontParams& prm,
+                                    cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long ctas = (long long)sms * per_sm;
+    if (ctas > work) ctas = work;
+    kern<<<(int)ctas, threads, smem, s>>>(prm);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t front_smem(int N, int es) { return (size_t)16 * ((N * 4 + 15) / 16) + 16 * 8 + (size_t)N * es * sizeof(float2); }
+
+cudaError_t launch_spectra_from_frames(const FrontParams& prm, int sms, cudaStream_t s) {
+    const long long units = (long long)prm.P * prm.K * prm.J;
+    if (units == 0) return cudaSuccess;
+    const size_t smem = front_smem(prm.N, prm.es);
+    switch (prm.N) {
+        case 48: return launch_persistent_front(spectra_kernel<48>, Geo<48>::THREADS, smem, units, sms, prm, s);
+        case 64: return launch_persistent_front(spectra_kernel<64>, Geo<64>::THREADS, smem, units, sms, prm, s);
+        case 96: return launch_persistent_front(spectra_kernel<96>, Geo<96>::THREADS, smem, units, sms, prm, s);
+        case 128: return launch_persistent_front(spectra_kernel<128>, Geo<128>::THREADS, smem, units, sms, prm, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_merge_objects(const FrontParams& prm, int sms, cudaStream_t s) {
+    const long long units = (long long)prm.P * prm.K;
+    if (units > 0) {
+        const size_t smem = (size_t)prm.N * prm.es * sizeof(float2);
+        cudaError_t e = cudaErrorInvalidValue;
+        switch (prm.N) {
+            case 48: e = launch_persistent_front(object_image_kernel<48>, Geo<48>::THREADS, smem, units, sms, prm, s); break;
+            case 64: e = launch_persistent_front(object_image_kernel<64>, Geo<64>::THREADS, smem, units, sms, prm, s); break;
+            case 96: e = launch_persistent_front(object_image_kernel<96>, Geo<96>::THREADS, smem, units, sms, prm, s); break;
+            case 128: e = launch_persistent_front(object_image_kernel<128>, Geo<128>::THREADS, smem, units, sms, prm, s); break;
+            default: break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    const long long pix = (long long)prm.H * prm.Wimg * prm.K;
+    if (pix == 0) return cudaSuccess;
+    long long blocks = (pix + 255) / 256;
+    if (blocks > 8ll * sms) blocks = 8ll * sms;
+    merge_kernel<<<(int)blocks, 256, (size_t)prm.N * sizeof(float), s>>>(prm);
+    return cudaGetLastError();
+}
+
+}  // namespace mfbd_dev

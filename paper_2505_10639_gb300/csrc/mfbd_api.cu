@@ -73,6 +73,7 @@ struct mfbd_plan {
     float2* d_gscr = nullptr;   // per unit [P][K][J][N][N/2+1]: OTF, then adjoint seed
     float2* d_pscr = nullptr;   // per unit [P][K][J][N*N]: field
     float2* d_uscr = nullptr;   // per unit [P][K][J][ustride]: pupil phasors on the box
+    float* d_oimg = nullptr;    // mfbd_merge_objects: patch objects in the image domain [P][K][N][N]
     float2* d_e2scr = nullptr;  // recompute, CTA-per-unit kernels: per-CTA second buffers [e2_ctas][N * es2]
     int e2_ctas = 0;
     int ustride = 0;
@@ -856,6 +857,75 @@ int mfbd_plan_set_diversity(mfbd_plan_t p, const float* diversity, void* stream)
         o.d_div = o.d_div_buf;
     }
     if ((e = cudaStreamSynchronize(s))) return cuda_fail(e, "upload diversity");
+    return MFBD_OK;
+}
+
+namespace {
+
+// Field geometry of the front and back end: patches of N px at stride
+// N - overlap that fit in height x width must number the plan's P.
+int front_params(mfbd_plan_t p, int height, int width, int overlap, int border, FrontParams* f) {
+    if (p->flags & MFBD_FLAG_FULL_SPECTRUM)
+        return fail(MFBD_ERR_UNSUPPORTED, "the field front and back end use half spectra");
+    const int n = p->N;
+    if (overlap < 0 || overlap >= n) return fail(MFBD_ERR_INVALID_ARG, "overlap must be in [0, n_pix)");
+    if (border < 0 || 2 * border > n) return fail(MFBD_ERR_INVALID_ARG, "border must be in [0, n_pix / 2]");
+    if (height < n || width < n) return fail(MFBD_ERR_INVALID_ARG, "the field is smaller than a patch");
+    const int st = n - overlap;
+    const long long ny = (height - n) / st + 1, nx = (width - n) / st + 1;
+    if (ny * nx != p->P)
+        return fail(MFBD_ERR_INVALID_ARG, "the plan's n_patches differs from the patches that fit in the field");
+    *f = FrontParams{};
+    f->N = n;
+    f->P = p->P;
+    f->K = p->K;
+    f->J = p->J;
+    f->H = height;
+    f->Wimg = width;
+    f->nx = (int)nx;
+    f->stride = st;
+    f->border = border;
+    f->es = (n / 2 + 1) | 1;
+    return MFBD_OK;
+}
+
+}  // namespace
+
+int mfbd_spectra_from_frames(mfbd_plan_t p, const float* frames, int height, int width, int overlap, int border,
+                             void* spectra, void* stream) {
+    int st = check_plan(p);
+    if (st) return st;
+    if (!frames || !spectra) return fail(MFBD_ERR_INVALID_ARG, "frames and spectra must not be NULL");
+    FrontParams f;
+    if ((st = front_params(p, height, width, overlap, border, &f))) return st;
+    if ((st = set_device(p))) return st;
+    f.frames = frames;
+    f.spectra = static_cast<float2*>(spectra);
+    cudaError_t e = launch_spectra_from_frames(f, p->sms, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        p->failed = true;
+        return cuda_fail(e, "spectra from frames");
+    }
+    return MFBD_OK;
+}
+
+int mfbd_merge_objects(mfbd_plan_t p, const void* object, int height, int width, int overlap, int border,
+                       float* image, void* stream) {
+    int st = check_plan(p);
+    if (st) return st;
+    if (!object || !image) return fail(MFBD_ERR_INVALID_ARG, "object and image must not be NULL");
+    FrontParams f;
+    if ((st = front_params(p, height, width, overlap, border, &f))) return st;
+    if ((st = set_device(p))) return st;
+    if (!p->d_oimg && (st = dev_alloc(p, &p->d_oimg, (size_t)p->P * p->K * p->N * p->N))) return st;
+    f.object = static_cast<const float2*>(object);
+    f.oimg = p->d_oimg;
+    f.image = image;
+    cudaError_t e = launch_merge_objects(f, p->sms, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        p->failed = true;
+        return cuda_fail(e, "merge objects");
+    }
     return MFBD_OK;
 }
 

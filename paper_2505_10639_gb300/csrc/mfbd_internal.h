@@ -153,6 +153,23 @@ cudaError_t launch_generic_forward(const GenericParams& prm, int sms, cudaStream
 cudaError_t launch_generic_reduction(const GenericParams& prm, int sms, cudaStream_t s);
 cudaError_t launch_generic_adjoint(const GenericParams& prm, int sms, cudaStream_t s);
 
+// ----------------------------------------- data front and back end of a field
+struct FrontParams {
+    int N, P, K, J;
+    int H, Wimg;            // frame / mosaic size
+    int nx, stride;         // patches per row, patch stride (N - overlap)
+    int border;             // window transition, px
+    int es;                 // exchange-buffer row stride (complex), >= N/2 + 1
+    const float* frames;    // [K][J][H][Wimg]
+    float2* spectra;        // [P][K][J][N][N/2+1]
+    const float2* object;   // [P][K][N][N/2+1]
+    float* oimg;            // [P][K][N][N] patch objects in the image domain (scratch)
+    float* image;           // [K][H][Wimg]
+};
+size_t front_smem(int N, int es);
+cudaError_t launch_spectra_from_frames(const FrontParams& prm, int sms, cudaStream_t s);
+cudaError_t launch_merge_objects(const FrontParams& prm, int sms, cudaStream_t s);
+
 // Record an error for mfbd_last_error() (fixed-size buffer, no allocation).
 int set_error(int status, const char* why);
 int set_cuda_error(cudaError_t e, const char* where);

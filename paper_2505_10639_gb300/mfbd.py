@@ -207,6 +207,32 @@ class Plan:
                    "mfbd_otf")
         return out
 
+    def spectra_from_frames(self, frames, overlap, border, out=None, stream=None):
+        """mfbd_spectra_from_frames: frames [K, J, H, W] float32 (device) ->
+        the plan's spectra [P, K, J, N, N//2+1] (patches, mean-subtracted
+        modified-Hanning apodisation, DFT)."""
+        if not isinstance(frames, torch.Tensor) or frames.dim() != 4:
+            raise ValueError("frames must be a [K, J, H, W] tensor")
+        h, w = int(frames.shape[2]), int(frames.shape[3])
+        if out is None:
+            out = torch.empty(self.spectra_shape(), dtype=torch.complex64, device=self.device)
+        _lib.check(self._lib.mfbd_spectra_from_frames(
+            self._h, _dev(frames, torch.float32, (self.n_objects, self.n_frames, h, w), "frames"), h, w,
+            int(overlap), int(border), _dev(out, torch.complex64, self.spectra_shape(), "spectra"), _stream(stream)),
+            "mfbd_spectra_from_frames")
+        return out
+
+    def merge_objects(self, obj, height, width, overlap, border, out=None, stream=None):
+        """mfbd_merge_objects: patch objects [P, K, N, N//2+1] -> mosaic
+        [K, height, width] float32."""
+        if out is None:
+            out = torch.empty((self.n_objects, height, width), dtype=torch.float32, device=self.device)
+        _lib.check(self._lib.mfbd_merge_objects(
+            self._h, _dev(obj, torch.complex64, self.object_shape(), "object"), int(height), int(width), int(overlap),
+            int(border), _dev(out, torch.float32, (self.n_objects, height, width), "image"), _stream(stream)),
+            "mfbd_merge_objects")
+        return out
+
     def set_diversity(self, diversity, stream=None):
         """mfbd_plan_set_diversity: known phases theta [K, J, N, N] (radians,
         host array) added to every patch's wavefronts, or None to remove them."""

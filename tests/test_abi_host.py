@@ -261,3 +261,8 @@ def test_uneven_problem_draws():
             assert d % 2 == 0 and 0.35 * p["n_pix"] - 1 <= d <= 0.5 * p["n_pix"] + 1
             assert abs(d * wl - p["diams"][0] * p["wavelengths"][0]) < 1e-6 * d * wl
     assert probs == synth.uneven_problems(20250518, 400)
+
+
+def test_field_front_end_refuses_without_a_plan(lib):
+    assert lib.mfbd_spectra_from_frames(None, None, 96, 96, 32, 6, None, None) == _lib.MFBD_ERR_INVALID_ARG
+    assert lib.mfbd_merge_objects(None, None, 96, 96, 32, 6, None, None) == _lib.MFBD_ERR_INVALID_ARG
