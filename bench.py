@@ -369,7 +369,55 @@ def run_gpu(args, rank, local_rank, world):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, w)
-    return finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk)
+    frontend = None if args.no_frontend else run_frontend(args, plan, coeffs, spectra, w)
+    line = finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk)
+    if frontend is not None:
+        line["frontend"] = frontend
+    return line
+
+
+def run_frontend(args, plan, coeffs, spectra, w):
+    """The field front and back end on the workload's field (not part of a
+    step): mfbd_spectra_from_frames over K x J seeded frames of fov^2 px
+    (overlap N/2, border 6), and mfbd_merge_objects of the Wiener objects;
+    CUDA-event times of each and their algorithmic HBM bytes per launch
+    (frames read + spectra written; objects read, patch images written and
+    read, mosaic written)."""
+    import torch
+    K, J, N, P, fov = len(w["diams"]), w["n_frames"], w["n_pix"], w["n_patches"], w["fov"]
+    if P != ((fov - N) // (N // 2) + 1) ** 2:
+        return None  # a partial field (--patches)
+    g = torch.Generator(device=plan.device)
+    g.manual_seed(w["seed"])
+    frames = 1.0 + 0.1 * torch.randn((K, J, fov, fov), generator=g, device=plan.device)
+    _, _, obj = plan.loss_grad(coeffs, spectra, want_object=True)
+    image = torch.empty((K, fov, fov), dtype=torch.float32, device=plan.device)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.spectra_from_frames(frames, N // 2, 6, out=spectra)
+        plan.merge_objects(obj, fov, fov, N // 2, 6, out=image)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        plan.spectra_from_frames(frames, N // 2, 6, out=spectra)
+    ev[1].record(stream)
+    ev[2].record(stream)
+    for _ in range(args.steps):
+        plan.merge_objects(obj, fov, fov, N // 2, 6, out=image)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    t_spec = ev[0].elapsed_time(ev[1]) / args.steps
+    t_merge = ev[2].elapsed_time(ev[3]) / args.steps
+    b_spec = frames.numel() * 4 + spectra.numel() * 8
+    b_merge = obj.numel() * 8 + 2 * P * K * N * N * 4 + image.numel() * 4
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "peak_gbs": hbm,
+            "spectra_from_frames": {"ms": t_spec, "bytes": b_spec, "gbs": b_spec / (t_spec * 1e-3) / 1e9,
+                                    "frac": b_spec / (t_spec * 1e-3) / 1e9 / hbm},
+            "merge_objects": {"ms": t_merge, "bytes": b_merge, "gbs": b_merge / (t_merge * 1e-3) / 1e9,
+                              "frac": b_merge / (t_merge * 1e-3) / 1e9 / hbm},
+            "field": "%d x %d px, %d patches of %d px, overlap %d, border 6" % (fov, fov, P, N, N // 2)}
 
 
 def run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, w):
@@ -725,6 +773,8 @@ def main():
     ap.add_argument("--patches", type=int, default=0,
                     help="use only the first N patches of the field (smaller profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-frontend", action="store_true",
+                    help="skip timing the field front end (spectra from frames) and back end (mosaic)")
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16_phase"],
                     help="bf16_phase: the phase projection with BF16 operands on the tensor cores")
     ap.add_argument("--projection", default="tensor", choices=["tensor", "simt"],
