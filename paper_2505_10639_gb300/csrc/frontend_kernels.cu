@@ -2,9 +2,9 @@
 // apodization"): the data spectra of every patch and frame from the frames,
 // and the mosaic of the patch objects.
 //
-// Spectra: one CTA per unit (patch, object, frame), persistent. The patch's
-// mean is subtracted, the modified Hanning window w[y] w[x] applied and the
-// mean added back; rows y and y + N/2 are transformed as one complex line
+// Spectra: one CTA per unit (patch, object, frame), persistent. The patch is
+// staged in shared memory by coalesced row loads; its mean is subtracted,
+// the modified Hanning window w[y] w[x] applied and the mean added back; rows y and y + N/2 are transformed as one complex line
 // and split into two half spectra, then the half-spectrum columns (columns
 // 0 and N/2, real after the row transforms, packed as one line) are
 // transformed along y: the unnormalised 2-D DFT of the apodised patch,
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) spectra_kernel(const FrontPar
     float* Ef = reinterpret_cast<float*>(E);
     const int es = prm.es;
     const int t = threadIdx.x, sub = t % S, li = t / S;
-    window_to_smem(win, N, prm.border);
+    window_to_smem(win, N, prm.border);  // read after the first barrier below
     const long long units = (long long)prm.P * prm.K * prm.J;
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
         const int j = (int)(u % prm.J);
@@ -54,28 +54,37 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) spectra_kernel(const FrontPar
         const int p = (int)(pk / prm.K);
         const int y0 = (p / prm.nx) * prm.stride, x0 = (p % prm.nx) * prm.stride;
         const float* F = prm.frames + ((size_t)k * prm.J + j) * prm.H * prm.Wimg + (size_t)y0 * prm.Wimg + x0;
-        // patch mean (FP64 sums, fixed order)
+        // the patch into shared memory (coalesced rows; float rows 2 es
+        // apart, in the exchange buffer) and its mean (FP64 sums, fixed order)
+        __syncthreads();  // the previous unit's column pass has read E
         double acc = 0.0;
-        for (int e = t; e < N * N; e += Geo<N>::THREADS) acc += F[(size_t)(e / N) * prm.Wimg + e % N];
+        for (int e = t; e < N * N; e += Geo<N>::THREADS) {
+            const int y = e / N, x = e - y * N;
+            const float v = F[(size_t)y * prm.Wimg + x];
+            Ef[(size_t)y * 2 * es + x] = v;
+            acc += v;
+        }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        __syncthreads();  // win ready; red free
         if ((t & 31) == 0) red[t >> 5] = acc;
         __syncthreads();
         double tot = 0.0;
         for (int w = 0; w < Geo<N>::THREADS / 32; ++w) tot += red[w];
         const float m = (float)(tot / (N * N));
-        // rows y and y + N/2 of the apodised patch as one complex line
+        // rows y and y + N/2 of the apodised patch as one complex line; the
+        // line's lanes read both rows before any of them writes the two half
+        // spectra over them
         for (int y = li; y < N / 2; y += LINES) {
             float2 v[L];
 #pragma unroll
             for (int n = 0; n < L; ++n) {
                 const int x = S * n + sub;
-                const float a = (F[(size_t)y * prm.Wimg + x] - m) * win[y] * win[x] + m;
-                const float b = (F[(size_t)(y + N / 2) * prm.Wimg + x] - m) * win[y + N / 2] * win[x] + m;
+                const float a = (Ef[(size_t)y * 2 * es + x] - m) * win[y] * win[x] + m;
+                const float b = (Ef[(size_t)(y + N / 2) * 2 * es + x] - m) * win[y + N / 2] * win[x] + m;
                 v[n] = make_float2(a, b);
             }
             line_fft<N, -1>(v, sub);
+            __syncwarp();
             fftreg::static_for<0, L>([&](auto kk) {
                 constexpr int kq = decltype(kk)::value;
                 const float2 pc = conj_partner<N, kq>(v);
