@@ -16,7 +16,7 @@ import numpy as np
 from oracle import mfbd, optics
 from paper_2505_10639_gb300 import synth
 
-SEED_C1 = 20250516  # 20250515 + config index
+SEED_C1 = 20250516  # seed of the single-patch 64 px workload
 
 
 def make_setup(n_pix, diams, wavelengths, n_frames, n_modes, basis="zernike",
@@ -57,7 +57,7 @@ def make_case(n_pix=64, diams=(32.0,), wavelengths=(8542.0,), n_frames=8,
                 obscuration=obscuration, variances=var)
 
 
-def config1():
+def single_patch_64px():
     """1 patch, 64 px, 1 object, 8 frames, 32 px pupil, Zernike Noll 2-21,
     D/r0 = 5."""
     return make_case()

@@ -119,7 +119,7 @@ def test_batch_otf_matches_plan_otf(small_batch):
         assert (hs[i] - hp).abs().max().item() <= 2e-6, i
 
 
-def test_batch_of_config3_kind_against_plans():
+def test_batch_of_uneven_draws_against_plans():
     """24 problems drawn like the 2000-problem workload (patch sizes 48-128,
     1-3 objects, 8-24 frames, 20-66 Zernike modes), spectra from the
     library's own OTFs: each problem's loss, dL/da and object against a plan

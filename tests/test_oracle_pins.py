@@ -109,7 +109,7 @@ def test_brute_force_gradient_8x8():
 # --------------------------------------------------- P2/P3: normalisation
 
 def test_parseval_and_psf_normalisation():
-    c = cases.config1()
+    c = cases.single_patch_64px()
     s = c["setup"]
     inter = mfbd.otf_patch(s, c["a_eval"][0])[0]
     n = c["n_pix"]
@@ -174,7 +174,7 @@ def test_tip_tilt_shifts_psf(shift):
 # ----------------------------------------------------------- P6: piston
 
 def test_piston_invariance():
-    c = cases.config1()
+    c = cases.single_patch_64px()
     s = c["setup"]
     a = c["a_eval"][0]
     piston = np.ones((1,) + s.bases[0].shape[1:]) * s.masks[0]
@@ -345,8 +345,8 @@ def _fd4(f, a, h=2e-4):
     return out
 
 
-def test_gradient_central_differences_config1():
-    c = cases.config1()
+def test_gradient_central_differences_single_patch():
+    c = cases.single_patch_64px()
     s = c["setup"]
     a = c["a_eval"][0]
     _, _, g = mfbd.loss_object_grad_patch(s, a, c["d"][0])
@@ -369,7 +369,7 @@ def test_gradient_central_differences_two_objects_weights():
 # ------------------------------------------------- P13: F versus F^-1
 
 def test_forward_and_inverse_psf_are_reflections():
-    c = cases.config1()
+    c = cases.single_patch_64px()
     s = c["setup"]
     phi = mfbd.phase(s.bases[0], c["a_eval"][0, 0], 1.0)
     pup = mfbd.pupil_function(s.masks[0], phi)

@@ -86,18 +86,18 @@ def _run_fused(plan, a32, d32, want_object=True):
 
 @pytest.fixture(scope="module")
 def c1():
-    return cases.config1()
+    return cases.single_patch_64px()
 
 
 @pytest.fixture(scope="module")
 def c2_slice():
-    # config-2 shapes: 2 objects (6563 A: 36 px pupil, 8542 A: 28 px), 12
+    # the 961-patch field's shapes: 2 objects (6563 A: 36 px pupil, 8542 A: 28 px), 12
     # frames, 44 KL modes; three patches
     return cases.make_case(diams=(36.0, 28.0), wavelengths=(6563.0, 8542.0), n_frames=12, n_modes=44,
                            basis="kl", n_patches=3, seed=20250517)
 
 
-def test_config1_fused_loss_object_grad(c1):
+def test_single_patch_loss_object_grad(c1):
     a32, d32, d_or = _inputs(c1)
     ref = _oracle(c1, a32, d_or)
     plan = _plan_for(c1)
@@ -105,7 +105,7 @@ def test_config1_fused_loss_object_grad(c1):
     _check(c1, loss, grad, obj, ref)
 
 
-def test_config1_otf(c1):
+def test_single_patch_otf(c1):
     a32, _, _ = _inputs(c1)
     plan = _plan_for(c1)
     h = plan.otf(torch.from_numpy(a32).cuda()).cpu().numpy()
@@ -114,7 +114,7 @@ def test_config1_otf(c1):
     assert np.abs(h[0, 0] - href).max() <= 2e-6
 
 
-def test_config2_slice_fused(c2_slice):
+def test_field_slice_loss_object_grad(c2_slice):
     a32, d32, d_or = _inputs(c2_slice)
     ref = _oracle(c2_slice, a32, d_or)
     plan = _plan_for(c2_slice)

@@ -52,10 +52,10 @@ def _noalloc(d, phase, spectra, want_object):
     return loss.cpu().numpy(), gphi.cpu().numpy(), (obj.cpu().numpy() if obj is not None else None)
 
 
-@pytest.mark.parametrize("kind", ["two_objects_kl", "config1"])
+@pytest.mark.parametrize("kind", ["two_objects_kl", "single_patch"])
 def test_noalloc_matches_plan_path_twice(kind):
-    if kind == "config1":
-        case = cases.config1()
+    if kind == "single_patch":
+        case = cases.single_patch_64px()
     else:
         case = cases.make_case(diams=(36.0, 28.0), wavelengths=(6563.0, 8542.0), n_frames=12, n_modes=44,
                                basis="kl", n_patches=3, seed=20250517)
