@@ -222,6 +222,18 @@ int mfbd_spectra_from_frames(mfbd_plan_t plan, const float* frames, int height, 
 int mfbd_merge_objects(mfbd_plan_t plan, const void* object, int height, int width, int overlap, int border,
                        float* image, void* stream);
 
+/* Fourier filter of the objects (Sec. 4.1.1, the top-hat filter with a
+ * cosine transition): O_k(u) *= H_k(u) in place, H = 1 for f <= f_lower[k],
+ * 0 for f >= f_upper[k], (1 + cos(pi (f - f_lower) / (f_upper - f_lower))) / 2
+ * between, f = |u| / D_p,k the frequency in units of object k's diffraction
+ * limit (|u| in frequency bins of the N x N grid, D_p,k its pupil diameter
+ * in px).
+ *   object           dev [P][K][N][N/2+1] (or [N][N]) complex64, as
+ *                    mfbd_forward returns it;
+ *   f_lower, f_upper host [K], 0 <= f_lower < f_upper.
+ * Asynchronous; allocates nothing. */
+int mfbd_filter_objects(mfbd_plan_t plan, void* object, const float* f_lower, const float* f_upper, void* stream);
+
 /* Host-only plan-time data (no GPU needed), for inspection and tests:
  *   mask     host [N][N] uint8, pupil k (1 inside), or NULL
  *   basis    host [M][N][N] float, modes of object k (0 outside pupil), or NULL

@@ -89,3 +89,17 @@ def merge(images, height, width, overlap, border):
     covered = den > 0
     out[:, covered] = num[:, covered] / den[covered]
     return out
+
+
+def tophat_cosine_filter(n, diam_px, f_lower, f_upper):
+    """The low-pass filter of the object (Sec. 4.1.1, "Fourier filtering"),
+    on the full n x n frequency grid [ky, kx]: 1 below f_lower, 0 above
+    f_upper, (1 + cos(pi (f - f_lower) / (f_upper - f_lower))) / 2 between,
+    f = |u| / D_p the frequency in units of the diffraction limit (the OTF of
+    a D_p px pupil reaches |u| = D_p frequency bins)."""
+    k = np.fft.fftfreq(n) * n  # signed frequency index
+    f = np.hypot(k[:, None], k[None, :]) / float(diam_px)
+    h = np.where(f <= f_lower, 1.0, 0.0)
+    mid = (f > f_lower) & (f < f_upper)
+    h[mid] = 0.5 * (1.0 + np.cos(np.pi * (f[mid] - f_lower) / (f_upper - f_lower)))
+    return h

@@ -103,6 +103,7 @@ _SIGNATURES = {
     "mfbd_plan_set_diversity": (ctypes.c_int, [_VP, _VP, _VP]),
     "mfbd_spectra_from_frames": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 _VP, _VP]),
+    "mfbd_filter_objects": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "mfbd_merge_objects": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
                                           _VP]),
     "mfbd_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(PlanDesc), ctypes.c_int, _VP]),

@@ -16,6 +16,9 @@
 // mosaic pixel, the average of the patches covering it weighted by the
 // window, summed in patch order (deterministic).
 //
+// Object filter: the top-hat filter with a cosine transition of Sec. 4.1.1
+// applied to objects in place (one thread per frequency).
+//
 // The window (a raised-cosine transition of `border` px at each edge,
 // evaluated at pixel centres) is computed per CTA in shared memory with
 // cosf.
@@ -222,6 +225,26 @@ __global__ void __launch_bounds__(256) merge_kernel(const FrontParams prm) {
     }
 }
 
+// Object filter (Sec. 4.1.1): O_k(u) *= H_k(u), 1 below f_lower, 0 above
+// f_upper, a cosine transition between, f = |u| / D_p,k.
+__global__ void __launch_bounds__(256) filter_kernel(const FilterParams prm) {
+    const int N = prm.N, ld = prm.ld;
+    const long long per = (long long)N * ld;
+    const long long n = (long long)prm.P * prm.K * per;
+    for (long long e = blockIdx.x * 256ll + threadIdx.x; e < n; e += (long long)gridDim.x * 256) {
+        const int k = (int)((e / per) % prm.K);
+        const long long r = e % per;
+        const int ky = (int)(r / ld), kx = (int)(r - (long long)ky * ld);
+        const float fy = (float)(ky <= N / 2 ? ky : ky - N), fx = (float)(kx <= N / 2 ? kx : kx - N);
+        const float f = sqrtf(fy * fy + fx * fx) * prm.inv_diam[k];
+        const float lo = prm.f_lower[k], hi = prm.f_upper[k];
+        float h = f <= lo ? 1.0f : 0.0f;
+        if (f > lo && f < hi) h = 0.5f * (1.0f + cosf(3.14159265358979f * (f - lo) / (hi - lo)));
+        const float2 o = prm.object[e];
+        prm.object[e] = make_float2(o.x * h, o.y * h);
+    }
+}
+
 template <class Kern>
 cudaError_t launch_persistent_front(Kern kern, int threads, size_t smem, long long work, int sms, const FrontParams& prm,
                                     cudaStream_t s) {
@@ -252,6 +275,15 @@ cudaError_t launch_spectra_from_frames(const FrontParams& prm, int sms, cudaStre
         case 128: return launch_persistent_front(spectra_kernel<128>, Geo<128>::THREADS, smem, units, sms, prm, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_filter_objects(const FilterParams& prm, int sms, cudaStream_t s) {
+    const long long n = (long long)prm.P * prm.K * prm.N * prm.ld;
+    if (n == 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 8ll * sms) blocks = 8ll * sms;
+    filter_kernel<<<(int)blocks, 256, 0, s>>>(prm);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_merge_objects(const FrontParams& prm, int sms, cudaStream_t s) {

@@ -34,6 +34,7 @@ int cuda_fail(cudaError_t e, const char* where) {
 
 struct ObjectData {
     int W = 0, x0 = 0, npup = 0;
+    float diam = 0.f;            // pupil diameter in px (the diffraction limit in frequency bins)
     float scale = 1.f, inv_z = 0.f;
     long long phi_off = 0;
     long long part_off = 0;     // offset of this object's modal-adjoint partial sums
@@ -638,6 +639,7 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
                     }
             if (npup == 0) throw fail(MFBD_ERR_INVALID_ARG, "pupil has no pixel");
             o.npup = npup;
+            o.diam = d->pupil_diam_px[k];
             o.x0 = lo;
             o.W = hi - lo + 1;
             max_box = std::max(max_box, o.W);
@@ -925,6 +927,32 @@ int mfbd_merge_objects(mfbd_plan_t p, const void* object, int height, int width,
     if (e != cudaSuccess) {
         p->failed = true;
         return cuda_fail(e, "merge objects");
+    }
+    return MFBD_OK;
+}
+
+int mfbd_filter_objects(mfbd_plan_t p, void* object, const float* f_lower, const float* f_upper, void* stream) {
+    int st = check_plan(p);
+    if (st) return st;
+    if (!object || !f_lower || !f_upper) return fail(MFBD_ERR_INVALID_ARG, "object and cutoffs must not be NULL");
+    FilterParams f{};
+    f.N = p->N;
+    f.P = p->P;
+    f.K = p->K;
+    f.ld = (p->flags & MFBD_FLAG_FULL_SPECTRUM) ? p->N : p->N / 2 + 1;
+    f.object = static_cast<float2*>(object);
+    for (int k = 0; k < p->K; ++k) {
+        if (!(f_lower[k] >= 0.f) || !(f_upper[k] > f_lower[k]) || !std::isfinite(f_upper[k]))
+            return fail(MFBD_ERR_INVALID_ARG, "cutoffs must satisfy 0 <= f_lower < f_upper");
+        f.inv_diam[k] = 1.0f / p->obj[k].diam;
+        f.f_lower[k] = f_lower[k];
+        f.f_upper[k] = f_upper[k];
+    }
+    if ((st = set_device(p))) return st;
+    cudaError_t e = launch_filter_objects(f, p->sms, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        p->failed = true;
+        return cuda_fail(e, "filter objects");
     }
     return MFBD_OK;
 }

@@ -166,6 +166,12 @@ struct FrontParams {
     float* oimg;            // [P][K][N][N] patch objects in the image domain (scratch)
     float* image;           // [K][H][Wimg]
 };
+struct FilterParams {
+    int N, P, K, ld;        // ld: N / 2 + 1 (half spectra) or N
+    float2* object;         // [P][K][N][ld]
+    float inv_diam[kMaxObjects], f_lower[kMaxObjects], f_upper[kMaxObjects];
+};
+cudaError_t launch_filter_objects(const FilterParams& prm, int sms, cudaStream_t s);
 size_t front_smem(int N, int es);
 cudaError_t launch_spectra_from_frames(const FrontParams& prm, int sms, cudaStream_t s);
 cudaError_t launch_merge_objects(const FrontParams& prm, int sms, cudaStream_t s);

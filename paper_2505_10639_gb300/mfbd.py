@@ -222,6 +222,16 @@ class Plan:
             "mfbd_spectra_from_frames")
         return out
 
+    def filter_objects(self, obj, f_lower, f_upper, stream=None):
+        """mfbd_filter_objects: the top-hat / cosine Fourier filter of every
+        object in place; cutoffs per object in units of the diffraction limit."""
+        lo = np.ascontiguousarray(np.broadcast_to(np.asarray(f_lower, np.float32), (self.n_objects,)))
+        hi = np.ascontiguousarray(np.broadcast_to(np.asarray(f_upper, np.float32), (self.n_objects,)))
+        _lib.check(self._lib.mfbd_filter_objects(
+            self._h, _dev(obj, torch.complex64, self.object_shape(), "object"), ctypes.c_void_p(lo.ctypes.data),
+            ctypes.c_void_p(hi.ctypes.data), _stream(stream)), "mfbd_filter_objects")
+        return obj
+
     def merge_objects(self, obj, height, width, overlap, border, out=None, stream=None):
         """mfbd_merge_objects: patch objects [P, K, N, N//2+1] -> mosaic
         [K, height, width] float32."""

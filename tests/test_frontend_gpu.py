@@ -91,3 +91,22 @@ def test_field_from_frames_to_mosaic():
     ref = opatches.merge(opatches.object_images(oo), h, w, ov, bd)
     err = np.abs(mosaic - ref).max() / np.abs(ref).max()
     assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("n,full", [(64, False), (64, True), (96, False)])
+def test_filter_objects(n, full):
+    """The top-hat / cosine Fourier filter of the objects in place, against
+    the oracle's filter, per object with its own pupil and cutoffs."""
+    from paper_2505_10639_gb300.mfbd import Plan
+    g = np.random.default_rng(n + full)
+    diams = (0.5 * n, 0.4 * n)
+    plan = Plan(n, 3, list(diams), [6563.0, 6563.0 * diams[0] / diams[1]], 2, 6, basis="zernike", gamma=1e-3,
+                full_spectrum=full)
+    cols = n if full else n // 2 + 1
+    o = (g.standard_normal((3, 2, n, cols)) + 1j * g.standard_normal((3, 2, n, cols))).astype(np.complex64)
+    t = torch.from_numpy(o).cuda()
+    plan.filter_objects(t, [0.7, 0.6], [0.8, 0.75])
+    got = t.cpu().numpy()
+    for k, (d, lo, hi) in enumerate(zip(diams, (0.7, 0.6), (0.8, 0.75))):
+        h = opatches.tophat_cosine_filter(n, d, lo, hi)[:, :cols]
+        assert np.abs(got[:, k] - o[:, k] * h[None]).max() <= 1e-6 * np.abs(o).max()

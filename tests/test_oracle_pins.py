@@ -577,3 +577,20 @@ def test_merge_of_unprocessed_patches_is_the_image():
     wmax = grid[-1][1] + n
     assert np.allclose(m[:, :hmax, :wmax], img[:, :hmax, :wmax], rtol=0, atol=1e-12)
     assert np.all(m[:, hmax:, :] == 0) and np.all(m[:, :, wmax:] == 0)
+
+
+def test_tophat_cosine_filter():
+    """1 at the zero frequency and below f_l, 0 beyond f_u, the cosine
+    transition at its midpoint 1/2, even (a real object stays real), and
+    monotone along an axis."""
+    from oracle import patches
+    n, d = 64, 32.0
+    h = patches.tophat_cosine_filter(n, d, 0.7, 0.8)
+    assert h[0, 0] == 1.0 and h[0, int(0.7 * d)] == 1.0 and h[0, int(0.8 * d) + 1] == 0.0
+    k = np.fft.fftfreq(n) * n
+    f = np.hypot(k[:, None], k[None, :]) / d
+    assert np.all(h[f >= 0.8] == 0.0) and np.all(h[f <= 0.7] == 1.0)
+    assert np.allclose(h, np.roll(np.flip(h, (0, 1)), 1, (0, 1)))  # h(-u) = h(u)
+    assert np.all(np.diff(h[0, : n // 2]) <= 0)
+    hm = patches.tophat_cosine_filter(64, 40.0, 0.5, 0.7)
+    assert abs(hm[0, 24] - 0.5) < 1e-12  # f = 0.6, the midpoint
