@@ -77,13 +77,20 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) spectra_kernel(const FrontPar
         // rows y and y + N/2 of the apodised patch as one complex line; the
         // line's lanes read both rows before any of them writes the two half
         // spectra over them
-        for (int y = li; y < N / 2; y += LINES) {
+        // (every lane of a warp runs every round, inactive ones on zeros, so
+        // that the warp-wide __syncwarp and shuffles see all lanes)
+        for (int y0 = 0; y0 < N / 2; y0 += LINES) {
+            const int y = y0 + li;
+            const bool act = y < N / 2;
             float2 v[L];
 #pragma unroll
             for (int n = 0; n < L; ++n) {
                 const int x = S * n + sub;
-                const float a = (Ef[(size_t)y * 2 * es + x] - m) * win[y] * win[x] + m;
-                const float b = (Ef[(size_t)(y + N / 2) * 2 * es + x] - m) * win[y + N / 2] * win[x] + m;
+                float a = 0.f, b = 0.f;
+                if (act) {
+                    a = (Ef[(size_t)y * 2 * es + x] - m) * win[y] * win[x] + m;
+                    b = (Ef[(size_t)(y + N / 2) * 2 * es + x] - m) * win[y + N / 2] * win[x] + m;
+                }
                 v[n] = make_float2(a, b);
             }
             line_fft<N, -1>(v, sub);
@@ -92,7 +99,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) spectra_kernel(const FrontPar
                 constexpr int kq = decltype(kk)::value;
                 const float2 pc = conj_partner<N, kq>(v);
                 const int kx = sub * L + kq;
-                if (kx <= N / 2) {
+                if (act && kx <= N / 2) {
                     const float2 ra = cscale(cadd(v[kq], pc), 0.5f);
                     const float2 d = cscale(csub(v[kq], pc), 0.5f);
                     E[y * es + kx] = ra;
@@ -103,19 +110,23 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) spectra_kernel(const FrontPar
         __syncthreads();
         // columns kx = 1 .. N/2 - 1; line 0 packs the real columns 0 and N/2
         float2* D = prm.spectra + (size_t)u * N * NH;
-        for (int kx = li; kx < N / 2; kx += LINES) {
+        for (int l0 = 0; l0 < N / 2; l0 += LINES) {
+            const int kx = l0 + li;
+            const bool act = kx < N / 2;
             float2 v[L];
 #pragma unroll
             for (int n = 0; n < L; ++n) {
                 const int ky = S * n + sub;
-                v[n] = kx == 0 ? make_float2(E[ky * es].x, E[ky * es + N / 2].x) : E[ky * es + kx];
+                v[n] = !act ? make_float2(0.f, 0.f)
+                            : kx == 0 ? make_float2(E[ky * es].x, E[ky * es + N / 2].x) : E[ky * es + kx];
             }
             line_fft<N, -1>(v, sub);
             fftreg::static_for<0, L>([&](auto kk) {
                 constexpr int kq = decltype(kk)::value;
                 const float2 pc = conj_partner<N, kq>(v);
                 const int ky = sub * L + kq;
-                if (kx > 0) {
+                if (!act) {
+                } else if (kx > 0) {
                     D[ky * NH + kx] = v[kq];
                 } else {
                     const float2 d0 = cscale(cadd(v[kq], pc), 0.5f);
@@ -142,13 +153,16 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) object_image_kernel(const Fro
         const float2* O = prm.object + (size_t)u * N * NH;
         // columns along ky: F^H of O[:, kx]; line 0 packs the columns 0 and
         // N/2 (both inverse transforms are real)
-        for (int kx = li; kx < N / 2; kx += LINES) {
+        for (int l0 = 0; l0 < N / 2; l0 += LINES) {
+            const int kx = l0 + li;
+            const bool act = kx < N / 2;
             float2 v[L];
 #pragma unroll
             for (int n = 0; n < L; ++n) {
                 const int ky = S * n + sub;
-                float2 z;
-                if (kx == 0) {
+                float2 z = make_float2(0.f, 0.f);
+                if (!act) {
+                } else if (kx == 0) {
                     const float2 a = O[ky * NH], b = O[ky * NH + N / 2];
                     z = make_float2(a.x - b.y, a.y + b.x);  // a + i b
                 } else {
@@ -157,20 +171,25 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) object_image_kernel(const Fro
                 v[n] = cconj(z);
             }
             line_fft<N, -1>(v, sub);
+            if (act) {
 #pragma unroll
-            for (int q = 0; q < L; ++q) E[(sub * L + q) * es + kx] = cconj(v[q]);
+                for (int q = 0; q < L; ++q) E[(sub * L + q) * es + kx] = cconj(v[q]);
+            }
         }
         __syncthreads();
         // rows y and y + N/2: F^H of the Hermitian-extended rows of T, packed
         // as T_y + i T_(y+N/2); both results real
         float* img = prm.oimg + (size_t)u * N * N;
-        for (int y = li; y < N / 2; y += LINES) {
+        for (int y0 = 0; y0 < N / 2; y0 += LINES) {
+            const int y = y0 + li;
+            const bool act = y < N / 2;
             float2 v[L];
 #pragma unroll
             for (int n = 0; n < L; ++n) {
                 const int x = S * n + sub;
-                float2 a, b;
-                if (x == 0) {
+                float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+                if (!act) {
+                } else if (x == 0) {
                     a = make_float2(E[y * es].x, 0.f);
                     b = make_float2(E[(y + N / 2) * es].x, 0.f);
                 } else if (x == N / 2) {
@@ -186,11 +205,13 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) object_image_kernel(const Fro
                 v[n] = make_float2(a.x - b.y, -(a.y + b.x));  // conj(a + i b)
             }
             line_fft<N, -1>(v, sub);
+            if (act) {
 #pragma unroll
-            for (int q = 0; q < L; ++q) {
-                const int x = sub * L + q;
-                img[(size_t)y * N + x] = v[q].x * sc;
-                img[(size_t)(y + N / 2) * N + x] = -v[q].y * sc;
+                for (int q = 0; q < L; ++q) {
+                    const int x = sub * L + q;
+                    img[(size_t)y * N + x] = v[q].x * sc;
+                    img[(size_t)(y + N / 2) * N + x] = -v[q].y * sc;
+                }
             }
         }
         __syncthreads();
