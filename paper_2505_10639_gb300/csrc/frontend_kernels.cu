@@ -58,15 +58,21 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) spectra_kernel(const FrontPar
         const int y0 = (p / prm.nx) * prm.stride, x0 = (p % prm.nx) * prm.stride;
         const float* F = prm.frames + ((size_t)k * prm.J + j) * prm.H * prm.Wimg + (size_t)y0 * prm.Wimg + x0;
         // the patch into shared memory (coalesced rows; float rows 2 es
-        // apart, in the exchange buffer) and its mean (FP64 sums, fixed order)
+        // apart, in the exchange buffer) and its mean
         __syncthreads();  // the previous unit's column pass has read E
-        double acc = 0.0;
-        for (int e = t; e < N * N; e += Geo<N>::THREADS) {
+        // per-thread FP32 partial sums over four interleaved accumulators
+        // (fixed order), combined across the CTA in FP64
+        constexpr int kPer = N * N / Geo<N>::THREADS;
+        float part[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int e = t + i * Geo<N>::THREADS;
             const int y = e / N, x = e - y * N;
             const float v = F[(size_t)y * prm.Wimg + x];
             Ef[(size_t)y * 2 * es + x] = v;
-            acc += v;
+            part[i & 3] += v;
         }
+        double acc = ((double)part[0] + (double)part[1]) + ((double)part[2] + (double)part[3]);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
         if ((t & 31) == 0) red[t >> 5] = acc;
