@@ -31,6 +31,14 @@ namespace {
 
 using namespace unitpass;
 
+// Threads per CTA: one warp for N <= 64 (32 lines per round, every lane
+// busy in the N/2-line passes), 128 for N = 96, 128 (64 lines of two lanes).
+template <int N>
+struct FrontCta {
+    static constexpr int THREADS = N <= 64 ? 32 : Geo<N>::THREADS;
+    static constexpr int LINES = N <= 64 ? 32 : Geo<N>::LINES;
+};
+
 __device__ void window_to_smem(float* w, int n, int border) {
     for (int x = threadIdx.x; x < n; x += blockDim.x) {
         const int e = x < n - 1 - x ? x : n - 1 - x;  // distance to the nearer edge
@@ -39,8 +47,9 @@ __device__ void window_to_smem(float* w, int n, int border) {
 }
 
 template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) spectra_kernel(const FrontParams prm) {
-    constexpr int S = Geo<N>::S, L = Geo<N>::L, NH = Geo<N>::NH, LINES = Geo<N>::LINES;
+__global__ void __launch_bounds__(FrontCta<N>::THREADS) spectra_kernel(const FrontParams prm) {
+    constexpr int S = Geo<N>::S, L = Geo<N>::L, NH = Geo<N>::NH, LINES = FrontCta<N>::LINES;
+    constexpr int T = FrontCta<N>::THREADS;
     extern __shared__ __align__(16) unsigned char fsm[];
     float* win = reinterpret_cast<float*>(fsm);                     // [N]
     double* red = reinterpret_cast<double*>(fsm + 16 * ((N * 4 + 15) / 16));  // [THREADS / 32]
@@ -62,11 +71,11 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) spectra_kernel(const FrontPar
         __syncthreads();  // the previous unit's column pass has read E
         // per-thread FP32 partial sums over four interleaved accumulators
         // (fixed order), combined across the CTA in FP64
-        constexpr int kPer = N * N / Geo<N>::THREADS;
+        constexpr int kPer = N * N / T;
         float part[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < kPer; ++i) {
-            const int e = t + i * Geo<N>::THREADS;
+            const int e = t + i * T;
             const int y = e / N, x = e - y * N;
             const float v = F[(size_t)y * prm.Wimg + x];
             Ef[(size_t)y * 2 * es + x] = v;
@@ -78,7 +87,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) spectra_kernel(const FrontPar
         if ((t & 31) == 0) red[t >> 5] = acc;
         __syncthreads();
         double tot = 0.0;
-        for (int w = 0; w < Geo<N>::THREADS / 32; ++w) tot += red[w];
+        for (int w = 0; w < T / 32; ++w) tot += red[w];
         const float m = (float)(tot / (N * N));
         // rows y and y + N/2 of the apodised patch as one complex line; the
         // line's lanes read both rows before any of them writes the two half
@@ -147,8 +156,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) spectra_kernel(const FrontPar
 }
 
 template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) object_image_kernel(const FrontParams prm) {
-    constexpr int S = Geo<N>::S, L = Geo<N>::L, NH = Geo<N>::NH, LINES = Geo<N>::LINES;
+__global__ void __launch_bounds__(FrontCta<N>::THREADS) object_image_kernel(const FrontParams prm) {
+    constexpr int S = Geo<N>::S, L = Geo<N>::L, NH = Geo<N>::NH, LINES = FrontCta<N>::LINES;
     extern __shared__ __align__(16) unsigned char fsm[];
     float2* E = reinterpret_cast<float2*>(fsm);
     const int es = prm.es;
@@ -296,10 +305,10 @@ cudaError_t launch_spectra_from_frames(const FrontParams& prm, int sms, cudaStre
     if (units == 0) return cudaSuccess;
     const size_t smem = front_smem(prm.N, prm.es);
     switch (prm.N) {
-        case 48: return launch_persistent_front(spectra_kernel<48>, Geo<48>::THREADS, smem, units, sms, prm, s);
-        case 64: return launch_persistent_front(spectra_kernel<64>, Geo<64>::THREADS, smem, units, sms, prm, s);
-        case 96: return launch_persistent_front(spectra_kernel<96>, Geo<96>::THREADS, smem, units, sms, prm, s);
-        case 128: return launch_persistent_front(spectra_kernel<128>, Geo<128>::THREADS, smem, units, sms, prm, s);
+        case 48: return launch_persistent_front(spectra_kernel<48>, FrontCta<48>::THREADS, smem, units, sms, prm, s);
+        case 64: return launch_persistent_front(spectra_kernel<64>, FrontCta<64>::THREADS, smem, units, sms, prm, s);
+        case 96: return launch_persistent_front(spectra_kernel<96>, FrontCta<96>::THREADS, smem, units, sms, prm, s);
+        case 128: return launch_persistent_front(spectra_kernel<128>, FrontCta<128>::THREADS, smem, units, sms, prm, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -319,10 +328,10 @@ cudaError_t launch_merge_objects(const FrontParams& prm, int sms, cudaStream_t s
         const size_t smem = (size_t)prm.N * prm.es * sizeof(float2);
         cudaError_t e = cudaErrorInvalidValue;
         switch (prm.N) {
-            case 48: e = launch_persistent_front(object_image_kernel<48>, Geo<48>::THREADS, smem, units, sms, prm, s); break;
-            case 64: e = launch_persistent_front(object_image_kernel<64>, Geo<64>::THREADS, smem, units, sms, prm, s); break;
-            case 96: e = launch_persistent_front(object_image_kernel<96>, Geo<96>::THREADS, smem, units, sms, prm, s); break;
-            case 128: e = launch_persistent_front(object_image_kernel<128>, Geo<128>::THREADS, smem, units, sms, prm, s); break;
+            case 48: e = launch_persistent_front(object_image_kernel<48>, FrontCta<48>::THREADS, smem, units, sms, prm, s); break;
+            case 64: e = launch_persistent_front(object_image_kernel<64>, FrontCta<64>::THREADS, smem, units, sms, prm, s); break;
+            case 96: e = launch_persistent_front(object_image_kernel<96>, FrontCta<96>::THREADS, smem, units, sms, prm, s); break;
+            case 128: e = launch_persistent_front(object_image_kernel<128>, FrontCta<128>::THREADS, smem, units, sms, prm, s); break;
             default: break;
         }
         if (e != cudaSuccess) return e;
