@@ -62,6 +62,24 @@ FP32_LANES_PER_SM = 128
 NCU_DRAM_BYTES_PER_UNIT = {"forward_passes": (72.987e6 + 503.382e6) / 9600,
                            "adjoint_passes": (659.338e6 + 33.887e6) / 9600,
                            "reduction": (324.479e6 + 120.270e6) / 9600}
+# the same for the 128 px CTA-per-unit kernels with the field recomputed in
+# the adjoint, from one capture (--metrics dram__bytes_read.sum,
+# dram__bytes_write.sum) of the first 48 patches of the 3969-patch field
+# (6144 units, 409 MB of spectra: larger than L2)
+NCU_DRAM_BYTES_PER_UNIT_128 = {"forward_passes": (67911680 + 344916992) / 6144,
+                               "adjoint_passes": (481574144 + 66861568) / 6144,
+                               "reduction": (818419968 + 364834048) / 6144}
+# DRAM bytes per launch of the front-end kernels on the 961-patch 64 px field
+# (one ncu capture of the full launch, --metrics dram__bytes_read.sum,
+# dram__bytes_write.sum): spectra_kernel; object_image_kernel + merge_kernel
+NCU_FRONT_DRAM_BYTES = {"spectra_from_frames": 100790784 + 329911296,
+                        "merge_objects": 37747712 + 5244160 + 31507968}
+# DRAM bytes of the batch kernel per 64 px-equivalent unit, from one ncu
+# capture of the first 200 problems of the 2000-problem batch (13869 units)
+# under the schedule the autotuner picks there (one launch, window 0, the
+# 170-register variant)
+NCU_BATCH_DRAM_BYTES_PER_UNIT64 = (1142750976 + 911612160) / 13868.964937802688
+NCU_BATCH_SCHEDULE = (0, 0, 1)  # mode, window_units, variant of that capture
 METRIC = "loss+grad evals/s (patch*obj*frame units at 64px)"
 UNIT = "units/s"
 
@@ -412,11 +430,14 @@ def run_frontend(args, plan, coeffs, spectra, w):
     b_spec = frames.numel() * 4 + spectra.numel() * 8
     b_merge = obj.numel() * 8 + 2 * P * K * N * N * 4 + image.numel() * 4
     hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    captured = N == 64 and P == 961  # the field of the ncu capture
     return {"bound": "hbm", "peak_gbs": hbm,
             "spectra_from_frames": {"ms": t_spec, "bytes": b_spec, "gbs": b_spec / (t_spec * 1e-3) / 1e9,
-                                    "frac": b_spec / (t_spec * 1e-3) / 1e9 / hbm},
+                                    "frac": b_spec / (t_spec * 1e-3) / 1e9 / hbm,
+                                    "traffic": NCU_FRONT_DRAM_BYTES["spectra_from_frames"] if captured else None},
             "merge_objects": {"ms": t_merge, "bytes": b_merge, "gbs": b_merge / (t_merge * 1e-3) / 1e9,
-                              "frac": b_merge / (t_merge * 1e-3) / 1e9 / hbm},
+                              "frac": b_merge / (t_merge * 1e-3) / 1e9 / hbm,
+                              "traffic": NCU_FRONT_DRAM_BYTES["merge_objects"] if captured else None},
             "field": "%d x %d px, %d patches of %d px, overlap %d, border 6" % (fov, fov, P, N, N // 2)}
 
 
@@ -482,27 +503,31 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
         ms_, n_ = prof[kind]
         return ms_ / max(1, n_)
 
-    # DRAM traffic from the committed ncu capture of the 64 px pass machine;
-    # not measured for the other kernel families
-    ncu_ok = w["n_pix"] == 64 and args.kernels == "pass" and not args.recompute
+    # DRAM traffic from the committed ncu captures of the 64 px pass machine
+    # and of the 128 px kernels with recompute; not measured for the others
+    ncu_tab, ncu_basis = None, "not captured for this kernel family"
+    if w["n_pix"] == 64 and args.kernels == "pass" and not args.recompute:
+        ncu_tab, ncu_basis = NCU_DRAM_BYTES_PER_UNIT, "ncu DRAM bytes per unit (400-patch capture) x units per launch"
+    elif w["n_pix"] == 128 and args.recompute:
+        ncu_tab, ncu_basis = NCU_DRAM_BYTES_PER_UNIT_128, "ncu DRAM bytes per unit (48-patch capture) x units per launch"
+    ncu_ok = ncu_tab is not None
     kernels = {}
     for name, kind, work in (("forward_passes", "forward", fwd_flops), ("adjoint_passes", "adjoint", adj_flops)):
         t = per_launch(kind)
         a = work / (t * 1e-3) / 1e12 if t > 0 else 0.0
         kernels[name] = {"bound": "alu", "ms": t, "achieved": a, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": a / alu_peak, "work_per_launch": work,
-                         "traffic": NCU_DRAM_BYTES_PER_UNIT[name] * units_of(w) if ncu_ok else None}
+                         "traffic": ncu_tab[name] * units_of(w) if ncu_ok else None}
     t = per_launch("reduction")
     a = red_bytes / (t * 1e-3) / 1e9 if t > 0 else 0.0
     kernels["reduction"] = {"bound": "hbm", "ms": t, "achieved": a, "peak": hbm_peak, "unit": "GB/s",
                             "frac": a / hbm_peak, "work_per_launch": red_bytes,
-                            "traffic": NCU_DRAM_BYTES_PER_UNIT["reduction"] * units_of(w) if ncu_ok else None}
+                            "traffic": ncu_tab["reduction"] * units_of(w) if ncu_ok else None}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     dk = kernels[dom]
     roofline = {"bound": dk["bound"], "kernel": dom, "achieved": dk["achieved"], "peak": dk["peak"],
                 "unit": dk["unit"], "frac": dk["frac"], "traffic": dk["traffic"],
-                "traffic_basis": ("ncu DRAM bytes per unit (400-patch capture) x units per launch" if ncu_ok
-                                  else "not captured for this kernel family"),
+                "traffic_basis": ncu_basis,
                 "peak_basis": ("FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock)"
                                % (n_sm, FP32_LANES_PER_SM, sm_max)) if dk["bound"] == "alu"
                 else "HBM copy bandwidth of MEASURED_PEAKS.json",
@@ -525,7 +550,9 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
         "roofline": roofline,
         "kernels": kernels,
         "kernels_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in prof.items()},
-        "gpu_launches": int(sum(v[1] for v in prof.values())),
+        # a split frame reduction adds the kernel that sums its per-split losses
+        "gpu_launches": int(sum(v[1] for v in prof.values())
+                            + (prof["reduction"][1] if info.get("reduction_split", 1) > 1 else 0)),
         "clocks": clk,
         "plan": info,
     }
@@ -735,6 +762,7 @@ def run_gpu_batch(args, rank, local_rank, world):
     flops = batch_flops(probs)
     achieved = flops / (local_ms * 1e-3) / 1e12
     units = sum(p["n_objects"] * p["n_frames"] for p in probs)
+    captured = (info["mode"], info["window_units"], info["variant"]) == NCU_BATCH_SCHEDULE
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -750,8 +778,11 @@ def run_gpu_batch(args, rank, local_rank, world):
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": e2e,
         "roofline": {"bound": "alu", "kernel": "batch_kernel", "achieved": achieved, "peak": alu_peak,
-                     "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
-                     "traffic_basis": "not captured for this kernel",
+                     "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                     "traffic": NCU_BATCH_DRAM_BYTES_PER_UNIT64 * u64 if captured else None,
+                     "traffic_basis": ("ncu DRAM bytes per 64 px-equivalent unit (first 200 problems, same "
+                                       "schedule) x units of the launch" if captured
+                                       else "not captured for this schedule"),
                      "peak_basis": "FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock)"
                                    % (n_sm, FP32_LANES_PER_SM, peaks.get("sm_max_mhz", 2070.0)),
                      "work_per_launch": flops, "kernel_ms": local_ms},

@@ -113,6 +113,8 @@ typedef struct {
     size_t workspace_bytes; /* device memory owned by the plan */
     int slots_per_cta;      /* frames a CTA of the fused kernel works on at once */
     int ctas;               /* CTAs of the fused kernel */
+    int reduction_split;    /* warps per (patch, object) of the frame reduction; > 1 adds a
+                               second launch that sums the per-split losses in order */
 } mfbd_plan_info;
 
 /* Create a plan: validates the descriptor, samples pupils, builds the modal

@@ -59,6 +59,7 @@ class PlanInfo(ctypes.Structure):
         ("workspace_bytes", ctypes.c_size_t),
         ("slots_per_cta", ctypes.c_int),
         ("ctas", ctypes.c_int),
+        ("reduction_split", ctypes.c_int),
     ]
 
 

@@ -2,6 +2,8 @@
 // 64 (48, 96, 128), and for 64 on request: one CTA per unit (patch, object,
 // frame), persistent over the units; for N <= 64 the CTA is one warp. The passes themselves (Sec. 3.1,
 // Eqs. 20-22 and their adjoint) are in unit_passes.cuh.
+#include <algorithm>
+
 #include "mfbd_internal.h"
 #include "unit_passes.cuh"
 
@@ -54,8 +56,9 @@ __global__ void __launch_bounds__(Cta<N>::THREADS, Cta<N>::MIN_CTAS) generic_for
     float2* E = reinterpret_cast<float2*>(gsm);
     const long long units = (long long)prm.P * prm.K * prm.J;
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-        if constexpr (Cta<N>::WARP) unit_forward_rounds<N, 32>(unit_ptr<N>(prm, u), E, prm.es, threadIdx.x, WarpBar{});
-        else unit_forward<N, 64>(unit_ptr<N>(prm, u), E, prm.es, threadIdx.x, CtaBar{});
+        constexpr int L = Cta<N>::LINES;
+        if constexpr (Cta<N>::WARP) unit_forward_rounds<N, L>(unit_ptr<N>(prm, u), E, prm.es, threadIdx.x, WarpBar{});
+        else unit_forward<N, L>(unit_ptr<N>(prm, u), E, prm.es, threadIdx.x, CtaBar{});
     }
 }
 
@@ -68,10 +71,11 @@ __global__ void __launch_bounds__(Cta<N>::THREADS, Cta<N>::MIN_CTAS) generic_adj
     float2* E2 = RECOMPUTE ? prm.e2scr + (size_t)blockIdx.x * N * prm.es2 : nullptr;
     const long long units = (long long)prm.P * prm.K * prm.J;
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        constexpr int L = Cta<N>::LINES;
         if constexpr (Cta<N>::WARP)
-            unit_adjoint<N, 32, RECOMPUTE>(unit_ptr<N>(prm, u), E, prm.es, E2, prm.es2, threadIdx.x, WarpBar{});
+            unit_adjoint<N, L, RECOMPUTE>(unit_ptr<N>(prm, u), E, prm.es, E2, prm.es2, threadIdx.x, WarpBar{});
         else
-            unit_adjoint<N, 64, RECOMPUTE>(unit_ptr<N>(prm, u), E, prm.es, E2, prm.es2, threadIdx.x, CtaBar{});
+            unit_adjoint<N, L, RECOMPUTE>(unit_ptr<N>(prm, u), E, prm.es, E2, prm.es2, threadIdx.x, CtaBar{});
     }
 }
 
@@ -82,7 +86,10 @@ __global__ void __launch_bounds__(32 * kMaxObjects) generic_reduce_kernel(const 
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = prm.N, half = N * (N / 2 + 1), J = prm.J;
     const size_t dstride = (size_t)N * prm.spec_ld;
-    for (int p = blockIdx.x; p < prm.P; p += gridDim.x) {
+    const int S = (prm.rsplit > 1 && prm.lpart) ? prm.rsplit : 1;
+    const long long work = (long long)prm.P * S;
+    for (long long u = blockIdx.x; u < work; u += gridDim.x) {
+        const int p = (int)(u / S), sp = (int)(u - (long long)p * S);
         const size_t unit0 = ((size_t)p * prm.K + k) * J;
         RedPtr r;
         r.N = N;
@@ -95,16 +102,27 @@ __global__ void __launch_bounds__(32 * kMaxObjects) generic_reduce_kernel(const 
         r.supp = prm.obj[k].supp;
         r.sw = prm.sw;
         r.obj = prm.object ? prm.object + ((size_t)p * prm.K + k) * dstride : nullptr;
-        const double v = reduce_warp(r, lane);
+        const double v = reduce_warp(r, lane, 32 * sp, 32 * S);
         if (lane == 0) sobj[k] = v;
         __syncthreads();
         if (threadIdx.x == 0) {
             double tot = 0.0;
             for (int i = 0; i < prm.K; ++i) tot += sobj[i];
-            prm.loss[p] = tot;
+            if (S == 1)
+                prm.loss[p] = tot;
+            else
+                prm.lpart[u] = tot;
         }
         __syncthreads();
     }
+}
+
+__global__ void loss_combine_kernel(const double* __restrict__ lpart, int S, double* __restrict__ loss, int P) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    double tot = 0.0;
+    for (int i = 0; i < S; ++i) tot += lpart[(size_t)p * S + i];
+    loss[p] = tot;
 }
 
 template <class Kern>
@@ -190,12 +208,27 @@ cudaError_t launch_generic_adjoint(const GenericParams& prm, int sms, cudaStream
 cudaError_t launch_generic_reduction(const GenericParams& prm, int sms, cudaStream_t s) {
     if (prm.P == 0) return cudaSuccess;
     const int threads = 32 * prm.K;
+    const int S = (prm.rsplit > 1 && prm.lpart) ? prm.rsplit : 1;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, generic_reduce_kernel, threads, 0);
     if (e != cudaSuccess) return e;
     long long ctas = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    if (ctas > prm.P) ctas = prm.P;
+    if (ctas > (long long)prm.P * S) ctas = (long long)prm.P * S;
     generic_reduce_kernel<<<(int)ctas, threads, 0, s>>>(prm);
+    if ((e = cudaGetLastError()) != cudaSuccess || S == 1) return e;
+    return launch_loss_combine(prm.lpart, S, prm.loss, prm.P, s);
+}
+
+int reduction_split(int P, int K, int N, int sms) {
+    const long long warps = (long long)P * K, want = 8LL * sms;
+    if (warps <= 0 || warps >= want) return 1;
+    const long long smax = std::max(1, N * (N / 2 + 1) / 128);
+    return (int)std::min((want + warps - 1) / warps, smax);
+}
+
+cudaError_t launch_loss_combine(const double* lpart, int S, double* loss, int P, cudaStream_t s) {
+    if (P == 0) return cudaSuccess;
+    loss_combine_kernel<<<(P + 127) / 128, 128, 0, s>>>(lpart, S, loss, P);
     return cudaGetLastError();
 }
 

@@ -77,6 +77,8 @@ struct mfbd_plan {
     float* d_oimg = nullptr;    // mfbd_merge_objects: patch objects in the image domain [P][K][N][N]
     float2* d_e2scr = nullptr;  // recompute, CTA-per-unit kernels: per-CTA second buffers [e2_ctas][N * es2]
     int e2_ctas = 0;
+    int rsplit = 1;             // warps per (patch, object) of the frame reduction
+    double* d_lpart = nullptr;  // rsplit > 1: per-split patch losses [P][rsplit]
     int ustride = 0;
     long long phi_floats = 0;
     size_t workspace = 0;
@@ -259,6 +261,8 @@ FusedParams fused_params(const mfbd_plan* p, int p0, int np, const void* spectra
     f.spec_ld = (p->flags & MFBD_FLAG_FULL_SPECTRUM) ? p->N : p->N / 2 + 1;
     f.loss = loss;
     f.object = static_cast<float2*>(object);
+    f.rsplit = p->rsplit;
+    f.lpart = p->d_lpart;
     for (int k = 0; k < p->K; ++k) {
         f.obj[k].W = p->obj[k].W;
         f.obj[k].x0 = p->obj[k].x0;
@@ -398,6 +402,8 @@ int run_generic(mfbd_plan_t p, int stages, const void* spectra, double* loss, vo
     g.es2 = p->es2;
     g.e2scr = p->d_e2scr;
     g.e2_ctas = p->e2_ctas;
+    g.rsplit = p->rsplit;
+    g.lpart = p->d_lpart;
     for (int k = 0; k < p->K; ++k) {
         const ObjectData& o = p->obj[k];
         g.obj[k].W = o.W;
@@ -744,6 +750,8 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
         if (keep && (st = dev_alloc(p, &p->d_uscr, (size_t)p->P * p->K * p->J * p->ustride))) throw st;
 
         p->sms = prop.multiProcessorCount;
+        p->rsplit = reduction_split(p->P, p->K, n, p->sms);
+        if (p->rsplit > 1 && (st = dev_alloc(p, &p->d_lpart, (size_t)p->P * p->rsplit))) throw st;
         if (!p->generic) {
             p->geo = fused_geometry(max_box);
             int per_sm = max_ctas_per_sm(p->geo);
@@ -971,6 +979,7 @@ int mfbd_plan_get_info(mfbd_plan_t p, mfbd_plan_info* info) {
     }
     info->workspace_bytes = p->workspace;
     info->slots_per_cta = p->generic ? 0 : p->geo.slots;
+    info->reduction_split = p->rsplit;
     info->ctas = p->ctas;
     return MFBD_OK;
 }

@@ -42,6 +42,8 @@ struct FusedParams {
     int spec_ld;              // row stride of D and O in complex elements (33 or 64)
     double* loss;             // [P]
     float2* object;           // [P][K][N][spec_ld] or null
+    int rsplit;               // warps per (patch, object) of the frame reduction (<= 1: one)
+    double* lpart;            // rsplit > 1: per-split patch losses [P][rsplit]
     ObjParams obj[kMaxObjects];
 };
 
@@ -143,6 +145,8 @@ struct GenericParams {
     int es, es2;            // row strides (complex) of the exchange buffers
     float2* e2scr;          // recompute: per-CTA second buffers [ctas][N * es2] in global memory (L2)
     int e2_ctas;            // CTAs e2scr has room for
+    int rsplit;             // warps per (patch, object) of the frame reduction (<= 1: one)
+    double* lpart;          // rsplit > 1: per-split patch losses [P][rsplit]
     GenericObj obj[kMaxObjects];
 };
 
@@ -152,6 +156,14 @@ int generic_adjoint_ctas(int N, int es, int sms);
 cudaError_t launch_generic_forward(const GenericParams& prm, int sms, cudaStream_t s);
 cudaError_t launch_generic_reduction(const GenericParams& prm, int sms, cudaStream_t s);
 cudaError_t launch_generic_adjoint(const GenericParams& prm, int sms, cudaStream_t s);
+
+// Warps per (patch, object) of a frame reduction over P patches of K objects
+// at N px: one while the patches alone give every SM 8 warps, more (each lane
+// keeping at least 4 frequencies) when they are few. A plan fixes it from its
+// patch count, so chunked calls sum the loss in the same order.
+int reduction_split(int P, int K, int N, int sms);
+// loss[p] = sum over s < S of lpart[p][s], in order.
+cudaError_t launch_loss_combine(const double* lpart, int S, double* loss, int P, cudaStream_t s);
 
 // ----------------------------------------- data front and back end of a field
 struct FrontParams {

@@ -462,7 +462,7 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
 // JM > 0: J <= JM, the J spectra and OTFs of a frequency are loaded once, all
 // at once, into registers. JM == 0: any J, streamed from memory twice.
 template <int JM>
-__device__ double reduce_object_warp(const FusedParams& prm, int p, int k) {
+__device__ double reduce_object_warp(const FusedParams& prm, int p, int k, int f0, int fstep) {
     const int lane = threadIdx.x & 31;
     const int J = prm.J;
     const size_t unit0 = ((size_t)p * prm.K + k) * J;
@@ -478,7 +478,7 @@ __device__ double reduce_object_warp(const FusedParams& prm, int p, int k) {
         for (int j = 0; j < JM; ++j) wv[j] = (j < J) ? w[j] : 0.f;
     }
     KahanSum acc;
-    for (int f = lane; f < kHalf; f += 32) {
+    for (int f = f0 + lane; f < kHalf; f += fstep) {
         const int ky = f / kNH, kx = f - ky * kNH;
         const size_t doff = (size_t)ky * prm.spec_ld + kx;
         const float2* dp = dbase + doff;
@@ -611,20 +611,28 @@ __global__ void __launch_bounds__(kThreads, 2) mfbd_pass_kernel(const FusedParam
     }
 }
 
-// Frame reduction: one CTA per patch, warp k reduces object k; the patch
-// loss sums the objects in order (deterministic).
+// Frame reduction: one CTA per (patch, split), warp k reduces the split's
+// frequencies of object k (32-wide blocks s, s + S, s + 2S, ...); the CTA
+// sums the objects in order, and with S > 1 a second kernel sums the splits
+// in order (deterministic for a given S).
 template <int JM>
 __global__ void __launch_bounds__(32 * kMaxObjects) mfbd_reduce_kernel(const FusedParams prm) {
     __shared__ double sobj[kMaxObjects];
     const int k = threadIdx.x >> 5;
-    for (int p = blockIdx.x; p < prm.P; p += gridDim.x) {
-        const double v = reduce_object_warp<JM>(prm, p, k);
+    const int S = (prm.rsplit > 1 && prm.lpart) ? prm.rsplit : 1;
+    const long long work = (long long)prm.P * S;
+    for (long long u = blockIdx.x; u < work; u += gridDim.x) {
+        const int p = (int)(u / S), sp = (int)(u - (long long)p * S);
+        const double v = reduce_object_warp<JM>(prm, p, k, 32 * sp, 32 * S);
         if ((threadIdx.x & 31) == 0) sobj[k] = v;
         __syncthreads();
         if (threadIdx.x == 0) {
             double tot = 0.0;
             for (int i = 0; i < prm.K; ++i) tot += sobj[i];
-            prm.loss[p] = tot;
+            if (S == 1)
+                prm.loss[p] = tot;
+            else
+                prm.lpart[u] = tot;
         }
         __syncthreads();
     }
@@ -668,13 +676,15 @@ cudaError_t launch_pass(const FusedParams& prm, const FusedGeometry& g, int sms,
 template <int JM>
 cudaError_t launch_reduction_jm(const FusedParams& prm, int sms, cudaStream_t s) {
     const int threads = 32 * prm.K;
+    const int S = (prm.rsplit > 1 && prm.lpart) ? prm.rsplit : 1;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mfbd_reduce_kernel<JM>, threads, 0);
     if (e != cudaSuccess) return e;
     long long ctas = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    if (ctas > prm.P) ctas = prm.P;
+    if (ctas > (long long)prm.P * S) ctas = (long long)prm.P * S;
     mfbd_reduce_kernel<JM><<<(int)ctas, threads, 0, s>>>(prm);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess || S == 1) return e;
+    return launch_loss_combine(prm.lpart, S, prm.loss, prm.P, s);
 }
 
 cudaError_t launch_reduction(const FusedParams& prm, int sms, cudaStream_t s) {

@@ -136,7 +136,8 @@ class Plan:
         _lib.check(self._lib.mfbd_plan_get_info(self._h, ctypes.byref(inf)), "mfbd_plan_get_info")
         k = self.n_objects
         return dict(pupil_pixels=list(inf.pupil_pixels[:k]), pupil_box=list(inf.pupil_box[:k]),
-                    workspace_bytes=inf.workspace_bytes, slots_per_cta=inf.slots_per_cta, ctas=inf.ctas)
+                    workspace_bytes=inf.workspace_bytes, slots_per_cta=inf.slots_per_cta, ctas=inf.ctas,
+                    reduction_split=inf.reduction_split)
 
     # ------------------------------------------------------------ calls
     def forward(self, coeffs, spectra, loss=None, obj=None, want_object=True, stream=None):

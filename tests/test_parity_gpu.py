@@ -326,6 +326,29 @@ def test_general_patch_sizes(n_pix, diams, recompute):
     _check(case, loss, grad, obj, ref)
 
 
+@pytest.mark.parametrize("n_pix,diams", [(64, (36.0, 28.0)), (96, (40.0, 30.0))])
+def test_split_frame_reduction(n_pix, diams):
+    """A plan of one patch splits its frame reduction over several warps per
+    object (and sums the per-split losses in a second kernel); a plan of 640
+    patches does not. Patch 0 gets the same object bits from both (every
+    frequency is reduced by one lane either way) and the same loss and dL/da
+    to FP32 summation order."""
+    case = cases.make_case(n_pix=n_pix, diams=diams, wavelengths=(6563.0, 8542.0), n_frames=3, n_modes=12,
+                           basis="kl", n_patches=1, seed=20250519 + n_pix)
+    a32, d32, d_or = _inputs(case)
+    ref = _oracle(case, a32, d_or)
+    one = _plan_for(case)
+    many = _plan_for(case, n_patches=640)
+    assert one.info()["reduction_split"] > 1 and many.info()["reduction_split"] == 1
+    l1, g1, o1 = _run_fused(one, a32, d32)
+    lm, gm, om = _run_fused(many, np.ascontiguousarray(np.tile(a32, (640, 1, 1))),
+                            np.ascontiguousarray(np.tile(d32, (640, 1, 1, 1, 1))))
+    assert np.array_equal(o1[0], om[0]) and np.array_equal(om[0], om[639])
+    assert abs(l1[0] - lm[0]) <= 1e-6 * abs(lm[0])
+    assert np.linalg.norm(g1[0] - gm[0]) <= 1e-5 * np.linalg.norm(gm[0])
+    _check(case, l1, g1, o1, ref)
+
+
 def test_general_kernels_match_64px_pass_machine(c2_slice):
     """N = 64 on the general-size kernels (with and without recompute)
     against the 64-pixel pass machine."""
