@@ -397,10 +397,12 @@ def run_gpu(args, rank, local_rank, world):
 def run_frontend(args, plan, coeffs, spectra, w):
     """The field front and back end on the workload's field (not part of a
     step): mfbd_spectra_from_frames over K x J seeded frames of fov^2 px
-    (overlap N/2, border 6), and mfbd_merge_objects of the Wiener objects;
-    CUDA-event times of each and their algorithmic HBM bytes per launch
-    (frames read + spectra written; objects read, patch images written and
-    read, mosaic written)."""
+    (overlap N/2, border 6), mfbd_merge_objects of the Wiener objects and
+    mfbd_ls_filter_objects (the Lofdahl-Scharmer filter from the spectra and
+    the OTFs); CUDA-event times of each and their algorithmic HBM bytes per
+    launch (frames read + spectra written; objects read, patch images written
+    and read, mosaic written; spectra and OTFs read, filter written, objects
+    read and written)."""
     import torch
     K, J, N, P, fov = len(w["diams"]), w["n_frames"], w["n_pix"], w["n_patches"], w["fov"]
     if P != ((fov - N) // (N // 2) + 1) ** 2:
@@ -427,6 +429,22 @@ def run_frontend(args, plan, coeffs, spectra, w):
     torch.cuda.synchronize()
     t_spec = ev[0].elapsed_time(ev[1]) / args.steps
     t_merge = ev[2].elapsed_time(ev[3]) / args.steps
+    # the Lofdahl-Scharmer filter of the objects from D and the OTFs, noise
+    # power N^2 sigma^2 (the synthetic noise's)
+    otf = plan.otf(coeffs)
+    nu = N * N * w["noise_sigma"] ** 2
+    flt = None
+    for _ in range(args.warmup):
+        flt = plan.ls_filter_objects(spectra, otf, nu, obj=obj)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        plan.ls_filter_objects(spectra, otf, nu, obj=obj)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    t_ls = ev[0].elapsed_time(ev[1]) / args.steps
+    b_ls = spectra.numel() * 8 + otf.numel() * 8 + flt.numel() * 4 + 2 * obj.numel() * 8
+    del otf
     b_spec = frames.numel() * 4 + spectra.numel() * 8
     b_merge = obj.numel() * 8 + 2 * P * K * N * N * 4 + image.numel() * 4
     hbm = measured_peaks().get("hbm_gbs", 6800.0)
@@ -438,6 +456,8 @@ def run_frontend(args, plan, coeffs, spectra, w):
             "merge_objects": {"ms": t_merge, "bytes": b_merge, "gbs": b_merge / (t_merge * 1e-3) / 1e9,
                               "frac": b_merge / (t_merge * 1e-3) / 1e9 / hbm,
                               "traffic": NCU_FRONT_DRAM_BYTES["merge_objects"] if captured else None},
+            "ls_filter_objects": {"ms": t_ls, "bytes": b_ls, "gbs": b_ls / (t_ls * 1e-3) / 1e9,
+                                  "frac": b_ls / (t_ls * 1e-3) / 1e9 / hbm},
             "field": "%d x %d px, %d patches of %d px, overlap %d, border 6" % (fov, fov, P, N, N // 2)}
 
 

@@ -236,6 +236,29 @@ int mfbd_merge_objects(mfbd_plan_t plan, const void* object, int height, int wid
  * Asynchronous; allocates nothing. */
 int mfbd_filter_objects(mfbd_plan_t plan, void* object, const float* f_lower, const float* f_upper, void* stream);
 
+/* The Lofdahl-Scharmer filter of the objects (Sec. 4.1.1, Eq. 25), per patch
+ * and object k:
+ *   H_k(u) = 1 - nu sum_j w_kj |S_kj(u)|^2 / |sum_j w_kj D_kj(u) conj(S_kj(u))|^2,
+ * values below 0.2 set to 0 and above 1 to 1, a 3 x 3 median over the
+ * periodic frequency plane, and every nonzero value not 4-connected to the
+ * zero frequency (periodically) set to 0; then O_k *= H_k.
+ *   spectra      dev D [P][K][J][N][N/2+1] (or [N][N]) complex64, the plan's
+ *                layout, as passed to mfbd_forward;
+ *   otf          dev S [P][K][J][N][N/2+1] complex64, as mfbd_otf writes it;
+ *   noise_power  nu, the noise power of one frame's spectrum per frequency in
+ *                the units of |D|^2 (N^2 sigma^2 for white noise of variance
+ *                sigma^2 per pixel); 1 gives the printed form; finite;
+ *   object       dev [P][K][N][N/2+1] (or [N][N]) complex64, multiplied in
+ *                place, or NULL;
+ *   filter       dev [P][K][N][N/2+1] float receives H, or NULL (not both
+ *                NULL).
+ * The frame weights are the plan's w_kj. FP32 with each product and sum
+ * rounded on its own in a fixed order (no fused multiply-add). One CTA per
+ * (patch, object) with the N x N plane in shared memory (9 N^2 bytes).
+ * Asynchronous; allocates nothing. */
+int mfbd_ls_filter_objects(mfbd_plan_t plan, const void* spectra, const void* otf, float noise_power, void* object,
+                           float* filter, void* stream);
+
 /* Host-only plan-time data (no GPU needed), for inspection and tests:
  *   mask     host [N][N] uint8, pupil k (1 inside), or NULL
  *   basis    host [M][N][N] float, modes of object k (0 outside pupil), or NULL

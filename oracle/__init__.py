@@ -19,11 +19,14 @@ It is a plain, slow, obviously correct restatement of the paper
   the analytic gradient of that loss with respect to the modal coefficients.
 * ``patches`` -- the patch grid, mean-subtracted modified-Hanning
   apodisation, data spectra of patches and the weighted merge of patch
-  objects into a mosaic (Sec. 5.2).
+  objects into a mosaic (Sec. 5.2), and the top-hat / cosine object filter
+  (Sec. 4.1.1).
+* ``filters`` -- the Lofdahl-Scharmer object filter (Sec. 4.1.1, Eq. 25):
+  threshold, 3 x 3 median and connectivity to the zero frequency.
 
 Every function computes in float64/complex128. Each one is pinned by tests
 in ``tests/test_oracle_*.py`` against closed forms, invariants, brute force
 and published tables; none is "parity unpinned".
 """
 
-from . import dft, optics, mfbd, patches  # noqa: F401
+from . import dft, optics, mfbd, patches, filters  # noqa: F401

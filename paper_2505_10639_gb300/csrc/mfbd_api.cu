@@ -965,6 +965,35 @@ int mfbd_filter_objects(mfbd_plan_t p, void* object, const float* f_lower, const
     return MFBD_OK;
 }
 
+int mfbd_ls_filter_objects(mfbd_plan_t p, const void* spectra, const void* otf, float noise_power, void* object,
+                           float* filter, void* stream) {
+    int st = check_plan(p);
+    if (st) return st;
+    if (!spectra || !otf) return fail(MFBD_ERR_INVALID_ARG, "spectra and otf must not be NULL");
+    if (!object && !filter) return fail(MFBD_ERR_INVALID_ARG, "object or filter must be given");
+    if (!std::isfinite(noise_power)) return fail(MFBD_ERR_INVALID_ARG, "noise_power must be finite");
+    LsFilterParams f{};
+    f.N = p->N;
+    f.P = p->P;
+    f.K = p->K;
+    f.J = p->J;
+    f.spec_ld = (p->flags & MFBD_FLAG_FULL_SPECTRUM) ? p->N : p->N / 2 + 1;
+    f.obj_ld = f.spec_ld;
+    f.noise_power = noise_power;
+    f.spectra = static_cast<const float2*>(spectra);
+    f.otf = static_cast<const float2*>(otf);
+    f.weights = p->d_weights;
+    f.object = static_cast<float2*>(object);
+    f.filter = filter;
+    if ((st = set_device(p))) return st;
+    cudaError_t e = launch_ls_filter(f, p->sms, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        p->failed = true;
+        return cuda_fail(e, "Lofdahl-Scharmer filter");
+    }
+    return MFBD_OK;
+}
+
 int mfbd_plan_get_info(mfbd_plan_t p, mfbd_plan_info* info) {
     if (!p || !info) return fail(MFBD_ERR_INVALID_ARG, "NULL argument");
     std::memset(info, 0, sizeof *info);

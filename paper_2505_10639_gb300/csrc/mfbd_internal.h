@@ -184,6 +184,20 @@ struct FilterParams {
     float inv_diam[kMaxObjects], f_lower[kMaxObjects], f_upper[kMaxObjects];
 };
 cudaError_t launch_filter_objects(const FilterParams& prm, int sms, cudaStream_t s);
+
+// Lofdahl-Scharmer filter (Sec. 4.1.1, Eq. 25): one CTA per (patch, object).
+struct LsFilterParams {
+    int N, P, K, J;
+    int spec_ld, obj_ld;    // row strides (complex) of D and of the object: N / 2 + 1 or N
+    float noise_power;      // nu, the noise power of one frame's spectrum per frequency
+    const float2* spectra;  // D [P][K][J][N][spec_ld]
+    const float2* otf;      // S [P][K][J][N][N/2+1]
+    const float* weights;   // [K][J]
+    float2* object;         // [P][K][N][obj_ld], multiplied in place, or null
+    float* filter;          // [P][K][N][N/2+1] receives H, or null
+};
+size_t ls_filter_smem(int N);
+cudaError_t launch_ls_filter(const LsFilterParams& prm, int sms, cudaStream_t s);
 size_t front_smem(int N, int es);
 cudaError_t launch_spectra_from_frames(const FrontParams& prm, int sms, cudaStream_t s);
 cudaError_t launch_merge_objects(const FrontParams& prm, int sms, cudaStream_t s);

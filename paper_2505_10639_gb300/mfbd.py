@@ -233,6 +233,25 @@ class Plan:
             ctypes.c_void_p(hi.ctypes.data), _stream(stream)), "mfbd_filter_objects")
         return obj
 
+    def ls_filter_objects(self, spectra, otf, noise_power, obj=None, want_filter=True, stream=None):
+        """mfbd_ls_filter_objects: the Lofdahl-Scharmer filter of every patch
+        and object from the data spectra and the OTFs (mfbd_otf); multiplies
+        `obj` in place when given and returns H [P, K, N, N//2+1] float32 (or
+        None when want_filter is False)."""
+        flt = None
+        if want_filter:
+            flt = torch.empty(self.object_shape()[:3] + (self.n_pix // 2 + 1,), dtype=torch.float32,
+                              device=self.device)
+        if obj is None and flt is None:
+            raise ValueError("give obj or ask for the filter")
+        _lib.check(self._lib.mfbd_ls_filter_objects(
+            self._h, _dev(spectra, torch.complex64, self.spectra_shape(), "spectra"),
+            _dev(otf, torch.complex64, self.otf_shape(), "otf"), ctypes.c_float(float(noise_power)),
+            _dev(obj, torch.complex64, self.object_shape(), "object") if obj is not None else None,
+            _dev(flt, torch.float32, tuple(flt.shape), "filter") if flt is not None else None, _stream(stream)),
+            "mfbd_ls_filter_objects")
+        return flt
+
     def merge_objects(self, obj, height, width, overlap, border, out=None, stream=None):
         """mfbd_merge_objects: patch objects [P, K, N, N//2+1] -> mosaic
         [K, height, width] float32."""

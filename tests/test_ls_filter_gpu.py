@@ -1,0 +1,127 @@
+"""GPU parity of the Lofdahl-Scharmer object filter (mfbd_ls_filter_objects,
+Sec. 4.1.1, Eq. 25) against the oracle, bit for bit.
+
+The kernel's inputs are the oracle's: data spectra D from the oracle's
+forward model and OTFs S from `oracle.mfbd.otf_patch`, both rounded to
+complex64. The oracle evaluates H in float32 with the kernel's order of
+operations (the threshold decisions are then the same); the median and the
+connectivity are exact, so the filters agree bit for bit and the filtered
+object is the input object times the filter.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import filters
+from oracle import mfbd as omfbd
+from tests import cases
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(n_pix, diams, n_frames, n_patches, seed):
+    wl = (6563.0, 8542.0, 5000.0)[:len(diams)]
+    return cases.make_case(n_pix=n_pix, diams=diams, wavelengths=wl, n_frames=n_frames, n_modes=12, basis="kl",
+                           n_patches=n_patches, seed=seed)
+
+
+def _plan(case, full_spectrum=False, weights=None):
+    from paper_2505_10639_gb300.mfbd import Plan
+    s = case["setup"]
+    return Plan(case["n_pix"], case["d"].shape[0], list(case["diams"]), list(case["wavelengths"]),
+                case["n_frames"], case["n_modes"], basis=case["basis"], gamma=s.gamma,
+                weights=s.weights if weights is None else weights, full_spectrum=full_spectrum)
+
+
+def _inputs(case):
+    """D (complex64, half or full layout chosen later) and S (complex64 half
+    spectra) from the oracle."""
+    n = case["n_pix"]
+    a = case["a_eval"]
+    s_half = np.array([[omfbd.half_spectrum(o["H"]) for o in omfbd.otf_patch(case["setup"], a[p])]
+                       for p in range(a.shape[0])]).astype(np.complex64)
+    return case["d"].astype(np.complex64), s_half, n
+
+
+def _oracle_filters(case, d64, s_half, nu, weights):
+    n = case["n_pix"]
+    P, K = s_half.shape[:2]
+    out = np.zeros((P, K, n, n))
+    for p in range(P):
+        for k in range(K):
+            d_full = omfbd.full_from_half(omfbd.half_spectrum(d64[p, k]).astype(np.complex128), n)
+            s_full = omfbd.full_from_half(s_half[p, k].astype(np.complex128), n)
+            out[p, k] = filters.lofdahl_scharmer_filter(d_full, s_full, weights[k], nu, np.float32)
+    return out
+
+
+def _noise_power(case, factor):
+    n = case["n_pix"]
+    return factor * n * n * 1e-6  # sigma = 1e-3 per pixel
+
+
+@pytest.mark.parametrize("n_pix,diams,n_frames,n_patches,factor",
+                         [(64, (36.0, 28.0), 12, 3, 200.0), (48, (22.0,), 5, 2, 50.0),
+                          (96, (40.0, 30.0), 4, 1, 100.0), (128, (56.0,), 3, 1, 400.0)])
+def test_ls_filter_matches_oracle_bits(n_pix, diams, n_frames, n_patches, factor):
+    case = _case(n_pix, diams, n_frames, n_patches, 20250521 + n_pix)
+    d64, s_half, n = _inputs(case)
+    nu = _noise_power(case, factor)
+    weights = np.asarray(case["setup"].weights, np.float32)
+    want = _oracle_filters(case, d64, s_half, nu, weights)
+    plan = _plan(case)
+    d = torch.from_numpy(np.ascontiguousarray(omfbd.half_spectrum(d64))).cuda()
+    s = torch.from_numpy(s_half).cuda()
+    rng = np.random.default_rng(3)
+    obj0 = (rng.standard_normal(plan.object_shape()) + 1j * rng.standard_normal(plan.object_shape())).astype(
+        np.complex64)
+    obj = torch.from_numpy(obj0).cuda()
+    h = plan.ls_filter_objects(d, s, nu, obj=obj)
+    torch.cuda.synchronize()
+    h = h.cpu().numpy()
+    want_half = want[..., : n // 2 + 1]
+    zeros = np.mean(want_half == 0)
+    print("N=%d: %.1f %% of the half plane filtered out" % (n, 100 * zeros))
+    assert 0.01 < zeros < 0.99  # the threshold matters here
+    assert np.array_equal(h.astype(np.float64), want_half)
+    got = obj.cpu().numpy()
+    assert np.array_equal(got.real, obj0.real * h) and np.array_equal(got.imag, obj0.imag * h)
+
+
+def test_ls_filter_full_spectrum_layout_and_weights():
+    """Full N x N spectra and objects, unequal frame weights: the object is
+    multiplied by the full plane of H (its mirror for kx > N/2)."""
+    case = _case(64, (32.0, 26.0), 6, 2, 20250530)
+    d64, s_half, n = _inputs(case)
+    w = np.array([[1.0, 0.5, 2.0, 1.0, 0.25, 1.5], [0.7, 1.0, 1.0, 3.0, 0.5, 1.0]], np.float32)
+    nu = _noise_power(case, 200.0)
+    want = _oracle_filters(case, d64, s_half, nu, w)
+    plan = _plan(case, full_spectrum=True, weights=w)
+    # the kernel reads D's full rows: give it the exactly Hermitian full planes the oracle used
+    d_full = np.array([[omfbd.full_from_half(omfbd.half_spectrum(d64[p, k]).astype(np.complex128), n)
+                        for k in range(d64.shape[1])] for p in range(d64.shape[0])]).astype(np.complex64)
+    obj0 = np.ones(plan.object_shape(), np.complex64) * (1.0 + 2.0j)
+    obj = torch.from_numpy(obj0).cuda()
+    h = plan.ls_filter_objects(torch.from_numpy(d_full).cuda(), torch.from_numpy(s_half).cuda(), nu, obj=obj)
+    torch.cuda.synchronize()
+    assert np.array_equal(h.cpu().numpy().astype(np.float64), want[..., : n // 2 + 1])
+    got = obj.cpu().numpy()
+    assert np.array_equal(got.real, (1.0 * want).astype(np.float32))
+    assert np.array_equal(got.imag, (2.0 * want).astype(np.float32))
+
+
+def test_ls_filter_argument_errors():
+    from paper_2505_10639_gb300 import _lib
+    case = _case(48, (22.0,), 3, 1, 20250531)
+    plan = _plan(case)
+    d = torch.zeros(plan.spectra_shape(), dtype=torch.complex64, device="cuda")
+    s = torch.zeros(plan.otf_shape(), dtype=torch.complex64, device="cuda")
+    with pytest.raises(_lib.MFBDError):
+        plan.ls_filter_objects(d, s, float("nan"))
+    with pytest.raises(ValueError):
+        plan.ls_filter_objects(d, s, 1.0, obj=None, want_filter=False)
+    # all-zero data: every |n|^2 = 0, so H = 0 everywhere
+    h = plan.ls_filter_objects(d, s, 1.0)
+    torch.cuda.synchronize()
+    assert not h.cpu().numpy().any()
