@@ -254,7 +254,7 @@ int mfbd_filter_objects(mfbd_plan_t plan, void* object, const float* f_lower, co
  *                NULL).
  * The frame weights are the plan's w_kj. FP32 with each product and sum
  * rounded on its own in a fixed order (no fused multiply-add). One CTA per
- * (patch, object) with the N x N plane in shared memory (9 N^2 bytes).
+ * (patch, object) with the N x N plane in shared memory (4 N^2 + 80 N bytes).
  * Asynchronous; allocates nothing. */
 int mfbd_ls_filter_objects(mfbd_plan_t plan, const void* spectra, const void* otf, float noise_power, void* object,
                            float* filter, void* stream);
