@@ -159,6 +159,42 @@ def loss_object_grad_patch(setup, coeffs, d):
     return total, np.array(objs), grad
 
 
+def explicit_loss_grad_patch(setup, coeffs, d, objects):
+    """The object-inferring loss of one patch (Sec. 2.2, Eq. 8, with the
+    regulariser R = sum_k sum_u |O_k|^2 and beta = gamma, under which the
+    Wiener object of Eq. 11 is its exact minimiser) for given objects:
+
+      L = sum_k sum_u [ sum_j w_kj |D_kj - O_k H_kj|^2 + gamma |O_k|^2 ]
+
+    coeffs [J, M], d [K, J, N, N], objects [K, N, N] (full spectra). Returns
+    (loss, dL/da [J, M], g_O [K, N, N]) with g_O(u) = dL/dconj(O(u)) per
+    frequency: gamma O - sum_j w conj(H_j) (D_j - O H_j).
+    dL/da follows the chain of loss_object_grad_patch from
+    G_j = dL/dconj(H_j) = -w_j conj(O) (D_j - O H_j) with O held fixed."""
+    coeffs = np.asarray(coeffs, np.float64)
+    objects = np.asarray(objects, np.complex128)
+    inter = otf_patch(setup, coeffs)
+    total = 0.0
+    grad = np.zeros_like(coeffs)
+    g_obj = []
+    for k in range(setup.n_objects):
+        it = inter[k]
+        h = it["H"]
+        w = setup.weights[k][:, None, None]
+        o = objects[k]
+        res = d[k] - o[None] * h
+        total += (w * (res * res.conj()).real).sum() + setup.gamma * (o * o.conj()).real.sum()
+        g_obj.append(setup.gamma * o - (w * h.conj() * res).sum(axis=0))
+        g_h = -w * o.conj()[None] * res
+        g_s = 2.0 * dft.ifft2_unnormalised(g_h).real
+        g_q = (g_s - (g_s * it["s"]).sum(axis=(-2, -1), keepdims=True)) / it["z"]
+        g_pp = dft.ifft2_unnormalised(g_q * it["p"])
+        g_phi = 2.0 * (it["P"].conj() * g_pp).imag
+        g_phi = np.where(setup.masks[k], g_phi, 0.0)
+        grad += setup.scales[k] * np.tensordot(g_phi, setup.bases[k], axes=([1, 2], [1, 2]))
+    return total, grad, np.array(g_obj)
+
+
 def loss_object_grad(setup, coeffs, d):
     """Batched over patches: coeffs [P, J, M], d [P, K, J, N, N]."""
     losses, objs, grads = [], [], []
