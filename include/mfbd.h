@@ -236,6 +236,26 @@ int mfbd_merge_objects(mfbd_plan_t plan, const void* object, int height, int wid
  * Asynchronous; allocates nothing. */
 int mfbd_filter_objects(mfbd_plan_t plan, void* object, const float* f_lower, const float* f_upper, void* stream);
 
+/* The object-inferring loss (Sec. 2.2, Eq. 8 with the regulariser
+ * R = sum_k sum_u |O_k|^2 and beta = gamma, under which the Wiener object of
+ * Eq. 11 is the exact minimiser) for given objects, and its gradients:
+ *   L_p = sum_k sum_u [ sum_j w_kj |D_kj - O_k H_kj|^2 + gamma |O_k|^2 ]
+ * (sum over the full frequency plane, from the half spectrum: columns 0 and
+ * N/2 once, the others twice).
+ *   coeffs, spectra, loss, grad  as mfbd_loss_grad (grad = dL/da with the
+ *                                objects held fixed);
+ *   object       dev [P][K][N][N/2+1] (or [N][N]) complex64, the given
+ *                objects (Hermitian spectra of real images: the columns
+ *                kx <= N/2 are read);
+ *   grad_object  dev, the layout of object, receives dL/dconj(O(u)) per
+ *                frequency: gamma O - sum_j w conj(H_j) (D_j - O H_j); NULL
+ *                to skip.
+ * FP32 with a frequency redone in FP64 where its residual energy falls
+ * below 1e-3 of the data's. A following mfbd_backward returns
+ * MFBD_ERR_STATE. Asynchronous; allocates nothing. */
+int mfbd_loss_grad_explicit(mfbd_plan_t plan, const float* coeffs, const void* spectra, const void* object,
+                            double* loss, float* grad, void* grad_object, void* stream);
+
 /* The Lofdahl-Scharmer filter of the objects (Sec. 4.1.1, Eq. 25), per patch
  * and object k:
  *   H_k(u) = 1 - nu sum_j w_kj |S_kj(u)|^2 / |sum_j w_kj D_kj(u) conj(S_kj(u))|^2,

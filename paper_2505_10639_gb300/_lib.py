@@ -105,6 +105,7 @@ _SIGNATURES = {
     "mfbd_spectra_from_frames": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 _VP, _VP]),
     "mfbd_filter_objects": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "mfbd_loss_grad_explicit": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "mfbd_ls_filter_objects": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_float, _VP, _VP, _VP]),
     "mfbd_merge_objects": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
                                           _VP]),

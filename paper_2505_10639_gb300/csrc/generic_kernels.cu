@@ -102,6 +102,8 @@ __global__ void __launch_bounds__(32 * kMaxObjects) generic_reduce_kernel(const 
         r.supp = prm.obj[k].supp;
         r.sw = prm.sw;
         r.obj = prm.object ? prm.object + ((size_t)p * prm.K + k) * dstride : nullptr;
+        r.oin = prm.oin ? prm.oin + ((size_t)p * prm.K + k) * dstride : nullptr;
+        r.gobj = prm.gobj ? prm.gobj + ((size_t)p * prm.K + k) * dstride : nullptr;
         const double v = reduce_warp(r, lane, 32 * sp, 32 * S);
         if (lane == 0) sobj[k] = v;
         __syncthreads();

@@ -77,6 +77,8 @@ struct mfbd_plan {
     float* d_oimg = nullptr;    // mfbd_merge_objects: patch objects in the image domain [P][K][N][N]
     float2* d_e2scr = nullptr;  // recompute, CTA-per-unit kernels: per-CTA second buffers [e2_ctas][N * es2]
     int e2_ctas = 0;
+    const void* x_oin = nullptr;  // mfbd_loss_grad_explicit: the given objects, during that call only
+    void* x_gobj = nullptr;       // and dL/dconj(O)
     int rsplit = 1;             // warps per (patch, object) of the frame reduction
     double* d_lpart = nullptr;  // rsplit > 1: per-split patch losses [P][rsplit]
     int ustride = 0;
@@ -263,6 +265,8 @@ FusedParams fused_params(const mfbd_plan* p, int p0, int np, const void* spectra
     f.object = static_cast<float2*>(object);
     f.rsplit = p->rsplit;
     f.lpart = p->d_lpart;
+    f.oin = static_cast<const float2*>(p->x_oin);
+    f.gobj = static_cast<float2*>(p->x_gobj);
     for (int k = 0; k < p->K; ++k) {
         f.obj[k].W = p->obj[k].W;
         f.obj[k].x0 = p->obj[k].x0;
@@ -404,6 +408,8 @@ int run_generic(mfbd_plan_t p, int stages, const void* spectra, double* loss, vo
     g.e2_ctas = p->e2_ctas;
     g.rsplit = p->rsplit;
     g.lpart = p->d_lpart;
+    g.oin = static_cast<const float2*>(p->x_oin);
+    g.gobj = static_cast<float2*>(p->x_gobj);
     for (int k = 0; k < p->K; ++k) {
         const ObjectData& o = p->obj[k];
         g.obj[k].W = o.W;
@@ -1056,6 +1062,26 @@ int mfbd_loss_grad(mfbd_plan_t p, const float* coeffs, const void* spectra, doub
     if ((st = run_grad(p, grad, s, 0, p->P))) return st;
     p->have_forward = true;
     return MFBD_OK;
+}
+
+int mfbd_loss_grad_explicit(mfbd_plan_t p, const float* coeffs, const void* spectra, const void* object,
+                            double* loss, float* grad, void* grad_object, void* stream) {
+    int st = check_plan(p);
+    if (st) return st;
+    if (p->P == 0) return MFBD_OK;
+    if (!coeffs || !spectra || !object || !loss || !grad)
+        return fail(MFBD_ERR_INVALID_ARG, "coeffs, spectra, object, loss and grad are required");
+    if ((st = set_device(p))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    p->have_forward = false;  // the seeds will belong to the given objects
+    if ((st = run_phase(p, coeffs, s, 0, p->P))) return st;
+    p->x_oin = object;
+    p->x_gobj = grad_object;
+    st = run_fused(p, ST_FWD | ST_RED | ST_ADJ, spectra, loss, nullptr, p->d_gscr, s, 0, p->P);
+    p->x_oin = nullptr;
+    p->x_gobj = nullptr;
+    if (st) return st;
+    return run_grad(p, grad, s, 0, p->P);
 }
 
 int mfbd_loss_grad_host(mfbd_plan_t p, const float* coeffs, const void* spectra, double* loss, void* object,

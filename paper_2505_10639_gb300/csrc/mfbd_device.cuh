@@ -63,4 +63,57 @@ __device__ __forceinline__ void fp64_frequency(int J, const float2* dp, size_t d
     o = make_float2((float)ox, (float)oy);
 }
 
+// One frequency of the object-inferring loss (the object o given): the
+// residuals r_j = D_j - o H_j, the loss term t = sum_j w |r_j|^2 + gamma |o|^2
+// (returned), the adjoint seeds -w conj(o) r_j (0 when `seed` is false)
+// written over H_j, and g = gamma o - sum_j w conj(H_j) r_j, the derivative
+// of the loss with respect to conj(O) at this frequency. FP32; redone in FP64
+// where the residual energy is below kCancel of the data's.
+__device__ __forceinline__ float explicit_frequency(int J, const float2* dp, size_t dstride, float2* hp,
+                                                    size_t hstride, const float* w, double gamma, bool seed,
+                                                    float2 o, float2& g) {
+    float tsum = 0.f, e = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < J; ++j) {
+        const float2 d = dp[(size_t)j * dstride];
+        const float2 h = hp[(size_t)j * hstride];
+        const float wj = w[j];
+        const float rx = d.x - (o.x * h.x - o.y * h.y), ry = d.y - (o.x * h.y + o.y * h.x);
+        tsum += wj * (rx * rx + ry * ry);
+        e += wj * (d.x * d.x + d.y * d.y);
+    }
+    if (tsum >= kCancel * e) {
+        const float gam = (float)gamma;
+        float gx = 0.f, gy = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < J; ++j) {
+            const float2 d = dp[(size_t)j * dstride];
+            const float2 h = hp[(size_t)j * hstride];
+            const float wj = w[j];
+            const float rx = d.x - (o.x * h.x - o.y * h.y), ry = d.y - (o.x * h.y + o.y * h.x);
+            gx += wj * (h.x * rx + h.y * ry);
+            gy += wj * (h.x * ry - h.y * rx);
+            hp[(size_t)j * hstride] = seed ? make_float2(-wj * (o.x * rx + o.y * ry), -wj * (o.x * ry - o.y * rx))
+                                           : make_float2(0.f, 0.f);
+        }
+        g = make_float2(gam * o.x - gx, gam * o.y - gy);
+        return tsum + gam * (o.x * o.x + o.y * o.y);
+    }
+    const double ox = o.x, oy = o.y;
+    double ts = 0.0, gx = 0.0, gy = 0.0;
+    for (int j = 0; j < J; ++j) {
+        const float2 d = dp[(size_t)j * dstride];
+        const float2 h = hp[(size_t)j * hstride];
+        const double wj = w[j];
+        const double rx = (double)d.x - (ox * h.x - oy * h.y), ry = (double)d.y - (ox * h.y + oy * h.x);
+        ts += wj * (rx * rx + ry * ry);
+        gx += wj * ((double)h.x * rx + (double)h.y * ry);
+        gy += wj * ((double)h.x * ry - (double)h.y * rx);
+        hp[(size_t)j * hstride] = seed ? make_float2((float)(-wj * (ox * rx + oy * ry)), (float)(-wj * (ox * ry - oy * rx)))
+                                       : make_float2(0.f, 0.f);
+    }
+    g = make_float2((float)(gamma * ox - gx), (float)(gamma * oy - gy));
+    return (float)(ts + gamma * (ox * ox + oy * oy));
+}
+
 }  // namespace mfbd_dev

@@ -44,6 +44,8 @@ struct FusedParams {
     float2* object;           // [P][K][N][spec_ld] or null
     int rsplit;               // warps per (patch, object) of the frame reduction (<= 1: one)
     double* lpart;            // rsplit > 1: per-split patch losses [P][rsplit]
+    const float2* oin;        // object-inferring loss: the given objects [P][K][N][spec_ld], else null
+    float2* gobj;             // with oin: dL/dconj(O) [P][K][N][spec_ld], or null
     ObjParams obj[kMaxObjects];
 };
 
@@ -147,6 +149,8 @@ struct GenericParams {
     int e2_ctas;            // CTAs e2scr has room for
     int rsplit;             // warps per (patch, object) of the frame reduction (<= 1: one)
     double* lpart;          // rsplit > 1: per-split patch losses [P][rsplit]
+    const float2* oin;      // object-inferring loss: the given objects [P][K][N][spec_ld], else null
+    float2* gobj;           // with oin: dL/dconj(O) [P][K][N][spec_ld], or null
     GenericObj obj[kMaxObjects];
 };
 

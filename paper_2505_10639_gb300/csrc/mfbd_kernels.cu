@@ -484,6 +484,18 @@ __device__ double reduce_object_warp(const FusedParams& prm, int p, int k, int f
         const float2* dp = dbase + doff;
         float2* hp = hbase + f;
         const bool seed = (f != 0) && bit(supp[ky], kx);
+        if (prm.oin) {  // object-inferring loss: the object is given
+            const size_t ooff = ((size_t)p * prm.K + k) * dstride;
+            float2 g;
+            const float t = explicit_frequency(J, dp, dstride, hp, kHalf, w, prm.gamma, seed, prm.oin[ooff + doff], g);
+            acc.add((kx == 0 || kx == kN / 2) ? t : 2.0f * t);
+            if (prm.gobj) {
+                prm.gobj[ooff + doff] = g;
+                if (prm.spec_ld == kN && kx > 0 && kx < kN / 2)
+                    prm.gobj[ooff + (size_t)((kN - ky) % kN) * kN + (kN - kx)] = cconj(g);
+            }
+            continue;
+        }
         float2 num = make_float2(0.f, 0.f), o;
         float e = 0.f, q = 0.f, t;
         if constexpr (JM > 0) {

@@ -723,7 +723,9 @@ struct RedPtr {
     const float* w;         // [J] frame weights
     const uint32_t* supp;   // [N][sw] OTF support rows
     int sw;
-    float2* obj;            // [N][spec_ld] or null
+    float2* obj = nullptr;           // [N][spec_ld] or null
+    const float2* oin = nullptr;     // object-inferring loss: the given object [N][spec_ld], else null
+    float2* gobj = nullptr;          // with oin: dL/dconj(O) [N][spec_ld], or null
 };
 
 // Lanes take the frequencies f0 + lane, f0 + lane + fstep, ... (fstep a
@@ -740,6 +742,16 @@ __device__ __forceinline__ double reduce_warp(const RedPtr& r, int lane, int f0 
         const float2* dp = r.d + doff;
         float2* hp = r.h + f;
         const bool seed = (f != 0) && wbit(r.supp, r.sw, ky, kx);
+        if (r.oin) {  // object-inferring loss: the object is given
+            float2 g;
+            const float t = explicit_frequency(J, dp, dstride, hp, half, r.w, r.gamma, seed, r.oin[doff], g);
+            acc.add((kx == 0 || kx == N / 2) ? t : 2.0f * t);
+            if (r.gobj) {
+                r.gobj[doff] = g;
+                if (r.spec_ld == N && kx > 0 && kx < N / 2) r.gobj[(size_t)((N - ky) % N) * N + (N - kx)] = cconj(g);
+            }
+            continue;
+        }
         float2 num = make_float2(0.f, 0.f), o;
         float e = 0.f, qs = 0.f, tval;
 #pragma unroll 4

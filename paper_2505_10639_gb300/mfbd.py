@@ -178,6 +178,26 @@ class Plan:
             _dev(grad, torch.float32, self.coeff_shape(), "grad"), _stream(stream)), "mfbd_loss_grad")
         return loss, grad, obj
 
+    def loss_grad_explicit(self, coeffs, spectra, obj, loss=None, grad=None, grad_obj=None, want_grad_object=True,
+                           stream=None):
+        """mfbd_loss_grad_explicit: the object-inferring loss for the given
+        objects -> (loss [P], dL/da [P, J, M], dL/dconj(O) or None)."""
+        if loss is None:
+            loss = torch.empty(self.n_patches, dtype=torch.float64, device=self.device)
+        if grad is None:
+            grad = torch.empty(self.coeff_shape(), dtype=torch.float32, device=self.device)
+        if grad_obj is None and want_grad_object:
+            grad_obj = torch.empty(self.object_shape(), dtype=torch.complex64, device=self.device)
+        _lib.check(self._lib.mfbd_loss_grad_explicit(
+            self._h, _dev(coeffs, torch.float32, self.coeff_shape(), "coeffs"),
+            _dev(spectra, torch.complex64, self.spectra_shape(), "spectra"),
+            _dev(obj, torch.complex64, self.object_shape(), "object"),
+            _dev(loss, torch.float64, (self.n_patches,), "loss"),
+            _dev(grad, torch.float32, self.coeff_shape(), "grad"),
+            _dev(grad_obj, torch.complex64, self.object_shape(), "grad_object") if grad_obj is not None else None,
+            _stream(stream)), "mfbd_loss_grad_explicit")
+        return loss, grad, grad_obj
+
     def loss_grad_host(self, coeffs, spectra, loss=None, grad=None, obj=None, want_object=False, n_chunks=0,
                        stream=None):
         """mfbd_loss_grad_host: the same outputs from CPU tensors (pin them for

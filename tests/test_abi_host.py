@@ -268,3 +268,4 @@ def test_field_front_end_refuses_without_a_plan(lib):
     assert lib.mfbd_merge_objects(None, None, 96, 96, 32, 6, None, None) == _lib.MFBD_ERR_INVALID_ARG
     assert lib.mfbd_filter_objects(None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
     assert lib.mfbd_ls_filter_objects(None, None, None, 1.0, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
+    assert lib.mfbd_loss_grad_explicit(None, None, None, None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
