@@ -236,7 +236,7 @@ int mfbd_merge_objects(mfbd_plan_t plan, const void* object, int height, int wid
  * Asynchronous; allocates nothing. */
 int mfbd_filter_objects(mfbd_plan_t plan, void* object, const float* f_lower, const float* f_upper, void* stream);
 
-/* The object-inferring loss (Sec. 2.2, Eq. 8 with the regulariser
+/* The object-inferring loss (Sec. 2.2.1, Eq. 8 with the regulariser
  * R = sum_k sum_u |O_k|^2 and beta = gamma, under which the Wiener object of
  * Eq. 11 is the exact minimiser) for given objects, and its gradients:
  *   L_p = sum_k sum_u [ sum_j w_kj |D_kj - O_k H_kj|^2 + gamma |O_k|^2 ]

@@ -160,7 +160,7 @@ def loss_object_grad_patch(setup, coeffs, d):
 
 
 def explicit_loss_grad_patch(setup, coeffs, d, objects):
-    """The object-inferring loss of one patch (Sec. 2.2, Eq. 8, with the
+    """The object-inferring loss of one patch (Sec. 2.2.1, Eq. 8, with the
     regulariser R = sum_k sum_u |O_k|^2 and beta = gamma, under which the
     Wiener object of Eq. 11 is its exact minimiser) for given objects:
 

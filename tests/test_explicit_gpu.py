@@ -1,5 +1,5 @@
 """GPU parity of the object-inferring loss (mfbd_loss_grad_explicit, Sec.
-2.2, Eq. 8 with the gamma |O|^2 regulariser) against the FP64 oracle: loss,
+2.2.1, Eq. 8 with the gamma |O|^2 regulariser) against the FP64 oracle: loss,
 dL/da and dL/dconj(O) for given objects, on the 64 px pass machine and the
 general-size kernels, in the half- and full-spectrum layouts.
 

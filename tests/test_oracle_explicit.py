@@ -1,4 +1,4 @@
-"""Pins of the oracle's object-inferring loss (Sec. 2.2, Eq. 8 with the
+"""Pins of the oracle's object-inferring loss (Sec. 2.2.1, Eq. 8 with the
 regulariser gamma sum |O|^2), CPU only: at the Wiener object it is the
 object-eliminated loss of Eq. 12 with zero object gradient and the same dL/da
 (the envelope theorem); its gradients match central differences; O = 0 has a
