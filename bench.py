@@ -388,10 +388,36 @@ def run_gpu(args, rank, local_rank, world):
     if not args.no_e2e:
         e2e = run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, w)
     frontend = None if args.no_frontend else run_frontend(args, plan, coeffs, spectra, w)
+    explicit = None if args.no_frontend else run_explicit(args, plan, coeffs, spectra, w)
     line = finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk)
     if frontend is not None:
         line["frontend"] = frontend
+    if explicit is not None:
+        line["object_inferring_loss"] = explicit
     return line
+
+
+def run_explicit(args, plan, coeffs, spectra, w):
+    """The object-inferring loss (mfbd_loss_grad_explicit) on the same inputs
+    with the Wiener objects given back (dL/da and dL/dconj(O) both
+    computed): CUDA-event time per call and the same metric (not part of a
+    step)."""
+    import torch
+    loss, grad, obj = plan.loss_grad(coeffs, spectra, want_object=True)
+    gobj = torch.empty_like(obj)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.loss_grad_explicit(coeffs, spectra, obj, loss=loss, grad=grad, grad_obj=gobj)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.loss_grad_explicit(coeffs, spectra, obj, loss=loss, grad=grad, grad_obj=gobj)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / args.steps
+    return {"ms": t, "value": units64_of(w) / (t * 1e-3), "unit": UNIT}
 
 
 def run_frontend(args, plan, coeffs, spectra, w):
