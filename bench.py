@@ -546,8 +546,9 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
 
     def per_launch(kind):
-        ms_, n_ = prof[kind]
-        return ms_ / max(1, n_)
+        # one forward, reduction and adjoint stage per step (the reduction
+        # stage includes the loss-combine kernel of a split reduction)
+        return prof[kind][0] / max(1, args.steps)
 
     # DRAM traffic from the committed ncu captures of the 64 px pass machine
     # and of the 128 px kernels with recompute; not measured for the others
@@ -596,9 +597,7 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
         "roofline": roofline,
         "kernels": kernels,
         "kernels_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in prof.items()},
-        # a split frame reduction adds the kernel that sums its per-split losses
-        "gpu_launches": int(sum(v[1] for v in prof.values())
-                            + (prof["reduction"][1] if info.get("reduction_split", 1) > 1 else 0)),
+        "gpu_launches": int(sum(v[1] for v in prof.values())),  # kernels, counted by the library
         "clocks": clk,
         "plan": info,
     }

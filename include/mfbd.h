@@ -274,8 +274,10 @@ int mfbd_loss_grad_explicit(mfbd_plan_t plan, const float* coeffs, const void* s
  *                NULL).
  * The frame weights are the plan's w_kj. FP32 with each product and sum
  * rounded on its own in a fixed order (no fused multiply-add). One CTA per
- * (patch, object) with the N x N plane in shared memory (4 N^2 + 80 N bytes).
- * Asynchronous; allocates nothing. */
+ * (patch, object) with the N x N plane in shared memory (4 N^2 + 80 N bytes),
+ * after a streaming pass that writes the thresholded H to `filter` (or, when
+ * `filter` is NULL, to P x K x N x (N/2+1) floats of plan scratch allocated
+ * by the first such call). Asynchronous. */
 int mfbd_ls_filter_objects(mfbd_plan_t plan, const void* spectra, const void* otf, float noise_power, void* object,
                            float* filter, void* stream);
 
@@ -290,13 +292,14 @@ int mfbd_describe_object(const mfbd_plan_desc* desc, int object, unsigned char* 
                          float* basis, double* variance, unsigned char* support);
 
 /* Kernel timing. When enabled, every compute call records a CUDA event pair
- * on its stream around each kernel it launches, from a pool of max_launches
- * pairs created here (enable = 0 destroys the pool). Calls made while the
- * pool is full are not timed. */
+ * on its stream around each stage it launches (per object for the phase
+ * projection), from a pool of max_launches pairs created here (enable = 0
+ * destroys the pool). Calls made while the pool is full are not timed. */
 int mfbd_plan_set_profiling(mfbd_plan_t plan, int enable, int max_launches);
 
 /* Waits for the recorded events, then returns the summed device time in ms
- * and the launch count of each kernel kind, arrays of 5: [0] modal phase
+ * and the number of kernels launched inside the timed pairs, per kind,
+ * arrays of 5: [0] modal phase
  * projection, [1] forward passes (pupil -> OTF), [2] frame reduction (loss,
  * object, adjoint seeds), [3] adjoint passes (-> dL/dphi), [4] modal adjoint
  * projection. With reset != 0 the pool is emptied for reuse. Arrays may be

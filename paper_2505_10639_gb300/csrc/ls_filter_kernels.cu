@@ -6,10 +6,12 @@
 // plane, and every nonzero value not 4-connected (periodically) to the zero
 // frequency set to zero; the object is multiplied by H.
 //
-// One CTA per (patch, object), persistent. The full N x N plane of H lives in
-// shared memory: the half spectrum kx <= N/2 is evaluated from the inputs
-// (columns 0 and N/2 from their own data) and mirrored to -u for
-// 0 < kx < N/2, where the sums are the conjugates of those at u. The values
+// Two kernels: a streaming pass, one thread per half-spectrum frequency,
+// writes the thresholded H (to the filter output, or plan scratch); then one
+// CTA per (patch, object), persistent, holds the full N x N plane in shared
+// memory: the half spectrum kx <= N/2 as evaluated (columns 0 and N/2 from
+// their own data), mirrored to -u for 0 < kx < N/2, where the sums are the
+// conjugates of those at u. The values
 // are >= 0, so a 3 x 3 median is nonzero exactly where at least 5 of the 9
 // neighbours are: the median's nonzero pattern comes from bit rows of the
 // thresholded plane by bit-sliced counting, and the median itself is
@@ -165,6 +167,40 @@ __device__ __forceinline__ float median_at(const float* h, int y, int x) {
     return median9(v);
 }
 
+// Thresholded H on the half spectra of every (patch, object), one thread per
+// frequency: a streaming pass over D and S.
+template <int N>
+__global__ void __launch_bounds__(kLsThreads) ls_raw_kernel(const LsFilterParams prm) {
+    constexpr int NH = N / 2 + 1, HALF = N * NH;
+    const int J = prm.J;
+    const float nu = prm.noise_power;
+    const long long total = (long long)prm.P * prm.K * HALF;
+    for (long long e = (long long)blockIdx.x * kLsThreads + threadIdx.x; e < total;
+         e += (long long)gridDim.x * kLsThreads) {
+        const long long pk = e / HALF;
+        const int f = (int)(e - pk * HALF);
+        const int k = (int)(pk % prm.K), ky = f / NH, kx = f - ky * NH;
+        const float* w = prm.weights + (size_t)k * J;
+        const float2* dp = prm.spectra + (size_t)pk * J * N * prm.spec_ld + (size_t)ky * prm.spec_ld + kx;
+        const float2* sp = prm.otf + (size_t)pk * J * HALF + f;
+        float nr = 0.f, ni = 0.f, q = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < J; ++j) {
+            const float2 d = dp[(size_t)j * N * prm.spec_ld];
+            const float2 s = sp[(size_t)j * HALF];
+            const float wj = w[j];
+            const float tr = __fadd_rn(__fmul_rn(d.x, s.x), __fmul_rn(d.y, s.y));
+            const float ti = __fsub_rn(__fmul_rn(d.y, s.x), __fmul_rn(d.x, s.y));
+            nr = __fadd_rn(nr, __fmul_rn(wj, tr));
+            ni = __fadd_rn(ni, __fmul_rn(wj, ti));
+            q = __fadd_rn(q, __fmul_rn(wj, __fadd_rn(__fmul_rn(s.x, s.x), __fmul_rn(s.y, s.y))));
+        }
+        const float n2 = __fadd_rn(__fmul_rn(nr, nr), __fmul_rn(ni, ni));
+        const float h = __fsub_rn(1.0f, __fdiv_rn(__fmul_rn(nu, q), n2));
+        prm.raw[e] = h >= 0.2f ? fminf(h, 1.0f) : 0.0f;  // NaN -> 0
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(kLsThreads) ls_filter_kernel(const LsFilterParams prm) {
     constexpr int NH = N / 2 + 1, HALF = N * NH, NN = N * N;
@@ -175,34 +211,14 @@ __global__ void __launch_bounds__(kLsThreads) ls_filter_kernel(const LsFilterPar
     Ring* rrow = mcol + N;                      // [N] reached pixels of row y
     Ring* rcol = rrow + N;                      // [N] reached pixels of column x
     float* hraw = reinterpret_cast<float*>(rcol + N);
-    const int tid = threadIdx.x, J = prm.J;
-    const float nu = prm.noise_power;
+    const int tid = threadIdx.x;
     const long long planes = (long long)prm.P * prm.K;
     for (long long pk = blockIdx.x; pk < planes; pk += gridDim.x) {
-        const int k = (int)(pk % prm.K);
-        const float* w = prm.weights + (size_t)k * J;
-        const float2* dbase = prm.spectra + (size_t)pk * J * N * prm.spec_ld;
-        const float2* sbase = prm.otf + (size_t)pk * J * HALF;
-        // H on the half spectrum, thresholded, mirrored
+        // the thresholded half plane, mirrored to -u
+        const float* rp = prm.raw + (size_t)pk * HALF;
         for (int f = tid; f < HALF; f += kLsThreads) {
             const int ky = f / NH, kx = f - ky * NH;
-            const float2* dp = dbase + (size_t)ky * prm.spec_ld + kx;
-            const float2* sp = sbase + f;
-            float nr = 0.f, ni = 0.f, q = 0.f;
-#pragma unroll 4
-            for (int j = 0; j < J; ++j) {
-                const float2 d = dp[(size_t)j * N * prm.spec_ld];
-                const float2 s = sp[(size_t)j * HALF];
-                const float wj = w[j];
-                const float tr = __fadd_rn(__fmul_rn(d.x, s.x), __fmul_rn(d.y, s.y));
-                const float ti = __fsub_rn(__fmul_rn(d.y, s.x), __fmul_rn(d.x, s.y));
-                nr = __fadd_rn(nr, __fmul_rn(wj, tr));
-                ni = __fadd_rn(ni, __fmul_rn(wj, ti));
-                q = __fadd_rn(q, __fmul_rn(wj, __fadd_rn(__fmul_rn(s.x, s.x), __fmul_rn(s.y, s.y))));
-            }
-            const float n2 = __fadd_rn(__fmul_rn(nr, nr), __fmul_rn(ni, ni));
-            float h = __fsub_rn(1.0f, __fdiv_rn(__fmul_rn(nu, q), n2));
-            h = h >= 0.2f ? fminf(h, 1.0f) : 0.0f;  // NaN -> 0
+            const float h = rp[f];
             hraw[ky * N + kx] = h;
             if (kx > 0 && kx < N / 2) hraw[(ky == 0 ? 0 : N - ky) * N + (N - kx)] = h;
         }
@@ -270,6 +286,14 @@ __global__ void __launch_bounds__(kLsThreads) ls_filter_kernel(const LsFilterPar
 
 template <int N>
 cudaError_t launch_ls(const LsFilterParams& prm, int sms, cudaStream_t s) {
+    {
+        const long long total = (long long)prm.P * prm.K * N * (N / 2 + 1);
+        long long blocks = (total + kLsThreads - 1) / kLsThreads;
+        if (blocks > 16ll * sms) blocks = 16ll * sms;
+        ls_raw_kernel<N><<<(int)blocks, kLsThreads, 0, s>>>(prm);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     const size_t smem = ls_filter_smem(N);
     auto* kern = ls_filter_kernel<N>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -75,6 +75,7 @@ struct mfbd_plan {
     float2* d_pscr = nullptr;   // per unit [P][K][J][N*N]: field
     float2* d_uscr = nullptr;   // per unit [P][K][J][ustride]: pupil phasors on the box
     float* d_oimg = nullptr;    // mfbd_merge_objects: patch objects in the image domain [P][K][N][N]
+    float* d_lsraw = nullptr;   // mfbd_ls_filter_objects without a filter output: [P][K][N][N/2+1]
     float2* d_e2scr = nullptr;  // recompute, CTA-per-unit kernels: per-CTA second buffers [e2_ctas][N * es2]
     int e2_ctas = 0;
     const void* x_oin = nullptr;  // mfbd_loss_grad_explicit: the given objects, during that call only
@@ -108,6 +109,7 @@ struct mfbd_plan {
     // kernel timing (mfbd_plan_set_profiling)
     std::vector<cudaEvent_t> ev;    // 2 per pair
     std::vector<int> ev_kind;       // kind of each used pair
+    std::vector<int> ev_nk;         // kernels launched inside each used pair
     int ev_used = 0;
 };
 
@@ -307,8 +309,10 @@ int prof_begin(mfbd_plan_t p, int kind, cudaStream_t s) {
     return i;
 }
 
-void prof_end(mfbd_plan_t p, int i, cudaStream_t s) {
-    if (i >= 0) cudaEventRecord(p->ev[2 * i + 1], s);
+void prof_end(mfbd_plan_t p, int i, cudaStream_t s, int kernels) {
+    if (i < 0) return;
+    p->ev_nk[i] = kernels;
+    cudaEventRecord(p->ev[2 * i + 1], s);
 }
 
 // Phases of patches [p0, p0 + np); coeffs points at patch p0.
@@ -326,7 +330,7 @@ int run_phase(mfbd_plan_t p, const float* coeffs, cudaStream_t s, int p0, int np
                                 : launch_phase_gemm(coeffs, np * p->J, p->M, o.d_basis, o.W * o.W, o.scale, out, s);
         if (e == cudaSuccess && o.d_div)  // phi_kj = c_k B_k a_j + theta_kj
             e = launch_add_diversity(out, o.d_div, np * p->J, p->J, o.W * o.W, p->sms, s);
-        prof_end(p, pi, s);
+        prof_end(p, pi, s, 1 + (o.tc_planes > 0 && k == 0 ? 1 : 0) + (o.d_div ? 1 : 0));
         if (e != cudaSuccess) {
             p->failed = true;
             return cuda_fail(e, "phase projection");
@@ -367,7 +371,7 @@ int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s, int p0, int np) {
     const int pi = prof_begin(p, 4, s);
     cudaError_t e = launch_grad_gemm(job, U, p->M, s);
     if (e == cudaSuccess) e = launch_grad_combine(gp, U, p->M, grad, s);
-    prof_end(p, pi, s);
+    prof_end(p, pi, s, 2);
     if (e != cudaSuccess) {
         p->failed = true;
         return cuda_fail(e, "modal adjoint");
@@ -425,17 +429,17 @@ int run_generic(mfbd_plan_t p, int stages, const void* spectra, double* loss, vo
     if (stages & ST_FWD) {
         const int pi = prof_begin(p, 1, s);
         e = launch_generic_forward(g, p->sms, s);
-        prof_end(p, pi, s);
+        prof_end(p, pi, s, 1);
     }
     if (e == cudaSuccess && (stages & ST_RED)) {
         const int pr = prof_begin(p, 2, s);
         e = launch_generic_reduction(g, p->sms, s);
-        prof_end(p, pr, s);
+        prof_end(p, pr, s, p->rsplit > 1 && p->d_lpart ? 2 : 1);  // + the loss combine
     }
     if (e == cudaSuccess && (stages & ST_ADJ)) {
         const int pb = prof_begin(p, 3, s);
         e = launch_generic_adjoint(g, p->sms, s);
-        prof_end(p, pb, s);
+        prof_end(p, pb, s, 1);
     }
     if (e != cudaSuccess) {
         p->failed = true;
@@ -455,17 +459,17 @@ int run_fused(mfbd_plan_t p, int stages, const void* spectra, double* loss, void
     if (stages & ST_FWD) {
         const int pi = prof_begin(p, 1, s);
         e = launch_forward_passes(f, p->geo, p->sms, s);
-        prof_end(p, pi, s);
+        prof_end(p, pi, s, 1);
     }
     if (e == cudaSuccess && (stages & ST_RED)) {
         const int pr = prof_begin(p, 2, s);
         e = launch_reduction(f, p->sms, s);
-        prof_end(p, pr, s);
+        prof_end(p, pr, s, p->rsplit > 1 && p->d_lpart ? 2 : 1);  // + the loss combine
     }
     if (e == cudaSuccess && (stages & ST_ADJ)) {
         const int pb = prof_begin(p, 3, s);
         e = launch_adjoint_passes(f, p->geo, p->sms, s);
-        prof_end(p, pb, s);
+        prof_end(p, pb, s, 1);
     }
     if (e != cudaSuccess) {
         p->failed = true;
@@ -797,17 +801,20 @@ int mfbd_plan_set_profiling(mfbd_plan_t p, int enable, int max_launches) {
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     p->ev.clear();
     p->ev_kind.clear();
+    p->ev_nk.clear();
     p->ev_used = 0;
     if (!enable) return MFBD_OK;
     if (max_launches < 1 || max_launches > 1 << 16) return fail(MFBD_ERR_INVALID_ARG, "max_launches out of range");
     p->ev.resize((size_t)2 * max_launches);
     p->ev_kind.assign(max_launches, 0);
+    p->ev_nk.assign(max_launches, 0);
     for (size_t i = 0; i < p->ev.size(); ++i) {
         cudaError_t e = cudaEventCreate(&p->ev[i]);
         if (e != cudaSuccess) {
             for (size_t j = 0; j < i; ++j) cudaEventDestroy(p->ev[j]);
             p->ev.clear();
             p->ev_kind.clear();
+            p->ev_nk.clear();
             return cuda_fail(e, "cudaEventCreate");
         }
     }
@@ -825,7 +832,7 @@ int mfbd_plan_read_profile(mfbd_plan_t p, double* ms, long long* launches, int r
         if ((e = cudaEventElapsedTime(&t, p->ev[2 * i], p->ev[2 * i + 1])) != cudaSuccess)
             return cuda_fail(e, "cudaEventElapsedTime");
         acc[p->ev_kind[i]] += t;
-        cnt[p->ev_kind[i]] += 1;
+        cnt[p->ev_kind[i]] += p->ev_nk[i];
     }
     for (int k = 0; k < 5; ++k) {
         if (ms) ms[k] = acc[k];
@@ -992,6 +999,9 @@ int mfbd_ls_filter_objects(mfbd_plan_t p, const void* spectra, const void* otf, 
     f.object = static_cast<float2*>(object);
     f.filter = filter;
     if ((st = set_device(p))) return st;
+    if (!filter && !p->d_lsraw && (st = dev_alloc(p, &p->d_lsraw, (size_t)p->P * p->K * p->N * (p->N / 2 + 1))))
+        return st;
+    f.raw = filter ? filter : p->d_lsraw;
     cudaError_t e = launch_ls_filter(f, p->sms, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         p->failed = true;

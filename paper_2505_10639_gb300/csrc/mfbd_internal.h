@@ -199,6 +199,7 @@ struct LsFilterParams {
     const float* weights;   // [K][J]
     float2* object;         // [P][K][N][obj_ld], multiplied in place, or null
     float* filter;          // [P][K][N][N/2+1] receives H, or null
+    float* raw;             // [P][K][N][N/2+1] thresholded H before the median (filter or plan scratch)
 };
 size_t ls_filter_smem(int N);
 cudaError_t launch_ls_filter(const LsFilterParams& prm, int sms, cudaStream_t s);

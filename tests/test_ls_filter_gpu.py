@@ -109,6 +109,12 @@ def test_ls_filter_full_spectrum_layout_and_weights():
     got = obj.cpu().numpy()
     assert np.array_equal(got.real, (1.0 * want).astype(np.float32))
     assert np.array_equal(got.imag, (2.0 * want).astype(np.float32))
+    # without a filter output (plan scratch holds the thresholded H): the same object
+    obj2 = torch.from_numpy(obj0).cuda()
+    assert plan.ls_filter_objects(torch.from_numpy(d_full).cuda(), torch.from_numpy(s_half).cuda(), nu, obj=obj2,
+                                  want_filter=False) is None
+    torch.cuda.synchronize()
+    assert np.array_equal(obj2.cpu().numpy(), got)
 
 
 def test_ls_filter_argument_errors():

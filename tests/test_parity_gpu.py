@@ -426,3 +426,21 @@ def test_lbfgs_driven_from_the_host(c2_slice):
     opt.step(closure)
     l1 = momfbd_loss(a, d, plan).detach()
     assert torch.all(l1 < 0.9 * l0), (l0, l1)
+
+
+def test_profile_counts_the_kernels_of_a_step(c2_slice):
+    """The profiling pairs count every kernel a step launches: per object a
+    phase projection (plus the coefficient split once, tensor path), the
+    forward passes, the frame reduction and, when it is split, the loss
+    combine, the adjoint passes, and the modal adjoint GEMM and combine."""
+    a32, d32, _ = _inputs(c2_slice)
+    plan = _plan_for(c2_slice)
+    split = plan.info()["reduction_split"]
+    assert split > 1  # three patches
+    plan.set_profiling(True, max_launches=64)
+    _run_fused(plan, a32, d32, want_object=False)
+    prof = plan.read_profile(reset=True)
+    counts = {k: v[1] for k, v in prof.items()}
+    K = len(c2_slice["diams"])
+    assert list(counts.values()) == [K + 1, 1, 2, 1, 2], counts
+    plan.set_profiling(False)
