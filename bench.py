@@ -71,9 +71,11 @@ NCU_DRAM_BYTES_PER_UNIT_128 = {"forward_passes": (67911680 + 344916992) / 6144,
                                "reduction": (818419968 + 364834048) / 6144}
 # DRAM bytes per launch of the front-end kernels on the 961-patch 64 px field
 # (one ncu capture of the full launch, --metrics dram__bytes_read.sum,
-# dram__bytes_write.sum): spectra_kernel; object_image_kernel + merge_kernel
+# dram__bytes_write.sum): spectra_kernel; object_image_kernel + merge_kernel;
+# ls_raw_kernel + ls_filter_kernel
 NCU_FRONT_DRAM_BYTES = {"spectra_from_frames": 100790784 + 329911296,
-                        "merge_objects": 37747712 + 5244160 + 31507968}
+                        "merge_objects": 37747712 + 5244160 + 31507968,
+                        "ls_filter_objects": 779402496 + 16724480 + 48732416 + 3328}
 # DRAM bytes of the batch kernel per 64 px-equivalent unit, from one ncu
 # capture of the first 200 problems of the 2000-problem batch (13869 units)
 # under the schedule the autotuner picks there (one launch, window 0, the
@@ -483,7 +485,8 @@ def run_frontend(args, plan, coeffs, spectra, w):
                               "frac": b_merge / (t_merge * 1e-3) / 1e9 / hbm,
                               "traffic": NCU_FRONT_DRAM_BYTES["merge_objects"] if captured else None},
             "ls_filter_objects": {"ms": t_ls, "bytes": b_ls, "gbs": b_ls / (t_ls * 1e-3) / 1e9,
-                                  "frac": b_ls / (t_ls * 1e-3) / 1e9 / hbm},
+                                  "frac": b_ls / (t_ls * 1e-3) / 1e9 / hbm,
+                                  "traffic": NCU_FRONT_DRAM_BYTES["ls_filter_objects"] if captured else None},
             "field": "%d x %d px, %d patches of %d px, overlap %d, border 6" % (fov, fov, P, N, N // 2)}
 
 
