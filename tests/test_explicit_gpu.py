@@ -98,3 +98,42 @@ def test_explicit_loss_at_the_wiener_object_is_the_eliminated_loss():
     from paper_2505_10639_gb300 import _lib
     with pytest.raises(_lib.MFBDError):
         plan.backward()
+
+
+def test_explicit_loss_with_phase_diversity_and_without_object_gradient():
+    """Phase diversity (a defocus on frames 2 and 3) under the object-inferring
+    loss against the oracle with the same diversity; asking for no dL/dO
+    gives the same loss and dL/da bits."""
+    from oracle import optics
+    from paper_2505_10639_gb300 import synth
+    n, diams = 64, (32.0, 26.0)
+    case = cases.make_case(n_pix=n, diams=diams, wavelengths=(6563.0, 8542.0), n_frames=4, n_modes=10,
+                           basis="zernike", n_patches=2, seed=20250610)
+    s = case["setup"]
+    theta = []
+    for dm in diams:
+        t = np.zeros((4, n, n))
+        t[2:] = 1.5 * optics.zernike_basis(n, dm, [4])[0]
+        theta.append(t)
+    sd = omfbd.Setup(s.masks, s.bases, s.scales, s.weights, s.gamma, diversity=theta)
+    noise = synth.noise(20250610, (2, 2, 4, n, n), 1e-3)
+    d = np.array([omfbd.synth_spectra(sd, case["a_true"][p], case["objects"][p], noise[p]) for p in range(2)])
+    a32 = case["a_eval"].astype(np.float32)
+    d32 = omfbd.half_spectrum(d).astype(np.complex64)
+    d_or = omfbd.full_from_half(d32.astype(np.complex128), n)
+    o_gpu, o_full = _given_objects(dict(case, setup=sd), d_or, a32.astype(np.float64), 11, False)
+    plan = _plan(case)
+    plan.set_diversity(np.array(theta, np.float32))
+    a, dd, o = (torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (a32, d32, o_gpu))
+    loss, grad, gobj = plan.loss_grad_explicit(a, dd, o)
+    loss2, grad2, none = plan.loss_grad_explicit(a, dd, o, want_grad_object=False)
+    torch.cuda.synchronize()
+    assert none is None
+    assert torch.equal(loss, loss2) and torch.equal(grad, grad2)
+    loss, grad, gobj = loss.cpu().numpy(), grad.cpu().numpy(), gobj.cpu().numpy().astype(np.complex128)
+    for p in range(2):
+        lo, go, gob = omfbd.explicit_loss_grad_patch(sd, a32[p].astype(np.float64), d_or[p], o_full[p])
+        assert abs(loss[p] - lo) <= 1e-5 * abs(lo)
+        assert np.linalg.norm(grad[p] - go) <= 1e-4 * np.linalg.norm(go)
+        want = omfbd.half_spectrum(gob)
+        assert np.linalg.norm(gobj[p] - want) <= OBJ_GRAD_RTOL * np.linalg.norm(want)
