@@ -14,7 +14,7 @@
 // spectrum, normalised by 1/N^2: columns along ky (0 and N/2 packed, both
 // transforms real), then row pairs Hermitian-extended along kx; (2) per
 // mosaic pixel, the average of the patches covering it weighted by the
-// window, summed in patch order (deterministic).
+// window, summed in patch order (deterministic); a CTA per mosaic row.
 //
 // Object filter: the top-hat filter with a cosine transition of Sec. 4.1.1
 // applied to objects in place (one thread per frequency).
@@ -240,24 +240,30 @@ __global__ void __launch_bounds__(256) merge_kernel(const FrontParams prm) {
     window_to_smem(win, N, prm.border);
     __syncthreads();
     const int ny = prm.P / prm.nx;
-    const long long pix = (long long)prm.H * prm.Wimg;
-    for (long long e = blockIdx.x * 256ll + threadIdx.x; e < pix * prm.K; e += (long long)gridDim.x * 256) {
-        const int k = (int)(e / pix);
-        const long long r = e - (long long)k * pix;
-        const int Y = (int)(r / prm.Wimg), X = (int)(r - (long long)Y * prm.Wimg);
+    // one mosaic row (object k, row Y) per CTA iteration: the patch rows
+    // covering it are the same for the whole row
+    const long long rows = (long long)prm.K * prm.H;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int k = (int)(row / prm.H), Y = (int)(row - (long long)k * prm.H);
         const int iy0 = Y >= N ? (Y - N + s) / s : 0, iy1 = min(ny - 1, Y / s);
-        const int ix0 = X >= N ? (X - N + s) / s : 0, ix1 = min(prm.nx - 1, X / s);
-        float num = 0.f, den = 0.f;
-        for (int iy = iy0; iy <= iy1; ++iy)
-            for (int ix = ix0; ix <= ix1; ++ix) {
-                const int dy = Y - iy * s, dx = X - ix * s;
-                if (dy >= N || dx >= N) continue;
-                const float w = win[dy] * win[dx];
-                const int p = iy * prm.nx + ix;
-                num = fmaf(w, prm.oimg[(((size_t)p * prm.K + k) * N + dy) * N + dx], num);
-                den += w;
+        float* out = prm.image + (size_t)row * prm.Wimg;
+        for (int X = threadIdx.x; X < prm.Wimg; X += 256) {
+            const int ix0 = X >= N ? (X - N + s) / s : 0, ix1 = min(prm.nx - 1, X / s);
+            float num = 0.f, den = 0.f;
+            for (int iy = iy0; iy <= iy1; ++iy) {
+                const int dy = Y - iy * s;
+                if (dy >= N) continue;
+                for (int ix = ix0; ix <= ix1; ++ix) {
+                    const int dx = X - ix * s;
+                    if (dx >= N) continue;
+                    const float w = win[dy] * win[dx];
+                    const int p = iy * prm.nx + ix;
+                    num = fmaf(w, prm.oimg[(((size_t)p * prm.K + k) * N + dy) * N + dx], num);
+                    den += w;
+                }
             }
-        prm.image[e] = den > 0.f ? num / den : 0.f;
+            out[X] = den > 0.f ? num / den : 0.f;
+        }
     }
 }
 
@@ -336,10 +342,10 @@ cudaError_t launch_merge_objects(const FrontParams& prm, int sms, cudaStream_t s
         }
         if (e != cudaSuccess) return e;
     }
-    const long long pix = (long long)prm.H * prm.Wimg * prm.K;
-    if (pix == 0) return cudaSuccess;
-    long long blocks = (pix + 255) / 256;
-    if (blocks > 8ll * sms) blocks = 8ll * sms;
+    const long long rows = (long long)prm.H * prm.K;
+    if (rows == 0 || prm.Wimg == 0) return cudaSuccess;
+    long long blocks = rows;  // one mosaic row per CTA
+    if (blocks > 16ll * sms) blocks = 16ll * sms;
     merge_kernel<<<(int)blocks, 256, (size_t)prm.N * sizeof(float), s>>>(prm);
     return cudaGetLastError();
 }
