@@ -195,16 +195,19 @@ __device__ __forceinline__ void quarter_round_pupil(const volatile Unit* su, flo
 // ----------------------------------------------------------- the machine
 
 // Runs passes [FIRST, LAST) of one unit on the calling warp.
+// Inactive warps (no unit left) only take part in the CTA barrier that ends
+// every pass: the CTA's warps run the same pass at a time.
 template <int FIRST, int LAST, int ES>
 __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __restrict__ E,
-                                           const uint64_t* __restrict__ cmask, const uint64_t* __restrict__ csupp) {
+                                           const uint64_t* __restrict__ cmask, const uint64_t* __restrict__ csupp,
+                                           bool active) {
     constexpr int R = ES < kN ? ES : kN;  // the box side W is at most R
     const int lane = threadIdx.x & 31;
-    const int W = su->W;
+    const int W = active ? su->W : 0;
 #pragma unroll 1
     for (int pass = FIRST; pass < LAST; ++pass) {
-        const int nr = pass_rounds(pass, W);
-        if (FIRST >= P_SEED && lane == 0) {  // L2 prefetch about one pass ahead of use
+        const int nr = active ? pass_rounds(pass, W) : 0;
+        if (FIRST >= P_SEED && lane == 0 && active) {  // L2 prefetch about one pass ahead of use
             if (pass == P_C2R && su->pp) prefetch_l2((const void*)su->pp, (size_t)W * W * sizeof(float2));
             if (pass == P_ADJ && su->hn) prefetch_l2((const void*)su->hn, (size_t)kHalf * sizeof(float2));
         }
@@ -446,6 +449,7 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
             }
         }
         __syncwarp();
+        __syncthreads();
     }
 }
 
@@ -576,8 +580,8 @@ __device__ double reduce_object_warp(const FusedParams& prm, int p, int k, int f
 
 // One warp per unit (patch, object, frame), persistent over the units;
 // FIRST..LAST selects the forward (PUPIL, FIELD, OTF) or adjoint (SEED,
-// C2R, ADJ) passes. No CTA-level synchronisation: warps progress
-// independently, so different warps overlap different passes.
+// C2R, ADJ) passes. A CTA barrier ends every pass, so the CTA's warps run
+// the same pass's code at a time.
 template <int FIRST, int LAST, int ES>
 __global__ void __launch_bounds__(kThreads, 2) mfbd_pass_kernel(const FusedParams prm) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -589,15 +593,19 @@ __global__ void __launch_bounds__(kThreads, 2) mfbd_pass_kernel(const FusedParam
     const int J = prm.J, K = prm.K;
     const long long units = (long long)prm.P * K * J;
     const long long stride = (long long)gridDim.x * nwarps;
-    for (long long u = (long long)blockIdx.x * nwarps + warp; u < units; u += stride) {
-        const int j = (int)(u % J);
-        const long long pk = u / J;
+    // a uniform trip count over the CTA (the passes end in CTA barriers)
+    for (long long base = (long long)blockIdx.x * nwarps; base < units; base += stride) {
+        const long long u = base + warp;
+        const bool active = u < units;
+        const long long ua = active ? u : 0;
+        const int j = (int)(ua % J);
+        const long long pk = ua / J;
         const int k = (int)(pk % K);
         const long long p = pk / K;
         const ObjParams& ob = prm.obj[k];
         const long long pj = p * J + j;  // index of the unit's phase image
         __syncwarp();
-        if (lane == 0) {
+        if (lane == 0 && active) {
             su->W = ob.W;
             su->ld = ob.phi_ld;
             su->inv_z = ob.inv_z;
@@ -619,7 +627,7 @@ __global__ void __launch_bounds__(kThreads, 2) mfbd_pass_kernel(const FusedParam
             }
         }
         __syncwarp();
-        run_passes<FIRST, LAST, ES>(su, E, ob.cmask, ob.csupp);
+        run_passes<FIRST, LAST, ES>(su, E, ob.cmask, ob.csupp, active);
     }
 }
 
