@@ -59,9 +59,9 @@ FP32_LANES_PER_SM = 128
 # kernel of the 64 px pass machine, from one ncu capture of the first 400
 # patches of the 961-patch workload (9600 units); a launch's traffic is this
 # times its units (the traffic is per unit: no cross-unit reuse)
-NCU_DRAM_BYTES_PER_UNIT = {"forward_passes": (73571328 + 503762944) / 9600,
-                           "adjoint_passes": (654928128 + 31121152) / 9600,
-                           "reduction": (324493824 + 115607296) / 9600}
+NCU_DRAM_BYTES_PER_UNIT = {"forward_passes": (71857152 + 503112704) / 9600,
+                           "adjoint_passes": (643635200 + 32342272) / 9600,
+                           "reduction": (324495360 + 115700480) / 9600}
 # the same for the 128 px CTA-per-unit kernels with the field recomputed in
 # the adjoint, from one capture (--metrics dram__bytes_read.sum,
 # dram__bytes_write.sum) of the first 48 patches of the 3969-patch field
