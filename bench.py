@@ -264,6 +264,13 @@ def pass_flops_per_unit(n_pix, npup):
     return fwd, adj
 
 
+def reduction_flops_per_unit(n_pix):
+    """Algorithmic FP32 flops per unit of the frame reduction, per
+    half-spectrum frequency: N += w D conj(H) (8), Q += w |H|^2 (4),
+    E += w |D|^2 (4), r = D - O H (8), w |r|^2 (4), seed -w conj(O) r (8)."""
+    return 36.0 * n_pix * (n_pix // 2 + 1)
+
+
 def reduction_bytes_per_unit(n_pix, n_frames, spec_cols):
     """Algorithmic bytes per unit of the frame reduction: D read, H read,
     G written (complex64 half spectra), object written once per J frames."""
@@ -280,6 +287,24 @@ def measured_peaks():
 
 def fp32_peak_tflops(n_sm, sm_mhz):
     return n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def probe_peaks(local_rank):
+    """FP32 and FP64 fused multiply-add rates of this GPU, measured by the
+    library's probe kernel (every SM full of independent FMA chains, one
+    launch timed with CUDA events) with nvidia-smi clocks sampled during
+    the probe. Outside any timed region."""
+    from paper_2505_10639_gb300 import mfbd
+    mfbd.probe_fma_rate(False, iters=20000)  # warm the clocks
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.2)
+    fp32, ms32, _ = mfbd.probe_fma_rate(False)
+    fp64, ms64, _ = mfbd.probe_fma_rate(True)
+    clk = clocks.stop()
+    return {"fp32_tflops": fp32, "fp32_ms": ms32, "fp64_tflops": fp64, "fp64_ms": ms64, "clocks": clk,
+            "how": "library probe mfbd_probe_fma_rate: 8 CTAs x 256 threads per SM, 8 independent FMA "
+                   "chains a thread, one launch timed with CUDA events"}
 
 
 # ------------------------------------------------------------ CPU oracle leg
@@ -338,65 +363,171 @@ def run_oracle_sample(w, seed, n_patches, cores):
 
 # ------------------------------------------------------------ GPU leg
 
-def run_gpu(args, rank, local_rank, world):
+def time_replays(graph, steps, stream, world, local_rank):
+    """Replays a captured step `steps` times on `stream`, every replay
+    between two CUDA events, with nvidia-smi clocks sampled meanwhile and a
+    barrier plus synchronisation on both sides; returns the mean (the K
+    steps' total / K), the per-step times and the clock record."""
     import torch
     import torch.distributed as dist
-    from paper_2505_10639_gb300.mfbd import Plan
-
-    torch.cuda.set_device(local_rank)
-    w = WORKLOAD
-    seed = SEED + rank
-    # the data always come from the FP32 forward model
-    coeffs, spectra = make_gpu_inputs(w, seed)
-    plan = Plan(w["n_pix"], w["n_patches"], w["diams"], w["wavelengths"], w["n_frames"], w["n_modes"],
-                basis=w["basis"], gamma=gamma_of(w), precision=args.precision, projection=args.projection,
-                recompute=args.recompute, generic=(args.kernels == "generic"))
-    info = plan.info()
-    loss = torch.empty(w["n_patches"], dtype=torch.float64, device=plan.device)
-    grad = torch.empty(plan.coeff_shape(), dtype=torch.float32, device=plan.device)
-    stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        plan.loss_grad(coeffs, spectra, loss=loss, grad=grad)
-    torch.cuda.synchronize()
-    if not np.isfinite(loss.cpu().numpy()).all():
-        raise RuntimeError("non-finite loss")
-
     clocks = ClockSampler(local_rank)
-    plan.set_profiling(True, max_launches=8 * (args.steps + 2) * (2 * plan.n_objects + 3))
-    plan.read_profile(reset=True)
     if world > 1:
         dist.barrier()
     clocks.start()
     time.sleep(0.2)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        plan.loss_grad(coeffs, spectra, loss=loss, grad=grad)
-    e1.record(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for i in range(steps):
+        graph.replay()
+        ev[i + 1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    local_ms = e0.elapsed_time(e1) / args.steps
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    return ev[0].elapsed_time(ev[steps]) / steps, per, clk
+
+
+def step_stats(per):
+    return {"median_ms": statistics.median(per), "min_ms": min(per), "max_ms": max(per), "replays": len(per)}
+
+
+def profile_steps(plan, steps, run):
+    """Per-kernel CUDA-event times of `steps` evaluations (the library's
+    profiling pairs), outside the timed region."""
+    import torch
+    plan.set_profiling(True, max_launches=8 * (steps + 2) * (2 * plan.n_objects + 4))
+    plan.read_profile(reset=True)
+    for _ in range(steps):
+        run()
+    torch.cuda.synchronize()
     prof = plan.read_profile(reset=True)
     plan.set_profiling(False)
+    return prof
 
+
+def make_plan(w, precision, projection, recompute, kernels):
+    from paper_2505_10639_gb300.mfbd import Plan
+    return Plan(w["n_pix"], w["n_patches"], w["diams"], w["wavelengths"], w["n_frames"], w["n_modes"],
+                basis=w["basis"], gamma=gamma_of(w), precision=precision, projection=projection,
+                recompute=recompute, generic=(kernels == "generic"), split=(kernels == "split"))
+
+
+def time_field(args, w, seed, local_rank, world, peaks):
+    """Inputs, plan, captured step, timed replays and the profiled kernel
+    pass of one field workload; returns (line, plan, buffers)."""
+    import torch
+    coeffs, spectra = make_gpu_inputs(w, seed)  # the data always come from the FP32 forward model
+    plan = make_plan(w, args.precision, args.projection, args.recompute, args.kernels)
+    info = plan.info()
+    loss = torch.empty(w["n_patches"], dtype=torch.float64, device=plan.device)
+    grad = torch.empty(plan.coeff_shape(), dtype=torch.float32, device=plan.device)
+    stream = torch.cuda.current_stream()
+    graph = plan.capture(coeffs, spectra, loss, grad)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    if not np.isfinite(loss.cpu().numpy()).all():
+        raise RuntimeError("non-finite loss")
+    local_ms, per, clk = time_replays(graph, args.steps, stream, world, local_rank)
+    del graph
+    prof = profile_steps(plan, args.steps, lambda: plan.loss_grad(coeffs, spectra, loss=loss, grad=grad))
     rmax, rsum = (torch_reducers() if world > 1 else (None, None))
     ms, units, value = aggregate(local_ms, units64_of(w), world, rmax, rsum)
+    line = finish_line(args, plan, info, w, world, ms, value, None, prof, clk, peaks)
+    line["timing"] = dict(step_stats(per), how="CUDA graph of one mfbd_loss_grad replayed per step, CUDA events "
+                                               "between replays on the launching stream; kernel times from a "
+                                               "separate profiled pass of the same number of steps")
+    return line, plan, (coeffs, spectra, loss, grad, stream, rmax, rsum, local_ms)
 
-    e2e = None
+
+def run_gpu(args, rank, local_rank, world, peaks):
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    w = WORKLOAD
+    line, plan, bufs = time_field(args, w, SEED + rank, local_rank, world, peaks)
+    coeffs, spectra, loss, grad, stream, rmax, rsum, local_ms = bufs
     if not args.no_e2e:
-        e2e = run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, w)
-    frontend = None if args.no_frontend else run_frontend(args, plan, coeffs, spectra, w)
-    explicit = None if args.no_frontend else run_explicit(args, plan, coeffs, spectra, w)
-    line = finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk)
-    if frontend is not None:
-        line["frontend"] = frontend
-    if explicit is not None:
-        line["object_inferring_loss"] = explicit
+        line["e2e"] = run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, w)
+    if not args.no_frontend:
+        line["frontend"] = run_frontend(args, plan, coeffs, spectra, w)
+        line["object_inferring_loss"] = run_explicit(args, plan, coeffs, spectra, w)
+    if world == 1 and not args.no_extras and w["n_pix"] == 64 and args.precision == "fp32":
+        line["bf16_phase"] = run_bf16_arm(args, w, coeffs, spectra, loss, grad, local_rank, peaks, local_ms)
+    plan.close()
     return line
+
+
+def compact(line):
+    """The figures of a workload's own line that another line carries."""
+    keep = ("value", "unit", "ms_per_step", "timing", "roofline", "step_roofline", "kernels_ms_per_step",
+            "gpu_launches", "clocks", "e2e")
+    out = {k: line[k] for k in keep if k in line}
+    out["workload"] = line["config"]["workload"]
+    for k in ("problems_per_s", "units_per_step", "units64_per_step", "precision", "recompute", "schedule"):
+        if k in line["config"]:
+            out[k] = line["config"][k]
+    return out
+
+
+def run_extras(args, local_rank, peaks):
+    """The other configurations of the benchmark in the same process, after
+    the headline: the 2000-problem uneven batch and the 128 px field (its
+    own precision and recompute settings), each timed like the headline."""
+    import copy
+    import torch
+    out = {}
+    a = copy.copy(args)
+    a.no_e2e, a.no_frontend = True, True
+    w = dict(WORKLOADS["batched2000"])
+    out["batched2000"] = compact(run_gpu_batch(a, 0, local_rank, 1, w=w, peaks=peaks))
+    torch.cuda.empty_cache()
+    w = dict(WORKLOADS["fov4096_128px"])
+    if args.extra_128px_patches:
+        w["n_patches"] = args.extra_128px_patches
+        w["workload"] += "_first%d" % args.extra_128px_patches
+    w["workload"] += "_bf16phase"
+    a.precision, a.recompute, a.projection, a.kernels = w["precision"], w["recompute"], "tensor", "pass"
+    line, plan, bufs = time_field(a, w, w["seed"], local_rank, 1, peaks)
+    plan.close()
+    del bufs
+    torch.cuda.empty_cache()
+    out["fov4096_128px"] = compact(line)
+    return out
+
+
+def run_bf16_arm(args, w, coeffs, spectra, loss32, grad32, local_rank, peaks, fp32_ms):
+    """The BF16-phase form of the same workload (the phase projection with
+    BF16 operands on the tensor cores, the rest as FP32) on the same inputs
+    in the same process: time per step as for the FP32 line, and its
+    difference from the FP32 results (max relative loss difference over the
+    patches, worst per-patch relative L2 difference of dL/da)."""
+    import torch
+    plan = make_plan(w, "bf16_phase", "tensor", args.recompute, args.kernels)
+    loss = torch.empty_like(loss32)
+    grad = torch.empty_like(grad32)
+    stream = torch.cuda.current_stream()
+    graph = plan.capture(coeffs, spectra, loss, grad)
+    for _ in range(args.warmup):
+        graph.replay()
+    ms, per, clk = time_replays(graph, args.steps, stream, 1, local_rank)
+    prof = profile_steps(plan, args.steps, lambda: plan.loss_grad(coeffs, spectra, loss=loss, grad=grad))
+    l32, g32 = loss32.cpu().numpy(), grad32.cpu().numpy()
+    l16, g16 = loss.cpu().numpy(), grad.cpu().numpy()
+    dl = float(np.max(np.abs(l16 - l32) / np.abs(l32)))
+    num = np.linalg.norm((g16 - g32).reshape(len(l32), -1), axis=1)
+    den = np.linalg.norm(g32.reshape(len(l32), -1), axis=1)
+    dg = float(np.max(num / den))
+    del graph
+    plan.close()
+    return {"workload": w["workload"] + "_bf16phase", "ms_per_step": ms, "value": units64_of(w) / (ms * 1e-3),
+            "unit": UNIT, "speedup_vs_fp32": fp32_ms / ms, "timing": step_stats(per), "clocks": clk,
+            "kernels_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in prof.items()},
+            "difference_from_fp32": {"loss_max_rel": dl, "grad_max_rel_l2": dg},
+            "accuracy": "errors against the FP64 oracle are bounded by the -m gpu tests (loss 1e-2, dL/da 2e-2, "
+                        "object 1e-3 relative)"}
 
 
 def run_explicit(args, plan, coeffs, spectra, w):
@@ -532,7 +663,30 @@ def run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, 
             "d2h_bytes_per_step": d2h, "chunks": args.e2e_chunks}
 
 
-def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
+def alu_peak_of(peaks, n_sm):
+    """FP32 peak for the ALU-bound kernels: the probe's measured FMA rate
+    when there is one, else SMs x 128 lanes x 2 flop x the maximum clock."""
+    mp = measured_peaks()
+    derived = fp32_peak_tflops(n_sm, mp.get("sm_max_mhz", 2070.0))
+    if peaks and peaks.get("fp32_tflops"):
+        basis = ("measured: FP32 FMA probe (mfbd_probe_fma_rate), %.1f TFLOP/s at %s MHz median SM clock; "
+                 "derived %d SMs x %d lanes x 2 flop x %.0f MHz = %.1f"
+                 % (peaks["fp32_tflops"], peaks["clocks"].get("sm_mhz"), n_sm, FP32_LANES_PER_SM,
+                    mp.get("sm_max_mhz", 2070.0), derived))
+        return peaks["fp32_tflops"], basis, derived
+    return derived, ("derived: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock)"
+                     % (n_sm, FP32_LANES_PER_SM, mp.get("sm_max_mhz", 2070.0))), derived
+
+
+def step_flops_per_unit(n_pix, npup, n_modes):
+    """Algorithmic FP32 flops of one unit of a whole step: the two pass
+    directions, the frame reduction, and the modal projection and its adjoint
+    on the pupil's pixels (2 n_pup M each)."""
+    f, a = pass_flops_per_unit(n_pix, npup)
+    return f + a + reduction_flops_per_unit(n_pix) + 4.0 * npup * n_modes
+
+
+def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk, peaks):
     import torch
     local_rank = dist_env()[1]
     # roofline: every kernel against its bound; the dominant one is reported
@@ -542,46 +696,65 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
     fwd_flops = sum(f for f, _ in per_obj) * units_obj
     adj_flops = sum(a for _, a in per_obj) * units_obj
     red_bytes = reduction_bytes_per_unit(w["n_pix"], w["n_frames"], w["n_pix"] // 2 + 1) * units_of(w)
-    peaks = measured_peaks()
+    mp = measured_peaks()
     n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = fp32_peak_tflops(n_sm, sm_max)
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    alu_peak, alu_basis, alu_derived = alu_peak_of(peaks, n_sm)
+    hbm_peak = mp.get("hbm_gbs", 6800.0)
 
     def per_launch(kind):
-        # one forward, reduction and adjoint stage per step (the reduction
-        # stage includes the loss-combine kernel of a split reduction)
+        # one launch of each stage per step (the reduction and fused stages
+        # include their loss-combine kernel)
         return prof[kind][0] / max(1, args.steps)
 
-    # DRAM traffic from the committed ncu captures of the 64 px pass machine
-    # and of the 128 px kernels with recompute; not measured for the others
+    # DRAM traffic from the committed ncu captures of the 64 px kernels and
+    # of the 128 px kernels with recompute; not measured for the others
     ncu_tab, ncu_basis = None, "not captured for this kernel family"
-    if w["n_pix"] == 64 and args.kernels == "pass" and not args.recompute:
+    if w["n_pix"] == 64 and args.kernels in ("pass", "split") and not args.recompute:
         ncu_tab, ncu_basis = NCU_DRAM_BYTES_PER_UNIT, "ncu DRAM bytes per unit (400-patch capture) x units per launch"
     elif w["n_pix"] == 128 and args.recompute:
         ncu_tab, ncu_basis = NCU_DRAM_BYTES_PER_UNIT_128, "ncu DRAM bytes per unit (48-patch capture) x units per launch"
-    ncu_ok = ncu_tab is not None
     kernels = {}
+    if prof.get("fused", (0.0, 0))[1] > 0:
+        # the fused per-(patch, object) kernel: the pass flops of both
+        # directions plus the frame reduction's, against the FP32 peak
+        red_flops = reduction_flops_per_unit(w["n_pix"]) * units_of(w)
+        work = fwd_flops + adj_flops + red_flops
+        t = per_launch("fused")
+        a = work / (t * 1e-3) / 1e12 if t > 0 else 0.0
+        tr = NCU_DRAM_BYTES_PER_UNIT.get("fused_pairs") if ncu_tab else None
+        kernels["fused_pairs"] = {"bound": "alu", "ms": t, "achieved": a, "peak": alu_peak, "unit": "TFLOP/s",
+                                  "frac": a / alu_peak, "frac_of_derived_peak": a / alu_derived,
+                                  "work_per_launch": work, "traffic": tr * units_of(w) if tr else None}
     for name, kind, work in (("forward_passes", "forward", fwd_flops), ("adjoint_passes", "adjoint", adj_flops)):
+        if prof.get(kind, (0.0, 0))[1] == 0:
+            continue
         t = per_launch(kind)
         a = work / (t * 1e-3) / 1e12 if t > 0 else 0.0
         kernels[name] = {"bound": "alu", "ms": t, "achieved": a, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": a / alu_peak, "work_per_launch": work,
-                         "traffic": ncu_tab[name] * units_of(w) if ncu_ok else None}
-    t = per_launch("reduction")
-    a = red_bytes / (t * 1e-3) / 1e9 if t > 0 else 0.0
-    kernels["reduction"] = {"bound": "hbm", "ms": t, "achieved": a, "peak": hbm_peak, "unit": "GB/s",
-                            "frac": a / hbm_peak, "work_per_launch": red_bytes,
-                            "traffic": ncu_tab["reduction"] * units_of(w) if ncu_ok else None}
+                         "frac": a / alu_peak, "frac_of_derived_peak": a / alu_derived, "work_per_launch": work,
+                         "traffic": ncu_tab[name] * units_of(w) if ncu_tab else None}
+    if prof.get("reduction", (0.0, 0))[1] > 0:
+        t = per_launch("reduction")
+        a = red_bytes / (t * 1e-3) / 1e9 if t > 0 else 0.0
+        kernels["reduction"] = {"bound": "hbm", "ms": t, "achieved": a, "peak": hbm_peak, "unit": "GB/s",
+                                "frac": a / hbm_peak, "work_per_launch": red_bytes,
+                                "traffic": ncu_tab["reduction"] * units_of(w) if ncu_tab else None}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     dk = kernels[dom]
     roofline = {"bound": dk["bound"], "kernel": dom, "achieved": dk["achieved"], "peak": dk["peak"],
                 "unit": dk["unit"], "frac": dk["frac"], "traffic": dk["traffic"],
                 "traffic_basis": ncu_basis,
-                "peak_basis": ("FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock)"
-                               % (n_sm, FP32_LANES_PER_SM, sm_max)) if dk["bound"] == "alu"
-                else "HBM copy bandwidth of MEASURED_PEAKS.json",
+                "peak_basis": alu_basis if dk["bound"] == "alu" else "HBM copy bandwidth of MEASURED_PEAKS.json",
                 "work_per_launch": dk["work_per_launch"], "kernel_ms": dk["ms"]}
+    # the whole step against the binding pipe (FP32: the FP64 and HBM work
+    # per unit bind later)
+    step_flops = sum(step_flops_per_unit(w["n_pix"], npup[k], w["n_modes"]) for k in range(len(npup))) * units_obj
+    step_tf = step_flops / (ms * 1e-3) / 1e12
+    step_roofline = {"bound": "alu", "achieved": step_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": step_tf / alu_peak, "work_per_step": step_flops,
+                     "work_per_unit": step_flops / units_of(w),
+                     "basis": "pass flops of both directions + frame reduction + modal projection and adjoint "
+                              "(4 n_pup M) per unit, over ms_per_step"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -598,10 +771,12 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk):
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": e2e,
         "roofline": roofline,
+        "step_roofline": step_roofline,
         "kernels": kernels,
         "kernels_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in prof.items()},
         "gpu_launches": int(sum(v[1] for v in prof.values())),  # kernels, counted by the library
         "clocks": clk,
+        "peaks_measured": peaks,
         "plan": info,
     }
     return line
@@ -719,16 +894,15 @@ def run_oracle_batch_sample(w, n_problems, cores):
     return units / (t1 - t0), t1 - t0, sum(r[2] for r in res), len(chunks)
 
 
-def run_gpu_batch(args, rank, local_rank, world):
+def run_gpu_batch(args, rank, local_rank, world, w=None, peaks=None):
     """One evaluation of the 2000-problem uneven batch per step: the captured
     CUDA graph of mfbd_batch_loss_grad (counter memset + one persistent
     launch, or the autotuner's schedule) replayed, inputs resident."""
     import torch
-    import torch.distributed as dist
     from paper_2505_10639_gb300.mfbd import Batch, Problem
 
     torch.cuda.set_device(local_rank)
-    w = dict(WORKLOAD)
+    w = dict(WORKLOAD if w is None else w)
     w["seed"] = w["seed"] + rank
     probs = batch_problems(w)
     batch = Batch([Problem(p["n_pix"], 1, p["diams"], p["wavelengths"], p["n_frames"], p["n_modes"],
@@ -748,24 +922,8 @@ def run_gpu_batch(args, rank, local_rank, world):
     batch.check()
     if not np.isfinite(loss.cpu().numpy()).all():
         raise RuntimeError("non-finite loss")
-    clocks = ClockSampler(local_rank)
-    if world > 1:
-        dist.barrier()
-    clocks.start()
-    time.sleep(0.2)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        graph.replay()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
+    local_ms, per, clk = time_replays(graph, args.steps, stream, world, local_rank)
     batch.check()
-    local_ms = e0.elapsed_time(e1) / args.steps
     rmax, rsum = (torch_reducers() if world > 1 else (None, None))
     u64 = batch_units64(probs)
     ms, _, value = aggregate(local_ms, u64, world, rmax, rsum)
@@ -804,9 +962,8 @@ def run_gpu_batch(args, rank, local_rank, world):
                "h2d_bytes_per_step": coeffs.numel() * 4 + spectra.numel() * 8,
                "d2h_bytes_per_step": loss.numel() * 8 + grad.numel() * 4}
 
-    peaks = measured_peaks()
     n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    alu_peak = fp32_peak_tflops(n_sm, peaks.get("sm_max_mhz", 2070.0))
+    alu_peak, alu_basis, alu_derived = alu_peak_of(peaks, n_sm)
     flops = batch_flops(probs)
     achieved = flops / (local_ms * 1e-3) / 1e12
     units = sum(p["n_objects"] * p["n_frames"] for p in probs)
@@ -831,11 +988,13 @@ def run_gpu_batch(args, rank, local_rank, world):
                      "traffic_basis": ("ncu DRAM bytes per 64 px-equivalent unit (first 200 problems, same "
                                        "schedule) x units of the launch" if captured
                                        else "not captured for this schedule"),
-                     "peak_basis": "FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock)"
-                                   % (n_sm, FP32_LANES_PER_SM, peaks.get("sm_max_mhz", 2070.0)),
+                     "peak_basis": alu_basis, "frac_of_derived_peak": achieved / alu_derived,
                      "work_per_launch": flops, "kernel_ms": local_ms},
         "gpu_launches": args.steps * (1 if info["mode"] == 0 else 5),
         "clocks": clk,
+        "timing": dict(step_stats(per), how="CUDA graph of one batch evaluation replayed per step, CUDA events "
+                                            "between replays"),
+        "peaks_measured": peaks,
         "batch": {k: info[k] for k in ("n_items", "workspace_bytes", "ctas", "smem_bytes", "max_ctas_per_sm")},
     }
     return line
@@ -863,12 +1022,21 @@ def main():
     ap.add_argument("--workload", default="fov1024_64px", choices=sorted(WORKLOADS),
                     help="fov1024_64px: 961 patches of 64 px (default); fov4096_128px: 3969 patches of "
                          "128 px; batched2000: 2000 uneven problems in one persistent launch")
-    ap.add_argument("--kernels", default="pass", choices=["pass", "generic"],
-                    help="64 px: the warp-per-unit pass machine or the CTA-per-unit kernels of the other sizes")
+    ap.add_argument("--kernels", default="pass", choices=["pass", "split", "generic"],
+                    help="64 px: the fused per-(patch, object) kernel (pass; the three-kernel path when the "
+                         "plan cannot fuse), the three-kernel path (split), or the CTA-per-unit kernels of the "
+                         "other sizes (generic)")
     ap.add_argument("--recompute", default=None, choices=["on", "off"],
                     help="recompute the field and phasors in the backward pass (default: the workload's)")
     ap.add_argument("--problems", type=int, default=0,
                     help="batched2000: use only the first N problems (smaller profiling cases)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time only the chosen workload (by default the 64 px field's line also carries the "
+                         "BF16-phase form, the 2000-problem batch and the 128 px field)")
+    ap.add_argument("--extra-128px-patches", type=int, default=0,
+                    help="time only the first N patches of the 128 px field in the extras (0: all 3969)")
+    ap.add_argument("--probe-peaks", action="store_true",
+                    help="only measure and print the FP32 and FP64 FMA rates of the GPU")
     ap.add_argument("--batch-schedule", default="auto",
                     help="batched2000: auto (autotuner) or <one_launch|staged>:<window units>:<kernel variant>")
     args = ap.parse_args()
@@ -893,6 +1061,8 @@ def main():
         WORKLOAD["workload"] += "_recompute" if args.recompute else "_keep"
     if args.kernels == "generic":
         WORKLOAD["workload"] += "_ctaperunit"
+    elif args.kernels == "split":
+        WORKLOAD["workload"] += "_threekernels"
     args.warmup = max(3, args.warmup)
     rank, local_rank, world = dist_env()
 
@@ -943,11 +1113,19 @@ def main():
         print(json.dumps(line))
         return 0
 
+    if args.probe_peaks:
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps(probe_peaks(local_rank)))
+        return 0
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    import torch
+    torch.cuda.set_device(local_rank)
+    peaks = probe_peaks(local_rank)
     if args.workload == "batched2000":
-        line = run_gpu_batch(args, rank, local_rank, world)
+        line = run_gpu_batch(args, rank, local_rank, world, peaks=peaks)
         if rank == 0:
             if world == 1 and not args.no_cpu_baseline:
                 n = args.cpu_patches or WORKLOAD["cpu_patches"]
@@ -960,7 +1138,10 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return 0
-    line = run_gpu(args, rank, local_rank, world)
+    line = run_gpu(args, rank, local_rank, world, peaks)
+    if world == 1 and not args.no_extras and args.workload == "fov1024_64px" and args.kernels == "pass" \
+            and args.precision == "fp32" and not args.patches:
+        line["configs"] = run_extras(args, local_rank, peaks)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             cores = os.cpu_count() or 1

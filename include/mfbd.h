@@ -86,6 +86,11 @@ typedef enum {
 #define MFBD_FLAG_GENERIC_KERNELS 0x8u /* run N = 64 on the kernels of the other patch
                                         * sizes (one CTA per unit) instead of the 64-pixel
                                         * pass machine (comparison runs) */
+#define MFBD_FLAG_SPLIT_PASSES 0x10u /* N = 64: run mfbd_loss_grad (and the explicit and
+                                      * host-buffer calls) as three kernels that exchange
+                                      * the OTFs, seeds, fields and phasors through the
+                                      * plan's workspaces, instead of the fused kernel
+                                      * that keeps them on chip (comparison runs) */
 
 typedef struct {
     int n_pix;      /* N, patch size in pixels: 48, 64, 96 or 128 */
@@ -115,6 +120,10 @@ typedef struct {
     int ctas;               /* CTAs of the fused kernel */
     int reduction_split;    /* warps per (patch, object) of the frame reduction; > 1 adds a
                                second launch that sums the per-split losses in order */
+    int fused_ctas;         /* CTAs of the fused per-(patch, object) kernel that
+                               mfbd_loss_grad runs (one per SM), or 0 when it runs the
+                               three-kernel path (N != 64, J > 12, a pupil box wider
+                               than 37 px, or MFBD_FLAG_SPLIT_PASSES) */
 } mfbd_plan_info;
 
 /* Create a plan: validates the descriptor, samples pupils, builds the modal
@@ -141,11 +150,18 @@ int mfbd_forward(mfbd_plan_t plan, const float* coeffs, const void* spectra,
 
 /* Backward pass: grad dev [P][J][M] float = dL_p/da_pjm for the coefficients
  * and spectra of the last mfbd_forward on this plan (MFBD_ERR_STATE if there
- * was none). */
+ * was none, or if an mfbd_loss_grad, mfbd_loss_grad_explicit or
+ * mfbd_loss_grad_host came after it). */
 int mfbd_backward(mfbd_plan_t plan, float* grad, void* stream);
 
-/* Forward and backward in one pass (one fused launch plus the two modal
- * projections): loss, object (or NULL) and grad as above. */
+/* Forward and backward in one call: loss, object (or NULL) and grad as
+ * above. For N = 64 with J <= 12 and pupil boxes up to 37 px the pass work is
+ * one fused launch (the fused per-(patch, object) kernel: forward passes,
+ * frame reduction and adjoint passes of a pair in one CTA, the OTFs and seeds
+ * in shared memory, the fields in a per-CTA buffer that stays in L2) plus a
+ * small loss-combine kernel, between the modal phase projection and the
+ * modal adjoint; otherwise the three-kernel path. Keeps nothing for
+ * mfbd_backward on the fused path. */
 int mfbd_loss_grad(mfbd_plan_t plan, const float* coeffs, const void* spectra,
                    double* loss, void* object, float* grad, void* stream);
 
@@ -299,11 +315,12 @@ int mfbd_plan_set_profiling(mfbd_plan_t plan, int enable, int max_launches);
 
 /* Waits for the recorded events, then returns the summed device time in ms
  * and the number of kernels launched inside the timed pairs, per kind,
- * arrays of 5: [0] modal phase
+ * arrays of 6: [0] modal phase
  * projection, [1] forward passes (pupil -> OTF), [2] frame reduction (loss,
  * object, adjoint seeds), [3] adjoint passes (-> dL/dphi), [4] modal adjoint
- * projection. With reset != 0 the pool is emptied for reuse. Arrays may be
- * NULL. */
+ * projection, [5] the fused per-(patch, object) kernel (forward passes,
+ * reduction and adjoint passes in one launch, with its loss combine). With
+ * reset != 0 the pool is emptied for reuse. Arrays may be NULL. */
 int mfbd_plan_read_profile(mfbd_plan_t plan, double* ms, long long* launches, int reset);
 
 /* Allocation-free variant of the fused kernel, for callers that cannot
@@ -332,7 +349,9 @@ int mfbd_plan_read_profile(mfbd_plan_t plan, double* ms, long long* launches, in
  * the plan path for large fields.
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it; make that first call before any
- * stream capture. Each call uploads its small constants with one
+ * stream capture. The cached address belongs to the device's context of
+ * that moment: after cudaDeviceReset on a device, do not call this entry
+ * point on that device again in the same process. Each call uploads its small constants with one
  * cudaMemcpyAsync from pageable host memory (which may wait for the
  * stream's earlier work) and clears grad_phase with cudaMemsetAsync.
  * Calls are serialised on the host, but every call shares the one array

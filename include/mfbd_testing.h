@@ -38,6 +38,17 @@ int mfbd_test_fft_host(int kind, const float* in, float* out);
 int mfbd_test_batch_items(const int* sizes, int n, int mode, int window_units, int* items, long long cap,
                           long long* count);
 
+/* Throughput probe of the fused multiply-add pipe on the current device
+ * (a measurement hook of the benchmark; it runs on the GPU, unlike the
+ * hooks above). fp64 = 0 times FP32 FMAs, 1 FP64 FMAs: 8 CTAs of 256
+ * threads per SM, each thread 8 independent chains of 16 x iters FMAs, one
+ * untimed warm-up launch and one launch timed with CUDA events on `stream`
+ * (a cudaStream_t as void*). Writes the flops of the timed launch (2 per
+ * FMA) to *flops and its time to *ms; synchronises the stream. Returns 0,
+ * MFBD_ERR_INVALID_ARG (NULL pointers, iters < 1), MFBD_ERR_UNSUPPORTED (no
+ * device) or MFBD_ERR_CUDA. */
+int mfbd_probe_fma_rate(int fp64, long long iters, void* stream, double* flops, float* ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,6 +24,7 @@ MFBD_FLAG_FULL_SPECTRUM = 0x1
 MFBD_FLAG_SIMT_PROJECTION = 0x2
 MFBD_FLAG_RECOMPUTE_BACKWARD = 0x4
 MFBD_FLAG_GENERIC_KERNELS = 0x8
+MFBD_FLAG_SPLIT_PASSES = 0x10
 MFBD_BATCH_ONE_LAUNCH = 0
 MFBD_BATCH_STAGED = 1
 
@@ -60,6 +61,7 @@ class PlanInfo(ctypes.Structure):
         ("slots_per_cta", ctypes.c_int),
         ("ctas", ctypes.c_int),
         ("reduction_split", ctypes.c_int),
+        ("fused_ctas", ctypes.c_int),
     ]
 
 
@@ -120,6 +122,7 @@ _SIGNATURES = {
     "mfbd_batch_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     "mfbd_test_batch_items": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_longlong,
                                              _VP]),
+    "mfbd_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, _VP, _VP, _VP]),
 }
 
 _lib = None

@@ -93,6 +93,9 @@ struct BatchParams {
     float* gphi;
 };
 
+constexpr int kBT = 128;  // threads per CTA of the batch kernel
+constexpr int kJC = 8;    // frames per register tile of its P and G items
+
 size_t batch_smem(int es_small, int es_large);
 // Kernel variants: 0, a register budget of up to 255 a thread (2 CTAs per
 // SM); 1, up to 170 (3 CTAs per SM). Also sets the variant's dynamic
@@ -100,5 +103,9 @@ size_t batch_smem(int es_small, int es_large);
 int batch_max_ctas_per_sm(size_t smem, int variant);
 // One launch of `ctas` CTAs over items [item0, item0 + n_items).
 cudaError_t launch_batch(const BatchParams& prm, int ctas, size_t smem, int variant, cudaStream_t s);
+// The same per register budget (MINB CTAs per SM), defined in
+// batch_kernels.cuh and instantiated in batch_kernel_v2.cu / batch_kernel_v3.cu.
+template <int MINB> int batch_max_ctas_variant(size_t smem);
+template <int MINB> cudaError_t launch_batch_variant(const BatchParams& prm, int ctas, size_t smem, cudaStream_t s);
 
 }  // namespace mfbd_dev

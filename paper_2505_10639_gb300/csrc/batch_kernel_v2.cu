@@ -1,0 +1,10 @@
+// The batch kernel of batch_kernels.cuh compiled for 2 CTAs per SM
+// (up to 255 registers a thread).
+#include "batch_kernels.cuh"
+
+namespace mfbd_dev {
+
+template int batch_max_ctas_variant<2>(size_t smem);
+template cudaError_t launch_batch_variant<2>(const BatchParams& prm, int ctas, size_t smem, cudaStream_t s);
+
+}  // namespace mfbd_dev

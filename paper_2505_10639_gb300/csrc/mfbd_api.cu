@@ -18,6 +18,8 @@ using namespace mfbd_dev;
 
 namespace {
 
+constexpr int kProfileKinds = 6;  // see mfbd_plan_read_profile
+
 thread_local char g_last_error[512] = "no error";
 
 int fail(int status, const char* why) {
@@ -61,6 +63,10 @@ struct mfbd_plan {
     unsigned flags = 0;
     int precision = MFBD_PREC_FP32;
     bool generic = false;       // CTA-per-unit kernels (N != 64, recompute, or on request)
+    bool fused = false;         // mfbd_loss_grad runs the fused per-(patch, object) kernel
+    int fused_ctas = 0;         // its CTAs (one per SM)
+    float2* d_fscr = nullptr;   // its field slots [fused_ctas][kFusedFrames][N*N]
+    double* d_lpair = nullptr;  // its per-(patch, object) losses [P][K]
     int es = 0, es2 = 0, sw = 0;  // their exchange-buffer strides and support-row words
     double gamma = 0;
     int* d_err = nullptr;       // set by a tensor-core kernel whose MMA wait gave up
@@ -146,7 +152,7 @@ int validate(const mfbd_plan_desc* d) {
     if (d->precision != MFBD_PREC_FP32 && d->precision != MFBD_PREC_BF16_PHASE)
         return fail(MFBD_ERR_INVALID_ARG, "unknown precision");
     if (d->flags & ~(MFBD_FLAG_FULL_SPECTRUM | MFBD_FLAG_SIMT_PROJECTION | MFBD_FLAG_RECOMPUTE_BACKWARD |
-                     MFBD_FLAG_GENERIC_KERNELS))
+                     MFBD_FLAG_GENERIC_KERNELS | MFBD_FLAG_SPLIT_PASSES))
         return fail(MFBD_ERR_INVALID_ARG, "unknown flags");
     if (d->n_pix != 48 && d->n_pix != 64 && d->n_pix != 96 && d->n_pix != 128)
         return fail(MFBD_ERR_UNSUPPORTED, "n_pix must be 48, 64, 96 or 128");
@@ -478,6 +484,22 @@ int run_fused(mfbd_plan_t p, int stages, const void* spectra, double* loss, void
     return MFBD_OK;
 }
 
+// The fused per-(patch, object) kernel for patches [p0, p0 + np): loss,
+// object and dL/dphi of the chunk in one launch (plus the loss combine).
+int run_pairs(mfbd_plan_t p, const void* spectra, double* loss, void* object, cudaStream_t s, int p0, int np) {
+    FusedParams f = fused_params(p, p0, np, spectra, loss, object, nullptr, nullptr, nullptr);
+    f.fscr = p->d_fscr;
+    f.lpair = p->d_lpair + (size_t)p0 * p->K;
+    const int pi = prof_begin(p, 5, s);
+    const cudaError_t e = launch_fused_pairs(f, p->geo.xs, p->fused_ctas, s);
+    prof_end(p, pi, s, 2);  // + the loss combine
+    if (e != cudaSuccess) {
+        p->failed = true;
+        return cuda_fail(e, "fused kernel");
+    }
+    return MFBD_OK;
+}
+
 // ------------------------------------------------------- host-buffer pipeline
 
 void host_release(mfbd_plan* p) {
@@ -767,6 +789,17 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
             int per_sm = max_ctas_per_sm(p->geo);
             if (per_sm < 1) throw fail(MFBD_ERR_UNSUPPORTED, "fused kernel does not fit on this device");
             p->ctas = prop.multiProcessorCount * per_sm;
+            // the fused per-(patch, object) kernel for mfbd_loss_grad when the
+            // frames and the pupil boxes fit its shared memory
+            if (!(p->flags & MFBD_FLAG_SPLIT_PASSES) && fused_pair_supported(p->J, p->geo.xs)) {
+                const int fper = fused_pair_ctas_per_sm(p->geo.xs);
+                if (fper >= 1) {
+                    p->fused = true;
+                    p->fused_ctas = prop.multiProcessorCount * fper;
+                    if ((st = dev_alloc(p, &p->d_fscr, (size_t)p->fused_ctas * kFusedFrames * n * n))) throw st;
+                    if ((st = dev_alloc(p, &p->d_lpair, (size_t)std::max(1, p->P * p->K)))) throw st;
+                }
+            }
         } else {
             // odd row strides: column accesses do not conflict in shared memory
             p->es = std::max(n / 2 + 1, max_box) | 1;
@@ -823,8 +856,8 @@ int mfbd_plan_set_profiling(mfbd_plan_t p, int enable, int max_launches) {
 
 int mfbd_plan_read_profile(mfbd_plan_t p, double* ms, long long* launches, int reset) {
     if (!p) return fail(MFBD_ERR_INVALID_ARG, "plan is NULL");
-    double acc[5] = {0, 0, 0, 0, 0};
-    long long cnt[5] = {0, 0, 0, 0, 0};
+    double acc[kProfileKinds] = {};
+    long long cnt[kProfileKinds] = {};
     for (int i = 0; i < p->ev_used; ++i) {
         cudaError_t e = cudaEventSynchronize(p->ev[2 * i + 1]);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
@@ -834,7 +867,7 @@ int mfbd_plan_read_profile(mfbd_plan_t p, double* ms, long long* launches, int r
         acc[p->ev_kind[i]] += t;
         cnt[p->ev_kind[i]] += p->ev_nk[i];
     }
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < kProfileKinds; ++k) {
         if (ms) ms[k] = acc[k];
         if (launches) launches[k] = cnt[k];
     }
@@ -1026,6 +1059,7 @@ int mfbd_plan_get_info(mfbd_plan_t p, mfbd_plan_info* info) {
     info->slots_per_cta = p->generic ? 0 : p->geo.slots;
     info->reduction_split = p->rsplit;
     info->ctas = p->ctas;
+    info->fused_ctas = p->fused ? p->fused_ctas : 0;
     return MFBD_OK;
 }
 
@@ -1068,6 +1102,11 @@ int mfbd_loss_grad(mfbd_plan_t p, const float* coeffs, const void* spectra, doub
     if ((st = set_device(p))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if ((st = run_phase(p, coeffs, s, 0, p->P))) return st;
+    if (p->fused) {  // one launch; nothing is kept for mfbd_backward
+        p->have_forward = false;
+        if ((st = run_pairs(p, spectra, loss, object, s, 0, p->P))) return st;
+        return run_grad(p, grad, s, 0, p->P);
+    }
     if ((st = run_fused(p, ST_FWD | ST_RED | ST_ADJ, spectra, loss, object, p->d_gscr, s, 0, p->P))) return st;
     if ((st = run_grad(p, grad, s, 0, p->P))) return st;
     p->have_forward = true;
@@ -1087,7 +1126,8 @@ int mfbd_loss_grad_explicit(mfbd_plan_t p, const float* coeffs, const void* spec
     if ((st = run_phase(p, coeffs, s, 0, p->P))) return st;
     p->x_oin = object;
     p->x_gobj = grad_object;
-    st = run_fused(p, ST_FWD | ST_RED | ST_ADJ, spectra, loss, nullptr, p->d_gscr, s, 0, p->P);
+    st = p->fused ? run_pairs(p, spectra, loss, nullptr, s, 0, p->P)
+                  : run_fused(p, ST_FWD | ST_RED | ST_ADJ, spectra, loss, nullptr, p->d_gscr, s, 0, p->P);
     p->x_oin = nullptr;
     p->x_gobj = nullptr;
     if (st) return st;
@@ -1143,11 +1183,17 @@ int mfbd_loss_grad_host(mfbd_plan_t p, const float* coeffs, const void* spectra,
         // phases and forward passes need only the coefficients: they run
         // while the chunk's spectra are still in flight
         if ((st = run_phase(p, h.d_coeffs + (size_t)p0 * J * M, s, p0, np))) return st;
-        if ((st = run_fused(p, ST_FWD, nullptr, nullptr, nullptr, p->d_gscr, s, p0, np))) return st;
-        MFBD_HOST_TRY(cudaStreamWaitEvent(s, h.ev_copied[b], 0));
-        if ((st = run_fused(p, ST_RED, h.d_spec[b], h.d_loss + p0, obj, p->d_gscr, s, p0, np))) return st;
-        MFBD_HOST_TRY(cudaEventRecord(h.ev_consumed[b], s));
-        if ((st = run_fused(p, ST_ADJ, nullptr, nullptr, nullptr, p->d_gscr, s, p0, np))) return st;
+        if (p->fused) {  // the fused kernel reads the spectra from its first pass on
+            MFBD_HOST_TRY(cudaStreamWaitEvent(s, h.ev_copied[b], 0));
+            if ((st = run_pairs(p, h.d_spec[b], h.d_loss + p0, obj, s, p0, np))) return st;
+            MFBD_HOST_TRY(cudaEventRecord(h.ev_consumed[b], s));
+        } else {
+            if ((st = run_fused(p, ST_FWD, nullptr, nullptr, nullptr, p->d_gscr, s, p0, np))) return st;
+            MFBD_HOST_TRY(cudaStreamWaitEvent(s, h.ev_copied[b], 0));
+            if ((st = run_fused(p, ST_RED, h.d_spec[b], h.d_loss + p0, obj, p->d_gscr, s, p0, np))) return st;
+            MFBD_HOST_TRY(cudaEventRecord(h.ev_consumed[b], s));
+            if ((st = run_fused(p, ST_ADJ, nullptr, nullptr, nullptr, p->d_gscr, s, p0, np))) return st;
+        }
         if ((st = run_grad(p, h.d_grad + (size_t)p0 * J * M, s, p0, np))) return st;
         MFBD_HOST_TRY(cudaEventRecord(h.ev_done, s));
         MFBD_HOST_TRY(cudaStreamWaitEvent(h.d2h, h.ev_done, 0));

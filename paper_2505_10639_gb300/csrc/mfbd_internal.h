@@ -10,6 +10,7 @@ constexpr int kMaxObjects = 8;
 constexpr int kN = 64;                  // patch size supported by the fused kernel
 constexpr int kNH = kN / 2 + 1;         // 33 half-spectrum columns
 constexpr int kHalf = kN * kNH;         // 2112 half-spectrum frequencies
+constexpr int kFusedFrames = 12;        // frames of a (patch, object) pair the fused kernel holds
 
 // Fused-kernel modes.
 enum Mode : int { MODE_FWD = 0, MODE_BWD = 1, MODE_FUSED = 2, MODE_OTF = 3 };
@@ -46,6 +47,8 @@ struct FusedParams {
     double* lpart;            // rsplit > 1: per-split patch losses [P][rsplit]
     const float2* oin;        // object-inferring loss: the given objects [P][K][N][spec_ld], else null
     float2* gobj;             // with oin: dL/dconj(O) [P][K][N][spec_ld], or null
+    float2* fscr;             // fused kernel: per CTA and frame slot the field p [ctas][kFusedFrames][N x N]
+    double* lpair;            // fused kernel: per (patch, object) losses [P][K]
     ObjParams obj[kMaxObjects];
 };
 
@@ -67,6 +70,17 @@ cudaError_t launch_adjoint_passes(const FusedParams& prm, const FusedGeometry& g
 // The kernels of `mode` in order (FWD: forward + reduction; BWD: adjoint;
 // FUSED: all three; OTF: forward only).
 cudaError_t launch_fused(const FusedParams& prm, int mode, const FusedGeometry& g, int sms, cudaStream_t s);
+
+// The fused evaluation (fused_kernels.cu): one persistent launch in which
+// a CTA of kFusedFrames warps carries one (patch, object) pair at a time
+// through the forward passes, the frame reduction and the adjoint passes,
+// then a small kernel sums the pair losses per patch. Needs J <= kFusedFrames
+// and an exchange-buffer stride es of 33 or 37 (pupil boxes up to 37 px);
+// fscr holds ctas x kFusedFrames fields, lpair P x K losses.
+size_t fused_pair_smem(int es);
+bool fused_pair_supported(int J, int es);
+int fused_pair_ctas_per_sm(int es);
+cudaError_t launch_fused_pairs(const FusedParams& prm, int es, int ctas, cudaStream_t s);
 
 // phase[u][i] += div[u mod J][i] for U units (U a multiple of J): the
 // known diversity phases of the J frames added to every patch's phases.
@@ -160,6 +174,11 @@ int generic_adjoint_ctas(int N, int es, int sms);
 cudaError_t launch_generic_forward(const GenericParams& prm, int sms, cudaStream_t s);
 cudaError_t launch_generic_reduction(const GenericParams& prm, int sms, cudaStream_t s);
 cudaError_t launch_generic_adjoint(const GenericParams& prm, int sms, cudaStream_t s);
+// The same per patch size, defined in generic_kernels.cuh and instantiated
+// in generic_n<N>.cu (one translation unit per size).
+template <int N> int generic_adjoint_ctas_n(int es, int sms);
+template <int N> cudaError_t launch_generic_forward_n(const GenericParams& prm, int sms, cudaStream_t s);
+template <int N> cudaError_t launch_generic_adjoint_n(const GenericParams& prm, int sms, cudaStream_t s);
 
 // Warps per (patch, object) of a frame reduction over P patches of K objects
 // at N px: one while the patches alone give every SM 8 warps, more (each lane

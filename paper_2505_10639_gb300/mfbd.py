@@ -14,7 +14,7 @@ from . import _lib
 
 _BASIS = {"zernike": _lib.MFBD_BASIS_ZERNIKE, "kl": _lib.MFBD_BASIS_KL, "user": _lib.MFBD_BASIS_USER}
 _PREC = {"fp32": _lib.MFBD_PREC_FP32, "bf16_phase": _lib.MFBD_PREC_BF16_PHASE}
-KERNEL_KINDS = ("phase", "forward", "reduction", "adjoint", "grad")
+KERNEL_KINDS = ("phase", "forward", "reduction", "adjoint", "grad", "fused")
 
 
 def _fptr(a, ctype):
@@ -26,7 +26,7 @@ class _Desc:
 
     def __init__(self, n_pix, n_patches, diams, wavelengths, n_frames, n_modes, basis, gamma,
                  weights, obscuration, user_basis, precision, full_spectrum, projection="tensor",
-                 recompute=False, generic=False):
+                 recompute=False, generic=False, split=False):
         if projection not in ("tensor", "simt"):
             raise ValueError("projection must be 'tensor' or 'simt'")
         k = len(diams)
@@ -43,7 +43,8 @@ class _Desc:
             flags=(_lib.MFBD_FLAG_FULL_SPECTRUM if full_spectrum else 0)
             | (_lib.MFBD_FLAG_SIMT_PROJECTION if projection == "simt" else 0)
             | (_lib.MFBD_FLAG_RECOMPUTE_BACKWARD if recompute else 0)
-            | (_lib.MFBD_FLAG_GENERIC_KERNELS if generic else 0))
+            | (_lib.MFBD_FLAG_GENERIC_KERNELS if generic else 0)
+            | (_lib.MFBD_FLAG_SPLIT_PASSES if split else 0))
 
 
 def describe_object(obj, n_pix, diams, wavelengths, n_frames, n_modes, basis="kl", gamma=1e-3,
@@ -101,10 +102,11 @@ class Plan:
 
     def __init__(self, n_pix, n_patches, diams, wavelengths, n_frames, n_modes, basis="kl",
                  gamma=1e-3, weights=None, obscuration=0.0, user_basis=None, precision="fp32",
-                 full_spectrum=False, projection="tensor", recompute=False, generic=False, stream=None):
+                 full_spectrum=False, projection="tensor", recompute=False, generic=False, split=False,
+                 stream=None):
         self._lib = _lib.load()
         self._d = _Desc(n_pix, n_patches, diams, wavelengths, n_frames, n_modes, basis, gamma, weights,
-                        obscuration, user_basis, precision, full_spectrum, projection, recompute, generic)
+                        obscuration, user_basis, precision, full_spectrum, projection, recompute, generic, split)
         self.n_pix, self.n_patches, self.n_objects = n_pix, n_patches, len(diams)
         self.n_frames, self.n_modes = n_frames, n_modes
         self.full_spectrum = full_spectrum
@@ -137,7 +139,7 @@ class Plan:
         k = self.n_objects
         return dict(pupil_pixels=list(inf.pupil_pixels[:k]), pupil_box=list(inf.pupil_box[:k]),
                     workspace_bytes=inf.workspace_bytes, slots_per_cta=inf.slots_per_cta, ctas=inf.ctas,
-                    reduction_split=inf.reduction_split)
+                    reduction_split=inf.reduction_split, fused_ctas=inf.fused_ctas)
 
     # ------------------------------------------------------------ calls
     def forward(self, coeffs, spectra, loss=None, obj=None, want_object=True, stream=None):
@@ -218,6 +220,21 @@ class Plan:
             _host(grad, torch.float32, self.coeff_shape(), "grad"), ctypes.c_int(int(n_chunks)),
             _stream(stream)), "mfbd_loss_grad_host")
         return loss, grad, obj
+
+    def capture(self, coeffs, spectra, loss, grad, obj=None):
+        """A CUDA graph of one mfbd_loss_grad on these buffers (the modal
+        phase projection, the pass kernels and the modal adjoint);
+        replay() re-runs it."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.loss_grad(coeffs, spectra, loss=loss, grad=grad, obj=obj, stream=side)  # warm-up
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.loss_grad(coeffs, spectra, loss=loss, grad=grad, obj=obj)
+        return graph
 
     def otf(self, coeffs, out=None, stream=None):
         """mfbd_otf -> H [P, K, J, N, N//2+1] complex64."""
@@ -303,8 +320,8 @@ class Plan:
 
     def read_profile(self, reset=True):
         """mfbd_plan_read_profile -> {kind: (ms, launches)} for KERNEL_KINDS."""
-        ms = np.zeros(5, np.float64)
-        n = np.zeros(5, np.int64)
+        ms = np.zeros(len(KERNEL_KINDS), np.float64)
+        n = np.zeros(len(KERNEL_KINDS), np.int64)
         _lib.check(self._lib.mfbd_plan_read_profile(self._h, ms.ctypes.data, n.ctypes.data, int(reset)),
                    "mfbd_plan_read_profile")
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
@@ -348,6 +365,20 @@ def phase_loss_grad_noalloc(phase, spectra, n_patches, diams, n_frames, gamma, w
         _dev(obj, torch.complex64, (n_patches, k, 64, cols), "object") if obj is not None else None,
         _dev(grad_phase, torch.float32, shape, "grad_phase"), _stream(stream)), "mfbd_phase_loss_grad_noalloc")
     return loss, grad_phase, obj
+
+
+def probe_fma_rate(fp64=False, iters=None, stream=None):
+    """mfbd_probe_fma_rate: the FP32 (or FP64) fused multiply-add rate of the
+    current device, one timed launch that fills every SM; returns
+    (TFLOP/s, ms, flops)."""
+    lib = _lib.load()
+    if iters is None:
+        iters = 4000 if fp64 else 200000
+    flops = ctypes.c_double(0.0)
+    ms = ctypes.c_float(0.0)
+    _lib.check(lib.mfbd_probe_fma_rate(1 if fp64 else 0, int(iters), _stream(stream), ctypes.byref(flops),
+                                       ctypes.byref(ms)), "mfbd_probe_fma_rate")
+    return flops.value / (ms.value * 1e-3) / 1e12, ms.value, flops.value
 
 
 class Problem:
@@ -514,17 +545,22 @@ class Batch:
 
 class MOMFBDLoss(torch.autograd.Function):
     """loss[P] = MOMFBD loss of every patch as a differentiable function of
-    the modal coefficients (spectra are data: no gradient)."""
+    the modal coefficients (spectra are data: no gradient).
+
+    The forward runs mfbd_loss_grad (the fused path) and keeps dL/da with
+    the node; the backward scales it by the incoming gradient. No node
+    depends on the plan's state after its forward, so any number of
+    evaluations on one plan may precede the backward."""
 
     @staticmethod
     def forward(ctx, coeffs, spectra, plan):
-        loss, _ = plan.forward(coeffs.detach().contiguous(), spectra.contiguous(), want_object=False)
-        ctx.plan = plan
+        loss, grad, _ = plan.loss_grad(coeffs.detach().contiguous(), spectra.detach().contiguous())
+        ctx.save_for_backward(grad)
         return loss
 
     @staticmethod
     def backward(ctx, grad_loss):
-        g = ctx.plan.backward()
+        (g,) = ctx.saved_tensors
         return g * grad_loss.to(g.dtype)[:, None, None], None, None
 
 

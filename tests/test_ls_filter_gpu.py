@@ -131,3 +131,55 @@ def test_ls_filter_argument_errors():
     h = plan.ls_filter_objects(d, s, 1.0)
     torch.cuda.synchronize()
     assert not h.cpu().numpy().any()
+
+
+@pytest.mark.parametrize("n_pix,diams,n_frames,n_patches,factor",
+                         [(64, (36.0, 28.0), 12, 3, 200.0), (128, (56.0,), 3, 1, 400.0)])
+def test_ls_filter_against_fp64_definition(n_pix, diams, n_frames, n_patches, factor):
+    """The FP32 kernel against Eq. 25 evaluated in FP64. The threshold turns
+    H into a decision, so the two may decide differently only where the FP64
+    H lies within the FP32 rounding error of 0.2 (the error of nu q / |n|^2
+    bounded per frequency from the sizes of the summed terms). Running the
+    FP64 pipeline with the FP32 decisions at exactly those frequencies must
+    then give the kernel's filter: the same zero pattern and the same values
+    to FP32 rounding."""
+    case = _case(n_pix, diams, n_frames, n_patches, 20250521 + n_pix)
+    d64, s_half, n = _inputs(case)
+    nu = _noise_power(case, factor)
+    weights = np.asarray(case["setup"].weights, np.float32)
+    plan = _plan(case)
+    d = torch.from_numpy(np.ascontiguousarray(omfbd.half_spectrum(d64))).cuda()
+    h = plan.ls_filter_objects(d, torch.from_numpy(s_half).cuda(), nu)
+    torch.cuda.synchronize()
+    h = h.cpu().numpy().astype(np.float64)
+    eps = 2.0 ** -24
+    ambiguous_total = 0
+    for p in range(s_half.shape[0]):
+        for k in range(s_half.shape[1]):
+            dd = omfbd.full_from_half(omfbd.half_spectrum(d64[p, k]).astype(np.complex128), n)
+            ss = omfbd.full_from_half(s_half[p, k].astype(np.complex128), n)
+            w = weights[k].astype(np.float64)
+            h64 = filters.ls_filter_raw(dd, ss, w, nu, np.float64)
+            h32 = filters.ls_filter_raw(dd, ss, w, nu, np.float32).astype(np.float64)
+            # FP32 error bound of H = 1 - r, r = nu q / |n|^2: q sums J
+            # positive terms (relative error <= (J + 2) eps); n sums J terms
+            # whose sizes add up to sum |w d s| (absolute error <= (J + 2)
+            # eps sum |w d s|, doubled in |n|^2); one more eps for the ratio
+            J = len(w)
+            nabs = np.abs(np.tensordot(w, dd * np.conj(ss), axes=1))
+            tsum = np.tensordot(np.abs(w), np.abs(dd) * np.abs(ss), axes=1)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                bound = np.abs(1.0 - h64) * eps * ((J + 3.0) + 2.0 * (J + 2.0) * tsum / nabs)
+            dec64 = np.nan_to_num(h64, nan=-1.0, neginf=-1.0) >= 0.2
+            dec32 = np.nan_to_num(h32, nan=-1.0, neginf=-1.0) >= 0.2
+            amb = np.abs(h64 - 0.2) <= 2.0 * np.nan_to_num(bound, nan=np.inf, posinf=np.inf)
+            assert not np.any((dec32 != dec64) & ~amb), (p, k)
+            ambiguous_total += int(np.sum(dec32 != dec64))
+            t = np.minimum(np.where(dec32, np.nan_to_num(h64), 0.0), 1.0)
+            med = filters.median3x3_periodic(t)
+            want = np.where(filters.connected_to_zero(med > 0), med, 0.0)[:, : n // 2 + 1]
+            got = h[p, k]
+            assert np.array_equal(got == 0, want == 0), (p, k)
+            assert np.allclose(got, want, rtol=1e-5, atol=0), (p, k, np.max(np.abs(got - want)))
+    print("N=%d: %d threshold decisions differ between FP32 and FP64, all within the rounding bound"
+          % (n, ambiguous_total))

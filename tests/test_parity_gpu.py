@@ -122,9 +122,12 @@ def test_field_slice_loss_object_grad(c2_slice):
     _check(c2_slice, loss, grad, obj, ref)
 
 
-def test_split_forward_backward_equals_fused(c2_slice):
+def test_split_forward_backward_equals_one_call(c2_slice):
+    """mfbd_forward + mfbd_backward (the three kernels with the plan's
+    workspaces) give the bits of mfbd_loss_grad on the same three kernels."""
     a32, d32, _ = _inputs(c2_slice)
-    plan = _plan_for(c2_slice)
+    plan = _plan_for(c2_slice, split=True)
+    assert plan.info()["fused_ctas"] == 0
     lf, gf, of = _run_fused(plan, a32, d32)
     a = torch.from_numpy(a32).cuda()
     d = torch.from_numpy(d32).cuda()
@@ -134,6 +137,35 @@ def test_split_forward_backward_equals_fused(c2_slice):
     assert np.array_equal(loss.cpu().numpy(), lf)
     assert np.array_equal(grad.cpu().numpy(), gf)
     assert np.array_equal(obj.cpu().numpy().astype(np.complex128), of)
+
+
+@pytest.mark.parametrize("case_name", ["c1", "c2_slice", "weights", "two_frames"])
+def test_fused_kernel_matches_three_kernel_path(case_name, c1, c2_slice):
+    """The fused per-(patch, object) kernel and the three-kernel path do the
+    same arithmetic per frequency and per line: the object and dL/da agree
+    bit for bit; the loss sums the same FP32 terms with another split into
+    per-thread Kahan sums (agreement to 1e-8; 3e-10 measured)."""
+    if case_name == "c1":
+        case = c1
+    elif case_name == "c2_slice":
+        case = c2_slice
+    elif case_name == "weights":
+        case = cases.make_case(diams=(36.0, 28.0), wavelengths=(6563.0, 8542.0), n_frames=7, n_modes=30,
+                               basis="kl", n_patches=5, seed=20250523,
+                               weights=np.linspace(0.5, 1.5, 14).reshape(2, 7))
+    else:
+        case = cases.make_case(diams=(30.0,), wavelengths=(8542.0,), n_frames=2, n_modes=12, n_patches=4,
+                               seed=20250524)
+    a32, d32, d_or = _inputs(case)
+    fused = _plan_for(case)
+    assert fused.info()["fused_ctas"] > 0
+    split = _plan_for(case, split=True)
+    lf, gf, of = _run_fused(fused, a32, d32)
+    ls, gs, os_ = _run_fused(split, a32, d32)
+    assert np.array_equal(gf, gs)
+    assert np.array_equal(of, os_)
+    assert np.all(np.abs(lf - ls) <= 1e-8 * np.abs(ls)), (lf, ls)
+    _check(case, lf, gf, of, _oracle(case, a32, d_or))
 
 
 def test_full_spectrum_layout(c1):
@@ -210,6 +242,26 @@ def test_autograd_function(c1):
     (3.0 * loss.sum()).backward()
     _, g, _ = _run_fused(plan, a32, d32, want_object=False)
     assert np.allclose(a.grad.cpu().numpy(), 3.0 * g, rtol=1e-6, atol=0)
+
+
+def test_autograd_two_forwards_before_one_backward(c2_slice):
+    """Two evaluations on one plan before one backward (a loss summed over
+    two evaluations): each node's gradient is that of its own inputs, not
+    of the plan's last evaluation."""
+    from paper_2505_10639_gb300.mfbd import momfbd_loss
+    a32, d32, _ = _inputs(c2_slice)
+    b32 = (a32 + 0.05 * np.sin(np.arange(a32.size, dtype=np.float32)).reshape(a32.shape)).astype(np.float32)
+    plan = _plan_for(c2_slice)
+    d = torch.from_numpy(d32).cuda()
+    a = torch.from_numpy(a32).cuda().requires_grad_(True)
+    b = torch.from_numpy(b32).cuda().requires_grad_(True)
+    total = 2.0 * momfbd_loss(a, d, plan).sum() + momfbd_loss(b, d, plan).sum()
+    total.backward()
+    _, ga, _ = _run_fused(plan, a32, d32, want_object=False)
+    _, gb, _ = _run_fused(plan, b32, d32, want_object=False)
+    assert not np.allclose(ga, gb)
+    assert np.array_equal(a.grad.cpu().numpy(), (2.0 * torch.from_numpy(ga)).numpy())
+    assert np.array_equal(b.grad.cpu().numpy(), gb)
 
 
 def test_gradient_central_differences_on_gpu(c1):
@@ -428,19 +480,21 @@ def test_lbfgs_driven_from_the_host(c2_slice):
     assert torch.all(l1 < 0.9 * l0), (l0, l1)
 
 
-def test_profile_counts_the_kernels_of_a_step(c2_slice):
+@pytest.mark.parametrize("split", [False, True])
+def test_profile_counts_the_kernels_of_a_step(c2_slice, split):
     """The profiling pairs count every kernel a step launches: per object a
-    phase projection (plus the coefficient split once, tensor path), the
-    forward passes, the frame reduction and, when it is split, the loss
-    combine, the adjoint passes, and the modal adjoint GEMM and combine."""
+    phase projection (plus the coefficient split once, tensor path); then
+    the fused kernel and its loss combine, or the forward passes, the frame
+    reduction and, when it is split, the loss combine, and the adjoint
+    passes; and the modal adjoint GEMM and combine."""
     a32, d32, _ = _inputs(c2_slice)
-    plan = _plan_for(c2_slice)
-    split = plan.info()["reduction_split"]
-    assert split > 1  # three patches
+    plan = _plan_for(c2_slice, split=split)
+    assert plan.info()["reduction_split"] > 1  # three patches
     plan.set_profiling(True, max_launches=64)
     _run_fused(plan, a32, d32, want_object=False)
     prof = plan.read_profile(reset=True)
     counts = {k: v[1] for k, v in prof.items()}
     K = len(c2_slice["diams"])
-    assert list(counts.values()) == [K + 1, 1, 2, 1, 2], counts
+    want = [K + 1, 1, 2, 1, 2, 0] if split else [K + 1, 0, 0, 0, 2, 2]
+    assert list(counts.values()) == want, counts
     plan.set_profiling(False)

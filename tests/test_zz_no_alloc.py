@@ -52,13 +52,22 @@ def _noalloc(d, phase, spectra, want_object):
     return loss.cpu().numpy(), gphi.cpu().numpy(), (obj.cpu().numpy() if obj is not None else None)
 
 
-@pytest.mark.parametrize("kind", ["two_objects_kl", "single_patch"])
+@pytest.mark.parametrize("kind", ["two_objects_kl", "single_patch", "two_objects_20_patches",
+                                  "one_object_300_frames"])
 def test_noalloc_matches_plan_path_twice(kind):
+    """The patches go through the static array in batches: 14 patches per
+    batch at 2 objects x 12 frames, so 20 patches take two batches (14 + 6),
+    and one patch per batch at 1 object x 300 frames, so 3 patches take
+    three; both check every per-batch offset against the one-launch plan."""
     if kind == "single_patch":
         case = cases.single_patch_64px()
+    elif kind == "one_object_300_frames":
+        case = cases.make_case(diams=(32.0,), wavelengths=(8542.0,), n_frames=300, n_modes=20,
+                               basis="zernike", n_patches=3, seed=20250519)
     else:
         case = cases.make_case(diams=(36.0, 28.0), wavelengths=(6563.0, 8542.0), n_frames=12, n_modes=44,
-                               basis="kl", n_patches=3, seed=20250517)
+                               basis="kl", n_patches=20 if kind == "two_objects_20_patches" else 3,
+                               seed=20250517)
     s = case["setup"]
     P, K, J, M = case["d"].shape[0], len(case["diams"]), case["n_frames"], case["n_modes"]
     a32 = case["a_eval"].astype(np.float32)
