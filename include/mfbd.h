@@ -137,6 +137,14 @@ int mfbd_plan_destroy(mfbd_plan_t plan);
 
 int mfbd_plan_get_info(mfbd_plan_t plan, mfbd_plan_info* info);
 
+/* Synchronise `stream`, then MFBD_ERR_TIMEOUT if a bounded device-side wait
+ * of an earlier call on this plan gave up (the tensor-core phase
+ * projection's MMA completion, the TMA loads of mfbd_spectra_from_frames):
+ * the outputs of the calls since the last check are then invalid. The flag
+ * is cleared. MFBD_OK otherwise. The paper has no counterpart (device-side
+ * failure detection of this library). */
+int mfbd_plan_check(mfbd_plan_t plan, void* stream);
+
 /* Forward pass (Eqs. 20-22, 11, 12).
  *   coeffs  dev [P][J][M] float: a_pjm, radians at wavelength[0].
  *   spectra dev [P][K][J][N][N/2+1] complex64 (or [N][N] with

@@ -123,6 +123,7 @@ _SIGNATURES = {
     "mfbd_test_batch_items": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_longlong,
                                              _VP]),
     "mfbd_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, _VP, _VP, _VP]),
+    "mfbd_plan_check": (ctypes.c_int, [_VP, _VP]),
 }
 
 _lib = None

@@ -19,10 +19,19 @@
 // Object filter: the top-hat filter with a cosine transition of Sec. 4.1.1
 // applied to objects in place (one thread per frequency).
 //
+// Spectra of 64 px patches whose columns start on 16-byte boundaries (patch
+// stride and frame width multiples of 4) take the TMA form: the patch comes
+// into shared memory as two 64 x 32 float boxes of a 2-D tensor map over the
+// frames (128-byte swizzle, so that a lane reading its row with 16-byte loads
+// meets no bank conflict), the next unit's patch is requested as soon as the
+// lanes hold the current one in registers, and its arrival is awaited on an
+// mbarrier with a bounded wait.
+//
 // The window (a raised-cosine transition of `border` px at each edge,
 // evaluated at pixel centres) is computed per CTA in shared memory with
 // cosf.
 #include "mfbd_internal.h"
+#include "tma.cuh"
 #include "unit_passes.cuh"
 
 namespace mfbd_dev {
@@ -152,6 +161,125 @@ __global__ void __launch_bounds__(FrontCta<N>::THREADS) spectra_kernel(const Fro
             });
         }
         __syncthreads();
+    }
+}
+
+constexpr int kTmaBoxCols = 32;                            // 128 bytes of float: the swizzle span
+constexpr uint32_t kTmaTileBytes = 64 * 64 * sizeof(float);  // one 64 x 64 patch, two boxes
+
+// Shared memory of the TMA form: the swizzled patch (1024-byte aligned), the
+// mbarrier, the window and the exchange buffer.
+size_t tma_front_smem(int es) { return 1024 + kTmaTileBytes + 16 + 64 * 4 + (size_t)64 * es * sizeof(float2); }
+
+// Row y of the swizzled patch as float4 chunks: chunk c (floats 4c..4c+3 of
+// the row) of the box `half` (columns 32 half .. 32 half + 31).
+__device__ __forceinline__ float4 tile_chunk(const float* tile, int half, int y, int c) {
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(tile) + half * (kTmaTileBytes / 2) + y * 128 +
+                             ((c ^ (y & 7)) << 4);
+    return *reinterpret_cast<const float4*>(b);
+}
+
+__global__ void __launch_bounds__(32) spectra_tma_kernel(const FrontParams prm, const __grid_constant__ CUtensorMap map) {
+    constexpr int N = 64, NH = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    unsigned char* base = fsm + ((1024 - (tma::smem_u32(fsm) & 1023)) & 1023);
+    float* tile = reinterpret_cast<float*>(base);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + kTmaTileBytes);
+    float* win = reinterpret_cast<float*>(base + kTmaTileBytes + 16);
+    float2* E = reinterpret_cast<float2*>(base + kTmaTileBytes + 16 + N * 4);
+    const int es = prm.es, lane = threadIdx.x;
+    const long long units = (long long)prm.P * prm.K * prm.J;
+    window_to_smem(win, N, prm.border);
+    // frame row and column of unit u's patch in the tensor map
+    auto request = [&](long long u) {
+        const int j = (int)(u % prm.J);
+        const long long pk = u / prm.J;
+        const int k = (int)(pk % prm.K);
+        const int p = (int)(pk / prm.K);
+        const int x0 = (p % prm.nx) * prm.stride;
+        const int row = (k * prm.J + j) * prm.H + (p / prm.nx) * prm.stride;
+        tma::mbar_arrive_expect_tx(bar, kTmaTileBytes);
+        tma::load_2d(tile, &map, x0, row, bar);
+        tma::load_2d(tile + kTmaTileBytes / 8, &map, x0 + kTmaBoxCols, row, bar);
+    };
+    if (lane == 0) {
+        tma::mbar_init(bar, 1);
+        if ((long long)blockIdx.x < units) request(blockIdx.x);
+    }
+    __syncwarp();
+    uint32_t parity = 0;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        if (!tma::mbar_wait(bar, parity)) {  // the copy never arrived: flag it and stop
+            if (lane == 0) atomicExch(prm.err, 1);
+            return;
+        }
+        parity ^= 1;
+        // rows lane and lane + N/2 of the patch as the real and imaginary
+        // parts of one line, with per-lane FP32 sums for the mean
+        float2 v[N];
+        float part[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float4 a = tile_chunk(tile, h, lane, c), b = tile_chunk(tile, h, lane + N / 2, c);
+                const int x = 32 * h + 4 * c;
+                v[x] = make_float2(a.x, b.x);
+                v[x + 1] = make_float2(a.y, b.y);
+                v[x + 2] = make_float2(a.z, b.z);
+                v[x + 3] = make_float2(a.w, b.w);
+                part[c & 3] += (a.x + a.y) + (a.z + a.w) + ((b.x + b.y) + (b.z + b.w));
+            }
+        }
+        __syncwarp();
+        // every lane holds its rows: the next unit's patch may land in the tile
+        if (lane == 0 && u + gridDim.x < units) {
+            tma::fence_proxy_async_smem();
+            request(u + gridDim.x);
+        }
+        double acc = ((double)part[0] + (double)part[1]) + ((double)part[2] + (double)part[3]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        const float m = (float)(acc / (N * N));
+        const float wa = win[lane], wb = win[lane + N / 2];
+#pragma unroll
+        for (int x = 0; x < N; ++x) {
+            const float wx = win[x];
+            v[x] = make_float2((v[x].x - m) * wa * wx + m, (v[x].y - m) * wb * wx + m);
+        }
+        // rows: split the line's transform into the two half spectra
+        line_fft<N, -1>(v, 0);
+        fftreg::static_for<0, N / 2 + 1>([&](auto kk) {
+            constexpr int kx = decltype(kk)::value;
+            const float2 pc = conj_partner<N, kx>(v);
+            const float2 ra = cscale(cadd(v[kx], pc), 0.5f);
+            const float2 d = cscale(csub(v[kx], pc), 0.5f);
+            E[lane * es + kx] = ra;
+            E[(lane + N / 2) * es + kx] = make_float2(d.y, -d.x);
+        });
+        __syncwarp();
+        // columns kx = 1 .. N/2 - 1; lane 0 packs the real columns 0 and N/2
+        float2* D = prm.spectra + (size_t)u * N * NH;
+        {
+            const int kx = lane;
+#pragma unroll
+            for (int ky = 0; ky < N; ++ky)
+                v[ky] = kx == 0 ? make_float2(E[ky * es].x, E[ky * es + N / 2].x) : E[ky * es + kx];
+            line_fft<N, -1>(v, 0);
+            fftreg::static_for<0, N>([&](auto kk) {
+                constexpr int ky = decltype(kk)::value;
+                const float2 pc = conj_partner<N, ky>(v);
+                if (kx > 0) {
+                    D[ky * NH + kx] = v[ky];
+                } else {
+                    const float2 d0 = cscale(cadd(v[ky], pc), 0.5f);
+                    const float2 d = cscale(csub(v[ky], pc), 0.5f);
+                    D[ky * NH] = d0;
+                    D[ky * NH + N / 2] = make_float2(d.y, -d.x);
+                }
+            });
+        }
+        __syncwarp();
     }
 }
 
@@ -306,9 +434,60 @@ cudaError_t launch_persistent_front(Kern kern, int threads, size_t smem, long lo
 
 size_t front_smem(int N, int es) { return (size_t)16 * ((N * 4 + 15) / 16) + 16 * 8 + (size_t)N * es * sizeof(float2); }
 
+namespace tma {
+
+bool encode_f32_2d_swizzle128(CUtensorMap* map, const float* base, uint64_t cols, uint64_t rows, uint32_t box_cols,
+                              uint32_t box_rows) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    if (box_cols * sizeof(float) != 128) return false;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * sizeof(float)};
+    const cuuint32_t box[2] = {box_cols, box_rows};
+    const cuuint32_t elem[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, elem,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace tma
+
+bool spectra_tma_eligible(const FrontParams& prm) {
+    return prm.N == 64 && prm.stride % 4 == 0 && prm.Wimg % 4 == 0 &&
+           (reinterpret_cast<uintptr_t>(prm.frames) & 15) == 0 && prm.err != nullptr &&
+           (long long)prm.K * prm.J * prm.H < (1ll << 31);
+}
+
 cudaError_t launch_spectra_from_frames(const FrontParams& prm, int sms, cudaStream_t s) {
     const long long units = (long long)prm.P * prm.K * prm.J;
     if (units == 0) return cudaSuccess;
+    if (spectra_tma_eligible(prm)) {
+        CUtensorMap map;
+        if (tma::encode_f32_2d_swizzle128(&map, prm.frames, (uint64_t)prm.Wimg,
+                                          (uint64_t)prm.K * prm.J * prm.H, kTmaBoxCols, 64)) {
+            const size_t smem = tma_front_smem(prm.es);
+            cudaError_t e = cudaFuncSetAttribute(spectra_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spectra_tma_kernel, 32, smem)) !=
+                cudaSuccess)
+                return e;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            long long ctas = (long long)sms * per_sm;
+            if (ctas > units) ctas = units;
+            spectra_tma_kernel<<<(int)ctas, 32, smem, s>>>(prm, map);
+            return cudaGetLastError();
+        }
+    }
     const size_t smem = front_smem(prm.N, prm.es);
     switch (prm.N) {
         case 48: return launch_persistent_front(spectra_kernel<48>, FrontCta<48>::THREADS, smem, units, sms, prm, s);

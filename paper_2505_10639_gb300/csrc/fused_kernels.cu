@@ -28,7 +28,10 @@
 //     ADJ    W columns: column F^H -> G_P; dL/dphi = 2 Im(conj(P) G_P) with
 //            P = exp(i phi) recomputed from the phase, which is copied into
 //            the column's shared-memory slots while the transform runs
-// A CTA barrier ends every pass, so the warps run one pass's code at a time.
+// CTA barriers stand only where the data cross warps: after the OTF pass (the
+// reduction reads every frame's OTF) and after the reduction (every seed is
+// written); the named barrier of the frame warps orders the OTF and SEED
+// passes against the exchange buffers they overlap.
 // The pair's loss (the threads' Kahan sums, combined in a fixed order) goes
 // to lpair[p][k]; the objects are summed per patch by a second small kernel.
 #include "mfbd_internal.h"
@@ -110,7 +113,8 @@ __device__ __forceinline__ void fused_quarter_pupil(const float* ph, int ld, flo
     }
 }
 
-template <int ES>
+// EXPL: the object-inferring loss (the objects given), else the Wiener loss.
+template <int ES, bool EXPL>
 __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams prm) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ FrameSlot slot[kFW];
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
             if (pass == F_SEED) {
                 // frame reduction over the J OTFs in shared memory (every
                 // OTF pass ended in the CTA barrier below)
-                double v = reduce_frequencies<kFW>(prm, (int)p, k, HA, threadIdx.x, kFT);
+                double v = reduce_frequencies<kFW, EXPL ? 2 : 1, true>(prm, (int)p, k, HA, threadIdx.x, kFT);
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
                 if (lane == 0) swarp[warp] = v;
@@ -223,10 +227,11 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
                         }
                     } else {  // conj(g_q p) of row y
                         const int y = lane + 32 * (r - 1);
+                        const uint64_t keep = l2_evict_last();  // the slot is written again by the next pair
 #pragma unroll
                         for (int i2 = 0; i2 < kN / 2; ++i2) {
                             const float2 g = E[y * ES + i2];  // g_q at x = 2 i2, 2 i2 + 1
-                            const float4 pp = pf[i2 * kN + y];   // p at x = 2 i2, 2 i2 + 1
+                            const float4 pp = ld_hint(pf + i2 * kN + y, keep);  // p at x = 2 i2, 2 i2 + 1
                             v[2 * i2] = make_float2(g.x * pp.x, -g.x * pp.y);
                             v[2 * i2 + 1] = make_float2(g.y * pp.z, -g.y * pp.w);
                         }
@@ -259,9 +264,11 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
                 } else if (pass == F_FIELD) {
                     if (r < 2) {  // keep the field row; PSF row s = |p|^2 / (N^2 n_pup) as float pairs
                         const int y = lane + 32 * r;
+                        const uint64_t keep = l2_evict_last();  // the field slots stay in L2 from FIELD to C2R
 #pragma unroll
                         for (int i2 = 0; i2 < kN / 2; ++i2)
-                            pf[i2 * kN + y] = make_float4(v[2 * i2].x, v[2 * i2].y, v[2 * i2 + 1].x, v[2 * i2 + 1].y);
+                            st_hint(pf + i2 * kN + y,
+                                    make_float4(v[2 * i2].x, v[2 * i2].y, v[2 * i2 + 1].x, v[2 * i2 + 1].y), keep);
                         const float iz = ob.inv_z;
 #pragma unroll
                         for (int i2 = 0; i2 < kN / 2; ++i2)
@@ -357,30 +364,33 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
                     }
                 }
             }
+            // the reduction needs every frame's OTF; the other passes work on
+            // the warp's own buffer
             __syncwarp();
-            __syncthreads();
+            if (pass == F_OTF) __syncthreads();
         }
     }
 }
 
-template <int ES>
+template <int ES, bool EXPL>
 cudaError_t launch_pairs_es(const FusedParams& prm, int ctas, cudaStream_t s) {
     const size_t smem = fused_pair_smem(ES);
-    cudaError_t e = cudaFuncSetAttribute(fused_pair_kernel<ES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(fused_pair_kernel<ES, EXPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    fused_pair_kernel<ES><<<ctas, kFT, smem, s>>>(prm);
+    fused_pair_kernel<ES, EXPL><<<ctas, kFT, smem, s>>>(prm);
     return cudaGetLastError();
 }
 
 template <int ES>
 int pair_ctas_per_sm_es() {
     const size_t smem = fused_pair_smem(ES);
-    if (cudaFuncSetAttribute(fused_pair_kernel<ES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(fused_pair_kernel<ES, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_pair_kernel<ES>, kFT, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_pair_kernel<ES, false>, kFT, smem) != cudaSuccess)
+        return 0;
     return n;
 }
 
@@ -403,7 +413,9 @@ cudaError_t launch_fused_pairs(const FusedParams& prm, int es, int ctas, cudaStr
     if (pairs == 0) return cudaSuccess;
     if (!fused_pair_supported(prm.J, es) || !prm.fscr || !prm.lpair) return cudaErrorInvalidValue;
     if (ctas > pairs) ctas = (int)pairs;
-    cudaError_t e = es == 33 ? launch_pairs_es<33>(prm, ctas, s) : launch_pairs_es<37>(prm, ctas, s);
+    const bool expl = prm.oin != nullptr;
+    cudaError_t e = es == 33 ? (expl ? launch_pairs_es<33, true>(prm, ctas, s) : launch_pairs_es<33, false>(prm, ctas, s))
+                             : (expl ? launch_pairs_es<37, true>(prm, ctas, s) : launch_pairs_es<37, false>(prm, ctas, s));
     if (e != cudaSuccess) return e;
     return launch_loss_combine(prm.lpair, prm.K, prm.loss, prm.P, s);
 }

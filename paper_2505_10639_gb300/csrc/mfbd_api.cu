@@ -957,6 +957,7 @@ int mfbd_spectra_from_frames(mfbd_plan_t p, const float* frames, int height, int
     if ((st = set_device(p))) return st;
     f.frames = frames;
     f.spectra = static_cast<float2*>(spectra);
+    f.err = p->d_err;
     cudaError_t e = launch_spectra_from_frames(f, p->sms, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         p->failed = true;
@@ -1039,6 +1040,26 @@ int mfbd_ls_filter_objects(mfbd_plan_t p, const void* spectra, const void* otf, 
     if (e != cudaSuccess) {
         p->failed = true;
         return cuda_fail(e, "Lofdahl-Scharmer filter");
+    }
+    return MFBD_OK;
+}
+
+int mfbd_plan_check(mfbd_plan_t p, void* stream) {
+    int st = check_plan(p);
+    if (st) return st;
+    if ((st = set_device(p))) return st;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        p->failed = true;
+        return cuda_fail(e, "plan stream");
+    }
+    int flag = 0;
+    if ((e = cudaMemcpy(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "read the plan's error flag");
+    if (flag) {
+        cudaMemset(p->d_err, 0, sizeof(int));
+        return fail(MFBD_ERR_TIMEOUT, "a bounded device-side wait gave up; the results of the calls since the "
+                                      "last check are invalid");
     }
     return MFBD_OK;
 }

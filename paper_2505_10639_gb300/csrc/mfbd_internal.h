@@ -200,6 +200,7 @@ struct FrontParams {
     const float2* object;   // [P][K][N][N/2+1]
     float* oimg;            // [P][K][N][N] patch objects in the image domain (scratch)
     float* image;           // [K][H][Wimg]
+    int* err;               // set when a bounded wait of a kernel gives up (TMA form of the spectra)
 };
 struct FilterParams {
     int N, P, K, ld;        // ld: N / 2 + 1 (half spectra) or N
@@ -223,6 +224,9 @@ struct LsFilterParams {
 size_t ls_filter_smem(int N);
 cudaError_t launch_ls_filter(const LsFilterParams& prm, int sms, cudaStream_t s);
 size_t front_smem(int N, int es);
+// Spectra from frames; 64 px patches on 16-byte column boundaries take the
+// TMA-staged kernel (spectra_tma_eligible), the rest the plain one.
+bool spectra_tma_eligible(const FrontParams& prm);
 cudaError_t launch_spectra_from_frames(const FrontParams& prm, int sms, cudaStream_t s);
 cudaError_t launch_merge_objects(const FrontParams& prm, int sms, cudaStream_t s);
 

@@ -81,6 +81,42 @@ __device__ __forceinline__ void fft64_quarters(float2 (&a)[kN / 4], int l) {
     }
 }
 
+// --------------------------------------------------------- L2 cache hints
+
+// Access policies for the L2: evict_first for data read once (the spectra),
+// evict_last for scratch that is written and read back soon (the fused
+// kernel's field slots), so that the stream of the one does not push the
+// other out.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float2 ld_hint(const float2* a, uint64_t pol) {
+    float2 v;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+                 : "=f"(v.x), "=f"(v.y)
+                 : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float4 ld_hint(const float4* a, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_hint(float4* a, float4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(pol)
+                 : "memory");
+}
+
 // ------------------------------------------------------- frame reduction
 
 // Frame reduction of one (patch, object): per frequency u,
@@ -99,7 +135,10 @@ __device__ __forceinline__ void fft64_quarters(float2 (&a)[kN / 4], int l) {
 // memory).
 // JM > 0: J <= JM, the J spectra and OTFs of a frequency are loaded once, all
 // at once, into registers. JM == 0: any J, streamed from memory twice.
-template <int JM>
+// MODE: 0 takes the object-inferring branch when prm.oin is set, 1 compiles
+// the Wiener loss only, 2 the object-inferring loss only. STREAM: the
+// spectra are read with an L2 evict-first hint (JM > 0).
+template <int JM, int MODE = 0, bool STREAM = false>
 __device__ __forceinline__ double reduce_frequencies(const FusedParams& prm, int p, int k, float2* hbase,
                                                      int fstart, int fstep) {
     const int J = prm.J;
@@ -114,6 +153,7 @@ __device__ __forceinline__ double reduce_frequencies(const FusedParams& prm, int
 #pragma unroll
         for (int j = 0; j < JM; ++j) wv[j] = (j < J) ? w[j] : 0.f;
     }
+    const uint64_t pol = STREAM ? l2_evict_first() : 0;
     KahanSum acc;
     for (int f = fstart; f < kHalf; f += fstep) {
         const int ky = f / kNH, kx = f - ky * kNH;
@@ -121,7 +161,7 @@ __device__ __forceinline__ double reduce_frequencies(const FusedParams& prm, int
         const float2* dp = dbase + doff;
         float2* hp = hbase + f;
         const bool seed = (f != 0) && bit(supp[ky], kx);
-        if (prm.oin) {  // object-inferring loss: the object is given
+        if (MODE == 2 || (MODE == 0 && prm.oin)) {  // object-inferring loss: the object is given
             const size_t ooff = ((size_t)p * prm.K + k) * dstride;
             float2 g;
             const float t = explicit_frequency(J, dp, dstride, hp, kHalf, w, prm.gamma, seed, prm.oin[ooff + doff], g);
@@ -139,7 +179,10 @@ __device__ __forceinline__ double reduce_frequencies(const FusedParams& prm, int
             float2 d[JM], h[JM];
 #pragma unroll
             for (int j = 0; j < JM; ++j) {
-                d[j] = (j < J) ? dp[(size_t)j * dstride] : make_float2(0.f, 0.f);
+                if constexpr (STREAM)
+                    d[j] = (j < J) ? ld_hint(dp + (size_t)j * dstride, pol) : make_float2(0.f, 0.f);
+                else
+                    d[j] = (j < J) ? dp[(size_t)j * dstride] : make_float2(0.f, 0.f);
                 h[j] = (j < J) ? hp[(size_t)j * kHalf] : make_float2(0.f, 0.f);
             }
 #pragma unroll

@@ -313,6 +313,12 @@ class Plan:
             ptr = ctypes.c_void_p(keep.ctypes.data)
         _lib.check(self._lib.mfbd_plan_set_diversity(self._h, ptr, _stream(stream)), "mfbd_plan_set_diversity")
 
+    def check(self, stream=None):
+        """mfbd_plan_check: synchronise, then raise MFBDError
+        (MFBD_ERR_TIMEOUT) if a bounded device-side wait gave up since the
+        last check."""
+        _lib.check(self._lib.mfbd_plan_check(self._h, _stream(stream)), "mfbd_plan_check")
+
     def set_profiling(self, enable=True, max_launches=4096):
         """mfbd_plan_set_profiling: time every kernel with CUDA events."""
         _lib.check(self._lib.mfbd_plan_set_profiling(self._h, int(enable), int(max_launches)),

