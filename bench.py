@@ -56,12 +56,16 @@ WORKLOAD = dict(WORKLOADS["fov1024_64px"])
 SEED = WORKLOAD["seed"]  # 20250515 + workload index
 FP32_LANES_PER_SM = 128
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of each
-# kernel of the 64 px pass machine, from one ncu capture of the first 400
-# patches of the 961-patch workload (9600 units); a launch's traffic is this
-# times its units (the traffic is per unit: no cross-unit reuse)
+# kernel of the 64 px three-kernel path, from one ncu capture of the first
+# 400 patches of the 961-patch workload (9600 units), and of the fused
+# kernel; a launch's traffic is this times its units (the traffic is per
+# unit: no cross-unit reuse)
 NCU_DRAM_BYTES_PER_UNIT = {"forward_passes": (71857152 + 503112704) / 9600,
                            "adjoint_passes": (643635200 + 32342272) / 9600,
-                           "reduction": (324495360 + 115700480) / 9600}
+                           "reduction": (324495360 + 115700480) / 9600,
+                           # the fused kernel, one capture of the full 961-patch
+                           # field (23,064 units)
+                           "fused_pairs": (684598016 + 512696576) / 23064}
 # the same for the 128 px CTA-per-unit kernels with the field recomputed in
 # the adjoint, from one capture (--metrics dram__bytes_read.sum,
 # dram__bytes_write.sum) of the first 48 patches of the 3969-patch field
@@ -339,6 +343,34 @@ def _oracle_worker(args):
     queue.put((t0, t1, len(patch_ids)))
 
 
+def run_oracle_config1(min_seconds=2.0):
+    """The FP64 oracle on the single-patch workload (64 px, 1 object, 8
+    frames, 32 px pupil, Noll 2-21, D/r0 = 5, seed 20250516) on one host
+    core: loss, object and gradient repeated for at least min_seconds;
+    returns (units/s, seconds, evaluations)."""
+    from oracle import mfbd as omfbd
+    from oracle import optics
+    from paper_2505_10639_gb300 import synth
+    n, diam, J, M, seed = 64, 32.0, 8, 20, 20250516
+    setup = omfbd.Setup([optics.pupil_mask(n, diam)], [optics.zernike_basis(n, diam, range(2, M + 2))], [1.0],
+                        np.ones((1, J)), 1e-3 * n * n * 1e-6)
+    var = optics.mode_variances("zernike", M)
+    a_true = synth.kolmogorov_coeffs(seed, var, 5.0, (1, J))
+    a_eval = a_true + 0.3 * synth.kolmogorov_coeffs(seed, var, 5.0, (1, J), sub=1)
+    obj = synth.object_field(seed, (1, 1, n, n))
+    noise = synth.noise(seed, (1, 1, J, n, n), 1e-3)
+    d = omfbd.synth_spectra(setup, a_true[0], obj[0], noise[0])
+    a = a_eval[0].astype(np.float32).astype(np.float64)
+    dd = d.astype(np.complex64).astype(np.complex128)
+    count, t0 = 0, time.time()
+    while True:
+        omfbd.loss_object_grad_patch(setup, a, dd)
+        count += 1
+        t = time.time() - t0
+        if t >= min_seconds:
+            return count * J / t, t, count
+
+
 def run_oracle_sample(w, seed, n_patches, cores):
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
@@ -449,13 +481,14 @@ def run_gpu(args, rank, local_rank, world, peaks):
     w = WORKLOAD
     line, plan, bufs = time_field(args, w, SEED + rank, local_rank, world, peaks)
     coeffs, spectra, loss, grad, stream, rmax, rsum, local_ms = bufs
+    if world == 1 and not args.no_extras and w["n_pix"] == 64 and args.precision == "fp32":
+        line["bf16_phase"] = run_bf16_arm(args, w, plan, coeffs, spectra, local_rank, local_ms)
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, w)
     if not args.no_frontend:
-        line["frontend"] = run_frontend(args, plan, coeffs, spectra, w)
+        # (the front end writes its own spectra over the workload's: last)
         line["object_inferring_loss"] = run_explicit(args, plan, coeffs, spectra, w)
-    if world == 1 and not args.no_extras and w["n_pix"] == 64 and args.precision == "fp32":
-        line["bf16_phase"] = run_bf16_arm(args, w, coeffs, spectra, loss, grad, local_rank, peaks, local_ms)
+        line["frontend"] = run_frontend(args, plan, coeffs, spectra, w)
     plan.close()
     return line
 
@@ -498,13 +531,14 @@ def run_extras(args, local_rank, peaks):
     return out
 
 
-def run_bf16_arm(args, w, coeffs, spectra, loss32, grad32, local_rank, peaks, fp32_ms):
+def run_bf16_arm(args, w, plan32, coeffs, spectra, local_rank, fp32_ms):
     """The BF16-phase form of the same workload (the phase projection with
     BF16 operands on the tensor cores, the rest as FP32) on the same inputs
     in the same process: time per step as for the FP32 line, and its
     difference from the FP32 results (max relative loss difference over the
     patches, worst per-patch relative L2 difference of dL/da)."""
     import torch
+    loss32, grad32, _ = plan32.loss_grad(coeffs, spectra)  # the FP32 results on these inputs
     plan = make_plan(w, "bf16_phase", "tensor", args.recompute, args.kernels)
     loss = torch.empty_like(loss32)
     grad = torch.empty_like(grad32)
@@ -722,6 +756,8 @@ def finish_line(args, plan, info, w, world, ms, value, e2e, prof, clk, peaks):
         t = per_launch("fused")
         a = work / (t * 1e-3) / 1e12 if t > 0 else 0.0
         tr = NCU_DRAM_BYTES_PER_UNIT.get("fused_pairs") if ncu_tab else None
+        if tr:
+            ncu_basis = "ncu DRAM bytes per unit (capture of the full 961-patch launch) x units per launch"
         kernels["fused_pairs"] = {"bound": "alu", "ms": t, "achieved": a, "peak": alu_peak, "unit": "TFLOP/s",
                                   "frac": a / alu_peak, "frac_of_derived_peak": a / alu_derived,
                                   "work_per_launch": work, "traffic": tr * units_of(w) if tr else None}
@@ -1152,6 +1188,11 @@ def main():
                                               % (npat, WORKLOAD["n_patches"], len(WORKLOAD["diams"]),
                                                  WORKLOAD["n_frames"], t)}
             line["cpu_baseline"]["value"] *= unit_weight_64(WORKLOAD["n_pix"])
+            r1, t1, n1 = run_oracle_config1()
+            line["cpu_baseline"]["config1_single_thread"] = {
+                "value": r1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "%d evaluations of the single-patch workload (1 patch, 1 object, 8 frames, 64 px, "
+                          "Noll 2-21), %.1f s" % (n1, t1)}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

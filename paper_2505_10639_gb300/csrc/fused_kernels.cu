@@ -124,7 +124,10 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
     float2* const E = reinterpret_cast<float2*>(smem) + (size_t)warp * kN * ES;
     float2* const HA = reinterpret_cast<float2*>(smem);  // [J][N][N/2+1]: OTFs, then seeds
     // this frame's field slot: [x / 2][y] pairs (p[y][x], p[y][x + 1]), one 16-byte access per pair
-    float4* const pf = reinterpret_cast<float4*>(prm.fscr) + ((size_t)blockIdx.x * kFW + warp) * (kN / 2) * kN;
+    // (recomputed where used rather than held in registers across the transforms)
+    auto field_slot = [&]() {
+        return reinterpret_cast<float4*>(prm.fscr) + ((size_t)blockIdx.x * kFW + (threadIdx.x >> 5)) * (kN / 2) * kN;
+    };
     const int J = prm.J, K = prm.K;
     const long long P = prm.P, pairs = P * K;
     const bool active = warp < J;
@@ -142,7 +145,8 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
             slot[warp].gphi = prm.gphi + ob.phi_off + img;
             // this frame's spectrum into L2 for the reduction, the next
             // pair's phase for the PUPIL pass
-            prefetch_l2(prm.spectra + (((size_t)p * K + k) * J + warp) * dstride, dstride * sizeof(float2));
+            prefetch_l2_hint(prm.spectra + (((size_t)p * K + k) * J + warp) * dstride, dstride * sizeof(float2),
+                             l2_evict_first());
             const long long in = i + gridDim.x;
             if (in < pairs) {
                 const int kn = (int)(in / P);
@@ -206,28 +210,28 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
                         v[ky] = make_float2(a.x - b.y, -(a.y + b.x));
                     }
                 } else if (pass == F_C2R) {
-                    if (r == 0) {  // conj of T_lane + i T_(lane+32), Hermitian-extended rows
+                    if (r == 0) {
+                        // conj of T_lane + i T_(lane+32), Hermitian-extended
+                        // rows; the buffer holds conj(T) (the SEED pass stores
+                        // its transform unconjugated)
 #pragma unroll
                         for (int kk = 0; kk < kN; ++kk) {
-                            float2 a, b;
                             if (kk == 0) {
-                                a = make_float2(E[lane * ES].x, 0.f);
-                                b = make_float2(E[(lane + 32) * ES].x, 0.f);
+                                v[kk] = make_float2(E[lane * ES].x, -E[(lane + 32) * ES].x);
                             } else if (kk == kN / 2) {
-                                a = make_float2(E[lane * ES].y, 0.f);
-                                b = make_float2(E[(lane + 32) * ES].y, 0.f);
+                                v[kk] = make_float2(-E[lane * ES].y, E[(lane + 32) * ES].y);
                             } else if (kk < kN / 2) {
-                                a = E[lane * ES + kk];
-                                b = E[(lane + 32) * ES + kk];
+                                const float2 a = E[lane * ES + kk], b = E[(lane + 32) * ES + kk];
+                                v[kk] = make_float2(a.x + b.y, a.y - b.x);
                             } else {
-                                a = cconj(E[lane * ES + (kN - kk)]);
-                                b = cconj(E[(lane + 32) * ES + (kN - kk)]);
+                                const float2 a = E[lane * ES + (kN - kk)], b = E[(lane + 32) * ES + (kN - kk)];
+                                v[kk] = make_float2(a.x - b.y, -(a.y + b.x));
                             }
-                            v[kk] = make_float2(a.x - b.y, -(a.y + b.x));
                         }
                     } else {  // conj(g_q p) of row y
                         const int y = lane + 32 * (r - 1);
                         const uint64_t keep = l2_evict_last();  // the slot is written again by the next pair
+                        const float4* pf = field_slot();
 #pragma unroll
                         for (int i2 = 0; i2 < kN / 2; ++i2) {
                             const float2 g = E[y * ES + i2];  // g_q at x = 2 i2, 2 i2 + 1
@@ -236,11 +240,12 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
                             v[2 * i2 + 1] = make_float2(g.y * pp.z, -g.y * pp.w);
                         }
                     }
-                } else {  // F_ADJ: conj of box column c; an inactive lane transforms a column no lane writes
+                } else {  // F_ADJ: conj of box column c (the C2R pass left conj(G_P) in the
+                          // buffer); an inactive lane transforms a column no lane writes
                     const int c = lane + 32 * r;
                     const int cc = c < W ? c : (c < ES ? c : c - 32);
 #pragma unroll
-                    for (int y = 0; y < kN; ++y) v[y] = cconj(E[y * ES + cc]);
+                    for (int y = 0; y < kN; ++y) v[y] = E[y * ES + cc];
                     if (c < W) {  // the column's phases are copied into it while the transform runs
                         const float* ph = slot[warp].phi + c;
 #pragma unroll
@@ -249,11 +254,10 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
                     }
                 }
                 // --------------------------------------------------- transform
+                // adjoint passes: F^H x = conj(F conj x); the loads above
+                // conjugate, and the outer conjugation is left to the next
+                // consumer (the stores below keep the transform as it is)
                 fftreg::fft4<kN, -1>(v);
-                if (pass >= F_SEED) {
-#pragma unroll
-                    for (int i2 = 0; i2 < kN; ++i2) v[i2].y = -v[i2].y;
-                }
                 // ----------------------------------------------------- store
                 if (pass == F_PUPIL) {
                     const int c = lane + 32 * r;
@@ -265,6 +269,7 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
                     if (r < 2) {  // keep the field row; PSF row s = |p|^2 / (N^2 n_pup) as float pairs
                         const int y = lane + 32 * r;
                         const uint64_t keep = l2_evict_last();  // the field slots stay in L2 from FIELD to C2R
+                        float4* pf = field_slot();
 #pragma unroll
                         for (int i2 = 0; i2 < kN / 2; ++i2)
                             st_hint(pf + i2 * kN + y,
@@ -330,35 +335,38 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
                     }
                 } else if (pass == F_SEED) {
                     // every frame warp has read its seed: the buffers over
-                    // the seed area are free again
+                    // the seed area are free again. conj(T) (lane 0: of
+                    // T_0 + i T_N/2)
                     frames_barrier(nframe_threads);
 #pragma unroll
-                    for (int y = 0; y < kN; ++y) E[y * ES + lane] = v[y];  // lane 0 keeps (T_0, T_N/2)
+                    for (int y = 0; y < kN; ++y) E[y * ES + lane] = v[y];
                 } else if (pass == F_C2R) {
-                    if (r == 0) {  // g_q rows lane and lane+32 as float pairs
+                    if (r == 0) {  // g_q rows lane and lane+32 (the real and imaginary parts of conj v)
                         const float sc = 2.0f * ob.inv_z;
 #pragma unroll
                         for (int i2 = 0; i2 < kN / 2; ++i2) {
                             E[lane * ES + i2] = make_float2(v[2 * i2].x * sc, v[2 * i2 + 1].x * sc);
-                            E[(lane + 32) * ES + i2] = make_float2(v[2 * i2].y * sc, v[2 * i2 + 1].y * sc);
+                            E[(lane + 32) * ES + i2] = make_float2(v[2 * i2].y * -sc, v[2 * i2 + 1].y * -sc);
                         }
-                    } else {  // box columns of the row's F^H
+                    } else {  // box columns of the row's conj(F^H)
                         const int y = lane + 32 * (r - 1);
 #pragma unroll
                         for (int x = 0; x < kN; ++x)
                             if (x < R && x < W) E[y * ES + x] = v[x];
                     }
-                } else {  // F_ADJ: dL/dphi = 2 Im(conj(P) G_P) on the pupil, P = exp(i phi)
+                } else {  // F_ADJ: dL/dphi = 2 Im(conj(P) G_P) on the pupil, P = exp(i phi), G_P = conj(v)
                     const int c = lane + 32 * r;
                     if (c < W) {
                         float* gph = slot[warp].gphi + c;
                         const uint64_t cm = ob.cmask[c];
+                        const uint64_t stream = l2_evict_first();  // read once, by the modal adjoint
                         cp_async_wait();
 #pragma unroll
                         for (int yy = 0; yy < kN; ++yy) {
                             if (yy < R && yy < W) {
                                 const float2 pv = expi(E[yy * ES + c].x);
-                                gph[yy * ob.phi_ld] = bit(cm, yy) ? 2.0f * (pv.x * v[yy].y - pv.y * v[yy].x) : 0.f;
+                                st_hint(gph + yy * ob.phi_ld,
+                                        bit(cm, yy) ? 2.0f * fmaf(pv.x, -v[yy].y, -(pv.y * v[yy].x)) : 0.f, stream);
                             }
                         }
                     }

@@ -372,7 +372,7 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                             for (int yy = 0; yy < kN; ++yy) {
                                 if (yy < R && yy < W) {
                                     const float2 pv = E[yy * ES + c];
-                                    gph[yy * ld] = bit(cm, yy) ? 2.0f * (pv.x * v[yy].y - pv.y * v[yy].x) : 0.f;
+                                    gph[yy * ld] = bit(cm, yy) ? 2.0f * fmaf(pv.x, v[yy].y, -(pv.y * v[yy].x)) : 0.f;
                                 }
                             }
                         } else {  // no phasor buffer: G_P parked, phasors from the phase (compact loop)
@@ -384,7 +384,7 @@ __device__ __forceinline__ void run_passes(const volatile Unit* su, float2* __re
                             for (int yy = 0; yy < W; ++yy) {
                                 const float2 pv = expi(ph[yy * ld]);
                                 const float2 g = E[yy * ES + c];
-                                gph[yy * ld] = bit(cm, yy) ? 2.0f * (pv.x * g.y - pv.y * g.x) : 0.f;
+                                gph[yy * ld] = bit(cm, yy) ? 2.0f * fmaf(pv.x, g.y, -(pv.y * g.x)) : 0.f;
                             }
                         }
                     }

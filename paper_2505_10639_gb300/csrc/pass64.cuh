@@ -42,6 +42,18 @@ __device__ __forceinline__ void prefetch_l2(const void* ptr, size_t bytes) {
                      : "memory");
 }
 
+// The same with an L2 access policy (createpolicy) for the prefetched lines.
+__device__ __forceinline__ void prefetch_l2_hint(const void* ptr, size_t bytes, uint64_t pol) {
+    uintptr_t a = reinterpret_cast<uintptr_t>(ptr);
+    uintptr_t b = (a + bytes + 15) & ~uintptr_t(15);
+    a &= ~uintptr_t(15);
+    if (b > a)
+        asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(__cvta_generic_to_global(
+                         reinterpret_cast<const void*>(a))),
+                     "r"((unsigned)(b - a)), "l"(pol)
+                     : "memory");
+}
+
 __device__ __forceinline__ bool bit(uint64_t w, int b) { return (w >> b) & 1ull; }
 
 // ----------------------------------------------- quarter-line transforms
@@ -110,6 +122,9 @@ __device__ __forceinline__ float4 ld_hint(const float4* a, uint64_t pol) {
                  : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                  : "l"(a), "l"(pol));
     return v;
+}
+__device__ __forceinline__ void st_hint(float* a, float v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
 }
 __device__ __forceinline__ void st_hint(float4* a, float4 v, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y),
