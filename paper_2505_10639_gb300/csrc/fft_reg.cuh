@@ -93,8 +93,23 @@ constexpr int bitrev(int i) {
     return r;
 }
 
-MFBD_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-MFBD_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add and subtract. On sm_100 and later each is one paired FP32
+// instruction (FADD2: two round-to-nearest adds, the same results as two
+// scalar adds) instead of two: the butterflies issue half the instructions.
+MFBD_HD float2 cadd(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+    return __fadd2_rn(a, b);
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+MFBD_HD float2 csub(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+#else
+    return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
 MFBD_HD float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 MFBD_HD float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 MFBD_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
@@ -180,12 +195,17 @@ MFBD_HD void fft4(float2 (&a)[N]) {
             const float2 a3 = twmul<4 * L, 3 * k, DIR>(b[i0 + 3 * L]);
             const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
             const float2 t2 = cadd(a1, a3), t3 = csub(a1, a3);
-            // DIR i t3
-            const float2 it3 = DIR < 0 ? make_float2(t3.y, -t3.x) : make_float2(-t3.y, t3.x);
             b[i0] = cadd(t0, t2);
             b[i0 + 2 * L] = csub(t0, t2);
-            b[i0 + L] = cadd(t1, it3);
-            b[i0 + 3 * L] = csub(t1, it3);
+            // t1 +- DIR i t3: the rotation swaps the parts, so these stay
+            // scalar adds (a paired add would need the swapped pair first)
+            if constexpr (DIR < 0) {
+                b[i0 + L] = make_float2(t1.x + t3.y, t1.y - t3.x);
+                b[i0 + 3 * L] = make_float2(t1.x - t3.y, t1.y + t3.x);
+            } else {
+                b[i0 + L] = make_float2(t1.x - t3.y, t1.y + t3.x);
+                b[i0 + 3 * L] = make_float2(t1.x + t3.y, t1.y - t3.x);
+            }
         });
     });
     static_for<0, N>([&](auto i) { a[decltype(i)::value] = b[decltype(i)::value]; });
