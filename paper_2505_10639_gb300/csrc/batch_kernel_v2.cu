@@ -1,5 +1,7 @@
 // The batch kernel of batch_kernels.cuh compiled for 2 CTAs per SM
 // (up to 255 registers a thread).
+// scalar complex adds in this kernel (see fft_reg.cuh)
+#define MFBD_SCALAR_COMPLEX_ADD 1
 #include "batch_kernels.cuh"
 
 namespace mfbd_dev {
