@@ -10,9 +10,10 @@
 // ES = 37). Per pair:
 //   forward passes, each warp on its frame (one register FFT instance):
 //     PUPIL  W columns: P = A exp(i phi) -> column FFT
-//     FIELD  rows: p = F P (kept in the CTA's field slot of the frame, a
-//            global buffer of 12 x 32 KB per CTA that stays in L2; x pairs
-//            of a row as one 16-byte access),
+//     FIELD  rows: p = F P (kept for the adjoint: rows 0..31 in the
+//            warp's tensor-memory columns, rows 32..63 in the frame's slot
+//            of a global buffer of 12 x 16 KB per CTA that stays in L2, x
+//            pairs of a row as one 16-byte access),
 //            s = |p|^2 / (N^2 n_pup); two real PSF rows per complex line
 //     OTF    columns: H = F s (half spectrum, columns 0 and N/2 packed),
 //            written into shared memory over the exchange buffers: the
@@ -74,6 +75,25 @@ __device__ __forceinline__ void frames_barrier(int nthreads) {
     asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
+// Tensor memory as a store for half of each frame's field: warp w owns the
+// TMEM lanes of its quarter (32 (w mod 4) ..) and 128 columns (w / 4) * 128 ..
+// of them, one lane per field row. tmem_st32 / tmem_ld32 move 32 consecutive
+// 32-bit columns of the calling thread's lane.
+constexpr uint32_t kTmemCols = 512;
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]), "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]), "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15]), "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]), "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]), "=f"(v[29]), "=f"(v[30]), "=f"(v[31])
+                 : "r"(taddr)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // 4-byte asynchronous global -> shared copy.
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
@@ -119,14 +139,31 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ FrameSlot slot[kFW];
     __shared__ double swarp[kFW];
+    __shared__ uint32_t s_tmem;
     constexpr int R = ES < kN ? ES : kN;  // the box side W is at most R
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2* const E = reinterpret_cast<float2*>(smem) + (size_t)warp * kN * ES;
     float2* const HA = reinterpret_cast<float2*>(smem);  // [J][N][N/2+1]: OTFs, then seeds
-    // this frame's field slot: [x / 2][y] pairs (p[y][x], p[y][x + 1]), one 16-byte access per pair
-    // (recomputed where used rather than held in registers across the transforms)
+    // the frame's field: rows 0 .. N/2-1 in the warp's tensor-memory columns
+    // (x pairs as 32-bit columns re, im), rows N/2 .. N-1 in its global slot,
+    // [x / 2][y - N/2] pairs (p[y][x], p[y][x + 1]), one 16-byte access per
+    // pair (recomputed where used rather than held in registers)
     auto field_slot = [&]() {
-        return reinterpret_cast<float4*>(prm.fscr) + ((size_t)blockIdx.x * kFW + (threadIdx.x >> 5)) * (kN / 2) * kN;
+        return reinterpret_cast<float4*>(prm.fscr) +
+               ((size_t)blockIdx.x * kFW + (threadIdx.x >> 5)) * (kN / 2) * (kN / 2);
+    };
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (unsigned)__cvta_generic_to_shared(&s_tmem)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem_base = s_tmem;
+    auto tmem_row = [&]() {  // this lane's row of the warp's columns
+        return tmem_base + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16) + (uint32_t)((threadIdx.x >> 7) * 128);
     };
     const int J = prm.J, K = prm.K;
     const long long P = prm.P, pairs = P * K;
@@ -228,14 +265,29 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
                                 v[kk] = make_float2(a.x - b.y, -(a.y + b.x));
                             }
                         }
-                    } else {  // conj(g_q p) of row y
-                        const int y = lane + 32 * (r - 1);
+                    } else if (r == 1) {  // conj(g_q p) of row y = lane, p from tensor memory
+                        const int y = lane;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float t[32];
+                            tmem_ld32(tmem_row() + 32 * q, t);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const int i2 = 8 * q + i;
+                                const float2 g = E[y * ES + i2];  // g_q at x = 2 i2, 2 i2 + 1
+                                v[2 * i2] = make_float2(g.x * t[4 * i], -g.x * t[4 * i + 1]);
+                                v[2 * i2 + 1] = make_float2(g.y * t[4 * i + 2], -g.y * t[4 * i + 3]);
+                            }
+                        }
+                    } else {  // conj(g_q p) of row y = lane + N/2, p from the global slot
+                        const int y = lane + 32;
                         const uint64_t keep = l2_evict_last();  // the slot is written again by the next pair
                         const float4* pf = field_slot();
 #pragma unroll
                         for (int i2 = 0; i2 < kN / 2; ++i2) {
                             const float2 g = E[y * ES + i2];  // g_q at x = 2 i2, 2 i2 + 1
-                            const float4 pp = ld_hint(pf + i2 * kN + y, keep);  // p at x = 2 i2, 2 i2 + 1
+                            const float4 pp = ld_hint(pf + i2 * (kN / 2) + lane, keep);  // p at x = 2 i2, 2 i2 + 1
                             v[2 * i2] = make_float2(g.x * pp.x, -g.x * pp.y);
                             v[2 * i2 + 1] = make_float2(g.y * pp.z, -g.y * pp.w);
                         }
@@ -268,12 +320,26 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
                 } else if (pass == F_FIELD) {
                     if (r < 2) {  // keep the field row; PSF row s = |p|^2 / (N^2 n_pup) as float pairs
                         const int y = lane + 32 * r;
-                        const uint64_t keep = l2_evict_last();  // the field slots stay in L2 from FIELD to C2R
-                        float4* pf = field_slot();
+                        if (r == 0) {  // rows 0 .. N/2-1 into tensor memory
 #pragma unroll
-                        for (int i2 = 0; i2 < kN / 2; ++i2)
-                            st_hint(pf + i2 * kN + y,
-                                    make_float4(v[2 * i2].x, v[2 * i2].y, v[2 * i2 + 1].x, v[2 * i2 + 1].y), keep);
+                            for (int q = 0; q < 4; ++q) {
+                                float t[32];
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) {
+                                    t[2 * i] = v[16 * q + i].x;
+                                    t[2 * i + 1] = v[16 * q + i].y;
+                                }
+                                tmem_st32(tmem_row() + 32 * q, t);
+                            }
+                            tmem_wait_st();
+                        } else {  // rows N/2 .. N-1 into the global slot, kept in L2 until C2R
+                            const uint64_t keep = l2_evict_last();
+                            float4* pf = field_slot();
+#pragma unroll
+                            for (int i2 = 0; i2 < kN / 2; ++i2)
+                                st_hint(pf + i2 * (kN / 2) + lane,
+                                        make_float4(v[2 * i2].x, v[2 * i2].y, v[2 * i2 + 1].x, v[2 * i2 + 1].y), keep);
+                        }
                         const float iz = ob.inv_z;
 #pragma unroll
                         for (int i2 = 0; i2 < kN / 2; ++i2)
@@ -378,6 +444,11 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
             if (pass == F_OTF) __syncthreads();
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols));
 }
 
 template <int ES, bool EXPL>

@@ -65,7 +65,7 @@ struct mfbd_plan {
     bool generic = false;       // CTA-per-unit kernels (N != 64, recompute, or on request)
     bool fused = false;         // mfbd_loss_grad runs the fused per-(patch, object) kernel
     int fused_ctas = 0;         // its CTAs (one per SM)
-    float2* d_fscr = nullptr;   // its field slots [fused_ctas][kFusedFrames][N*N]
+    float2* d_fscr = nullptr;   // its field slots [fused_ctas][kFusedFrames][N*N/2] (rows N/2..N-1)
     double* d_lpair = nullptr;  // its per-(patch, object) losses [P][K]
     int es = 0, es2 = 0, sw = 0;  // their exchange-buffer strides and support-row words
     double gamma = 0;
@@ -796,7 +796,7 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
                 if (fper >= 1) {
                     p->fused = true;
                     p->fused_ctas = prop.multiProcessorCount * fper;
-                    if ((st = dev_alloc(p, &p->d_fscr, (size_t)p->fused_ctas * kFusedFrames * n * n))) throw st;
+                    if ((st = dev_alloc(p, &p->d_fscr, (size_t)p->fused_ctas * kFusedFrames * n * n / 2))) throw st;
                     if ((st = dev_alloc(p, &p->d_lpair, (size_t)std::max(1, p->P * p->K)))) throw st;
                 }
             }

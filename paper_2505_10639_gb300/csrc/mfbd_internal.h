@@ -47,7 +47,7 @@ struct FusedParams {
     double* lpart;            // rsplit > 1: per-split patch losses [P][rsplit]
     const float2* oin;        // object-inferring loss: the given objects [P][K][N][spec_ld], else null
     float2* gobj;             // with oin: dL/dconj(O) [P][K][N][spec_ld], or null
-    float2* fscr;             // fused kernel: per CTA and frame slot the field p [ctas][kFusedFrames][N x N]
+    float2* fscr;             // fused kernel: per CTA and frame slot rows N/2.. of the field p [ctas][kFusedFrames][N x N/2]
     double* lpair;            // fused kernel: per (patch, object) losses [P][K]
     ObjParams obj[kMaxObjects];
 };
