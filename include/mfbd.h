@@ -75,9 +75,9 @@ typedef enum {
 
 /* flags */
 #define MFBD_FLAG_FULL_SPECTRUM 0x1u /* spectra/object are [N][N], else [N][N/2+1] */
-#define MFBD_FLAG_SIMT_PROJECTION 0x2u /* FP32 phase projection on the SIMT kernel instead
-                                        * of the tensor cores (comparison runs; not with
-                                        * MFBD_PREC_BF16_PHASE) */
+#define MFBD_FLAG_SIMT_PROJECTION 0x2u /* FP32 phase projection and modal adjoint on the
+                                        * SIMT kernels instead of the tensor cores
+                                        * (comparison runs; not with MFBD_PREC_BF16_PHASE) */
 #define MFBD_FLAG_RECOMPUTE_BACKWARD 0x4u /* the adjoint recomputes the field F P and the
                                            * pupil phasors instead of keeping them from
                                            * the forward pass: 8 N^2 + 8 W^2 fewer bytes of
@@ -124,6 +124,12 @@ typedef struct {
                                mfbd_loss_grad runs (one per SM), or 0 when it runs the
                                three-kernel path (N != 64, J > 12, a pupil box wider
                                than 37 px, or MFBD_FLAG_SPLIT_PASSES) */
+    int tc_projection;      /* 1: the phase projection phi = c B a runs on the tensor cores */
+    int tc_adjoint;         /* 1: the modal adjoint dL/da = c B^T dL/dphi runs on the tensor
+                               cores (dL/dphi and the basis split into three BF16 planes,
+                               FP32 accumulation); 0: on the SIMT kernel
+                               (MFBD_FLAG_SIMT_PROJECTION, an odd pupil box side, or more
+                               than 256 modes) */
 } mfbd_plan_info;
 
 /* Create a plan: validates the descriptor, samples pupils, builds the modal

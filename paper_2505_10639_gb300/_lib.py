@@ -62,6 +62,8 @@ class PlanInfo(ctypes.Structure):
         ("ctas", ctypes.c_int),
         ("reduction_split", ctypes.c_int),
         ("fused_ctas", ctypes.c_int),
+        ("tc_projection", ctypes.c_int),
+        ("tc_adjoint", ctypes.c_int),
     ]
 
 

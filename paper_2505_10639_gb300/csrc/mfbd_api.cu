@@ -52,6 +52,10 @@ struct ObjectData {
     // tile layout, [n_tiles][planes][Nt * Mp]; planes == 0: SIMT kernel
     uint16_t* d_basis_tc = nullptr;
     int tc_planes = 0;
+    // tensor-core modal adjoint: the box basis as BF16 planes per 32-pixel
+    // stage, and the TMA map of this object's dL/dphi (all P*J units)
+    uint16_t* d_gbasis_tc = nullptr;
+    CUtensorMap gmap{};
     float* d_div = nullptr;       // known diversity phases [J][W*W] (phase diversity), or null
     float* d_div_buf = nullptr;   // their buffer, allocated by the first mfbd_plan_set_diversity
 };
@@ -71,6 +75,7 @@ struct mfbd_plan {
     double gamma = 0;
     int* d_err = nullptr;       // set by a tensor-core kernel whose MMA wait gave up
     uint16_t* d_acoef = nullptr;  // coefficients as BF16 planes in the MMA tile layout
+    bool tc_grad = false;         // the modal adjoint runs on the tensor cores
     int device = 0;
     ObjectData obj[kMaxObjects];
     float* d_weights = nullptr;
@@ -323,20 +328,43 @@ void prof_end(mfbd_plan_t p, int i, cudaStream_t s, int kernels) {
 
 // Phases of patches [p0, p0 + np); coeffs points at patch p0.
 int run_phase(mfbd_plan_t p, const float* coeffs, cudaStream_t s, int p0, int np) {
+    const int U = np * p->J;
+    if (p->obj[0].tc_planes > 0) {  // tensor cores: one split, one launch for all objects
+        const uint16_t* bt[kMaxObjects];
+        int npix[kMaxObjects];
+        float scale[kMaxObjects];
+        float* out[kMaxObjects];
+        int ndiv = 0;
+        for (int k = 0; k < p->K; ++k) {
+            const ObjectData& o = p->obj[k];
+            bt[k] = o.d_basis_tc;
+            npix[k] = o.W * o.W;
+            scale[k] = o.scale;
+            out[k] = p->d_phi + o.phi_off + (size_t)p0 * p->J * o.W * o.W;
+            ndiv += o.d_div ? 1 : 0;
+        }
+        const int pi = prof_begin(p, 0, s);
+        cudaError_t e = launch_split_coeffs(coeffs, U, p->M, p->obj[0].tc_planes, p->d_acoef, s);
+        if (e == cudaSuccess)
+            e = launch_phase_mma(p->d_acoef, U, p->M, p->K, bt, npix, p->obj[0].tc_planes, scale, out, p->d_err,
+                                 p->sms, s);
+        for (int k = 0; k < p->K && e == cudaSuccess; ++k)  // phi_kj = c_k B_k a_j + theta_kj
+            if (p->obj[k].d_div) e = launch_add_diversity(out[k], p->obj[k].d_div, U, p->J, npix[k], p->sms, s);
+        prof_end(p, pi, s, 2 + ndiv);
+        if (e != cudaSuccess) {
+            p->failed = true;
+            return cuda_fail(e, "phase projection");
+        }
+        return MFBD_OK;
+    }
     for (int k = 0; k < p->K; ++k) {
         const ObjectData& o = p->obj[k];
         const int pi = prof_begin(p, 0, s);
         float* out = p->d_phi + o.phi_off + (size_t)p0 * p->J * o.W * o.W;
-        cudaError_t e = cudaSuccess;
-        if (o.tc_planes > 0 && k == 0)  // the coefficients are shared by all objects: split once
-            e = launch_split_coeffs(coeffs, np * p->J, p->M, o.tc_planes, p->d_acoef, s);
-        if (e == cudaSuccess)
-            e = o.tc_planes > 0 ? launch_phase_mma(p->d_acoef, np * p->J, p->M, o.d_basis_tc, o.W * o.W, o.tc_planes,
-                                                   o.scale, out, p->d_err, p->sms, s)
-                                : launch_phase_gemm(coeffs, np * p->J, p->M, o.d_basis, o.W * o.W, o.scale, out, s);
+        cudaError_t e = launch_phase_gemm(coeffs, U, p->M, o.d_basis, o.W * o.W, o.scale, out, s);
         if (e == cudaSuccess && o.d_div)  // phi_kj = c_k B_k a_j + theta_kj
-            e = launch_add_diversity(out, o.d_div, np * p->J, p->J, o.W * o.W, p->sms, s);
-        prof_end(p, pi, s, 1 + (o.tc_planes > 0 && k == 0 ? 1 : 0) + (o.d_div ? 1 : 0));
+            e = launch_add_diversity(out, o.d_div, U, p->J, o.W * o.W, p->sms, s);
+        prof_end(p, pi, s, 1 + (o.d_div ? 1 : 0));
         if (e != cudaSuccess) {
             p->failed = true;
             return cuda_fail(e, "phase projection");
@@ -375,7 +403,25 @@ int run_grad(mfbd_plan_t p, float* grad, cudaStream_t s, int p0, int np) {
         gp.part[k] = job.part[k];
     }
     const int pi = prof_begin(p, 4, s);
-    cudaError_t e = launch_grad_gemm(job, U, p->M, s);
+    cudaError_t e;
+    if (p->tc_grad) {
+        GradMmaJob mj{};
+        mj.K = p->K;
+        mj.U = U;
+        mj.M = p->M;
+        mj.row0 = p0 * p->J;
+        mj.err = p->d_err;
+        for (int k = 0; k < p->K; ++k) {
+            mj.gmap[k] = &p->obj[k].gmap;
+            mj.bpl[k] = p->obj[k].d_gbasis_tc;
+            mj.part[k] = job.part[k];
+            mj.npix[k] = npix[k];
+            mj.chunk[k] = chunk[k];
+        }
+        e = launch_grad_mma(mj, p->sms, s);
+    } else {
+        e = launch_grad_gemm(job, U, p->M, s);
+    }
     if (e == cudaSuccess) e = launch_grad_combine(gp, U, p->M, grad, s);
     prof_end(p, pi, s, 2);
     if (e != cudaSuccess) {
@@ -760,11 +806,28 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
         if (p->obj[0].tc_planes > 0 &&
             (st = dev_alloc(p, &p->d_acoef, split_coeffs_elems(p->P * p->J, p->M, p->obj[0].tc_planes))))
             throw st;
+        // the modal adjoint on the tensor cores: every pupil box of an even
+        // side (rows of whole 16-byte groups for the TMA maps), M <= 256
+        p->tc_grad = !(p->flags & MFBD_FLAG_SIMT_PROJECTION) && grad_mma_ring(p->M) >= 2;
+        for (int k = 0; k < p->K; ++k)
+            if ((p->obj[k].W * p->obj[k].W) % 4 != 0) p->tc_grad = false;
+        if (p->tc_grad)
+            for (int k = 0; k < p->K; ++k) {
+                ObjectData& o = p->obj[k];
+                std::vector<uint16_t> hg(grad_mma_basis_elems(o.W * o.W, p->M));
+                grad_mma_basis(hb[k].data(), o.W * o.W, p->M, hg.data());
+                if ((st = dev_alloc(p, &o.d_gbasis_tc, hg.size()))) throw st;
+                if ((e = cudaMemcpyAsync(o.d_gbasis_tc, hg.data(), hg.size() * 2, cudaMemcpyHostToDevice, s)))
+                    throw cuda_fail(e, "upload tensor-core adjoint basis");
+            }
         long long part_floats = 0;
         {
             int npix[kMaxObjects], chunk[kMaxObjects], splits[kMaxObjects];
             for (int k = 0; k < p->K; ++k) npix[k] = p->obj[k].W * p->obj[k].W;
-            grad_layout(p->K, npix, p->P * p->J, prop.multiProcessorCount, chunk, splits);
+            if (p->tc_grad)  // chunks of whole 32-pixel stages, which the SIMT kernel also takes
+                grad_mma_layout(p->K, npix, p->M, p->P * p->J, prop.multiProcessorCount, chunk, splits);
+            else
+                grad_layout(p->K, npix, p->P * p->J, prop.multiProcessorCount, chunk, splits);
             for (int k = 0; k < p->K; ++k) {
                 p->obj[k].g_chunk = chunk[k];
                 p->obj[k].g_splits = splits[k];
@@ -775,6 +838,11 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
         if ((st = dev_alloc(p, &p->d_gpart, (size_t)part_floats))) throw st;
         if ((st = dev_alloc(p, &p->d_phi, (size_t)phi_floats))) throw st;
         if ((st = dev_alloc(p, &p->d_gphi, (size_t)phi_floats))) throw st;
+        for (int k = 0; k < p->K && p->tc_grad; ++k) {
+            ObjectData& o = p->obj[k];
+            if (!encode_grad_map(&o.gmap, p->d_gphi + o.phi_off, o.W * o.W, (long long)p->P * p->J))
+                p->tc_grad = false;  // the SIMT kernel takes the same chunks
+        }
         const bool keep = !(p->flags & MFBD_FLAG_RECOMPUTE_BACKWARD);
         if ((st = dev_alloc(p, &p->d_gscr, (size_t)p->P * p->K * p->J * n * (n / 2 + 1)))) throw st;
         if (keep && (st = dev_alloc(p, &p->d_pscr, (size_t)p->P * p->K * p->J * n * n))) throw st;
@@ -1081,6 +1149,8 @@ int mfbd_plan_get_info(mfbd_plan_t p, mfbd_plan_info* info) {
     info->reduction_split = p->rsplit;
     info->ctas = p->ctas;
     info->fused_ctas = p->fused ? p->fused_ctas : 0;
+    info->tc_projection = p->obj[0].tc_planes > 0 ? 1 : 0;
+    info->tc_adjoint = p->tc_grad ? 1 : 0;
     return MFBD_OK;
 }
 

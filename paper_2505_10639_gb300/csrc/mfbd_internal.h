@@ -1,6 +1,7 @@
 // Internal launch interface between the C-ABI layer and the kernels.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -98,8 +99,10 @@ cudaError_t launch_phase_gemm(const float* a, int U, int M, const float* basis, 
 size_t phase_mma_smem(int M, int planes);
 size_t split_coeffs_elems(int U, int M, int planes);
 cudaError_t launch_split_coeffs(const float* a, int U, int M, int planes, uint16_t* at, cudaStream_t s);
-cudaError_t launch_phase_mma(const uint16_t* at, int U, int M, const uint16_t* bt, int npix, int planes,
-                             float scale, float* phase, int* err, int sms, cudaStream_t s);
+// One launch for the K objects: bt[k] the basis planes of object k (npix[k]
+// pixels), phase[k] its [U][npix[k]] output, scaled by scale[k].
+cudaError_t launch_phase_mma(const uint16_t* at, int U, int M, int K, const uint16_t* const* bt, const int* npix,
+                             int planes, const float* scale, float* const* phase, int* err, int sms, cudaStream_t s);
 
 // Modal adjoint, one launch for all objects: part_k[z][u][m] = sum over
 // pixel chunk z of object k of gphi_k[u][i] basis_k[m][i]. grad_layout picks
@@ -118,6 +121,32 @@ struct GradJob {
 };
 void grad_layout(int K, const int* npix, int U, int sms, int* chunk, int* splits);
 cudaError_t launch_grad_gemm(GradJob job, int U, int M, cudaStream_t s);
+
+// The modal adjoint on the tensor cores (tc_grad.cu): dL/dphi read in FP32
+// through a TMA tensor map per object (encode_grad_map: rows P*J of npix
+// pixels; npix a multiple of 4 and the base 16-byte aligned), split into
+// three BF16 planes on the fly; the basis comes from the plan as BF16 planes
+// per 32-pixel stage (grad_mma_basis, grad_mma_basis_elems elements). chunk
+// (pixels, a multiple of 32) and splits come from grad_mma_layout; the
+// partial sums have the layout of the SIMT kernel's. grad_mma_ring: the
+// pipeline depth for M modes, 0 when the kernel does not fit.
+struct GradMmaJob {
+    int K, U, M;
+    int row0;                          // the call's first unit among the tensor maps' rows
+    const CUtensorMap* gmap[kMaxObjects];
+    const uint16_t* bpl[kMaxObjects];
+    float* part[kMaxObjects];
+    int npix[kMaxObjects];
+    int chunk[kMaxObjects];
+    int* err;                          // set to 1 when a wait gives up
+};
+int grad_mma_ring(int M);
+size_t grad_mma_smem(int M, int ring);
+size_t grad_mma_basis_elems(int npix, int M);
+void grad_mma_basis(const float* basis, int npix, int M, uint16_t* out);
+void grad_mma_layout(int K, const int* npix, int M, int U, int sms, int* chunk, int* splits);
+bool encode_grad_map(CUtensorMap* map, const float* gphi, int npix, long long rows);
+cudaError_t launch_grad_mma(const GradMmaJob& job, int sms, cudaStream_t s);
 
 // grad[u][m] = sum_k scale_k sum_z part_k[z][u][m] (fixed summation order)
 struct GradParts {

@@ -22,6 +22,7 @@
 // n + 1 is in flight. In the epilogue a lane holds one pixel, so each store
 // instruction writes 32 consecutive pixels of one unit's phase row.
 #include "mfbd_internal.h"
+#include "umma.cuh"
 
 #include <cstdint>
 
@@ -33,48 +34,10 @@ constexpr int kTcThreads = 256;           // 8 warps: two per TMEM lane quarter
 constexpr int kTile = 128;                // pixels (MMA M) and units (MMA N) per tile
 constexpr long long kWaitLimit = 1ll << 22;  // bounded mbarrier polls
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// tcgen05 shared-memory descriptor: no swizzle, K-major.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-    return d;                // base offset 0, absolute LBO mode, layout 0 = no swizzle
-}
-
-// kind::f16 instruction descriptor: BF16 A and B, both K-major, FP32 D.
-__host__ __device__ constexpr uint32_t instr_desc_bf16(int m, int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(da), "l"(db), "r"(idesc), "r"(acc));
-}
-
-// The MMAs of one tile or chunk from one thread: the plane pairs of weight
-// >= 2^-16 in decreasing weight (one pair with one plane), `ksteps` K-steps of
-// 16 each. da0 / db0 describe plane 0 of A / B; a plane is a_plane / b_plane
-// bytes further and a K-step 256 bytes (the descriptor's address field counts
-// 16-byte units, and no shared-memory address overflows it).
-__device__ __forceinline__ void issue_mmas(uint32_t tmem_d, uint64_t da0, uint64_t db0, uint32_t a_plane,
-                                           uint32_t b_plane, int ksteps, int planes, uint32_t idesc, bool accumulate) {
-    const uint32_t pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
-    const int npairs = planes == 3 ? 6 : 1;
-    uint32_t acc = accumulate ? 1u : 0u;
-    for (int pp = 0; pp < npairs; ++pp) {
-        const uint64_t da = da0 + ((pa[pp] * a_plane) >> 4), db = db0 + ((pb[pp] * b_plane) >> 4);
-        for (int s = 0; s < ksteps; ++s) {
-            mma_bf16(tmem_d, da + (uint64_t)(s * 16), db + (uint64_t)(s * 16), idesc, acc);
-            acc = 1u;
-        }
-    }
-}
+using umma::smem_addr;
+using umma::smem_desc;
+using umma::instr_desc_bf16;
+using umma::issue_mmas;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(__cvta_generic_to_global(gmem))
@@ -144,13 +107,15 @@ __global__ void __launch_bounds__(256) split_coeffs_kernel(const float* __restri
 }
 
 struct PhaseMmaParams {
-    const uint16_t* at;      // coefficient planes [n_utiles][planes][128 x Mp]
-    int U, Mp;
-    const uint16_t* bt;      // basis planes [n_itiles][planes][128 x Mp]
-    int npix, n_itiles, planes;
-    float scale;
-    float* out;              // [U][npix]
-    int* err;                // set to 1 when an MMA wait gives up
+    const uint16_t* at;                 // coefficient planes [n_utiles][planes][128 x Mp]
+    int U, Mp, planes, K;
+    int groups;                         // CTAs per pixel tile (the unit tiles are dealt among them)
+    const uint16_t* bt[kMaxObjects];    // basis planes of object k [n_itiles_k][planes][128 x Mp]
+    int npix[kMaxObjects], n_itiles[kMaxObjects];
+    int cta0[kMaxObjects + 1];          // first CTA of object k
+    float scale[kMaxObjects];
+    float* out[kMaxObjects];            // [U][npix_k]
+    int* err;                           // set to 1 when an MMA wait gives up
 };
 
 __global__ void __launch_bounds__(kTcThreads, 1) phase_mma_kernel(const PhaseMmaParams q) {
@@ -165,8 +130,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_mma_kernel(const PhaseMma
     unsigned char* sU[2] = {tc_smem + tile_bytes, tc_smem + 2 * tile_bytes};  // coefficient (units) tiles
     const uint32_t sbo = (uint32_t)Mp * 16;
 
-    const int it = blockIdx.x % q.n_itiles;
-    const int g0 = blockIdx.x / q.n_itiles, gs = gridDim.x / q.n_itiles;
+    int k = 0;
+    while (k + 1 < q.K && (int)blockIdx.x >= q.cta0[k + 1]) ++k;
+    const int local = (int)blockIdx.x - q.cta0[k];
+    const int npix = q.npix[k];
+    const float scale = q.scale[k];
+    float* const out = q.out[k];
+    const int it = local % q.n_itiles[k];
+    const int g0 = local / q.n_itiles[k], gs = q.groups;
     const int n_utiles = (q.U + kTile - 1) / kTile;
     const int i0 = it * kTile;
     const int n_tiles = g0 < n_utiles ? (n_utiles - g0 + gs - 1) / gs : 0;  // this CTA's unit tiles
@@ -178,7 +149,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_mma_kernel(const PhaseMma
     };
     auto unit_src = [&](int n) { return q.at + (size_t)(g0 + n * gs) * planes * kTile * Mp; };
 
-    copy_tile(sP, q.bt + (size_t)it * planes * kTile * Mp);
+    copy_tile(sP, q.bt[k] + (size_t)it * planes * kTile * Mp);
     if (n_tiles > 0) copy_tile(sU[0], unit_src(0));
     cp_async_commit();
     if (n_tiles > 1) copy_tile(sU[1], unit_src(1));
@@ -203,8 +174,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_mma_kernel(const PhaseMma
     auto epilogue = [&](int n, int buf) {
         const int u0 = (g0 + n * gs) * kTile;
         const int pix = lq * 32 + lane;
-        float* ocol = q.out + i0 + pix;
-        const bool pix_ok = i0 + pix < q.npix;
+        float* ocol = out + i0 + pix;
+        const bool pix_ok = i0 + pix < npix;
         for (int c0 = ch * (kTile / 2); c0 < (ch + 1) * (kTile / 2); c0 += 32) {
             uint32_t v[32];
             const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * kTile + c0);
@@ -222,7 +193,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_mma_kernel(const PhaseMma
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int u = u0 + c0 + j;
-                    if (u < q.U) ocol[(size_t)u * q.npix] = q.scale * __uint_as_float(v[j]);
+                    if (u < q.U) ocol[(size_t)u * npix] = scale * __uint_as_float(v[j]);
                 }
             }
         }
@@ -286,20 +257,26 @@ cudaError_t launch_split_coeffs(const float* a, int U, int M, int planes, uint16
     return cudaGetLastError();
 }
 
-cudaError_t launch_phase_mma(const uint16_t* at, int U, int M, const uint16_t* bt, int npix, int planes,
-                             float scale, float* phase, int* err, int sms, cudaStream_t s) {
-    if (U == 0) return cudaSuccess;
+cudaError_t launch_phase_mma(const uint16_t* at, int U, int M, int K, const uint16_t* const* bt, const int* npix,
+                             int planes, const float* scale, float* const* phase, int* err, int sms, cudaStream_t s) {
+    if (U == 0 || K == 0) return cudaSuccess;
+    if (K > kMaxObjects) return cudaErrorInvalidValue;
     PhaseMmaParams q;
     q.at = at;
     q.U = U;
     q.Mp = (M + 15) / 16 * 16;
-    q.bt = bt;
-    q.npix = npix;
-    q.n_itiles = (npix + kTile - 1) / kTile;
     q.planes = planes;
-    q.scale = scale;
-    q.out = phase;
+    q.K = K;
     q.err = err;
+    int total_itiles = 0;
+    for (int k = 0; k < K; ++k) {
+        q.bt[k] = bt[k];
+        q.npix[k] = npix[k];
+        q.n_itiles[k] = (npix[k] + kTile - 1) / kTile;
+        q.scale[k] = scale[k];
+        q.out[k] = phase[k];
+        total_itiles += q.n_itiles[k];
+    }
     // tensor memory holds 512 columns per SM and a CTA takes 256: the dynamic
     // shared memory is padded until at most two CTAs fit on an SM, so that
     // every resident CTA's allocation succeeds at once
@@ -318,11 +295,16 @@ cudaError_t launch_phase_mma(const uint16_t* at, int U, int M, const uint16_t* b
         smem += 4096;
     }
     if (per_sm < 1 || per_sm > cap) return cudaErrorInvalidConfiguration;
+    // one wave: every pixel tile of every object gets the same number of
+    // CTAs, and all CTAs are resident at once
     const int n_utiles = (U + kTile - 1) / kTile;
-    int groups = (sms * per_sm + q.n_itiles - 1) / q.n_itiles;  // CTAs per pixel tile
+    int groups = sms * per_sm / total_itiles;
     if (groups > n_utiles) groups = n_utiles;
     if (groups < 1) groups = 1;
-    phase_mma_kernel<<<groups * q.n_itiles, kTcThreads, smem, s>>>(q);
+    q.groups = groups;
+    q.cta0[0] = 0;
+    for (int k = 0; k < K; ++k) q.cta0[k + 1] = q.cta0[k] + groups * q.n_itiles[k];
+    phase_mma_kernel<<<q.cta0[K], kTcThreads, smem, s>>>(q);
     return cudaGetLastError();
 }
 

@@ -139,7 +139,8 @@ class Plan:
         k = self.n_objects
         return dict(pupil_pixels=list(inf.pupil_pixels[:k]), pupil_box=list(inf.pupil_box[:k]),
                     workspace_bytes=inf.workspace_bytes, slots_per_cta=inf.slots_per_cta, ctas=inf.ctas,
-                    reduction_split=inf.reduction_split, fused_ctas=inf.fused_ctas)
+                    reduction_split=inf.reduction_split, fused_ctas=inf.fused_ctas,
+                    tc_projection=inf.tc_projection, tc_adjoint=inf.tc_adjoint)
 
     # ------------------------------------------------------------ calls
     def forward(self, coeffs, spectra, loss=None, obj=None, want_object=True, stream=None):

@@ -331,12 +331,15 @@ def test_host_pipeline_bits_at_larger_field(c2_slice):
 
 
 def test_tensor_projection_matches_simt_projection(c2_slice):
-    """The FP32 phase projection on the tensor cores (three BF16 planes per
-    operand) and on the SIMT kernel give the same loss and gradient to FP32
-    rounding."""
+    """The FP32 phase projection and modal adjoint on the tensor cores (three
+    BF16 planes per operand) and on the SIMT kernels give the same loss and
+    gradient to FP32 rounding."""
     a32, d32, _ = _inputs(c2_slice)
-    lt, gt, _ = _run_fused(_plan_for(c2_slice), a32, d32, want_object=False)
-    ls, gs, _ = _run_fused(_plan_for(c2_slice, projection="simt"), a32, d32, want_object=False)
+    pt, ps = _plan_for(c2_slice), _plan_for(c2_slice, projection="simt")
+    assert pt.info()["tc_projection"] == 1 and pt.info()["tc_adjoint"] == 1
+    assert ps.info()["tc_projection"] == 0 and ps.info()["tc_adjoint"] == 0
+    lt, gt, _ = _run_fused(pt, a32, d32, want_object=False)
+    ls, gs, _ = _run_fused(ps, a32, d32, want_object=False)
     el = np.max(np.abs(lt - ls) / np.abs(ls))
     eg = max(np.linalg.norm(gt[p] - gs[p]) / np.linalg.norm(gs[p]) for p in range(len(ls)))
     print("tensor vs SIMT projection: loss %.3e grad %.3e" % (el, eg))
@@ -482,8 +485,8 @@ def test_lbfgs_driven_from_the_host(c2_slice):
 
 @pytest.mark.parametrize("split", [False, True])
 def test_profile_counts_the_kernels_of_a_step(c2_slice, split):
-    """The profiling pairs count every kernel a step launches: per object a
-    phase projection (plus the coefficient split once, tensor path); then
+    """The profiling pairs count every kernel a step launches: the
+    coefficient split and one tensor-core phase projection for all objects; then
     the fused kernel and its loss combine, or the forward passes, the frame
     reduction and, when it is split, the loss combine, and the adjoint
     passes; and the modal adjoint GEMM and combine."""
@@ -494,7 +497,6 @@ def test_profile_counts_the_kernels_of_a_step(c2_slice, split):
     _run_fused(plan, a32, d32, want_object=False)
     prof = plan.read_profile(reset=True)
     counts = {k: v[1] for k, v in prof.items()}
-    K = len(c2_slice["diams"])
-    want = [K + 1, 1, 2, 1, 2, 0] if split else [K + 1, 0, 0, 0, 2, 2]
+    want = [2, 1, 2, 1, 2, 0] if split else [2, 0, 0, 0, 2, 2]
     assert list(counts.values()) == want, counts
     plan.set_profiling(False)
