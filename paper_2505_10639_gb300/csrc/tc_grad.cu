@@ -108,6 +108,11 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
     return false;
 }
 
+// mbarrier init without the fence (one fence after all of them)
+__device__ __forceinline__ void bar_init(uint64_t* bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
 __device__ __forceinline__ void arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
@@ -149,16 +154,18 @@ __global__ void __launch_bounds__(kGThreads, 1) grad_mma_kernel(const __grid_con
 
     if (tid == 0) {
         for (int i = 0; i < S; ++i) {
-            tma::mbar_init(&full[i], 1);
-            tma::mbar_init(&empty[i], 1);
+            bar_init(&full[i], 1);
+            bar_init(&empty[i], 1);
         }
         for (int b = 0; b < 2; ++b) {
-            tma::mbar_init(&conv[b], kGConv * 32);
-            tma::mbar_init(&afree[b], 1);
-            tma::mbar_init(&accf[b], 1);
-            tma::mbar_init(&accfree[b], kGConv * 32);
+            bar_init(&conv[b], kGConv);
+            bar_init(&afree[b], 1);
+            bar_init(&accf[b], 1);
+            bar_init(&accfree[b], kGConv);
         }
-        tma::mbar_init(&fin, 1);
+        bar_init(&fin, 1);
+        // the initialised barriers, visible to the asynchronous proxy
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_s = 0;
     }
     if (warp == 0) {
@@ -240,7 +247,7 @@ __global__ void __launch_bounds__(kGThreads, 1) grad_mma_kernel(const __grid_con
         const int lq = warp & 3, half = warp >> 2;
         auto epilogue = [&](int c, const Item& it) -> bool {
             const int a = c & 1;
-            if (!wait_or_abort(&accf[a], (c >> 1) & 1, abort_flag, q.err)) return false;
+            if (!__all_sync(0xFFFFFFFFu, wait_or_abort(&accf[a], (c >> 1) & 1, abort_flag, q.err))) return false;
             umma::fence_after_sync();
             const int u = it.t * kGR + lq * 32 + lane;
             float* prow = q.part[it.k] + ((size_t)it.z * q.U + u) * q.M;
@@ -273,7 +280,8 @@ __global__ void __launch_bounds__(kGThreads, 1) grad_mma_kernel(const __grid_con
                 }
             }
             umma::fence_before_sync();
-            arrive(&accfree[a]);
+            __syncwarp();
+            if (lane == 0) arrive(&accfree[a]);
             return true;
         };
 
@@ -285,8 +293,10 @@ __global__ void __launch_bounds__(kGThreads, 1) grad_mma_kernel(const __grid_con
             const Item it = item_of(q, i);
             for (int s = 0; s < it.ns; ++s, ++n) {
                 const int slot = (int)(n % (uint32_t)S), b = (int)(n & 1);
-                if (!wait_or_abort(&full[slot], (n / S) & 1, abort_flag, q.err) ||
-                    (n >= 2 && !wait_or_abort(&afree[b], ((n >> 1) - 1) & 1, abort_flag, q.err))) {
+                bool w = wait_or_abort(&full[slot], (n / S) & 1, abort_flag, q.err);
+                if (w && n >= 2) w = wait_or_abort(&afree[b], ((n >> 1) - 1) & 1, abort_flag, q.err);
+                // the outcome is warp-uniform: one elected lane arrives for the warp
+                if (!__all_sync(0xFFFFFFFFu, w)) {
                     ok = false;
                     break;
                 }
@@ -314,7 +324,8 @@ __global__ void __launch_bounds__(kGThreads, 1) grad_mma_kernel(const __grid_con
                             make_uint4(pl[p][0], pl[p][1], pl[p][2], pl[p][3]);
                 }
                 tma::fence_proxy_async_smem();  // the planes -> the tensor core's reads
-                arrive(&conv[b]);
+                __syncwarp();
+                if (lane == 0) arrive(&conv[b]);
                 if (s == 0 && c >= 1 && !epilogue(c - 1, prev)) {
                     ok = false;
                     break;
