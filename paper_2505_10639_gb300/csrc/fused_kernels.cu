@@ -34,7 +34,8 @@
 // written); the named barrier of the frame warps orders the OTF and SEED
 // passes against the exchange buffers they overlap.
 // The pair's loss (the threads' Kahan sums, combined in a fixed order) goes
-// to lpair[p][k]; the objects are summed per patch by a second small kernel.
+// to lpair[p][k]; the CTA that completes a patch's last object (a per-patch
+// counter, reset after use) sums its objects' losses in object order.
 #include "mfbd_internal.h"
 #include "fft_reg.cuh"
 #include "mfbd_device.cuh"
@@ -210,6 +211,16 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
                     double tot = 0.0;
                     for (int w = 0; w < kFW; ++w) tot += swarp[w];
                     prm.lpair[p * K + k] = tot;
+                    // the CTA that finishes the patch's last object sums the
+                    // objects' losses in object order and resets the count
+                    __threadfence();
+                    if (atomicAdd(&prm.lcnt[p], 1) == K - 1) {
+                        __threadfence();
+                        double sum = 0.0;
+                        for (int kk = 0; kk < K; ++kk) sum += __ldcg(&prm.lpair[p * K + kk]);
+                        prm.loss[p] = sum;
+                        prm.lcnt[p] = 0;
+                    }
                 }
             }
             const int nr = active ? fused_rounds(pass, W) : 0;
@@ -492,13 +503,12 @@ int fused_pair_ctas_per_sm(int es) {
 cudaError_t launch_fused_pairs(const FusedParams& prm, int es, int ctas, cudaStream_t s) {
     const long long pairs = (long long)prm.P * prm.K;
     if (pairs == 0) return cudaSuccess;
-    if (!fused_pair_supported(prm.J, es) || !prm.fscr || !prm.lpair) return cudaErrorInvalidValue;
+    if (!fused_pair_supported(prm.J, es) || !prm.fscr || !prm.lpair || !prm.lcnt) return cudaErrorInvalidValue;
     if (ctas > pairs) ctas = (int)pairs;
     const bool expl = prm.oin != nullptr;
     cudaError_t e = es == 33 ? (expl ? launch_pairs_es<33, true>(prm, ctas, s) : launch_pairs_es<33, false>(prm, ctas, s))
                              : (expl ? launch_pairs_es<37, true>(prm, ctas, s) : launch_pairs_es<37, false>(prm, ctas, s));
-    if (e != cudaSuccess) return e;
-    return launch_loss_combine(prm.lpair, prm.K, prm.loss, prm.P, s);
+    return e;
 }
 
 }  // namespace mfbd_dev

@@ -71,6 +71,7 @@ struct mfbd_plan {
     int fused_ctas = 0;         // its CTAs (one per SM)
     float2* d_fscr = nullptr;   // its field slots [fused_ctas][kFusedFrames][N*N/2] (rows N/2..N-1)
     double* d_lpair = nullptr;  // its per-(patch, object) losses [P][K]
+    int* d_lcnt = nullptr;      // its per-patch counts of finished objects [P], 0 between calls
     int es = 0, es2 = 0, sw = 0;  // their exchange-buffer strides and support-row words
     double gamma = 0;
     int* d_err = nullptr;       // set by a tensor-core kernel whose MMA wait gave up
@@ -536,9 +537,10 @@ int run_pairs(mfbd_plan_t p, const void* spectra, double* loss, void* object, cu
     FusedParams f = fused_params(p, p0, np, spectra, loss, object, nullptr, nullptr, nullptr);
     f.fscr = p->d_fscr;
     f.lpair = p->d_lpair + (size_t)p0 * p->K;
+    f.lcnt = p->d_lcnt + p0;
     const int pi = prof_begin(p, 5, s);
     const cudaError_t e = launch_fused_pairs(f, p->geo.xs, p->fused_ctas, s);
-    prof_end(p, pi, s, 2);  // + the loss combine
+    prof_end(p, pi, s, 1);
     if (e != cudaSuccess) {
         p->failed = true;
         return cuda_fail(e, "fused kernel");
@@ -866,6 +868,9 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
                     p->fused_ctas = prop.multiProcessorCount * fper;
                     if ((st = dev_alloc(p, &p->d_fscr, (size_t)p->fused_ctas * kFusedFrames * n * n / 2))) throw st;
                     if ((st = dev_alloc(p, &p->d_lpair, (size_t)std::max(1, p->P * p->K)))) throw st;
+                    if ((st = dev_alloc(p, &p->d_lcnt, (size_t)std::max(1, p->P)))) throw st;
+                    if ((e = cudaMemsetAsync(p->d_lcnt, 0, (size_t)std::max(1, p->P) * sizeof(int), s)))
+                        throw cuda_fail(e, "clear loss counters");
                 }
             }
         } else {

@@ -50,6 +50,7 @@ struct FusedParams {
     float2* gobj;             // with oin: dL/dconj(O) [P][K][N][spec_ld], or null
     float2* fscr;             // fused kernel: per CTA and frame slot rows N/2.. of the field p [ctas][kFusedFrames][N x N/2]
     double* lpair;            // fused kernel: per (patch, object) losses [P][K]
+    int* lcnt;                // fused kernel: per patch, the objects done [P] (0 between calls)
     ObjParams obj[kMaxObjects];
 };
 

@@ -487,7 +487,7 @@ def test_lbfgs_driven_from_the_host(c2_slice):
 def test_profile_counts_the_kernels_of_a_step(c2_slice, split):
     """The profiling pairs count every kernel a step launches: the
     coefficient split and one tensor-core phase projection for all objects; then
-    the fused kernel and its loss combine, or the forward passes, the frame
+    the fused kernel (which also sums each patch's object losses), or the forward passes, the frame
     reduction and, when it is split, the loss combine, and the adjoint
     passes; and the modal adjoint GEMM and combine."""
     a32, d32, _ = _inputs(c2_slice)
@@ -497,6 +497,6 @@ def test_profile_counts_the_kernels_of_a_step(c2_slice, split):
     _run_fused(plan, a32, d32, want_object=False)
     prof = plan.read_profile(reset=True)
     counts = {k: v[1] for k, v in prof.items()}
-    want = [2, 1, 2, 1, 2, 0] if split else [2, 0, 0, 0, 2, 2]
+    want = [2, 1, 2, 1, 2, 0] if split else [2, 0, 0, 0, 2, 1]
     assert list(counts.values()) == want, counts
     plan.set_profiling(False)
