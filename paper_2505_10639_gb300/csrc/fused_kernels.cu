@@ -173,28 +173,28 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
     const bool active = warp < J;
     const int nframe_threads = 32 * (J < kFW ? J : kFW);
     const size_t dstride = (size_t)kN * prm.spec_ld;
-    for (long long i = blockIdx.x; i < pairs; i += gridDim.x) {
-        // pairs object-major: consecutive CTAs mix objects of different pupils
-        const int k = (int)(i / P);
-        const long long p = i - (long long)k * P;
+    // Pairs in object order prm.korder (widest pupil box first, the costliest
+    // pairs first), patch by patch. A CTA starts on pair blockIdx.x and takes
+    // each next pair from a ticket counter when it starts the current one
+    // (longest-first greedy dealing); the ticket goes through shared memory,
+    // two slots used in turn, and is read after the CTA barrier that follows
+    // the OTF pass.
+    __shared__ long long s_next[2];
+    int par = 0;
+    for (long long i = blockIdx.x; i < pairs; par ^= 1) {
+        if (threadIdx.x == 0) s_next[par] = (long long)gridDim.x + atomicAdd(prm.fticket, 1);
+        const int k = prm.korder[(int)(i / P)];
+        const long long p = i % P;
         const ObjParams& ob = prm.obj[k];
         const int W = ob.W;
+        long long next = pairs;
         if (lane == 0 && active) {
             const long long img = (p * J + warp) * ob.phi_unit + ob.phi_org;
             slot[warp].phi = prm.phi + ob.phi_off + img;
             slot[warp].gphi = prm.gphi + ob.phi_off + img;
-            // this frame's spectrum into L2 for the reduction, the next
-            // pair's phase for the PUPIL pass
+            // this frame's spectrum into L2 for the reduction
             prefetch_l2_hint(prm.spectra + (((size_t)p * K + k) * J + warp) * dstride, dstride * sizeof(float2),
                              l2_evict_first());
-            const long long in = i + gridDim.x;
-            if (in < pairs) {
-                const int kn = (int)(in / P);
-                const long long pn = in - (long long)kn * P;
-                const ObjParams& on = prm.obj[kn];
-                prefetch_l2(prm.phi + on.phi_off + (pn * J + warp) * on.phi_unit + on.phi_org,
-                            ((size_t)(on.W - 1) * on.phi_ld + on.W) * sizeof(float));
-            }
         }
         __syncwarp();
 #pragma unroll 1
@@ -454,7 +454,29 @@ __global__ void __launch_bounds__(kFT, 1) fused_pair_kernel(const FusedParams pr
             // the reduction needs every frame's OTF; the other passes work on
             // the warp's own buffer
             __syncwarp();
-            if (pass == F_OTF) __syncthreads();
+            if (pass == F_OTF) {
+                __syncthreads();
+                // the next pair (its ticket is visible after the barrier), and
+                // its phase into L2 for its PUPIL pass
+                next = s_next[par];
+                if (lane == 0 && active && next < pairs) {
+                    const int kn = prm.korder[(int)(next / P)];
+                    const long long pn = next % P;
+                    const ObjParams& on = prm.obj[kn];
+                    prefetch_l2(prm.phi + on.phi_off + (pn * J + warp) * on.phi_unit + on.phi_org,
+                                ((size_t)(on.W - 1) * on.phi_ld + on.W) * sizeof(float));
+                }
+            }
+        }
+        i = next;
+    }
+    // the last CTA out resets the counters for the next launch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(prm.fticket + 1, 1) == (int)gridDim.x - 1) {
+            prm.fticket[0] = 0;
+            prm.fticket[1] = 0;
+            __threadfence();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -503,7 +525,8 @@ int fused_pair_ctas_per_sm(int es) {
 cudaError_t launch_fused_pairs(const FusedParams& prm, int es, int ctas, cudaStream_t s) {
     const long long pairs = (long long)prm.P * prm.K;
     if (pairs == 0) return cudaSuccess;
-    if (!fused_pair_supported(prm.J, es) || !prm.fscr || !prm.lpair || !prm.lcnt) return cudaErrorInvalidValue;
+    if (!fused_pair_supported(prm.J, es) || !prm.fscr || !prm.lpair || !prm.lcnt || !prm.fticket)
+        return cudaErrorInvalidValue;
     if (ctas > pairs) ctas = (int)pairs;
     const bool expl = prm.oin != nullptr;
     cudaError_t e = es == 33 ? (expl ? launch_pairs_es<33, true>(prm, ctas, s) : launch_pairs_es<33, false>(prm, ctas, s))

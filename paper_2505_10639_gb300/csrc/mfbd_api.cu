@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -72,6 +73,7 @@ struct mfbd_plan {
     float2* d_fscr = nullptr;   // its field slots [fused_ctas][kFusedFrames][N*N/2] (rows N/2..N-1)
     double* d_lpair = nullptr;  // its per-(patch, object) losses [P][K]
     int* d_lcnt = nullptr;      // its per-patch counts of finished objects [P], 0 between calls
+    int* d_fticket = nullptr;   // its pair ticket and count of finished CTAs, 0 between calls
     int es = 0, es2 = 0, sw = 0;  // their exchange-buffer strides and support-row words
     double gamma = 0;
     int* d_err = nullptr;       // set by a tensor-core kernel whose MMA wait gave up
@@ -538,6 +540,10 @@ int run_pairs(mfbd_plan_t p, const void* spectra, double* loss, void* object, cu
     f.fscr = p->d_fscr;
     f.lpair = p->d_lpair + (size_t)p0 * p->K;
     f.lcnt = p->d_lcnt + p0;
+    f.fticket = p->d_fticket;
+    // pairs of the widest pupil boxes (the costliest) are dealt first
+    for (int k = 0; k < p->K; ++k) f.korder[k] = k;
+    std::stable_sort(f.korder, f.korder + p->K, [&](int a, int b) { return p->obj[a].W > p->obj[b].W; });
     const int pi = prof_begin(p, 5, s);
     const cudaError_t e = launch_fused_pairs(f, p->geo.xs, p->fused_ctas, s);
     prof_end(p, pi, s, 1);
@@ -869,8 +875,10 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
                     if ((st = dev_alloc(p, &p->d_fscr, (size_t)p->fused_ctas * kFusedFrames * n * n / 2))) throw st;
                     if ((st = dev_alloc(p, &p->d_lpair, (size_t)std::max(1, p->P * p->K)))) throw st;
                     if ((st = dev_alloc(p, &p->d_lcnt, (size_t)std::max(1, p->P)))) throw st;
-                    if ((e = cudaMemsetAsync(p->d_lcnt, 0, (size_t)std::max(1, p->P) * sizeof(int), s)))
-                        throw cuda_fail(e, "clear loss counters");
+                    if ((st = dev_alloc(p, &p->d_fticket, 2))) throw st;
+                    if ((e = cudaMemsetAsync(p->d_lcnt, 0, (size_t)std::max(1, p->P) * sizeof(int), s)) ||
+                        (e = cudaMemsetAsync(p->d_fticket, 0, 2 * sizeof(int), s)))
+                        throw cuda_fail(e, "clear fused-kernel counters");
                 }
             }
         } else {

@@ -51,6 +51,8 @@ struct FusedParams {
     float2* fscr;             // fused kernel: per CTA and frame slot rows N/2.. of the field p [ctas][kFusedFrames][N x N/2]
     double* lpair;            // fused kernel: per (patch, object) losses [P][K]
     int* lcnt;                // fused kernel: per patch, the objects done [P] (0 between calls)
+    int* fticket;             // fused kernel: [0] next-pair ticket, [1] CTAs done (0 between calls)
+    int korder[kMaxObjects];  // fused kernel: objects in the order their pairs are dealt
     ObjParams obj[kMaxObjects];
 };
 
