@@ -17,9 +17,10 @@
 // memory already in that layout (the basis from the plan, the coefficients
 // from a split kernel), so staging is a plain asynchronous copy. A CTA keeps
 // one pixel tile of the basis and loops over unit tiles with two coefficient
-// buffers and two TMEM accumulators: the MMAs of tile n run while the
-// epilogue of tile n - 1 drains the other accumulator and the copy of tile
-// n + 1 is in flight. In the epilogue a lane holds one pixel, so each store
+// buffers and two TMEM accumulators: one thread of a ninth warp issues the
+// MMAs of tile n (the issue itself takes about as long as the MMAs) while the
+// eight epilogue warps drain tile n - 1 from the other accumulator and the
+// copy of tile n + 1 is in flight. In the epilogue a lane holds one pixel, so each store
 // instruction writes 32 consecutive pixels of one unit's phase row.
 #include "mfbd_internal.h"
 #include "umma.cuh"
@@ -30,7 +31,8 @@ namespace mfbd_dev {
 
 namespace {
 
-constexpr int kTcThreads = 256;           // 8 warps: two per TMEM lane quarter
+constexpr int kEpiWarps = 8;              // epilogue warps: two per TMEM lane quarter
+constexpr int kTcThreads = 32 * (kEpiWarps + 1);  // + a warp that issues the MMAs
 constexpr int kTile = 128;                // pixels (MMA M) and units (MMA N) per tile
 constexpr long long kWaitLimit = 1ll << 22;  // bounded mbarrier polls
 
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_mma_kernel(const PhaseMma
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // copies -> tensor core reads
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
+        if (warp == kEpiWarps && lane == 0) {
             // A: basis (pixel rows), B: coefficients (unit rows); a fresh accumulator per tile
             issue_mmas(tmem + (uint32_t)(buf * kTile), smem_desc(smem_addr(sP), 128, sbo),
                        smem_desc(smem_addr(sU[buf]), 128, sbo), plane_bytes, plane_bytes, Mp / 16, planes, idesc,
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_mma_kernel(const PhaseMma
                              smem_addr(&mbar[buf]))
                          : "memory");
         }
-        if (n >= 1) epilogue(n - 1, buf ^ 1);  // overlaps the MMAs of tile n
+        if (n >= 1 && warp < kEpiWarps) epilogue(n - 1, buf ^ 1);  // overlaps the MMAs of tile n
         const bool done = mbar_wait(&mbar[buf], (uint32_t)((n >> 1) & 1));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (__syncthreads_or(!done)) {  // an MMA never completed: report, stop
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_mma_kernel(const PhaseMma
         if (n + 2 < n_tiles) copy_tile(sU[buf], unit_src(n + 2));
         cp_async_commit();
     }
-    if (ok && n_tiles > 0) epilogue(n_tiles - 1, (n_tiles - 1) & 1);
+    if (ok && n_tiles > 0 && warp < kEpiWarps) epilogue(n_tiles - 1, (n_tiles - 1) & 1);
     cp_async_wait_all();
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
