@@ -182,7 +182,7 @@ int mfbd_loss_grad(mfbd_plan_t plan, const float* coeffs, const void* spectra,
 /* mfbd_loss_grad (loss of Sec. 2.2.1, Eq. 12, object of Eq. 11 and dL/da)
  * from HOST buffers, with the copies overlapped with the
  * kernels: the patches go through in n_chunks chunks (n_chunks <= 0: about
- * 320 patches per chunk, 1 to 8 chunks); the
+ * 120 patches per chunk, 1 to 16 chunks); the
  * spectra of chunk c + 1 are copied to the device while chunk c is computed
  * (a chunk's phases and forward passes run while its own spectra are still
  * in flight: only the frame reduction reads them), and the loss, grad (and
