@@ -63,9 +63,10 @@ FP32_LANES_PER_SM = 128
 NCU_DRAM_BYTES_PER_UNIT = {"forward_passes": (71857152 + 503112704) / 9600,
                            "adjoint_passes": (643635200 + 32342272) / 9600,
                            "reduction": (324495360 + 115700480) / 9600,
-                           # the fused kernel, one capture of the full 961-patch
+                           # the fused kernel (pairs dealt by ticket, patch losses
+                           # summed in the kernel), one capture of the full 961-patch
                            # field (23,064 units)
-                           "fused_pairs": (500505856 + 120883200) / 23064}
+                           "fused_pairs": (499180288 + 113483776) / 23064}
 # the same for the 128 px CTA-per-unit kernels with the field recomputed in
 # the adjoint, from one capture (--metrics dram__bytes_read.sum,
 # dram__bytes_write.sum) of the first 48 patches of the 3969-patch field
