@@ -51,7 +51,7 @@ extern "C" {
 typedef enum {
     MFBD_OK = 0,
     MFBD_ERR_INVALID_ARG = 1, /* bad descriptor, NULL pointer, size mismatch */
-    MFBD_ERR_UNSUPPORTED = 2, /* valid request this build cannot run (N, no GPU) */
+    MFBD_ERR_UNSUPPORTED = 2, /* valid request the library cannot run (N, no GPU) */
     MFBD_ERR_OOM = 3,         /* device or host allocation failed in create */
     MFBD_ERR_CUDA = 4,        /* a CUDA call or kernel launch failed */
     MFBD_ERR_STATE = 5,       /* wrong call order or a failed plan */

@@ -628,7 +628,7 @@ const char* mfbd_status_string(int status) {
     switch (status) {
         case MFBD_OK: return "MFBD_OK";
         case MFBD_ERR_INVALID_ARG: return "MFBD_ERR_INVALID_ARG: invalid argument";
-        case MFBD_ERR_UNSUPPORTED: return "MFBD_ERR_UNSUPPORTED: not supported by this build or device";
+        case MFBD_ERR_UNSUPPORTED: return "MFBD_ERR_UNSUPPORTED: not supported by the library or the device";
         case MFBD_ERR_OOM: return "MFBD_ERR_OOM: allocation failed";
         case MFBD_ERR_CUDA: return "MFBD_ERR_CUDA: CUDA error";
         case MFBD_ERR_STATE: return "MFBD_ERR_STATE: wrong call order or failed plan";
@@ -685,7 +685,7 @@ int mfbd_plan_create(mfbd_plan_t* out, const mfbd_plan_desc* d, void* stream) {
     cudaDeviceProp prop;
     if ((e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
     if (prop.major * 10 + prop.minor != 103)
-        return fail(MFBD_ERR_UNSUPPORTED, "this build targets sm_103a (GB300)");
+        return fail(MFBD_ERR_UNSUPPORTED, "the library targets sm_103a (GB300)");
 
     mfbd_plan* p = new (std::nothrow) mfbd_plan();
     if (!p) return fail(MFBD_ERR_OOM, "host allocation failed");
