@@ -23,9 +23,11 @@
 // stride and frame width multiples of 4) take the TMA form: the patch comes
 // into shared memory as two 64 x 32 float boxes of a 2-D tensor map over the
 // frames (128-byte swizzle, so that a lane reading its row with 16-byte loads
-// meets no bank conflict), the next unit's patch is requested as soon as the
-// lanes hold the current one in registers, and its arrival is awaited on an
-// mbarrier with a bounded wait.
+// meets no bank conflict); the half spectra between the row and column
+// passes go to the same bytes, and the next unit's patch is requested into
+// them as soon as the lanes hold their columns in registers. 18 KB of shared
+// memory and at most 168 registers per warp give twelve warps per SM; its
+// arrival is awaited on an mbarrier with a bounded wait.
 //
 // The window (a raised-cosine transition of `border` px at each edge,
 // evaluated at pixel centres) is computed per CTA in shared memory with
@@ -167,9 +169,14 @@ __global__ void __launch_bounds__(FrontCta<N>::THREADS) spectra_kernel(const Fro
 constexpr int kTmaBoxCols = 32;                            // 128 bytes of float: the swizzle span
 constexpr uint32_t kTmaTileBytes = 64 * 64 * sizeof(float);  // one 64 x 64 patch, two boxes
 
-// Shared memory of the TMA form: the swizzled patch (1024-byte aligned), the
-// mbarrier, the window and the exchange buffer.
-size_t tma_front_smem(int es) { return 1024 + kTmaTileBytes + 16 + 64 * 4 + (size_t)64 * es * sizeof(float2); }
+// Shared memory of the TMA form: one area (1024-byte aligned) that holds the
+// swizzled patch and then, once the lanes hold their rows, the exchange
+// buffer of the half spectra; the mbarrier; the window.
+__host__ __device__ inline size_t tma_front_area(int es) {
+    const size_t ex = ((size_t)64 * es * sizeof(float2) + 15) & ~(size_t)15;
+    return ex > kTmaTileBytes ? ex : kTmaTileBytes;
+}
+size_t tma_front_smem(int es) { return 1024 + tma_front_area(es) + 16 + 64 * 4; }
 
 // Row y of the swizzled patch as float4 chunks: chunk c (floats 4c..4c+3 of
 // the row) of the box `half` (columns 32 half .. 32 half + 31).
@@ -179,15 +186,16 @@ __device__ __forceinline__ float4 tile_chunk(const float* tile, int half, int y,
     return *reinterpret_cast<const float4*>(b);
 }
 
-__global__ void __launch_bounds__(32) spectra_tma_kernel(const FrontParams prm, const __grid_constant__ CUtensorMap map) {
+__global__ void __launch_bounds__(32, 12) spectra_tma_kernel(const FrontParams prm, const __grid_constant__ CUtensorMap map) {
     constexpr int N = 64, NH = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char fsm[];
     unsigned char* base = fsm + ((1024 - (tma::smem_u32(fsm) & 1023)) & 1023);
-    float* tile = reinterpret_cast<float*>(base);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(base + kTmaTileBytes);
-    float* win = reinterpret_cast<float*>(base + kTmaTileBytes + 16);
-    float2* E = reinterpret_cast<float2*>(base + kTmaTileBytes + 16 + N * 4);
     const int es = prm.es, lane = threadIdx.x;
+    const size_t area = tma_front_area(es);
+    float* tile = reinterpret_cast<float*>(base);
+    float2* E = reinterpret_cast<float2*>(base);  // the same bytes as the tile
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + area);
+    float* win = reinterpret_cast<float*>(base + area + 16);
     const long long units = (long long)prm.P * prm.K * prm.J;
     window_to_smem(win, N, prm.border);
     // frame row and column of unit u's patch in the tensor map
@@ -231,12 +239,7 @@ __global__ void __launch_bounds__(32) spectra_tma_kernel(const FrontParams prm, 
                 part[c & 3] += (a.x + a.y) + (a.z + a.w) + ((b.x + b.y) + (b.z + b.w));
             }
         }
-        __syncwarp();
-        // every lane holds its rows: the next unit's patch may land in the tile
-        if (lane == 0 && u + gridDim.x < units) {
-            tma::fence_proxy_async_smem();
-            request(u + gridDim.x);
-        }
+        __syncwarp();  // every lane holds its rows: the half spectra may overwrite the tile
         double acc = ((double)part[0] + (double)part[1]) + ((double)part[2] + (double)part[3]);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
@@ -265,6 +268,13 @@ __global__ void __launch_bounds__(32) spectra_tma_kernel(const FrontParams prm, 
 #pragma unroll
             for (int ky = 0; ky < N; ++ky)
                 v[ky] = kx == 0 ? make_float2(E[ky * es].x, E[ky * es + N / 2].x) : E[ky * es + kx];
+            __syncwarp();
+            // every lane holds its column: the next unit's patch may land in
+            // the area, under this unit's column transforms and stores
+            if (lane == 0 && u + gridDim.x < units) {
+                tma::fence_proxy_async_smem();
+                request(u + gridDim.x);
+            }
             line_fft<N, -1>(v, 0);
             fftreg::static_for<0, N>([&](auto kk) {
                 constexpr int ky = decltype(kk)::value;
