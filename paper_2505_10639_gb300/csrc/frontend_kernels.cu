@@ -36,6 +36,8 @@
 #include "tma.cuh"
 #include "unit_passes.cuh"
 
+#include <cmath>
+
 namespace mfbd_dev {
 
 namespace {
@@ -171,12 +173,12 @@ constexpr uint32_t kTmaTileBytes = 64 * 64 * sizeof(float);  // one 64 x 64 patc
 
 // Shared memory of the TMA form: one area (1024-byte aligned) that holds the
 // swizzled patch and then, once the lanes hold their rows, the exchange
-// buffer of the half spectra; the mbarrier; the window.
+// buffer of the half spectra; the mbarrier.
 __host__ __device__ inline size_t tma_front_area(int es) {
     const size_t ex = ((size_t)64 * es * sizeof(float2) + 15) & ~(size_t)15;
     return ex > kTmaTileBytes ? ex : kTmaTileBytes;
 }
-size_t tma_front_smem(int es) { return 1024 + tma_front_area(es) + 16 + 64 * 4; }
+size_t tma_front_smem(int es) { return 1024 + tma_front_area(es) + 16; }
 
 // Row y of the swizzled patch as float4 chunks: chunk c (floats 4c..4c+3 of
 // the row) of the box `half` (columns 32 half .. 32 half + 31).
@@ -186,7 +188,17 @@ __device__ __forceinline__ float4 tile_chunk(const float* tile, int half, int y,
     return *reinterpret_cast<const float4*>(b);
 }
 
-__global__ void __launch_bounds__(32, 12) spectra_tma_kernel(const FrontParams prm, const __grid_constant__ CUtensorMap map) {
+// The window of the TMA form, from the host: w[x] for the 64 columns (the
+// same factors serve the rows).
+struct Window64 {
+    float w[64];
+};
+
+// Apodisation (p - m) w_y w_x + m as a transform of (p - m) w_x along x,
+// the factor w_y applied to each row's half spectrum, and the transform of
+// the constant m (m N^2 at frequency 0) added to the DC term.
+__global__ void __launch_bounds__(32, 12) spectra_tma_kernel(const FrontParams prm, const __grid_constant__ CUtensorMap map,
+                                                             const Window64 win) {
     constexpr int N = 64, NH = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char fsm[];
     unsigned char* base = fsm + ((1024 - (tma::smem_u32(fsm) & 1023)) & 1023);
@@ -195,9 +207,7 @@ __global__ void __launch_bounds__(32, 12) spectra_tma_kernel(const FrontParams p
     float* tile = reinterpret_cast<float*>(base);
     float2* E = reinterpret_cast<float2*>(base);  // the same bytes as the tile
     uint64_t* bar = reinterpret_cast<uint64_t*>(base + area);
-    float* win = reinterpret_cast<float*>(base + area + 16);
     const long long units = (long long)prm.P * prm.K * prm.J;
-    window_to_smem(win, N, prm.border);
     // frame row and column of unit u's patch in the tensor map
     auto request = [&](long long u) {
         const int j = (int)(u % prm.J);
@@ -215,6 +225,8 @@ __global__ void __launch_bounds__(32, 12) spectra_tma_kernel(const FrontParams p
         if ((long long)blockIdx.x < units) request(blockIdx.x);
     }
     __syncwarp();
+    // half the window factors of this lane's rows (the row split's 1/2)
+    const float ha = 0.5f * win.w[lane], hb = 0.5f * win.w[lane + N / 2];
     uint32_t parity = 0;
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
         if (!tma::mbar_wait(bar, parity)) {  // the copy never arrived: flag it and stop
@@ -244,50 +256,67 @@ __global__ void __launch_bounds__(32, 12) spectra_tma_kernel(const FrontParams p
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
         const float m = (float)(acc / (N * N));
-        const float wa = win[lane], wb = win[lane + N / 2];
+        const float2 nm = make_float2(-m, -m);
 #pragma unroll
-        for (int x = 0; x < N; ++x) {
-            const float wx = win[x];
-            v[x] = make_float2((v[x].x - m) * wa * wx + m, (v[x].y - m) * wb * wx + m);
-        }
-        // rows: split the line's transform into the two half spectra
-        line_fft<N, -1>(v, 0);
-        fftreg::static_for<0, N / 2 + 1>([&](auto kk) {
-            constexpr int kx = decltype(kk)::value;
-            const float2 pc = conj_partner<N, kx>(v);
-            const float2 ra = cscale(cadd(v[kx], pc), 0.5f);
-            const float2 d = cscale(csub(v[kx], pc), 0.5f);
-            E[lane * es + kx] = ra;
-            E[(lane + N / 2) * es + kx] = make_float2(d.y, -d.x);
-        });
-        __syncwarp();
-        // columns kx = 1 .. N/2 - 1; lane 0 packs the real columns 0 and N/2
+        for (int x = 0; x < N; ++x) v[x] = __fmul2_rn(__fadd2_rn(v[x], nm), make_float2(win.w[x], win.w[x]));
         float2* D = prm.spectra + (size_t)u * N * NH;
-        {
-            const int kx = lane;
-#pragma unroll
-            for (int ky = 0; ky < N; ++ky)
-                v[ky] = kx == 0 ? make_float2(E[ky * es].x, E[ky * es + N / 2].x) : E[ky * es + kx];
-            __syncwarp();
-            // every lane holds its column: the next unit's patch may land in
-            // the area, under this unit's column transforms and stores
-            if (lane == 0 && u + gridDim.x < units) {
-                tma::fence_proxy_async_smem();
-                request(u + gridDim.x);
-            }
+        const int kx = lane;
+        // pass 0 transforms the row pairs, pass 1 the half-spectrum columns:
+        // one copy of the transform's code serves both
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
             line_fft<N, -1>(v, 0);
-            fftreg::static_for<0, N>([&](auto kk) {
-                constexpr int ky = decltype(kk)::value;
-                const float2 pc = conj_partner<N, ky>(v);
-                if (kx > 0) {
-                    D[ky * NH + kx] = v[ky];
-                } else {
-                    const float2 d0 = cscale(cadd(v[ky], pc), 0.5f);
-                    const float2 d = cscale(csub(v[ky], pc), 0.5f);
-                    D[ky * NH] = d0;
-                    D[ky * NH + N / 2] = make_float2(d.y, -d.x);
+            if (pass == 0) {
+                // rows: split the line's transform into the two rows' half
+                // spectra, each times its w_y; columns 0 and N/2 (real) are
+                // stored packed as one complex column in column 0
+                E[lane * es] = make_float2(v[0].x * (2.f * ha), v[N / 2].x * (2.f * ha));
+                E[(lane + N / 2) * es] = make_float2(v[0].y * (2.f * hb), v[N / 2].y * (2.f * hb));
+                fftreg::static_for<1, N / 2>([&](auto kk) {
+                    constexpr int k = decltype(kk)::value;
+                    const float2 pc = conj_partner<N, k>(v);
+                    const float2 ra = cscale(cadd(v[k], pc), ha);
+                    const float2 d = cscale(csub(v[k], pc), hb);
+                    E[lane * es + k] = ra;
+                    E[(lane + N / 2) * es + k] = make_float2(d.y, -d.x);
+                });
+                __syncwarp();
+                // columns kx = 1 .. N/2 - 1, and in lane 0 the packed real columns
+#pragma unroll
+                for (int ky = 0; ky < N; ++ky) v[ky] = E[ky * es + kx];
+                __syncwarp();
+                // every lane holds its column: the next unit's patch may land
+                // in the area, under this unit's column transforms and stores
+                if (lane == 0 && u + gridDim.x < units) {
+                    tma::fence_proxy_async_smem();
+                    request(u + gridDim.x);
                 }
-            });
+            } else {
+                // lane 0 stores the transform of the packed columns in column 0
+#pragma unroll
+                for (int ky = 0; ky < N; ++ky) D[ky * NH + kx] = v[ky];
+            }
+        }
+        __syncwarp();
+        // split the packed columns' transform Z into kx = 0 and N/2:
+        // X0 = (Z[ky] + conj Z[-ky]) / 2, X(N/2) = (Z[ky] - conj Z[-ky]) / (2i);
+        // lane l takes ky = l and l + N/2
+        float2 z[2], zp[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int ky = lane + h * (N / 2);
+            z[h] = D[ky * NH];
+            zp[h] = cconj(D[((N - ky) & (N - 1)) * NH]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int ky = lane + h * (N / 2);
+            float2 d0 = cscale(cadd(z[h], zp[h]), 0.5f);
+            const float2 d = cscale(csub(z[h], zp[h]), 0.5f);
+            if (ky == 0) d0.x += m * (float)(N * N);  // the constant's transform
+            D[ky * NH] = d0;
+            D[ky * NH + N / 2] = make_float2(d.y, -d.x);
         }
         __syncwarp();
     }
@@ -494,7 +523,14 @@ cudaError_t launch_spectra_from_frames(const FrontParams& prm, int sms, cudaStre
             if (per_sm < 1) return cudaErrorInvalidConfiguration;
             long long ctas = (long long)sms * per_sm;
             if (ctas > units) ctas = units;
-            spectra_tma_kernel<<<(int)ctas, 32, smem, s>>>(prm, map);
+            Window64 win;  // the window of window_to_smem, evaluated in double
+            for (int x = 0; x < 64; ++x) {
+                const int e = x < 63 - x ? x : 63 - x;
+                win.w[x] = e < prm.border ? (float)(0.5 * (1.0 - std::cos(3.14159265358979323846 * (e + 0.5) /
+                                                                          prm.border)))
+                                          : 1.0f;
+            }
+            spectra_tma_kernel<<<(int)ctas, 32, smem, s>>>(prm, map, win);
             return cudaGetLastError();
         }
     }
