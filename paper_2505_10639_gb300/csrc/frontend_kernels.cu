@@ -176,7 +176,8 @@ constexpr uint32_t kTmaTileBytes = 64 * 64 * sizeof(float);  // one 64 x 64 patc
 // buffer of the half spectra; the mbarrier.
 __host__ __device__ inline size_t tma_front_area(int es) {
     const size_t ex = ((size_t)64 * es * sizeof(float2) + 15) & ~(size_t)15;
-    return ex > kTmaTileBytes ? ex : kTmaTileBytes;
+    const size_t z = kTmaTileBytes + 64 * sizeof(float2);  // the tile and, past it, one packed column
+    return ex > z ? ex : z;
 }
 size_t tma_front_smem(int es) { return 1024 + tma_front_area(es) + 16; }
 
@@ -206,6 +207,8 @@ __global__ void __launch_bounds__(32, 12) spectra_tma_kernel(const FrontParams p
     const size_t area = tma_front_area(es);
     float* tile = reinterpret_cast<float*>(base);
     float2* E = reinterpret_cast<float2*>(base);  // the same bytes as the tile
+    // lane 0's packed column, past the bytes the next patch's TMA load fills
+    float2* Z = reinterpret_cast<float2*>(base + kTmaTileBytes);
     uint64_t* bar = reinterpret_cast<uint64_t*>(base + area);
     const long long units = (long long)prm.P * prm.K * prm.J;
     // frame row and column of unit u's patch in the tensor map
@@ -292,28 +295,24 @@ __global__ void __launch_bounds__(32, 12) spectra_tma_kernel(const FrontParams p
                     request(u + gridDim.x);
                 }
             } else {
-                // lane 0 stores the transform of the packed columns in column 0
+                // lane 0 keeps the transform of the packed columns in shared memory
 #pragma unroll
-                for (int ky = 0; ky < N; ++ky) D[ky * NH + kx] = v[ky];
+                for (int ky = 0; ky < N; ++ky) {
+                    if (kx > 0) D[ky * NH + kx] = v[ky];
+                    else Z[ky] = v[ky];
+                }
             }
         }
         __syncwarp();
         // split the packed columns' transform Z into kx = 0 and N/2:
         // X0 = (Z[ky] + conj Z[-ky]) / 2, X(N/2) = (Z[ky] - conj Z[-ky]) / (2i);
         // lane l takes ky = l and l + N/2
-        float2 z[2], zp[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int ky = lane + h * (N / 2);
-            z[h] = D[ky * NH];
-            zp[h] = cconj(D[((N - ky) & (N - 1)) * NH]);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int ky = lane + h * (N / 2);
-            float2 d0 = cscale(cadd(z[h], zp[h]), 0.5f);
-            const float2 d = cscale(csub(z[h], zp[h]), 0.5f);
+            const float2 z = Z[ky], zp = cconj(Z[(N - ky) & (N - 1)]);
+            float2 d0 = cscale(cadd(z, zp), 0.5f);
+            const float2 d = cscale(csub(z, zp), 0.5f);
             if (ky == 0) d0.x += m * (float)(N * N);  // the constant's transform
             D[ky * NH] = d0;
             D[ky * NH + N / 2] = make_float2(d.y, -d.x);
