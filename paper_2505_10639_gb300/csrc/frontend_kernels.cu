@@ -386,12 +386,14 @@ __global__ void __launch_bounds__(FrontCta<N>::THREADS) object_image_kernel(cons
                 v[n] = make_float2(a.x - b.y, -(a.y + b.x));  // conj(a + i b)
             }
             line_fft<N, -1>(v, sub);
-            if (act) {
+            if (act) {  // 16-byte stores: four consecutive pixels of a row
+                static_assert(L % 4 == 0, "rows are stored four pixels at a time");
+                float4* ra = reinterpret_cast<float4*>(img + (size_t)y * N + sub * L);
+                float4* rb = reinterpret_cast<float4*>(img + (size_t)(y + N / 2) * N + sub * L);
 #pragma unroll
-                for (int q = 0; q < L; ++q) {
-                    const int x = sub * L + q;
-                    img[(size_t)y * N + x] = v[q].x * sc;
-                    img[(size_t)(y + N / 2) * N + x] = -v[q].y * sc;
+                for (int q = 0; q < L; q += 4) {
+                    ra[q / 4] = make_float4(v[q].x * sc, v[q + 1].x * sc, v[q + 2].x * sc, v[q + 3].x * sc);
+                    rb[q / 4] = make_float4(-v[q].y * sc, -v[q + 1].y * sc, -v[q + 2].y * sc, -v[q + 3].y * sc);
                 }
             }
         }
