@@ -484,6 +484,7 @@ def run_gpu(args, rank, local_rank, world, peaks):
     coeffs, spectra, loss, grad, stream, rmax, rsum, local_ms = bufs
     if world == 1 and not args.no_extras and w["n_pix"] == 64 and args.precision == "fp32":
         line["bf16_phase"] = run_bf16_arm(args, w, plan, coeffs, spectra, local_rank, local_ms)
+        line["dictionary_model"] = run_dictionary(args, w)
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, plan, coeffs, spectra, loss, grad, stream, world, rmax, rsum, w)
     if not args.no_frontend:
@@ -586,6 +587,59 @@ def run_explicit(args, plan, coeffs, spectra, w):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / args.steps
     return {"ms": t, "value": units64_of(w) / (t * 1e-3), "unit": UNIT}
+
+
+DICT_ATOMS = 8
+
+
+def run_dictionary(args, w):
+    """The spatially variant dictionary model (mfbd_dict_loss_grad, Sec.
+    2.2.2) on the workload's patches, objects and frames with an 8-atom
+    dictionary, both gradients computed (not part of a step): the inputs of
+    synth.dictionary_case drawn for 31 patches and tiled over the field's
+    patches (timing does not depend on the values); CUDA-event time per call,
+    units (patch, object, frame) per second, and the HBM roofline of the unit
+    kernel's algorithmic bytes (coefficient maps read, their gradient written,
+    spectra read: 2 M N^2 4 + N (N/2+1) 8 bytes per unit)."""
+    import torch
+    from paper_2505_10639_gb300 import synth
+    from paper_2505_10639_gb300.mfbd import dict_loss_grad
+    P, K, J, N, M = w["n_patches"], len(w["diams"]), w["n_frames"], w["n_pix"], DICT_ATOMS
+    blk = 31
+    atoms, atom_otf, gamma, obj, coeff, spectra = synth.dictionary_case(SEED, blk, K, J, M, n=N)
+    rep = (P + blk - 1) // blk
+
+    def tiled(x):
+        t = torch.from_numpy(x).cuda()
+        return t.repeat((rep,) + (1,) * (t.dim() - 1))[:P].contiguous()
+
+    t_otf, t_gamma = torch.from_numpy(atom_otf).cuda(), torch.from_numpy(gamma).cuda()
+    t_obj, t_coeff, t_spec = tiled(obj), tiled(coeff), tiled(spectra)
+    loss, go, ga = dict_loss_grad(t_otf, t_gamma, t_obj, t_coeff, t_spec)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup - 1, 0)):
+        dict_loss_grad(t_otf, t_gamma, t_obj, t_coeff, t_spec, loss=loss, grad_object=go, grad_coeff=ga)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dict_loss_grad(t_otf, t_gamma, t_obj, t_coeff, t_spec, loss=loss, grad_object=go, grad_coeff=ga)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / args.steps
+    units = P * K * J
+    nbytes = units * (2 * M * N * N * 4 + N * (N // 2 + 1) * 8)
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    out = {"ms": t, "value": units / (t * 1e-3), "unit": "units/s (patch*obj*frame, %d atoms)" % M,
+           "workload": "fov1024_64px_961patches_2obj_12frames_%datoms" % M,
+           "roofline": {"bound": "hbm", "achieved": nbytes / (t * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": nbytes / (t * 1e-3) / 1e9 / hbm, "traffic": None,
+                        "algorithmic_bytes": nbytes},
+           "gpu_launches": 2}
+    del t_coeff, ga
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_frontend(args, plan, coeffs, spectra, w):

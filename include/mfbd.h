@@ -478,6 +478,53 @@ int mfbd_batch_check(mfbd_batch_t batch, void* stream);
 int mfbd_batch_autotune(mfbd_batch_t batch, const float* coeffs, const void* spectra, double* loss,
                         void* object, float* grad, int reps, void* stream);
 
+/* ---- Spatially variant PSF on a dictionary (Sec. 2.2.2, "Spatially variant
+ * convolution"; the PSF expansion, the image as a sum of convolutions and the
+ * Fourier-domain log-posterior). Plan-free: the PSF at object point r' is
+ * sum_i a_i(r') phi_i(r), and per patch the data term is
+ *   L_p = sum_k sum_j gamma_kj sum_u |I_kj(u) - sum_i F(o_k a_ikj)(u) Phi_i(u)|^2
+ * over the full N x N frequency plane (from the half spectrum: columns 0 and
+ * N/2 once, the others twice), F unnormalised, Phi_i = F(phi_i). The
+ * regulariser of the paper's log-posterior is left to the caller. ---- */
+typedef struct {
+    int n;          /* patch size N; 64 */
+    int n_patches;  /* P >= 0 */
+    int n_objects;  /* K >= 1 */
+    int n_frames;   /* J >= 1 */
+    int n_atoms;    /* M >= 1, dictionary functions */
+} mfbd_dict_desc;
+
+/* Bytes of device workspace mfbd_dict_loss_grad needs for `desc`
+ * (P K J doubles and P K J N^2 floats, with alignment padding); 0 for an
+ * invalid descriptor. */
+size_t mfbd_dict_workspace_bytes(const mfbd_dict_desc* desc);
+
+/* L_p and its gradients for given objects and coefficient maps:
+ *   dL/da_ikj = o_k g_ikj,  dL/do_k = sum_j sum_i a_ikj g_ikj,
+ *   g_ikj = Re F^H[conj(Phi_i) (-2 gamma_kj R_kj)],
+ *   R_kj = I_kj - sum_i F(o_k a_ikj) Phi_i.
+ *   atom_otf     dev [M][N][N/2+1] complex64, Phi_i (half spectra of the real
+ *                dictionary functions phi_i), 8-byte aligned;
+ *   gamma        dev [K][J] float, the frame weights gamma_kj;
+ *   object       dev [P][K][N][N] float, o_k (image domain), 16-byte aligned;
+ *   coeff        dev [P][K][J][M][N][N] float, a_ikj(r'), 16-byte aligned;
+ *   spectra      dev [P][K][J][N][N/2+1] complex64, I_kj, half spectra of
+ *                real images (the plan's spectra layout), 8-byte aligned;
+ *   workspace    dev, mfbd_dict_workspace_bytes(desc) bytes, 16-byte aligned,
+ *                owned by the caller, contents undefined on return;
+ *   loss         dev [P] double, L_p;
+ *   grad_object  dev [P][K][N][N] float, dL/do, or NULL to skip;
+ *   grad_coeff   dev [P][K][J][M][N][N] float, dL/da, 16-byte aligned, or
+ *                NULL to skip.
+ * FP32 transforms and products; the loss sums each frame's terms in FP64,
+ * and both sums over frames and objects run in a fixed order. Errors:
+ * MFBD_ERR_INVALID_ARG (descriptor, NULL or misaligned pointer),
+ * MFBD_ERR_UNSUPPORTED (n other than 64), MFBD_ERR_CUDA. Asynchronous on
+ * `stream`; allocates nothing. */
+int mfbd_dict_loss_grad(const mfbd_dict_desc* desc, const void* atom_otf, const float* gamma, const float* object,
+                        const float* coeff, const void* spectra, void* workspace, double* loss, float* grad_object,
+                        float* grad_coeff, void* stream);
+
 /* Static description of a status code (never NULL). */
 const char* mfbd_status_string(int status);
 

@@ -67,6 +67,16 @@ class PlanInfo(ctypes.Structure):
     ]
 
 
+class DictDesc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("n_patches", ctypes.c_int),
+        ("n_objects", ctypes.c_int),
+        ("n_frames", ctypes.c_int),
+        ("n_atoms", ctypes.c_int),
+    ]
+
+
 class BatchInfo(ctypes.Structure):
     _fields_ = [
         ("n_problems", ctypes.c_int),
@@ -106,6 +116,9 @@ _SIGNATURES = {
     "mfbd_plan_read_profile": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
     "mfbd_phase_loss_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(PlanDesc), _VP, _VP, _VP, _VP, _VP, _VP]),
     "mfbd_plan_set_diversity": (ctypes.c_int, [_VP, _VP, _VP]),
+    "mfbd_dict_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(DictDesc)]),
+    "mfbd_dict_loss_grad": (ctypes.c_int, [ctypes.POINTER(DictDesc), _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                           _VP]),
     "mfbd_spectra_from_frames": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 _VP, _VP]),
     "mfbd_filter_objects": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),

@@ -24,7 +24,7 @@ INCLUDE = os.path.join(ROOT, "include")
 SOURCES = [
     "mfbd_kernels.cu", "fused_kernels.cu", "generic_kernels.cu", "generic_n48.cu", "generic_n64.cu", "generic_n96.cu",
     "generic_n128.cu", "batch_kernels.cu", "batch_kernel_v2.cu", "batch_kernel_v3.cu",
-    "batch_api.cu", "frontend_kernels.cu", "ls_filter_kernels.cu", "gemm_kernels.cu", "tc_gemm.cu", "tc_grad.cu",
+    "batch_api.cu", "frontend_kernels.cu", "ls_filter_kernels.cu", "gemm_kernels.cu", "tc_gemm.cu", "tc_grad.cu", "dict_kernels.cu",
     "mfbd_api.cu", "mfbd_noalloc.cu", "mfbd_selftest.cu", "probe_kernels.cu", "optics_host.cpp"
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -374,6 +374,41 @@ def phase_loss_grad_noalloc(phase, spectra, n_patches, diams, n_frames, gamma, w
     return loss, grad_phase, obj
 
 
+def dict_loss_grad(atom_otf, gamma, obj, coeff, spectra, want_grad_object=True, want_grad_coeff=True,
+                   loss=None, grad_object=None, grad_coeff=None, workspace=None, stream=None):
+    """mfbd_dict_loss_grad: the spatially variant dictionary model's data term
+    L [P] (float64) and its gradients dL/do [P, K, 64, 64], dL/da
+    [P, K, J, M, 64, 64] for atom_otf [M, 64, 33] complex64, gamma [K, J],
+    obj [P, K, 64, 64], coeff [P, K, J, M, 64, 64] float32 and spectra
+    [P, K, J, 64, 33] complex64, all on the device (plan-free; the workspace
+    is allocated here unless given)."""
+    lib = _lib.load()
+    n_atoms = int(atom_otf.shape[0])
+    n_patches, k, j = int(coeff.shape[0]), int(coeff.shape[1]), int(coeff.shape[2])
+    desc = _lib.DictDesc(64, n_patches, k, j, n_atoms)
+    dev = coeff.device
+    if loss is None:
+        loss = torch.empty(n_patches, dtype=torch.float64, device=dev)
+    if grad_object is None and want_grad_object:
+        grad_object = torch.empty((n_patches, k, 64, 64), dtype=torch.float32, device=dev)
+    if grad_coeff is None and want_grad_coeff:
+        grad_coeff = torch.empty_like(coeff)
+    if workspace is None:
+        nbytes = int(lib.mfbd_dict_workspace_bytes(ctypes.byref(desc)))
+        workspace = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=dev)
+    cshape = (n_patches, k, j, n_atoms, 64, 64)
+    _lib.check(lib.mfbd_dict_loss_grad(
+        ctypes.byref(desc), _dev(atom_otf, torch.complex64, (n_atoms, 64, 33), "atom_otf"),
+        _dev(gamma, torch.float32, (k, j), "gamma"), _dev(obj, torch.float32, (n_patches, k, 64, 64), "object"),
+        _dev(coeff, torch.float32, cshape, "coeff"),
+        _dev(spectra, torch.complex64, (n_patches, k, j, 64, 33), "spectra"),
+        ctypes.c_void_p(workspace.data_ptr()), _dev(loss, torch.float64, (n_patches,), "loss"),
+        _dev(grad_object, torch.float32, (n_patches, k, 64, 64), "grad_object") if grad_object is not None else None,
+        _dev(grad_coeff, torch.float32, cshape, "grad_coeff") if grad_coeff is not None else None,
+        _stream(stream)), "mfbd_dict_loss_grad")
+    return loss, grad_object, grad_coeff
+
+
 def probe_fma_rate(fp64=False, iters=None, stream=None):
     """mfbd_probe_fma_rate: the FP32 (or FP64) fused multiply-add rate of the
     current device, one timed launch that fills every SM; returns

@@ -107,3 +107,45 @@ def uneven_problems(seed, n, sizes=(48, 64, 96, 128), objects=(1, 3), frames=(8,
         wls = [wavelength0 * diams[0] / d for d in diams]
         out.append(dict(n_pix=npx, n_objects=k, n_frames=j, n_modes=m, diams=diams, wavelengths=wls))
     return out
+
+
+def dictionary_case(seed, n_patches, n_objects, n_frames, n_atoms, n=64):
+    """Inputs of the spatially variant dictionary model (Sec. 2.2.2).
+
+    Recipe (the paper's NMF dictionary, learned from simulated PSFs, is not
+    available): atoms phi_i are periodic elliptical Gaussians centred near the
+    origin, widths 0.8-4 px, normalised to unit sum (non-negative, unit
+    integral, as the expansion requires); coefficient maps a_ikj(r') are
+    uniform draws in [0.1, 1.1) normalised so that sum_i a_i = 1 at every
+    point; objects are k^-3 granulation-like fields (object_field); the data
+    are half spectra of further k^-3 fields (the loss is defined for any
+    data), made exactly Hermitian in the columns 0 and n/2; gamma = 1 / J.
+
+    Returns float32 / complex64 arrays: atoms [M, n, n], atom_otf [M, n,
+    n/2+1], gamma [K, J], obj [P, K, n, n], coeff [P, K, J, M, n, n],
+    spectra [P, K, J, n, n/2+1]."""
+    g = rng(seed, "misc", 77)
+    atoms = np.empty((n_atoms, n, n))
+    for i in range(n_atoms):
+        sy, sx = g.uniform(0.8, 4.0, size=2)
+        cy, cx = g.uniform(-1.5, 1.5, size=2)
+        dy = np.minimum(np.abs(np.arange(n) - cy), n - np.abs(np.arange(n) - cy))
+        dx = np.minimum(np.abs(np.arange(n) - cx), n - np.abs(np.arange(n) - cx))
+        atoms[i] = np.exp(-0.5 * (dy[:, None] / sy) ** 2 - 0.5 * (dx[None, :] / sx) ** 2)
+        atoms[i] /= atoms[i].sum()
+    coeff = g.uniform(0.1, 1.1, size=(n_patches, n_objects, n_frames, n_atoms, n, n))
+    coeff /= coeff.sum(axis=3, keepdims=True)
+    obj = object_field(seed, (n_patches, n_objects, n, n), sub=7)
+    data = object_field(seed, (n_patches, n_objects, n_frames, n, n), sub=8)
+
+    def half(x):
+        h = np.fft.rfft2(x).astype(np.complex64)
+        for c in (0, n // 2):  # exactly Hermitian along ky
+            col = h[..., :, c].astype(np.complex128)
+            mirror = np.conj(np.roll(col[..., ::-1], 1, axis=-1))
+            h[..., :, c] = (0.5 * (col + mirror)).astype(np.complex64)
+        return h
+
+    gamma = np.full((n_objects, n_frames), 1.0 / n_frames, np.float32)
+    return (atoms.astype(np.float32), half(atoms), gamma, obj.astype(np.float32), coeff.astype(np.float32),
+            half(data))

@@ -269,3 +269,21 @@ def test_field_front_end_refuses_without_a_plan(lib):
     assert lib.mfbd_filter_objects(None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
     assert lib.mfbd_ls_filter_objects(None, None, None, 1.0, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
     assert lib.mfbd_loss_grad_explicit(None, None, None, None, None, None, None, None) == _lib.MFBD_ERR_INVALID_ARG
+
+
+def test_dictionary_model_descriptor_and_workspace(lib):
+    """mfbd_dict_workspace_bytes / mfbd_dict_loss_grad validate before any
+    device call: bad sizes and n != 64 are refused, an empty problem is a
+    no-op, and the workspace holds P K J doubles and P K J N^2 floats."""
+    d = _lib.DictDesc(64, 3, 2, 5, 4)
+    units = 3 * 2 * 5
+    nbytes = lib.mfbd_dict_workspace_bytes(ctypes.byref(d))
+    assert nbytes >= units * 8 + units * 64 * 64 * 4 and nbytes % 4 == 0
+    for bad in (_lib.DictDesc(64, -1, 2, 5, 4), _lib.DictDesc(64, 3, 0, 5, 4), _lib.DictDesc(64, 3, 2, 0, 4),
+                _lib.DictDesc(64, 3, 2, 5, 0)):
+        assert lib.mfbd_dict_workspace_bytes(ctypes.byref(bad)) == 0
+        assert lib.mfbd_dict_loss_grad(ctypes.byref(bad), *([None] * 10)) == 1  # MFBD_ERR_INVALID_ARG
+    assert lib.mfbd_dict_loss_grad(None, *([None] * 10)) == 1
+    assert lib.mfbd_dict_loss_grad(ctypes.byref(_lib.DictDesc(48, 3, 2, 5, 4)), *([None] * 10)) == 2  # UNSUPPORTED
+    assert lib.mfbd_dict_loss_grad(ctypes.byref(_lib.DictDesc(64, 0, 2, 5, 4)), *([None] * 10)) == 0  # empty
+    assert lib.mfbd_dict_loss_grad(ctypes.byref(d), *([None] * 10)) == 1  # NULL inputs
