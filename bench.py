@@ -75,11 +75,12 @@ NCU_DRAM_BYTES_PER_UNIT_128 = {"forward_passes": (67911680 + 344916992) / 6144,
                                "adjoint_passes": (481574144 + 66861568) / 6144,
                                "reduction": (818419968 + 364834048) / 6144}
 # DRAM bytes per launch of the front-end kernels on the 961-patch 64 px field
-# (one ncu capture of the full launch, --metrics dram__bytes_read.sum,
-# dram__bytes_write.sum): spectra_kernel; object_image_kernel + merge_kernel;
-# ls_raw_kernel + ls_filter_kernel
-NCU_FRONT_DRAM_BYTES = {"spectra_from_frames": None,  # spectra_tma_kernel changed since its capture
-                        "merge_objects": None,  # object_image_kernel changed since its capture
+# (one ncu capture of the full launch each): spectra_tma_kernel (MemoryWorkload
+# section: 3.734345 TB/s x 121.088 us); object_image_kernel + merge_kernel
+# (none since the object images are stored 16 bytes at a time);
+# ls_raw_kernel + ls_filter_kernel (dram__bytes_read.sum + dram__bytes_write.sum)
+NCU_FRONT_DRAM_BYTES = {"spectra_from_frames": int(3.734345e12 * 121.088e-6),
+                        "merge_objects": None,
                         "ls_filter_objects": 779402496 + 16724480 + 48732416 + 3328}
 # DRAM bytes of the batch kernel per 64 px-equivalent unit, from one ncu
 # capture of the first 200 problems of the 2000-problem batch (13869 units)
